@@ -1,0 +1,212 @@
+/*
+ * rbe.h -- C ABI of librbe, a GB300 (sm_103a) implementation of the per-step
+ * force evaluation of the random batch Ewald (RBE) method of Jin, Li, Xu and
+ * Zhao, "A random batch Ewald method for particle systems with Coulomb
+ * interactions" (arXiv:2010.01559).
+ *
+ * What one force evaluation computes (paper section / equation):
+ *   - P wave vectors k = 2 pi m / L, m in Z^3 \ {0}, drawn i.i.d. from the
+ *     discrete Gaussian P_k = exp(-k^2 / 4 alpha) / S            (Eq. probexpression)
+ *     with S = H^3 - 1                                          (Eq. S, Eq. psf);
+ *   - the structure factors rho(k_l) = sum_j q_j exp(i k_l . r_j)        (Sec. 2);
+ *   - the RBE Fourier force
+ *       F*_i = -sum_l (S/P) 4 pi q_i k_l / (V k_l^2) Im(e^{-i k_l.r_i} rho(k_l))
+ *                                                                (Eq. rbmapprox);
+ *   - the real-space force -q_i sum_j q_j G(r) r_ij / r under the cutoff r_c,
+ *     G(r) = erfc(sqrt(alpha) r)/r^2 + 2 sqrt(alpha) exp(-alpha r^2)/(sqrt(pi) r)
+ *                                                           (Eq. force, 2nd term);
+ *   - a shifted Lennard-Jones force                           (Eq. Ljpotential);
+ *   - optionally the energy (FP64): frozen-batch estimator of U_1 (Sec. 2 with
+ *     the S/P weights of Eq. rbmapprox), self term -sqrt(alpha/pi) sum q^2,
+ *     neutralising background -pi (sum q)^2 / (2 V alpha), truncated U_2, LJ;
+ *   - optionally dE/dq_i (the electrostatic potential at particle i).
+ * One MD step (rbe_step) adds the Langevin thermostat of Sec. 3.3 as a kick /
+ * exact Ornstein-Uhlenbeck / drift update, closing the loop of Algorithm 1.
+ *
+ * Conventions for every entry point:
+ *   - Array pointers are caller-owned DEVICE memory (except the *_host entry
+ *     points), 16-byte aligned, contiguous.  The library owns only its
+ *     workspace, allocated by rbe_create / rbe_create_batch for n_max
+ *     particles and freed by rbe_destroy.
+ *   - Particles are float4 / double4 records (x, y, z, q); positions may lie
+ *     anywhere, they are wrapped into the periodic cube [0, L)^3 internally.
+ *     Forces are float4 / double4 records (Fx, Fy, Fz, 0).
+ *   - Work is enqueued on the handle's CUDA stream (rbe_set_stream; default:
+ *     the legacy default stream) and the calls return without synchronising,
+ *     except the *_host entry points and rbe_sync.
+ *   - No exception crosses the ABI; every call returns an rbe_status.  Argument
+ *     errors are detected on the host before anything is enqueued.  CUDA errors
+ *     are reported as RBE_ERR_CUDA.  Device-side conditions (a k-sample that
+ *     exhausted its 32 attempts) are latched in a device word and reported by
+ *     the next rbe_sync (or *_host call).  rbe_last_error(h) gives a message.
+ *   - Units are the caller's; coulomb_prefactor multiplies every Coulomb term
+ *     (1 in the reduced units of Sec. 4.1, the Bjerrum length in Sec. 4.2).
+ */
+#ifndef RBE_H
+#define RBE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rbe_ctx *rbe_handle;
+
+typedef enum {
+    RBE_OK = 0,
+    RBE_ERR_ARG = 1,        /* invalid argument (null pointer, size, parameter range) */
+    RBE_ERR_CUDA = 2,       /* a CUDA runtime call failed                              */
+    RBE_ERR_OOM = 3,        /* device allocation failed                                */
+    RBE_ERR_SAMPLER = 4,    /* a k-sample hit (0,0,0) on 32 attempts in a row           */
+    RBE_ERR_TIMEOUT = 5,    /* reserved: a bounded device wait gave up                  */
+    RBE_ERR_NONFINITE = 6,  /* reserved: non-finite input detected                      */
+    RBE_ERR_STATE = 7       /* call not valid for this handle (e.g. wrong n for a batch) */
+} rbe_status;
+
+enum { RBE_FP64 = 0, RBE_MIXED = 1 };
+
+/* Parts selectable in rbe_forces_ex. */
+enum { RBE_PART_FOURIER = 1, RBE_PART_REAL = 2, RBE_PART_LJ = 4, RBE_PART_ALL = 7 };
+
+/* Parameters of one periodic system (cubic box, reduced units).  112 bytes. */
+typedef struct {
+    double box;               /* L > 0: edge of the cubic periodic box (Sec. 2)          */
+    double alpha;             /* Ewald splitting parameter, erfc(sqrt(alpha) r) (Sec. 2) */
+    double r_c;               /* real-space cutoff, 0 < r_c <= L/3 (cells of side >= r_c) */
+    double coulomb_prefactor; /* multiplies all Coulomb terms (Sec. 4.1: 1)              */
+    double lj_eps;            /* shifted-LJ epsilon; 0 disables LJ (Eq. Ljpotential)     */
+    double lj_sigma;          /* LJ sigma (r_off = 0)                                    */
+    double lj_rcut;           /* LJ cutoff R_c (<= r_c); V_shift makes V(R_c) = 0         */
+    double gamma;             /* Langevin friction (Sec. 3.3)                            */
+    double kT;                /* temperature 1/beta (k_B = 1)                            */
+    double dt;                /* time step                                               */
+    double mass;              /* particle mass (all particles)                           */
+    uint64_t seed;            /* Philox key of this system                               */
+    uint32_t stream;          /* Philox stream id (distinct per replica)                 */
+    int32_t P;                /* batch size p >= 1 (Eq. rbmapprox)                        */
+    int32_t n_max;            /* capacity in particles (single-system handles)           */
+    int32_t precision;        /* RBE_MIXED (default path of rbe_step) or RBE_FP64         */
+} rbe_params;
+
+/* Derived constants of system `sys` of a handle (for inspection and tests). */
+typedef struct {
+    double H;                 /* sum_m exp(-pi^2 m^2 / (alpha L^2)) over |m| <= M (Eq. psf) */
+    double S;                 /* H^3 - 1 (Eq. S)                                           */
+    int32_t M;                /* per-axis table half-width: tail weight < 2^-64            */
+    int32_t n_cells_dim;      /* cells per box edge of the real-space cell list            */
+    int32_t n;                /* particles of this system (batch) or n_max (single)        */
+    int32_t P;                /* batch size                                                */
+    int32_t n_systems;        /* systems in the handle                                     */
+    int32_t first_particle;   /* offset of this system in concatenated particle arrays     */
+    int32_t first_k;          /* offset of this system in concatenated k arrays            */
+    int32_t reserved;
+} rbe_info;
+
+/* Create a handle for one system of up to p->n_max particles.  Builds the
+ * per-axis sampling table (Eq. probexpression, per-axis marginal) and S
+ * (Eq. S) in FP64 on the host and allocates the device workspace.
+ * Errors: RBE_ERR_ARG for out-of-range parameters (L, alpha, r_c, P <= 0,
+ * r_c > L/3, lj_rcut > r_c, n_max < 0), RBE_ERR_OOM, RBE_ERR_CUDA. */
+rbe_status rbe_create(const rbe_params *p, rbe_handle *out);
+
+/* Create a handle for n_replicas independent systems (replica r has
+ * per_replica[r] and n_per_replica[r] particles) evaluated together: every
+ * kernel launch covers all replicas.  Particle arrays passed to the batched
+ * calls are the replicas' arrays concatenated in replica order; energies are
+ * n_replicas x 4 doubles.  Same errors as rbe_create. */
+rbe_status rbe_create_batch(const rbe_params *per_replica, const int32_t *n_per_replica,
+                            int32_t n_replicas, rbe_handle *out);
+
+/* Free the workspace and the handle (NULL is ignored).  Synchronises the stream. */
+void rbe_destroy(rbe_handle h);
+
+/* Message describing the last failure on h (thread-local global if h is NULL). */
+const char *rbe_last_error(rbe_handle h);
+
+/* Set the CUDA stream (a cudaStream_t) used for all work of h. */
+rbe_status rbe_set_stream(rbe_handle h, void *cuda_stream);
+
+/* Fill *info for system `sys` of h.  RBE_ERR_ARG for a bad index. */
+rbe_status rbe_get_info(rbe_handle h, int32_t sys, rbe_info *info);
+
+/* Copy system sys's per-axis sampling table (2M+1 uint64, host memory) to
+ * table_out: entry j = floor(2^32 CDF(j - M)), last entry 2^32. */
+rbe_status rbe_get_table(rbe_handle h, int32_t sys, uint64_t *table_out);
+
+/* Draw the k-batch of step `step` for every system (Eq. probexpression):
+ * m_out (device, int32, total-P x 4) receives (m_x, m_y, m_z, attempts) per
+ * sample.  Sample l of a system uses Philox4x32-10 with key (seed_lo, seed_hi)
+ * and counter (l, attempt, step_lo, (stream << 8) | 1); each 32-bit word maps
+ * to one axis by the integer table; (0,0,0) is discarded and redrawn
+ * (Sec. 3.1), at most 32 attempts. */
+rbe_status rbe_sample_k(rbe_handle h, uint64_t step, int32_t *m_out);
+
+/* One RBE force evaluation, mixed precision (FP32 phases / sincos / forces
+ * from exact 32-bit fixed-point fractional coordinates; FP64 rho(k) sums and
+ * energies).  n: number of particles (== n_max-capacity-bounded; for a batch
+ * handle, the total).  pos_q: float4[n].  step selects the k-batch.
+ * F_out: float4[n] total force.  E_out (nullable): double[4 * n_systems] =
+ * {total, Fourier incl. self and background, real-space Coulomb, LJ}.
+ * phi_out (nullable): float[n], dE/dq_i. */
+rbe_status rbe_forces(rbe_handle h, int32_t n, const float *pos_q, uint64_t step,
+                      float *F_out, double *E_out, float *phi_out);
+
+/* As rbe_forces, restricted to the parts in `parts` (RBE_PART_* mask);
+ * energies and phi of the parts left out are zero. */
+rbe_status rbe_forces_ex(rbe_handle h, int32_t n, const float *pos_q, uint64_t step,
+                         int32_t parts, float *F_out, double *E_out, float *phi_out);
+
+/* The plain FP64 path: the same steps with FP64 positions, phases, sincos,
+ * erfc and sums throughout.  pos_q: double4[n], F_out: double4[n],
+ * phi_out: double[n]. */
+rbe_status rbe_forces_f64(rbe_handle h, int32_t n, const double *pos_q, uint64_t step,
+                          int32_t parts, double *F_out, double *E_out, double *phi_out);
+
+/* nsteps MD steps (Algorithm 1 with the Langevin thermostat of Sec. 3.3),
+ * mixed precision, updating pos_q (float4[n]) and vel (float4[n], w unused)
+ * in place.  step_dev (device uint64) holds the index of the next step; each
+ * step reads it to select its k-batch and noise and increments it on the
+ * device, so a captured replay advances the stream.  The step sequence is
+ * replayed from a CUDA graph when use_graph was enabled (rbe_set_graph). */
+rbe_status rbe_step(rbe_handle h, int32_t n, float *pos_q, float *vel, int32_t nsteps,
+                    uint64_t *step_dev);
+
+/* FP64 MD steps: pos_q, vel double4[n]. */
+rbe_status rbe_step_f64(rbe_handle h, int32_t n, double *pos_q, double *vel, int32_t nsteps,
+                        uint64_t *step_dev);
+
+/* Enable (1) or disable (0) CUDA-graph replay of rbe_step.  The first
+ * rbe_step call after enabling captures one step per distinct argument set. */
+rbe_status rbe_set_graph(rbe_handle h, int32_t use_graph);
+
+/* Host-memory variants: copy the inputs from host (preferably pinned)
+ * memory, run, copy the outputs back and synchronise.  Staging buffers are
+ * the handle's own.  rbe_forces_host: pos_q float4[n] in, F_out float4[n]
+ * out, E_out (nullable) double[4 n_systems] out.  rbe_step_host: pos_q and
+ * vel float4[n] in/out, steps step0 .. step0 + nsteps - 1. */
+rbe_status rbe_forces_host(rbe_handle h, int32_t n, const float *pos_q, uint64_t step,
+                           float *F_out, double *E_out);
+rbe_status rbe_step_host(rbe_handle h, int32_t n, float *pos_q, float *vel, int32_t nsteps,
+                         uint64_t step0);
+
+/* Synchronise h's stream and report latched device conditions
+ * (RBE_ERR_SAMPLER) and asynchronous CUDA errors.  Clears the latch. */
+rbe_status rbe_sync(rbe_handle h);
+
+/* Tuning of the Fourier kernels: particles per structure-factor chunk
+ * (power of two, 32..8192; 0 = automatic) and threads cooperating on one
+ * particle in the force pass (1, 2, 4 or 8; 0 = automatic). */
+rbe_status rbe_set_tuning(rbe_handle h, int32_t rho_chunk, int32_t force_split);
+
+/* Time the candidate tunings on the given input (device pos_q, n particles)
+ * with CUDA events and keep the fastest; returns it in *rho_chunk and
+ * *force_split (nullable). */
+rbe_status rbe_autotune(rbe_handle h, int32_t n, const float *pos_q, int32_t *rho_chunk,
+                        int32_t *force_split);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBE_H */

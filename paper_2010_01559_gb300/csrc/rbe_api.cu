@@ -1,0 +1,871 @@
+// rbe_api.cu -- host side of the C ABI declared in include/rbe.h.
+//
+// Builds, in FP64 on the host, everything that is fixed per system: the
+// per-axis inverse-CDF table of the k distribution (Eq. probexpression with the
+// per-axis marginal exp(-pi^2 m^2 / (alpha L^2))), H (Eq. psf) and S = H^3 - 1
+// (Eq. S), the coefficient scales of Eq. rbmapprox and of the energy, the LJ
+// shift of Eq. Ljpotential and the Langevin constants of Sec. 3.3.  Then it
+// enqueues the kernels of one evaluation / MD step on the handle's stream.
+//
+// Sampling table (the exact arithmetic both this library and any independent
+// implementation must follow to draw the same k):
+//   M   = ceil( sqrt(alpha L^2 * 64 ln 2) / pi )
+//   a   = pi^2 / (alpha L^2);  w_j = exp(-(a * (j - M)^2)),  j = 0 .. 2M
+//   Z   = sum_j w_j in increasing j;   c_j = running sum in increasing j
+//   T_j = min(floor((c_j / Z) * 2^32), 2^32 - 1) for j < 2M;  T_2M = 2^32
+//   H   = Z,  S = H^3 - 1.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rbe.h"
+#include "rbe_internal.cuh"
+
+using namespace rbe;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct SysHost {
+    rbe_params p;
+    int n = 0;
+    int M = 0;
+    double H = 0.0, S = 0.0;
+    int ncd = 0;
+    std::vector<uint64_t> table;
+    int off_p = 0, off_c = 0, off_k = 0, off_t = 0;
+};
+
+struct GraphEntry {
+    int n;
+    const void* pos;
+    const void* vel;
+    const void* step;
+    int prec;
+    cudaGraphExec_t exec;
+};
+
+int axis_M(double alpha, double L) {
+    const double x = std::sqrt(alpha * L * L * (64.0 * std::log(2.0))) / M_PI;
+    return (int)std::ceil(x);
+}
+
+double build_table(double alpha, double L, int M, std::vector<uint64_t>& T) {
+    const double a = (M_PI * M_PI) / (alpha * L * L);
+    const int n = 2 * M + 1;
+    T.assign(n, 0);
+    double Z = 0.0;
+    for (int j = 0; j < n; ++j) {
+        const long long d = (long long)(j - M);
+        Z += std::exp(-(a * (double)(d * d)));
+    }
+    double cum = 0.0;
+    for (int j = 0; j < n; ++j) {
+        const long long d = (long long)(j - M);
+        cum += std::exp(-(a * (double)(d * d)));
+        if (j == n - 1) {
+            T[j] = 4294967296ull;
+        } else {
+            double f = std::floor((cum / Z) * 4294967296.0);
+            if (f > 4294967295.0) f = 4294967295.0;
+            T[j] = (uint64_t)f;
+        }
+    }
+    return Z;
+}
+
+int pow2_ceil(long long v) {
+    int p = 1;
+    while (p < v && p < (1 << 30)) p <<= 1;
+    return p;
+}
+
+template <class T>
+rbe_status dalloc(T** ptr, size_t count) {
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc((void**)ptr, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return RBE_ERR_OOM;
+    }
+    return RBE_OK;
+}
+
+}  // namespace
+
+struct rbe_ctx {
+    bool batch = false;
+    int nsys = 0;
+    int ntot = 0;          // particle capacity (batch: exact total)
+    int ncell = 0;
+    int ktot = 0;
+    int ttot = 0;
+    int pmax = 0;
+    std::vector<SysHost> sys;
+    std::vector<SysDev> sysdev;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int rho_chunk = 0, force_split = 0;      // 0 = automatic
+    int cur_n = -1, cur_chunk = -1, cur_split = -1;
+    int npblk = 0, nfblk = 0, nchunks = 0, split = 1;
+    int max_pblk = 0, max_fblk = 0, max_chunks = 0;
+    size_t max_part = 0;
+    bool use_graph = false;
+    std::vector<GraphEntry> graphs;
+    std::string err;
+
+    SysDev* d_sys = nullptr;
+    Tile* d_pblk = nullptr;
+    Tile* d_fblk = nullptr;
+    Tile* d_chunks = nullptr;
+    int* d_kstart = nullptr;
+    uint64_t* d_table = nullptr;
+    uint4* d_fx = nullptr;
+    uint4* d_spos = nullptr;
+    double4* d_fx64 = nullptr;
+    double4* d_spos64 = nullptr;
+    int* d_cid = nullptr;
+    int* d_rank = nullptr;
+    int* d_perm = nullptr;
+    float4* d_fs = nullptr;
+    double4* d_fs64 = nullptr;
+    int* d_cell_cnt = nullptr;
+    int* d_cell_start = nullptr;
+    float2* d_part = nullptr;
+    double2* d_part64 = nullptr;
+    int4* d_ksamp = nullptr;
+    float2* d_kab = nullptr;
+    double2* d_kab64 = nullptr;
+    double2* d_rho = nullptr;
+    double* d_eterm = nullptr;
+    double2* d_blk_e = nullptr;
+    double2* d_blk_q = nullptr;
+    double2* d_qsum = nullptr;
+    uint64_t* d_cur_step = nullptr;
+    uint64_t* d_stage_step = nullptr;
+    int* d_err = nullptr;
+    float4* d_stage_pos = nullptr;
+    float4* d_stage_vel = nullptr;
+    float4* d_stage_F = nullptr;
+    double* d_stage_E = nullptr;
+};
+
+namespace {
+
+rbe_status fail(rbe_ctx* h, rbe_status s, const std::string& msg) {
+    g_last_error = msg;
+    if (h) h->err = msg;
+    return s;
+}
+
+rbe_status cuda_fail(rbe_ctx* h, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(h, RBE_ERR_CUDA, m);
+}
+
+#define RBE_CUDA(h, call)                                   \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+rbe_status validate_params(const rbe_params& p, std::string& why) {
+    if (!(p.box > 0.0) || !std::isfinite(p.box)) { why = "box must be > 0"; return RBE_ERR_ARG; }
+    if (!(p.alpha > 0.0) || !std::isfinite(p.alpha)) { why = "alpha must be > 0"; return RBE_ERR_ARG; }
+    if (!(p.r_c > 0.0)) { why = "r_c must be > 0"; return RBE_ERR_ARG; }
+    if (p.box / p.r_c < 3.0) { why = "r_c must be <= L/3 (at least 3 cells per edge)"; return RBE_ERR_ARG; }
+    if (p.P < 1) { why = "P must be >= 1"; return RBE_ERR_ARG; }
+    if (p.n_max < 0) { why = "n_max must be >= 0"; return RBE_ERR_ARG; }
+    if (p.lj_eps != 0.0) {
+        if (!(p.lj_sigma > 0.0) || !(p.lj_rcut > 0.0)) { why = "LJ sigma and cutoff must be > 0"; return RBE_ERR_ARG; }
+        if (p.lj_rcut > p.r_c) { why = "lj_rcut must be <= r_c"; return RBE_ERR_ARG; }
+    }
+    if (!(p.mass > 0.0)) { why = "mass must be > 0"; return RBE_ERR_ARG; }
+    if (p.gamma < 0.0 || p.kT < 0.0) { why = "gamma and kT must be >= 0"; return RBE_ERR_ARG; }
+    const int M = axis_M(p.alpha, p.box);
+    if (M > 200000) { why = "alpha L^2 too large for the sampling table"; return RBE_ERR_ARG; }
+    // (0,0,0) is drawn with probability 1/H^3; keep the 32-attempt loop safe.
+    const double H = std::sqrt(p.alpha * p.box * p.box / M_PI);
+    if (H * H * H < 2.0) { why = "alpha L^2 too small: k = 0 would dominate the sampler"; return RBE_ERR_ARG; }
+    return RBE_OK;
+}
+
+void fill_sysdev(const SysHost& s, SysDev& d) {
+    const rbe_params& p = s.p;
+    const double L = p.box;
+    d.L = L;
+    d.invL = 1.0 / L;
+    d.V = L * L * L;
+    d.alpha = p.alpha;
+    d.sqrt_alpha = std::sqrt(p.alpha);
+    d.r_c = p.r_c;
+    d.lB = p.coulomb_prefactor;
+    d.S = s.S;
+    d.coef_scale = p.coulomb_prefactor * (s.S / (double)p.P) * 4.0 * M_PI / d.V;
+    d.self_coef = p.coulomb_prefactor * std::sqrt(p.alpha / M_PI);
+    d.bg_coef = p.coulomb_prefactor * M_PI / (d.V * p.alpha);
+    d.lj_eps = p.lj_eps;
+    d.lj_sigma2 = p.lj_sigma * p.lj_sigma;
+    d.lj_rcut2 = p.lj_rcut * p.lj_rcut;
+    if (p.lj_eps != 0.0) {
+        const double sr6 = std::pow(p.lj_sigma / p.lj_rcut, 6.0);
+        d.lj_shift = -4.0 * p.lj_eps * (sr6 * sr6 - sr6);
+    } else {
+        d.lj_shift = 0.0;
+    }
+    d.c1 = std::exp(-p.gamma * p.dt / p.mass);
+    d.c2 = std::sqrt((1.0 - d.c1 * d.c1) * p.kT / p.mass);
+    d.dt = p.dt;
+    d.dt_over_m = p.dt / p.mass;
+    const double scale = 4294967296.0 / L;
+    d.fx_hi = (float)scale;
+    d.fx_lo = (float)(scale - (double)d.fx_hi);
+    d.Lf = (float)L;
+    d.L_over_2_32 = (float)(L / 4294967296.0);
+    d.seed = p.seed;
+    d.stream = p.stream;
+    d.n = s.n;
+    d.P = p.P;
+    d.M = s.M;
+    d.ncd = s.ncd;
+    d.off_p = s.off_p;
+    d.off_c = s.off_c;
+    d.off_k = s.off_k;
+    d.off_t = s.off_t;
+    d.off_part = 0;
+    d.nchunk = 0;
+    d.off_b = 0;
+    d.nb = 0;
+}
+
+int auto_chunk(const rbe_ctx* h, long long ntot) {
+    const int ltiles = (h->pmax + kLTile - 1) / kLTile;
+    const long long target_blocks = 152LL * 12;
+    long long chunks = std::max(1LL, target_blocks / std::max(1, ltiles));
+    long long c = (ntot + chunks - 1) / chunks;
+    int p = pow2_ceil(std::max(1LL, c));
+    return std::min(4096, std::max(32, p));
+}
+
+int auto_split(long long ntot) {
+    const long long target_threads = 152LL * 8 * kBlockP;
+    int s = 1;
+    while (s < 8 && ntot * s < target_threads) s <<= 1;
+    return s;
+}
+
+// (Re)build the work tables for the current particle counts and tuning.
+rbe_status prepare(rbe_ctx* h, int n) {
+    if (!h->batch) h->sys[0].n = n;
+    const long long ntot = h->batch ? h->ntot : n;
+    const int chunk = h->rho_chunk > 0 ? h->rho_chunk : auto_chunk(h, ntot);
+    const int split = h->force_split > 0 ? h->force_split : auto_split(ntot);
+    if (h->cur_n == n && h->cur_chunk == chunk && h->cur_split == split) return RBE_OK;
+    std::vector<Tile> pblk, fblk, chunks;
+    const int ftile = kBlockP / split;
+    int off_part = 0;
+    for (int s = 0; s < h->nsys; ++s) {
+        SysHost& sh = h->sys[s];
+        SysDev& d = h->sysdev[s];
+        fill_sysdev(sh, d);
+        d.off_b = (int)pblk.size();
+        int nb = 0;
+        for (int f = 0; f < sh.n || (f == 0 && nb == 0); f += kBlockP) {
+            pblk.push_back(Tile{s, sh.off_p + f, std::min(kBlockP, sh.n - f), 0});
+            ++nb;
+            if (sh.n == 0) break;
+        }
+        d.nb = nb;
+        for (int f = 0; f < sh.n || f == 0; f += ftile) {
+            fblk.push_back(Tile{s, sh.off_p + f, std::max(0, std::min(ftile, sh.n - f)), 0});
+            if (sh.n == 0) break;
+        }
+        d.off_part = off_part;
+        int nc = 0;
+        for (int f = 0; f < sh.n || f == 0; f += chunk) {
+            chunks.push_back(Tile{s, sh.off_p + f, std::max(0, std::min(chunk, sh.n - f)),
+                                  off_part + nc * sh.p.P});
+            ++nc;
+            if (sh.n == 0) break;
+        }
+        d.nchunk = nc;
+        off_part += nc * sh.p.P;
+    }
+    if ((int)pblk.size() > h->max_pblk || (int)fblk.size() > h->max_fblk ||
+        (int)chunks.size() > h->max_chunks || (size_t)off_part > h->max_part)
+        return fail(h, RBE_ERR_ARG, "work tables exceed the workspace (n > capacity?)");
+    RBE_CUDA(h, cudaMemcpyAsync(h->d_sys, h->sysdev.data(), sizeof(SysDev) * h->nsys,
+                                cudaMemcpyHostToDevice, h->stream));
+    RBE_CUDA(h, cudaMemcpyAsync(h->d_pblk, pblk.data(), sizeof(Tile) * pblk.size(),
+                                cudaMemcpyHostToDevice, h->stream));
+    RBE_CUDA(h, cudaMemcpyAsync(h->d_fblk, fblk.data(), sizeof(Tile) * fblk.size(),
+                                cudaMemcpyHostToDevice, h->stream));
+    RBE_CUDA(h, cudaMemcpyAsync(h->d_chunks, chunks.data(), sizeof(Tile) * chunks.size(),
+                                cudaMemcpyHostToDevice, h->stream));
+    RBE_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->npblk = (int)pblk.size();
+    h->nfblk = (int)fblk.size();
+    h->nchunks = (int)chunks.size();
+    h->split = split;
+    h->cur_n = n;
+    h->cur_chunk = chunk;
+    h->cur_split = split;
+    return RBE_OK;
+}
+
+rbe_status allocate(rbe_ctx* h) {
+    // capacities (chunks as small as 32 particles, force tiles as small as 16)
+    long long pb = 0, fb = 0, ch = 0, part = 0;
+    for (auto& s : h->sys) {
+        const long long n = h->batch ? s.n : s.p.n_max;
+        pb += (n + kBlockP - 1) / kBlockP + 1;
+        fb += (n + 15) / 16 + 1;
+        const long long c = (n + 31) / 32 + 1;
+        ch += c;
+        part += c * s.p.P;
+    }
+    h->max_pblk = (int)pb;
+    h->max_fblk = (int)fb;
+    h->max_chunks = (int)ch;
+    h->max_part = (size_t)part;
+    const size_t N = (size_t)std::max(h->ntot, 1);
+    rbe_status st = RBE_OK;
+#define RBE_ALLOC(ptr, cnt) \
+    if ((st = dalloc(&(ptr), (size_t)(cnt))) != RBE_OK) return fail(h, st, "cudaMalloc failed: " #ptr)
+    RBE_ALLOC(h->d_sys, h->nsys);
+    RBE_ALLOC(h->d_pblk, pb);
+    RBE_ALLOC(h->d_fblk, fb);
+    RBE_ALLOC(h->d_chunks, ch);
+    RBE_ALLOC(h->d_kstart, h->nsys + 1);
+    RBE_ALLOC(h->d_table, h->ttot);
+    RBE_ALLOC(h->d_fx, N);
+    RBE_ALLOC(h->d_spos, N);
+    RBE_ALLOC(h->d_fx64, N);
+    RBE_ALLOC(h->d_spos64, N);
+    RBE_ALLOC(h->d_cid, N);
+    RBE_ALLOC(h->d_rank, N);
+    RBE_ALLOC(h->d_perm, N);
+    RBE_ALLOC(h->d_fs, N);
+    RBE_ALLOC(h->d_fs64, N);
+    RBE_ALLOC(h->d_cell_cnt, h->ncell + 1);
+    RBE_ALLOC(h->d_cell_start, h->ncell + 1);
+    RBE_ALLOC(h->d_part, part);
+    RBE_ALLOC(h->d_part64, part);
+    RBE_ALLOC(h->d_ksamp, h->ktot);
+    RBE_ALLOC(h->d_kab, h->ktot);
+    RBE_ALLOC(h->d_kab64, h->ktot);
+    RBE_ALLOC(h->d_rho, h->ktot);
+    RBE_ALLOC(h->d_eterm, h->ktot);
+    RBE_ALLOC(h->d_blk_e, pb);
+    RBE_ALLOC(h->d_blk_q, pb);
+    RBE_ALLOC(h->d_qsum, h->nsys);
+    RBE_ALLOC(h->d_cur_step, 1);
+    RBE_ALLOC(h->d_stage_step, 1);
+    RBE_ALLOC(h->d_err, 1);
+    RBE_ALLOC(h->d_stage_pos, N);
+    RBE_ALLOC(h->d_stage_vel, N);
+    RBE_ALLOC(h->d_stage_F, N);
+    RBE_ALLOC(h->d_stage_E, 4 * h->nsys);
+#undef RBE_ALLOC
+    RBE_CUDA(h, cudaMemset(h->d_cell_cnt, 0, sizeof(int) * (h->ncell + 1)));
+    RBE_CUDA(h, cudaMemset(h->d_err, 0, sizeof(int)));
+    RBE_CUDA(h, cudaMemset(h->d_qsum, 0, sizeof(double2) * h->nsys));
+    std::vector<uint64_t> tab;
+    std::vector<int> kstart;
+    for (auto& s : h->sys) {
+        tab.insert(tab.end(), s.table.begin(), s.table.end());
+        kstart.push_back(s.off_k);
+    }
+    kstart.push_back(h->ktot);
+    RBE_CUDA(h, cudaMemcpy(h->d_table, tab.data(), sizeof(uint64_t) * tab.size(),
+                           cudaMemcpyHostToDevice));
+    RBE_CUDA(h, cudaMemcpy(h->d_kstart, kstart.data(), sizeof(int) * kstart.size(),
+                           cudaMemcpyHostToDevice));
+    RBE_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    return RBE_OK;
+}
+
+void release(rbe_ctx* h) {
+    if (!h) return;
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    void* ptrs[] = {h->d_sys, h->d_pblk, h->d_fblk, h->d_chunks, h->d_kstart, h->d_table,
+                    h->d_fx, h->d_spos, h->d_fx64, h->d_spos64, h->d_cid, h->d_rank,
+                    h->d_perm, h->d_fs, h->d_fs64, h->d_cell_cnt, h->d_cell_start, h->d_part,
+                    h->d_part64, h->d_ksamp, h->d_kab, h->d_kab64, h->d_rho, h->d_eterm,
+                    h->d_blk_e, h->d_blk_q, h->d_qsum, h->d_cur_step, h->d_stage_step,
+                    h->d_err, h->d_stage_pos, h->d_stage_vel, h->d_stage_F, h->d_stage_E};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+}
+
+rbe_status create_common(const rbe_params* ps, const int32_t* ns, int nsys, bool batch,
+                         rbe_handle* out) {
+    if (!out) return fail(nullptr, RBE_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!ps || nsys < 1) return fail(nullptr, RBE_ERR_ARG, "no systems");
+    rbe_ctx* h = new rbe_ctx();
+    h->batch = batch;
+    h->nsys = nsys;
+    h->sys.resize(nsys);
+    h->sysdev.resize(nsys);
+    int off_p = 0, off_c = 0, off_k = 0, off_t = 0;
+    for (int s = 0; s < nsys; ++s) {
+        SysHost& sh = h->sys[s];
+        sh.p = ps[s];
+        std::string why;
+        if (validate_params(sh.p, why) != RBE_OK) {
+            rbe_status st = fail(nullptr, RBE_ERR_ARG, "system " + std::to_string(s) + ": " + why);
+            delete h;
+            return st;
+        }
+        sh.n = batch ? ns[s] : sh.p.n_max;
+        if (batch && ns[s] < 0) {
+            delete h;
+            return fail(nullptr, RBE_ERR_ARG, "negative particle count");
+        }
+        sh.M = axis_M(sh.p.alpha, sh.p.box);
+        sh.H = build_table(sh.p.alpha, sh.p.box, sh.M, sh.table);
+        sh.S = sh.H * sh.H * sh.H - 1.0;
+        sh.ncd = std::min(256, (int)std::floor(sh.p.box / sh.p.r_c));
+        sh.off_p = off_p;
+        sh.off_c = off_c;
+        sh.off_k = off_k;
+        sh.off_t = off_t;
+        off_p += sh.n;
+        off_c += sh.ncd * sh.ncd * sh.ncd;
+        off_k += sh.p.P;
+        off_t += 2 * sh.M + 1;
+        h->pmax = std::max(h->pmax, sh.p.P);
+    }
+    h->ntot = off_p;
+    h->ncell = off_c;
+    h->ktot = off_k;
+    h->ttot = off_t;
+    rbe_status st = allocate(h);
+    if (st != RBE_OK) {
+        std::string m = h->err;
+        release(h);
+        delete h;
+        return fail(nullptr, st, m);
+    }
+    *out = h;
+    return RBE_OK;
+}
+
+// Enqueue one evaluation (and optionally one Langevin step) on stream st.
+struct EvalArgs {
+    int prec;                 // RBE_MIXED or RBE_FP64
+    int parts;
+    const float4* pos;        // mixed input
+    const double4* pos64;     // fp64 input
+    uint64_t step;
+    uint64_t* step_dev;       // nullable: device step counter (incremented)
+    float4* F;
+    double4* F64;
+    double* E;
+    float* phi;
+    double* phi64;
+    float4* md_pos;
+    float4* md_vel;
+    double4* md_pos64;
+    double4* md_vel64;
+};
+
+void enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
+    const bool mixed = a.prec == RBE_MIXED;
+    const bool fourier = (a.parts & RBE_PART_FOURIER) != 0;
+    const int want_q = (fourier && (a.E || a.phi || a.phi64)) ? 1 : 0;
+    const int n = h->batch ? h->ntot : h->cur_n;
+    if (mixed)
+        launch_prep_mixed(st, h->d_sys, h->d_pblk, h->npblk, a.pos, h->d_fx, h->d_cid,
+                          h->d_rank, h->d_cell_cnt, h->d_blk_q, want_q);
+    else
+        launch_prep_f64(st, h->d_sys, h->d_pblk, h->npblk, a.pos64, h->d_fx64, h->d_cid,
+                        h->d_rank, h->d_cell_cnt, h->d_blk_q, want_q);
+    launch_scan(st, h->d_cell_cnt, h->d_cell_start, h->ncell, a.step_dev, a.step, h->d_cur_step);
+    launch_scatter(st, n, h->d_cid, h->d_rank, h->d_cell_start, mixed ? h->d_fx : nullptr,
+                   h->d_spos, mixed ? nullptr : h->d_fx64, h->d_spos64, h->d_perm);
+    launch_cell_fixup(st, h->ncell, h->d_cell_start, mixed ? h->d_spos : nullptr,
+                      mixed ? nullptr : h->d_spos64, h->d_perm);
+    const int ltiles = (h->pmax + kLTile - 1) / kLTile;
+    if (fourier) {
+        if (mixed) {
+            launch_rho_mixed(st, h->d_sys, h->d_chunks, h->nchunks, ltiles, h->d_table,
+                             h->d_cur_step, h->d_spos, h->d_part, h->d_ksamp, h->d_err);
+            launch_finalize(st, h->d_sys, h->nsys, h->ktot, h->d_kstart, h->d_part, nullptr,
+                            h->d_ksamp, h->d_rho, h->d_kab, nullptr, h->d_eterm,
+                            want_q ? h->d_blk_q : nullptr, h->d_qsum);
+            launch_fourier_force_mixed(st, h->d_sys, h->split == 1 ? h->d_pblk : h->d_fblk,
+                                       h->split == 1 ? h->npblk : h->nfblk, h->split, h->d_spos,
+                                       h->d_ksamp, h->d_kab, h->d_fs);
+        } else {
+            launch_rho_f64(st, h->d_sys, h->d_chunks, h->nchunks, ltiles, h->d_table,
+                           h->d_cur_step, h->d_spos64, h->d_part64, h->d_ksamp, h->d_err);
+            launch_finalize(st, h->d_sys, h->nsys, h->ktot, h->d_kstart, nullptr, h->d_part64,
+                            h->d_ksamp, h->d_rho, nullptr, h->d_kab64, h->d_eterm,
+                            want_q ? h->d_blk_q : nullptr, h->d_qsum);
+            launch_fourier_force_f64(st, h->d_sys, h->d_pblk, h->npblk, h->d_spos64, h->d_ksamp,
+                                     h->d_kab64, h->d_fs64);
+        }
+    }
+    RealArgs r{};
+    r.sys = h->d_sys;
+    r.pblk = h->d_pblk;
+    r.npblk = h->npblk;
+    r.parts = a.parts;
+    r.cell_start = h->d_cell_start;
+    r.perm = h->d_perm;
+    r.cur_step = h->d_cur_step;
+    r.qsum = h->d_qsum;
+    r.spos = h->d_spos;
+    r.fs = h->d_fs;
+    r.F_out = a.F;
+    r.phi_out = a.phi;
+    r.md_pos = a.md_pos;
+    r.md_vel = a.md_vel;
+    r.spos64 = h->d_spos64;
+    r.fs64 = h->d_fs64;
+    r.F_out64 = a.F64;
+    r.phi_out64 = a.phi64;
+    r.md_pos64 = a.md_pos64;
+    r.md_vel64 = a.md_vel64;
+    r.blk_e = a.E ? h->d_blk_e : nullptr;
+    if (mixed) launch_real_mixed(st, r); else launch_real_f64(st, r);
+    if (a.E) launch_energy(st, h->d_sys, h->nsys, h->d_eterm, h->d_blk_e, h->d_qsum, a.parts, a.E);
+}
+
+rbe_status check_n(rbe_ctx* h, int n) {
+    if (n < 0) return fail(h, RBE_ERR_ARG, "n must be >= 0");
+    if (h->batch) {
+        if (n != h->ntot) return fail(h, RBE_ERR_STATE, "batch handle: n must equal the total particle count");
+    } else if (n > h->sys[0].p.n_max) {
+        return fail(h, RBE_ERR_ARG, "n exceeds n_max");
+    }
+    return RBE_OK;
+}
+
+rbe_status finish(rbe_ctx* h, const char* where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, where);
+    return RBE_OK;
+}
+
+rbe_status forces_impl(rbe_ctx* h, int n, int prec, const void* pos, uint64_t step, int parts,
+                       void* F, double* E, void* phi) {
+    if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
+    rbe_status s = check_n(h, n);
+    if (s != RBE_OK) return s;
+    if (parts < 0 || parts > RBE_PART_ALL) return fail(h, RBE_ERR_ARG, "bad parts mask");
+    if (n > 0 && (!pos || !F)) return fail(h, RBE_ERR_ARG, "pos_q and F_out must be non-null");
+    if ((s = prepare(h, n)) != RBE_OK) return s;
+    EvalArgs a{};
+    a.prec = prec;
+    a.parts = parts;
+    a.step = step;
+    a.E = E;
+    if (prec == RBE_MIXED) {
+        a.pos = (const float4*)pos;
+        a.F = (float4*)F;
+        a.phi = (float*)phi;
+    } else {
+        a.pos64 = (const double4*)pos;
+        a.F64 = (double4*)F;
+        a.phi64 = (double*)phi;
+    }
+    enqueue_eval(h, h->stream, a);
+    return finish(h, "rbe_forces");
+}
+
+rbe_status step_impl(rbe_ctx* h, int n, int prec, void* pos, void* vel, int nsteps,
+                     uint64_t* step_dev) {
+    if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
+    rbe_status s = check_n(h, n);
+    if (s != RBE_OK) return s;
+    if (nsteps < 0) return fail(h, RBE_ERR_ARG, "nsteps must be >= 0");
+    if (!step_dev) return fail(h, RBE_ERR_ARG, "step_dev must be non-null");
+    if (n > 0 && (!pos || !vel)) return fail(h, RBE_ERR_ARG, "pos_q and vel must be non-null");
+    if ((s = prepare(h, n)) != RBE_OK) return s;
+    EvalArgs a{};
+    a.prec = prec;
+    a.parts = RBE_PART_ALL;
+    a.step_dev = step_dev;
+    if (prec == RBE_MIXED) {
+        a.pos = (const float4*)pos;
+        a.md_pos = (float4*)pos;
+        a.md_vel = (float4*)vel;
+    } else {
+        a.pos64 = (const double4*)pos;
+        a.md_pos64 = (double4*)pos;
+        a.md_vel64 = (double4*)vel;
+    }
+    if (!h->use_graph) {
+        for (int k = 0; k < nsteps; ++k) enqueue_eval(h, h->stream, a);
+        return finish(h, "rbe_step");
+    }
+    cudaGraphExec_t exec = nullptr;
+    for (auto& g : h->graphs)
+        if (g.n == n && g.pos == pos && g.vel == vel && g.step == step_dev && g.prec == prec) exec = g.exec;
+    if (!exec) {
+        // Capture on the handle's private stream, then replay on the caller's.
+        RBE_CUDA(h, cudaStreamSynchronize(h->stream));
+        RBE_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        enqueue_eval(h, h->cap_stream, a);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+        h->graphs.push_back(GraphEntry{n, pos, vel, step_dev, prec, exec});
+    }
+    for (int k = 0; k < nsteps; ++k) RBE_CUDA(h, cudaGraphLaunch(exec, h->stream));
+    return finish(h, "rbe_step");
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+rbe_status rbe_create(const rbe_params* p, rbe_handle* out) {
+    if (!p) return fail(nullptr, RBE_ERR_ARG, "params is NULL");
+    return create_common(p, nullptr, 1, false, out);
+}
+
+rbe_status rbe_create_batch(const rbe_params* per_replica, const int32_t* n_per_replica,
+                            int32_t n_replicas, rbe_handle* out) {
+    if (!per_replica || !n_per_replica || n_replicas < 1)
+        return fail(nullptr, RBE_ERR_ARG, "bad batch arguments");
+    return create_common(per_replica, n_per_replica, n_replicas, true, out);
+}
+
+void rbe_destroy(rbe_handle h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
+    release(h);
+    delete h;
+}
+
+const char* rbe_last_error(rbe_handle h) {
+    if (h) return h->err.c_str();
+    return g_last_error.c_str();
+}
+
+rbe_status rbe_set_stream(rbe_handle h, void* cuda_stream) {
+    if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
+    h->stream = (cudaStream_t)cuda_stream;
+    return RBE_OK;
+}
+
+rbe_status rbe_get_info(rbe_handle h, int32_t sys, rbe_info* info) {
+    if (!h || !info) return fail(h, RBE_ERR_ARG, "null argument");
+    if (sys < 0 || sys >= h->nsys) return fail(h, RBE_ERR_ARG, "system index out of range");
+    const SysHost& s = h->sys[sys];
+    std::memset(info, 0, sizeof(*info));
+    info->H = s.H;
+    info->S = s.S;
+    info->M = s.M;
+    info->n_cells_dim = s.ncd;
+    info->n = h->batch ? s.n : s.p.n_max;
+    info->P = s.p.P;
+    info->n_systems = h->nsys;
+    info->first_particle = s.off_p;
+    info->first_k = s.off_k;
+    return RBE_OK;
+}
+
+rbe_status rbe_get_table(rbe_handle h, int32_t sys, uint64_t* table_out) {
+    if (!h || !table_out) return fail(h, RBE_ERR_ARG, "null argument");
+    if (sys < 0 || sys >= h->nsys) return fail(h, RBE_ERR_ARG, "system index out of range");
+    std::memcpy(table_out, h->sys[sys].table.data(), sizeof(uint64_t) * h->sys[sys].table.size());
+    return RBE_OK;
+}
+
+rbe_status rbe_sample_k(rbe_handle h, uint64_t step, int32_t* m_out) {
+    if (!h || !m_out) return fail(h, RBE_ERR_ARG, "null argument");
+    const int n = h->batch ? h->ntot : std::max(h->cur_n, 0);
+    rbe_status s = prepare(h, n);
+    if (s != RBE_OK) return s;
+    RBE_CUDA(h, cudaMemcpyAsync(h->d_stage_step, &step, sizeof(uint64_t), cudaMemcpyHostToDevice,
+                                h->stream));
+    launch_sample(h->stream, h->d_sys, h->nsys, h->ktot, h->d_kstart, h->d_table,
+                  h->d_stage_step, (int4*)m_out, h->d_err);
+    RBE_CUDA(h, cudaStreamSynchronize(h->stream));
+    return finish(h, "rbe_sample_k");
+}
+
+rbe_status rbe_forces(rbe_handle h, int32_t n, const float* pos_q, uint64_t step, float* F_out,
+                      double* E_out, float* phi_out) {
+    return forces_impl(h, n, RBE_MIXED, pos_q, step, RBE_PART_ALL, F_out, E_out, phi_out);
+}
+
+rbe_status rbe_forces_ex(rbe_handle h, int32_t n, const float* pos_q, uint64_t step,
+                         int32_t parts, float* F_out, double* E_out, float* phi_out) {
+    return forces_impl(h, n, RBE_MIXED, pos_q, step, parts, F_out, E_out, phi_out);
+}
+
+rbe_status rbe_forces_f64(rbe_handle h, int32_t n, const double* pos_q, uint64_t step,
+                          int32_t parts, double* F_out, double* E_out, double* phi_out) {
+    return forces_impl(h, n, RBE_FP64, pos_q, step, parts, F_out, E_out, phi_out);
+}
+
+rbe_status rbe_step(rbe_handle h, int32_t n, float* pos_q, float* vel, int32_t nsteps,
+                    uint64_t* step_dev) {
+    return step_impl(h, n, RBE_MIXED, pos_q, vel, nsteps, step_dev);
+}
+
+rbe_status rbe_step_f64(rbe_handle h, int32_t n, double* pos_q, double* vel, int32_t nsteps,
+                        uint64_t* step_dev) {
+    return step_impl(h, n, RBE_FP64, pos_q, vel, nsteps, step_dev);
+}
+
+rbe_status rbe_set_graph(rbe_handle h, int32_t use_graph) {
+    if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
+    h->use_graph = use_graph != 0;
+    return RBE_OK;
+}
+
+rbe_status rbe_forces_host(rbe_handle h, int32_t n, const float* pos_q, uint64_t step,
+                           float* F_out, double* E_out) {
+    if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
+    rbe_status s = check_n(h, n);
+    if (s != RBE_OK) return s;
+    if (n > 0 && (!pos_q || !F_out)) return fail(h, RBE_ERR_ARG, "null host buffer");
+    const size_t bytes = sizeof(float4) * (size_t)n;
+    if (n > 0)
+        RBE_CUDA(h, cudaMemcpyAsync(h->d_stage_pos, pos_q, bytes, cudaMemcpyHostToDevice, h->stream));
+    s = forces_impl(h, n, RBE_MIXED, h->d_stage_pos, step, RBE_PART_ALL, h->d_stage_F,
+                    E_out ? h->d_stage_E : nullptr, nullptr);
+    if (s != RBE_OK) return s;
+    if (n > 0)
+        RBE_CUDA(h, cudaMemcpyAsync(F_out, h->d_stage_F, bytes, cudaMemcpyDeviceToHost, h->stream));
+    if (E_out)
+        RBE_CUDA(h, cudaMemcpyAsync(E_out, h->d_stage_E, sizeof(double) * 4 * h->nsys,
+                                    cudaMemcpyDeviceToHost, h->stream));
+    return rbe_sync(h);
+}
+
+rbe_status rbe_step_host(rbe_handle h, int32_t n, float* pos_q, float* vel, int32_t nsteps,
+                         uint64_t step0) {
+    if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
+    rbe_status s = check_n(h, n);
+    if (s != RBE_OK) return s;
+    if (n > 0 && (!pos_q || !vel)) return fail(h, RBE_ERR_ARG, "null host buffer");
+    const size_t bytes = sizeof(float4) * (size_t)n;
+    if (n > 0) {
+        RBE_CUDA(h, cudaMemcpyAsync(h->d_stage_pos, pos_q, bytes, cudaMemcpyHostToDevice, h->stream));
+        RBE_CUDA(h, cudaMemcpyAsync(h->d_stage_vel, vel, bytes, cudaMemcpyHostToDevice, h->stream));
+    }
+    RBE_CUDA(h, cudaMemcpyAsync(h->d_stage_step, &step0, sizeof(uint64_t), cudaMemcpyHostToDevice,
+                                h->stream));
+    s = step_impl(h, n, RBE_MIXED, h->d_stage_pos, h->d_stage_vel, nsteps, h->d_stage_step);
+    if (s != RBE_OK) return s;
+    if (n > 0) {
+        RBE_CUDA(h, cudaMemcpyAsync(pos_q, h->d_stage_pos, bytes, cudaMemcpyDeviceToHost, h->stream));
+        RBE_CUDA(h, cudaMemcpyAsync(vel, h->d_stage_vel, bytes, cudaMemcpyDeviceToHost, h->stream));
+    }
+    return rbe_sync(h);
+}
+
+rbe_status rbe_sync(rbe_handle h) {
+    if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
+    RBE_CUDA(h, cudaStreamSynchronize(h->stream));
+    int err = 0;
+    RBE_CUDA(h, cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        RBE_CUDA(h, cudaMemset(h->d_err, 0, sizeof(int)));
+        if (err & kErrSampler)
+            return fail(h, RBE_ERR_SAMPLER, "a k-sample drew (0,0,0) on 32 attempts in a row");
+    }
+    return finish(h, "rbe_sync");
+}
+
+rbe_status rbe_set_tuning(rbe_handle h, int32_t rho_chunk, int32_t force_split) {
+    if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
+    if (rho_chunk != 0 && (rho_chunk < 32 || rho_chunk > 8192 || (rho_chunk & (rho_chunk - 1))))
+        return fail(h, RBE_ERR_ARG, "rho_chunk must be 0 or a power of two in [32, 8192]");
+    if (force_split != 0 && force_split != 1 && force_split != 2 && force_split != 4 &&
+        force_split != 8)
+        return fail(h, RBE_ERR_ARG, "force_split must be 0, 1, 2, 4 or 8");
+    h->rho_chunk = rho_chunk;
+    h->force_split = force_split;
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    return RBE_OK;
+}
+
+rbe_status rbe_autotune(rbe_handle h, int32_t n, const float* pos_q, int32_t* rho_chunk,
+                        int32_t* force_split) {
+    if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
+    rbe_status s = check_n(h, n);
+    if (s != RBE_OK) return s;
+    if (n > 0 && !pos_q) return fail(h, RBE_ERR_ARG, "pos_q is NULL");
+    cudaEvent_t e0, e1;
+    RBE_CUDA(h, cudaEventCreate(&e0));
+    RBE_CUDA(h, cudaEventCreate(&e1));
+    const int ltiles = (h->pmax + kLTile - 1) / kLTile;
+    const int chunks[] = {32, 64, 128, 256, 512, 1024, 2048, 4096};
+    const int splits[] = {1, 2, 4, 8};
+    float best = 1e30f;
+    int best_chunk = 0, best_split = 0;
+    EvalArgs a{};
+    a.prec = RBE_MIXED;
+    a.parts = RBE_PART_ALL;
+    a.pos = (const float4*)pos_q;
+    a.F = h->d_stage_F;
+    // structure-factor chunk
+    for (int c : chunks) {
+        h->rho_chunk = c;
+        if ((s = prepare(h, n)) != RBE_OK) return s;
+        enqueue_eval(h, h->stream, a);   // builds the sorted order and k data
+        float tot = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, h->stream);
+            launch_rho_mixed(h->stream, h->d_sys, h->d_chunks, h->nchunks, ltiles, h->d_table,
+                             h->d_cur_step, h->d_spos, h->d_part, h->d_ksamp, h->d_err);
+            cudaEventRecord(e1, h->stream);
+            RBE_CUDA(h, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tot += ms;
+        }
+        if (tot < best) { best = tot; best_chunk = c; }
+    }
+    h->rho_chunk = best_chunk;
+    best = 1e30f;
+    for (int sp : splits) {
+        h->force_split = sp;
+        if ((s = prepare(h, n)) != RBE_OK) return s;
+        enqueue_eval(h, h->stream, a);
+        float tot = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, h->stream);
+            launch_fourier_force_mixed(h->stream, h->d_sys, h->split == 1 ? h->d_pblk : h->d_fblk,
+                                       h->split == 1 ? h->npblk : h->nfblk, h->split, h->d_spos,
+                                       h->d_ksamp, h->d_kab, h->d_fs);
+            cudaEventRecord(e1, h->stream);
+            RBE_CUDA(h, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tot += ms;
+        }
+        if (tot < best) { best = tot; best_split = sp; }
+    }
+    h->force_split = best_split;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    if ((s = prepare(h, n)) != RBE_OK) return s;
+    if (rho_chunk) *rho_chunk = best_chunk;
+    if (force_split) *force_split = best_split;
+    return finish(h, "rbe_autotune");
+}
+
+}  // extern "C"

@@ -1,0 +1,276 @@
+// rbe_cells.cu -- per-step preparation: fixed-point fractional coordinates,
+// cell assignment and a counting sort of the particles by cell.
+//
+// The real-space sum of Eq. force (second term) needs every pair closer than
+// r_c.  Cells of side >= r_c (n_cells_dim = floor(L / r_c) >= 3 per edge) make
+// that a walk over the 27 neighbouring cells.  The sort is a counting sort
+// (histogram with atomics, one exclusive scan, scatter), followed by a per-cell
+// re-ordering by original index so that the order inside a cell -- and with it
+// every floating-point sum over neighbours -- is the same on every run.
+//
+// Mixed path: a coordinate x is stored as the 32-bit fixed-point fraction
+// round(2^32 x / L) mod 2^32.  The product 2^32 x / L is formed exactly enough
+// in FP32 by splitting 2^32 / L into a float pair (hi + lo) and recovering the
+// rounding error of x * hi with an FMA, so the stored fraction is within one
+// unit (L / 2^32) of the exact one for any float x.  Periodic wrapping is then
+// the natural 2^32 modulus, m . s mod 1 is exact in integer arithmetic, and
+// the minimum-image displacement is the signed difference of two fractions.
+#include "rbe_internal.cuh"
+
+namespace rbe {
+
+__device__ __forceinline__ uint32_t to_fixed(float x, float hi, float lo) {
+    const float p = x * hi;
+    const float e = fmaf(x, hi, -p);       // exact: x * hi = p + e
+    float corr = fmaf(x, lo, e);
+    const float pr = rintf(p);
+    corr += (p - pr);                      // exact (p and pr differ by < 1 ulp-scale)
+    const long long ip = (long long)pr;
+    const long long ic = __float2ll_rn(corr);
+    return (uint32_t)(unsigned long long)(ip + ic);
+}
+
+__device__ __forceinline__ int cell_of_fixed(uint32_t s, int ncd) {
+    return (int)(((unsigned long long)s * (unsigned long long)ncd) >> 32);
+}
+
+// Deterministic block sum of two doubles (fixed shuffle tree, then warps in order).
+__device__ __forceinline__ double2 block_sum2(double a, double b) {
+    __shared__ double sa[32], sb[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sa[w] = a; sb[w] = b; }
+    __syncthreads();
+    double2 r = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int k = 0; k < nw; ++k) { r.x += sa[k]; r.y += sb[k]; }
+    }
+    return r;
+}
+
+__global__ void __launch_bounds__(kBlockP)
+k_prep_mixed(const SysDev* __restrict__ sysv, const Tile* __restrict__ pblk,
+             const float4* __restrict__ pos_q, uint4* __restrict__ fx, int* __restrict__ cid,
+             int* __restrict__ rank, int* __restrict__ cell_cnt, double2* __restrict__ blk_q,
+             int want_q) {
+    const Tile tl = pblk[blockIdx.x];
+    const SysDev& S = sysv[tl.sys];
+    const int t = threadIdx.x;
+    double qs = 0.0, q2s = 0.0;
+    if (t < tl.count) {
+        const int i = tl.first + t;
+        const float4 p = pos_q[i];
+        const uint32_t sx = to_fixed(p.x, S.fx_hi, S.fx_lo);
+        const uint32_t sy = to_fixed(p.y, S.fx_hi, S.fx_lo);
+        const uint32_t sz = to_fixed(p.z, S.fx_hi, S.fx_lo);
+        const int ncd = S.ncd;
+        const int c = S.off_c + (cell_of_fixed(sz, ncd) * ncd + cell_of_fixed(sy, ncd)) * ncd +
+                      cell_of_fixed(sx, ncd);
+        cid[i] = c;
+        rank[i] = atomicAdd(cell_cnt + c, 1);
+        fx[i] = make_uint4(sx, sy, sz, __float_as_uint(p.w));
+        qs = (double)p.w;
+        q2s = (double)p.w * (double)p.w;
+    }
+    if (want_q) {
+        const double2 r = block_sum2(qs, q2s);
+        if (t == 0) blk_q[blockIdx.x] = r;
+    }
+}
+
+__device__ __forceinline__ double wrap_f64(double x, double L, double invL) {
+    double w = x - L * floor(x * invL);
+    if (w >= L) w -= L;
+    if (!(w >= 0.0)) w = 0.0;      // also maps NaN to 0
+    return w;
+}
+
+__device__ __forceinline__ int cell_of_f64(double w, double invL, int ncd) {
+    const double u = w * invL * (double)ncd;
+    int c = (u >= 0.0 && u < (double)ncd) ? (int)u : 0;
+    return c;
+}
+
+__global__ void __launch_bounds__(kBlockP)
+k_prep_f64(const SysDev* __restrict__ sysv, const Tile* __restrict__ pblk,
+           const double4* __restrict__ pos_q, double4* __restrict__ fx64, int* __restrict__ cid,
+           int* __restrict__ rank, int* __restrict__ cell_cnt, double2* __restrict__ blk_q,
+           int want_q) {
+    const Tile tl = pblk[blockIdx.x];
+    const SysDev& S = sysv[tl.sys];
+    const int t = threadIdx.x;
+    double qs = 0.0, q2s = 0.0;
+    if (t < tl.count) {
+        const int i = tl.first + t;
+        const double4 p = pos_q[i];
+        const double x = wrap_f64(p.x, S.L, S.invL);
+        const double y = wrap_f64(p.y, S.L, S.invL);
+        const double z = wrap_f64(p.z, S.L, S.invL);
+        const int ncd = S.ncd;
+        const int c = S.off_c +
+                      (cell_of_f64(z, S.invL, ncd) * ncd + cell_of_f64(y, S.invL, ncd)) * ncd +
+                      cell_of_f64(x, S.invL, ncd);
+        cid[i] = c;
+        rank[i] = atomicAdd(cell_cnt + c, 1);
+        fx64[i] = make_double4(x, y, z, p.w);
+        qs = p.w;
+        q2s = p.w * p.w;
+    }
+    if (want_q) {
+        const double2 r = block_sum2(qs, q2s);
+        if (t == 0) blk_q[blockIdx.x] = r;
+    }
+}
+
+// Exclusive scan of the cell counts (one block), zeroing the counts for the
+// next call.  Thread 0 also latches the step index of this evaluation: the
+// caller's device counter (incremented here, once per step) or the host value.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 4;
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan(int* __restrict__ cell_cnt, int* __restrict__ cell_start, int ncell,
+       uint64_t* __restrict__ step_dev, uint64_t step_arg, uint64_t* __restrict__ cur_step) {
+    __shared__ int warp_tot[kScanThreads / 32];
+    __shared__ int carry_s;
+    if (threadIdx.x == 0) {
+        carry_s = 0;
+        if (step_dev) {
+            const uint64_t s = *step_dev;
+            *cur_step = s;
+            *step_dev = s + 1;
+        } else {
+            *cur_step = step_arg;
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = 0; base < ncell; base += kScanThreads * kScanPer) {
+        const int i0 = base + threadIdx.x * kScanPer;
+        int v[kScanPer];
+        int sum = 0;
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            const int i = i0 + k;
+            v[k] = (i < ncell) ? cell_cnt[i] : 0;
+            sum += v[k];
+        }
+        // inclusive warp scan of per-thread sums
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_tot[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            int t = warp_tot[lane];
+            int ti = t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, ti, o);
+                if (lane >= o) ti += y;
+            }
+            warp_tot[lane] = ti - t;    // exclusive prefix of warp totals
+        }
+        __syncthreads();
+        int run = carry_s + warp_tot[w] + (incl - sum);
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            const int i = i0 + k;
+            if (i < ncell) {
+                cell_start[i] = run;
+                cell_cnt[i] = 0;
+            }
+            run += v[k];
+        }
+        __syncthreads();
+        if (threadIdx.x == kScanThreads - 1) carry_s = run;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) cell_start[ncell] = carry_s;
+}
+
+__global__ void k_scatter(int n, const int* __restrict__ cid, const int* __restrict__ rank,
+                          const int* __restrict__ cell_start, const uint4* __restrict__ fx,
+                          uint4* __restrict__ spos, const double4* __restrict__ fx64,
+                          double4* __restrict__ spos64, int* __restrict__ perm) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int dst = cell_start[cid[i]] + rank[i];
+    if (fx) spos[dst] = fx[i];
+    if (fx64) spos64[dst] = fx64[i];
+    perm[dst] = i;
+}
+
+// Order each cell's members by original index (insertion sort; cells hold a
+// handful of particles at the densities of interest).
+__global__ void k_cell_fixup(int ncell, const int* __restrict__ cell_start,
+                             uint4* __restrict__ spos, double4* __restrict__ spos64,
+                             int* __restrict__ perm) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const int s = cell_start[c], e = cell_start[c + 1];
+    for (int k = s + 1; k < e; ++k) {
+        const int key = perm[k];
+        int j = k - 1;
+        if (perm[j] <= key) continue;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        double4 v64 = make_double4(0, 0, 0, 0);
+        if (spos) v = spos[k];
+        if (spos64) v64 = spos64[k];
+        while (j >= s && perm[j] > key) {
+            perm[j + 1] = perm[j];
+            if (spos) spos[j + 1] = spos[j];
+            if (spos64) spos64[j + 1] = spos64[j];
+            --j;
+        }
+        perm[j + 1] = key;
+        if (spos) spos[j + 1] = v;
+        if (spos64) spos64[j + 1] = v64;
+    }
+}
+
+// ------------------------------------------------------------- launchers
+void launch_prep_mixed(cudaStream_t st, const SysDev* sys, const Tile* pblk, int npblk,
+                       const float4* pos_q, uint4* fx, int* cid, int* rank, int* cell_cnt,
+                       double2* blk_q, int want_q) {
+    if (npblk <= 0) return;
+    k_prep_mixed<<<npblk, kBlockP, 0, st>>>(sys, pblk, pos_q, fx, cid, rank, cell_cnt, blk_q,
+                                            want_q);
+}
+
+void launch_prep_f64(cudaStream_t st, const SysDev* sys, const Tile* pblk, int npblk,
+                     const double4* pos_q, double4* fx64, int* cid, int* rank, int* cell_cnt,
+                     double2* blk_q, int want_q) {
+    if (npblk <= 0) return;
+    k_prep_f64<<<npblk, kBlockP, 0, st>>>(sys, pblk, pos_q, fx64, cid, rank, cell_cnt, blk_q,
+                                          want_q);
+}
+
+void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell,
+                 uint64_t* step_dev, uint64_t step_arg, uint64_t* cur_step) {
+    k_scan<<<1, kScanThreads, 0, st>>>(cell_cnt, cell_start, ncell, step_dev, step_arg, cur_step);
+}
+
+void launch_scatter(cudaStream_t st, int n, const int* cid, const int* rank,
+                    const int* cell_start, const uint4* fx, uint4* spos, const double4* fx64,
+                    double4* spos64, int* perm) {
+    if (n <= 0) return;
+    k_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, cid, rank, cell_start, fx, spos, fx64, spos64,
+                                               perm);
+}
+
+void launch_cell_fixup(cudaStream_t st, int ncell, const int* cell_start, uint4* spos,
+                       double4* spos64, int* perm) {
+    if (ncell <= 0) return;
+    k_cell_fixup<<<(ncell + 127) / 128, 128, 0, st>>>(ncell, cell_start, spos, spos64, perm);
+}
+
+}  // namespace rbe

@@ -1,0 +1,155 @@
+// rbe_internal.cuh -- device-side data layout and kernel launchers of librbe.
+//
+// One handle holds one or more independent periodic systems ("replicas").
+// Every kernel covers all systems of the handle in one launch; work items are
+// (system, tile) pairs from small tables built on the host, so a single system
+// is just the one-entry case of the batch.
+//
+// HBM layout (per handle, sized at create for the total particle count N):
+//   fx     uint4 [N]   unsorted 32-bit fixed-point fractional coordinates
+//                      (x/L, y/L, z/L mod 1, scaled by 2^32) and the charge bits
+//   cid    int   [N]   global cell index;   rank int [N]: slot within the cell
+//   spos   uint4 [N]   fx sorted by cell (the order all later kernels use)
+//   perm   int   [N]   sorted index -> caller's index
+//   fs     float4[N]   Fourier force (xyz) and Fourier dE/dq (w), sorted order
+//   cell_cnt / cell_start  int [C + 1] over all systems' cells
+//   part   float2 [sum_s nchunk_s * P_s]  per-chunk partial rho(k_l)
+//   ksamp  int4   [K] (m_x, m_y, m_z, attempts)   K = sum_s P_s
+//   kab    float2 [K] (coef * Im rho, coef * Re rho)
+//   rho    double2[K], eterm double [K]
+//   blk_e  double2[nblk] per-block (E_coul, E_lj); blk_q double2[nblk] (sum q, sum q^2)
+// and the same with double4 / double2 records for the FP64 path.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rbe {
+
+constexpr int kBlockP = 128;      // particles per block of the per-particle kernels
+constexpr int kLTile = 128;       // wave vectors per block of the structure-factor kernel
+constexpr int kMaxAttempts = 32;  // bound on the (0,0,0) rejection loop
+constexpr int kErrSampler = 1;    // bit in the device error word
+
+// Per-system constants (device copy).  All derived in FP64 on the host.
+struct SysDev {
+    double L, invL, V, alpha, sqrt_alpha, r_c, lB, S;
+    double coef_scale;      // lB * (S / P) * 4 pi / V ; coef_l = coef_scale / k_l^2
+    double self_coef;       // lB * sqrt(alpha / pi)
+    double bg_coef;         // lB * pi / (V alpha)
+    double lj_eps, lj_sigma2, lj_rcut2, lj_shift;
+    double c1, c2, dt, dt_over_m;
+    float fx_hi, fx_lo;     // 2^32 / L as an unevaluated float pair (hi + lo)
+    float Lf, L_over_2_32;  // L and L / 2^32 in FP32
+    uint64_t seed;
+    uint32_t stream;
+    int n, P, M, ncd;
+    int off_p;              // first particle (concatenated arrays)
+    int off_c;              // first cell
+    int off_k;              // first k sample
+    int off_t;              // first table entry
+    int off_part;           // first partial of the structure-factor chunks
+    int nchunk;             // structure-factor chunks of this system
+    int off_b, nb;          // first per-particle block and block count
+};
+
+// A tile of particles of one system: (system, first particle, count, aux).
+// aux = first partial index (chunks) or unused (particle blocks).
+struct Tile {
+    int sys, first, count, aux;
+};
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// multiplies, the key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Index of the system owning global particle i (pstart has nsys + 1 entries).
+__device__ __forceinline__ int find_sys(const int* __restrict__ pstart, int nsys, int i) {
+    int lo = 0, hi = nsys - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(pstart + mid) <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------- launchers
+// cells / sorting (rbe_cells.cu)
+void launch_prep_mixed(cudaStream_t st, const SysDev* sys, const Tile* pblk, int npblk,
+                       const float4* pos_q, uint4* fx, int* cid, int* rank, int* cell_cnt,
+                       double2* blk_q, int want_q);
+void launch_prep_f64(cudaStream_t st, const SysDev* sys, const Tile* pblk, int npblk,
+                     const double4* pos_q, double4* fx64, int* cid, int* rank, int* cell_cnt,
+                     double2* blk_q, int want_q);
+void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell,
+                 uint64_t* step_dev, uint64_t step_arg, uint64_t* cur_step);
+void launch_scatter(cudaStream_t st, int n, const int* cid, const int* rank,
+                    const int* cell_start, const uint4* fx, uint4* spos, const double4* fx64,
+                    double4* spos64, int* perm);
+void launch_cell_fixup(cudaStream_t st, int ncell, const int* cell_start, uint4* spos,
+                       double4* spos64, int* perm);
+
+// Fourier part (rbe_fourier.cu)
+void launch_sample(cudaStream_t st, const SysDev* sys, int nsys, int ktot, const int* kstart,
+                   const uint64_t* table, const uint64_t* cur_step, int4* ksamp, int* err);
+void launch_rho_mixed(cudaStream_t st, const SysDev* sys, const Tile* chunks, int nchunks,
+                      int ltiles, const uint64_t* table, const uint64_t* cur_step,
+                      const uint4* spos, float2* part, int4* ksamp, int* err);
+void launch_rho_f64(cudaStream_t st, const SysDev* sys, const Tile* chunks, int nchunks,
+                    int ltiles, const uint64_t* table, const uint64_t* cur_step,
+                    const double4* spos64, double2* part64, int4* ksamp, int* err);
+void launch_finalize(cudaStream_t st, const SysDev* sys, int nsys, int ktot, const int* kstart,
+                     const float2* part, const double2* part64, const int4* ksamp,
+                     double2* rho, float2* kab, double2* kab64, double* eterm,
+                     const double2* blk_q, double2* qsum);
+void launch_fourier_force_mixed(cudaStream_t st, const SysDev* sys, const Tile* pblk, int npblk,
+                                int split, const uint4* spos, const int4* ksamp,
+                                const float2* kab, float4* fs);
+void launch_fourier_force_f64(cudaStream_t st, const SysDev* sys, const Tile* pblk, int npblk,
+                              const double4* spos64, const int4* ksamp, const double2* kab64,
+                              double4* fs64);
+
+// real space, LJ, Langevin, energies (rbe_real.cu)
+struct RealArgs {
+    const SysDev* sys;
+    const Tile* pblk;
+    int npblk;
+    int parts;               // RBE_PART_* mask
+    const int* cell_start;
+    const int* perm;
+    const uint64_t* cur_step;
+    const double2* qsum;     // per system (sum q, sum q^2)
+    // mixed
+    const uint4* spos;
+    const float4* fs;
+    float4* F_out;
+    float* phi_out;
+    float4* md_pos;          // non-null: Langevin update in place
+    float4* md_vel;
+    // fp64
+    const double4* spos64;
+    const double4* fs64;
+    double4* F_out64;
+    double* phi_out64;
+    double4* md_pos64;
+    double4* md_vel64;
+    double2* blk_e;          // per block (E_coul, E_lj), nullable
+};
+void launch_real_mixed(cudaStream_t st, const RealArgs& a);
+void launch_real_f64(cudaStream_t st, const RealArgs& a);
+void launch_energy(cudaStream_t st, const SysDev* sys, int nsys, const double* eterm,
+                   const double2* blk_e, const double2* qsum, int parts, double* E_out);
+
+}  // namespace rbe

@@ -116,12 +116,29 @@ def electrolyte(name: str, n_pos: int, n_neg: int, q_pos: float, q_neg: float,
     return Workload(name, params, pos, q, vel)
 
 
+def place_jittered_lattice(n: int, L: float, min_sep: float,
+                           rng: np.random.Generator) -> np.ndarray:
+    """n distinct random sites of the smallest simple-cubic lattice with at
+    least n sites, each moved uniformly within +-(a - min_sep)/2 per axis
+    (a = lattice spacing), so every pair stays at least min_sep apart.  Used
+    where the packing is too dense for re-drawing uniform points."""
+    side = int(math.ceil(n ** (1.0 / 3.0) - 1e-9))
+    a = L / side
+    if a < min_sep:
+        raise ValueError("lattice spacing below min_sep")
+    sites = rng.choice(side ** 3, size=n, replace=False)
+    idx = np.stack([sites % side, (sites // side) % side, sites // (side * side)], 1)
+    jitter = rng.uniform(-(a - min_sep) / 2, (a - min_sep) / 2, size=(n, 3))
+    return (idx + 0.5) * a + jitter
+
+
 def water_like(name: str, n_mol: int, density: float, params: SystemParams,
                min_oo: float = 2.5) -> Workload:
-    """3 n_mol point charges; centres at ``density`` molecules per unit volume."""
+    """3 n_mol point charges; centres at ``density`` molecules per unit volume,
+    on a jittered lattice with O-O distances of at least ``min_oo``."""
     rng = np.random.default_rng([params.seed, 0xAA7E, n_mol])
     L = params.box
-    centres = place_uniform(n_mol, L, min_oo, rng).astype(np.float64)
+    centres = place_jittered_lattice(n_mol, L, min_oo, rng)
     # uniform random rotations from normalised Gaussian quaternions
     qt = rng.standard_normal((n_mol, 4))
     qt /= np.linalg.norm(qt, axis=1, keepdims=True)
