@@ -1,0 +1,440 @@
+#!/usr/bin/env python3
+"""Benchmark: random batch Ewald MD steps on one GB300 (or N, one replica each).
+
+One benchmark step = one MD step of the whole hot path on the 2:1 electrolyte
+(N = 8001: 2667 cations +2, 5334 anions -1, number density 0.05, alpha = 0.2,
+r_c = 6, P = 200, WCA LJ, Langevin T = 1, gamma = 1, dt = 1e-3): k-sampling,
+structure factors, FP64 rho(k), Fourier forces, cell list, real space + LJ and
+the Langevin update, mixed precision, replayed from a CUDA graph.
+
+Printed as one JSON line (rank 0):
+  value       particle-steps/s over all ranks (inputs resident in HBM; L2
+              flushed by a 256 MiB write between timed steps, outside the timing)
+  e2e         the same through rbe_step_host: pinned host pos/vel copied in and
+              out every step, wall-clock
+  roofline    dominant kernel (from a profiled pass of the same steps) against
+              the special-function-unit rate (sin/cos) or HBM bandwidth
+  cpu_baseline  the FP64 CPU oracle on a bounded sample, host cores
+  fp64_path   the plain FP64 GPU path on the same steps; speedup_vs_fp64
+  accuracy    rel-RMS of the mixed forces against the FP64 GPU forces
+``--impl reference`` times the FP64 CPU oracle instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("RBE force evals/sec & particle-steps/sec at force rel-RMS≤1e-5 vs FP64 path, "
+          "same GPU")
+UNIT = "particle-steps/s"
+SM_COUNT = 152
+SFU_PER_SM_PER_CLK = 16          # sin/cos results per SM per clock (special-function unit)
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="budget of the CPU-oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_2010_01559_gb300 import workloads
+    return workloads.config_2to1_mixed()
+
+
+# --------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "20"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------- CPU oracle
+def oracle_steps(wl, nsteps, sub=None, step0=0):
+    """Run nsteps oracle MD steps (forces for `sub` only if given); returns seconds."""
+    import numpy as np
+    import oracle
+    p = wl.params
+    pos = wl.pos.astype(np.float64)
+    vel = wl.vel.astype(np.float64)
+    q = wl.q.astype(np.float64)
+    t0 = time.perf_counter()
+    for s in range(nsteps):
+        out = oracle.rbe_forces(pos, q, p.box, p.alpha, p.r_c, p.P, p.seed, p.stream, step0 + s,
+                                lB=p.coulomb_prefactor, lj_eps=p.lj_eps, lj_sigma=p.lj_sigma,
+                                lj_rcut=p.lj_rcut, sub=sub)
+        if sub is None:
+            pos, vel = oracle.langevin_step(pos, vel, out["F"], p.box, p.gamma, p.kT, p.dt,
+                                            p.mass, p.seed, p.stream, step0 + s)
+    return time.perf_counter() - t0
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(wl, budget_s):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    t1 = oracle_steps(wl, 1)                       # one full step (also warms up)
+    n = max(1, min(200, int(budget_s / max(t1, 1e-6))))
+    t = oracle_steps(wl, n, step0=1)
+    return {"value": wl.n * n / t, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"{n} full FP64 oracle MD steps (all {wl.n} particles: sample k, "
+                      f"rho, Fourier + real-space + LJ forces, Langevin)"}
+
+
+# --------------------------------------------------------------------- distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def reduce_sum(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t.item()
+
+
+# --------------------------------------------------------------------- roofline
+def source_hash(kernel_file):
+    return hashlib.sha256(open(kernel_file, "rb").read()).hexdigest()[:16]
+
+
+def traffic_for(kernel, workload_name):
+    """dram bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        db = json.load(open(path))
+    except ValueError:
+        return None
+    e = db.get(kernel)
+    if not e or e.get("workload") != workload_name:
+        return None
+    src = os.path.join(ROOT, "paper_2010_01559_gb300", "csrc", e["source"])
+    if not os.path.exists(src) or source_hash(src) != e.get("source_sha256_16"):
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def roofline(prof, wl, peaks, clocks):
+    """Dominant kernel of the profiled pass against its bound."""
+    name, (ms, cnt) = max(prof.items(), key=lambda kv: kv[1][0])
+    avg_s = ms / max(cnt, 1) / 1e3
+    N, P = wl.n, wl.params.P
+    if name in ("rho", "fourier_force"):
+        # each (particle, wave vector) pair takes one sine and one cosine
+        work = 2.0 * N * P
+        peak = SM_COUNT * SFU_PER_SM_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
+        achieved = work / avg_s / 1e12
+        out = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
+               "unit": "Tsfu/s", "frac": achieved / peak,
+               "peak_basis": "152 SMs x 16 sin/cos per clock x 2070 MHz (max SM clock)",
+               "algorithmic": f"2 SFU ops per (particle, k) pair x {N} x {P}"}
+    else:
+        # bytes the kernel must move: records read/written per particle
+        per_particle = {"prep": 16 + 16 + 4 + 4, "scatter": 16 + 4 + 4 + 16 + 4,
+                        "cell_order": 0, "real": 16 + 16 + 4 + 16 + 32,
+                        "scan": 0, "finalize": 0, "energy": 0}.get(name, 0)
+        bytes_ = per_particle * N
+        peak = peaks.get("hbm_gbs", 6800.0)
+        achieved = bytes_ / avg_s / 1e9
+        out = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak,
+               "unit": "GB/s", "frac": achieved / peak,
+               "algorithmic": f"{per_particle} B per particle x {N}"}
+    out["avg_launch_us"] = avg_s * 1e6
+    out["traffic"] = traffic_for(name, wl.name)
+    return out
+
+
+# --------------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2010_01559_gb300 as rbe
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = workload()
+    if world > 1:
+        wl.params.stream = rank                      # independent replica per rank
+    K, W = args.steps, args.warmup
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peaks = json.load(open(pp))
+
+    stream = torch.cuda.Stream(device=dev)
+    h = rbe.RBE(rbe.params_from(wl.params, n_max=wl.n))
+    pos0 = torch.from_numpy(wl.pos_q()).to(dev)
+    vel0 = torch.zeros((wl.n, 4), dtype=torch.float32, device=dev)
+    vel0[:, :3] = torch.from_numpy(wl.vel).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed_steps(pos, vel, step_dev, nsteps, profile=False):
+        evs = []
+        h.profile(profile)
+        with torch.cuda.stream(stream):
+            for k in range(nsteps):
+                flush.fill_(k & 0xFF)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h.step(pos, vel, 1, step_dev)
+                e1.record(stream)
+                evs.append((e0, e1))
+        stream.synchronize()
+        h.profile(False)
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    # ---------------------------------------------------------------- mixed path
+    with torch.cuda.stream(stream):
+        pos = pos0.clone()
+        vel = vel0.clone()
+        step_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+        h.set_graph(True)
+        for _ in range(W):
+            h.step(pos, vel, 1, step_dev)
+    stream.synchronize()
+    launches0 = h.launch_count()
+    clocks = Clocks(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    total_ms = timed_steps(pos, vel, step_dev, K)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    launches = h.launch_count() - launches0
+    h.sync()
+    t_max = reduce_max(total_ms / 1e3, world, dev)
+    n_all = reduce_sum(float(wl.n), world, dev)
+    value = n_all * K / t_max
+    ms_per_step = t_max * 1e3 / K
+
+    # per-kernel profile of the same steps (events around each kernel)
+    timed_steps(pos, vel, step_dev, K, profile=True)
+    prof = h.profile_read()
+    kernels_us = {k: (ms / c * 1e3 if c else 0.0) for k, (ms, c) in prof.items()}
+
+    # accuracy at this configuration: mixed vs FP64 forces on the same input
+    with torch.cuda.stream(stream):
+        F32, E32, _ = h.forces(pos0, 0)
+        F64, E64, _ = h.forces_f64(pos0.double().contiguous(), 0)
+    stream.synchronize()
+    d = (F32[:, :3].double() - F64[:, :3])
+    acc = (d.norm() / F64[:, :3].norm()).item()
+
+    # ---------------------------------------------------------------- FP64 path
+    K64 = max(3, min(K, 50))
+    with torch.cuda.stream(stream):
+        pos64 = pos0.double().contiguous()
+        vel64 = vel0.double().contiguous()
+        step64 = torch.zeros(1, dtype=torch.int64, device=dev)
+        for _ in range(3):
+            h.step(pos64, vel64, 1, step64)
+    stream.synchronize()
+    ms64 = timed_steps(pos64, vel64, step64, K64)
+    value64 = wl.n * K64 / (ms64 / 1e3)
+
+    # ---------------------------------------------------------------- end to end
+    hpos = pos0.cpu().pin_memory()
+    hvel = vel0.cpu().pin_memory()
+    for s in range(3):
+        h.step_host(hpos, hvel, 1, 10_000 + s)
+    e2e_t = 0.0
+    for s in range(K):
+        with torch.cuda.stream(stream):
+            flush.fill_(s & 0xFF)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        h.step_host(hpos, hvel, 1, 20_000 + s)
+        e2e_t += time.perf_counter() - t0
+    e2e_t = reduce_max(e2e_t, world, dev)
+    e2e_value = n_all * K / e2e_t
+    bytes_io = 2 * 16 * wl.n
+
+    result = None
+    if rank == 0:
+        rl = roofline(prof, wl, peaks, clk)
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "N": wl.n, "P": wl.params.P,
+                       "alpha": wl.params.alpha, "r_c": wl.params.r_c,
+                       "box": round(wl.params.box, 4), "path": "mixed (FP32 phases/forces, "
+                       "FP64 rho(k) and energy sums)", "graph": True,
+                       "l2": "flushed between timed steps (256 MiB write, untimed)",
+                       "parallelism": f"replicas x{world}"},
+            "force_evals_per_s": value / wl.n,
+            "clocks": clk,
+            "roofline": rl,
+            "kernels_avg_us": kernels_us,
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_io,
+                    "d2h_bytes_per_step": bytes_io,
+                    "api": "rbe_step_host (pinned host pos/vel in and out every step)"},
+            "fp64_path": {"value": value64, "unit": UNIT, "steps": K64,
+                          "ms_per_step": ms64 / K64},
+            "speedup_vs_fp64": value / value64,
+            "accuracy": {"force_rel_rms_mixed_vs_fp64_gpu": acc, "target": 1e-5},
+        }
+        if not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+        print(json.dumps(result), flush=True)
+    h.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return result
+
+
+# --------------------------------------------------------------------- reference arm
+def run_reference(args):
+    """The FP64 CPU oracle as it stands, on this host's cores, same workload and
+    metric.  Each step is one oracle MD step; if K steps of the whole system
+    would not fit a few minutes, each step evaluates forces for a fixed subset
+    of particles (rho(k) still over all of them) and counts only that subset."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import numpy as np
+    import oracle
+    oracle.build()
+    wl = workload()
+    K, W = args.steps, args.warmup
+    t1 = oracle_steps(wl, 1)
+    budget = 150.0
+    if t1 * (K + W) <= budget:
+        sub, n_per_step = None, wl.n
+    else:
+        frac = budget / (t1 * (K + W))
+        n_per_step = max(16, int(wl.n * frac))
+        sub = np.linspace(0, wl.n - 1, n_per_step).astype(int)
+    oracle_steps(wl, W, sub=sub, step0=100)
+    t = oracle_steps(wl, K, sub=sub, step0=1000)
+    value = n_per_step * K / t
+    sample = (f"{K} oracle MD steps over all {wl.n} particles" if sub is None else
+              f"{K} oracle steps: rho(k) over all {wl.n} particles, forces for "
+              f"{n_per_step} evenly spaced particles per step")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+           "steps": K, "warmup": W, "ms_per_step": t * 1e3 / K, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": wl.name, "N": wl.n, "P": wl.params.P},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -205,6 +205,34 @@ rbe_status rbe_set_tuning(rbe_handle h, int32_t rho_chunk, int32_t force_split);
 rbe_status rbe_autotune(rbe_handle h, int32_t n, const float *pos_q, int32_t *rho_chunk,
                         int32_t *force_split);
 
+/* Kernels of one evaluation, in launch order (per-kernel profile indices). */
+enum {
+    RBE_K_PREP = 0,          /* fixed-point coordinates, cell ids, charge sums      */
+    RBE_K_SCAN = 1,          /* exclusive scan of cell counts, step latch           */
+    RBE_K_SCATTER = 2,       /* counting-sort scatter                               */
+    RBE_K_CELL_ORDER = 3,    /* order inside each cell by original index            */
+    RBE_K_RHO = 4,           /* k-sampling + per-chunk structure factors            */
+    RBE_K_FINALIZE = 5,      /* FP64 rho(k), energy terms, force coefficients       */
+    RBE_K_FOURIER_FORCE = 6, /* RBE Fourier force and dE/dq (Eq. rbmapprox)         */
+    RBE_K_REAL = 7,          /* real space + LJ + assembly (+ Langevin)             */
+    RBE_K_ENERGY = 8,        /* FP64 energy reduction                               */
+    RBE_K_COUNT = 9
+};
+
+/* Enable (1) or disable (0) per-kernel timing.  While enabled, rbe_forces*,
+ * rbe_step* record CUDA events around every kernel on the handle's stream,
+ * wait for them at the end of each evaluation and accumulate the device time
+ * per kernel; graph replay is bypassed. */
+rbe_status rbe_profile(rbe_handle h, int32_t enable);
+
+/* Read and reset the accumulated profile: ms[RBE_K_COUNT] device milliseconds
+ * and launches[RBE_K_COUNT] (either may be NULL). */
+rbe_status rbe_profile_read(rbe_handle h, double *ms, int64_t *launches);
+
+/* Kernels launched through h since it was created (graph replays count the
+ * kernels of the replayed step). */
+rbe_status rbe_launch_count(rbe_handle h, int64_t *count);
+
 #ifdef __cplusplus
 }
 #endif

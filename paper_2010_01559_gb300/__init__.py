@@ -113,6 +113,23 @@ class _HandleBase:
                                          ctypes.byref(b)), self._h)
         return a.value, b.value
 
+    def profile(self, on=True):
+        capi.check(self.lib.rbe_profile(self._h, 1 if on else 0), self._h)
+
+    def profile_read(self):
+        """{kernel name: (device ms, launches)} accumulated since the last read."""
+        import numpy as np
+        ms = np.zeros(len(capi.KERNELS), dtype=np.float64)
+        cnt = np.zeros(len(capi.KERNELS), dtype=np.int64)
+        capi.check(self.lib.rbe_profile_read(self._h, ms.ctypes.data_as(ctypes.c_void_p),
+                                             cnt.ctypes.data_as(ctypes.c_void_p)), self._h)
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(capi.KERNELS)}
+
+    def launch_count(self):
+        c = ctypes.c_int64()
+        capi.check(self.lib.rbe_launch_count(self._h, ctypes.byref(c)), self._h)
+        return c.value
+
     def set_graph(self, on=True):
         capi.check(self.lib.rbe_set_graph(self._h, 1 if on else 0), self._h)
 

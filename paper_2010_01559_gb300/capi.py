@@ -68,7 +68,14 @@ _SIGS = {
     "rbe_set_tuning": ([_H, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "rbe_autotune": ([_H, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_int32),
                       ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "rbe_profile": ([_H, ctypes.c_int32], ctypes.c_int),
+    "rbe_profile_read": ([_H, _P, _P], ctypes.c_int),
+    "rbe_launch_count": ([_H, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
 }
+
+#: kernel names in RBE_K_* order
+KERNELS = ("prep", "scan", "scatter", "cell_order", "rho", "finalize", "fourier_force",
+           "real", "energy")
 
 #: every symbol include/rbe.h declares
 EXPORTED = tuple(_SIGS)

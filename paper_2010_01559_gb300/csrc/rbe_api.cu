@@ -47,6 +47,7 @@ struct GraphEntry {
     const void* step;
     int prec;
     cudaGraphExec_t exec;
+    int kernels;           // kernels in one replay
 };
 
 int axis_M(double alpha, double L) {
@@ -117,6 +118,13 @@ struct rbe_ctx {
     bool use_graph = false;
     std::vector<GraphEntry> graphs;
     std::string err;
+    // per-kernel profile
+    bool prof_on = false;
+    cudaEvent_t ev_beg[RBE_K_COUNT] = {};
+    cudaEvent_t ev_end[RBE_K_COUNT] = {};
+    double prof_ms[RBE_K_COUNT] = {};
+    int64_t prof_cnt[RBE_K_COUNT] = {};
+    int64_t kernel_count = 0;
 
     SysDev* d_sys = nullptr;
     Tile* d_pblk = nullptr;
@@ -402,6 +410,10 @@ void release(rbe_ctx* h) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (int k = 0; k < RBE_K_COUNT; ++k) {
+        if (h->ev_beg[k]) cudaEventDestroy(h->ev_beg[k]);
+        if (h->ev_end[k]) cudaEventDestroy(h->ev_end[k]);
+    }
 }
 
 rbe_status create_common(const rbe_params* ps, const int32_t* ns, int nsys, bool batch,
@@ -477,41 +489,77 @@ struct EvalArgs {
     double4* md_vel64;
 };
 
-void enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
+// Returns the number of kernels enqueued.  With profiling on (and st the
+// handle's own stream, i.e. not capturing) every kernel is bracketed by events
+// and the per-kernel device times are accumulated after the last one.
+int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     const bool mixed = a.prec == RBE_MIXED;
     const bool fourier = (a.parts & RBE_PART_FOURIER) != 0;
     const int want_q = (fourier && (a.E || a.phi || a.phi64)) ? 1 : 0;
     const int n = h->batch ? h->ntot : h->cur_n;
-    if (mixed)
-        launch_prep_mixed(st, h->d_sys, h->d_pblk, h->npblk, a.pos, h->d_fx, h->d_cid,
-                          h->d_rank, h->d_cell_cnt, h->d_blk_q, want_q);
-    else
-        launch_prep_f64(st, h->d_sys, h->d_pblk, h->npblk, a.pos64, h->d_fx64, h->d_cid,
-                        h->d_rank, h->d_cell_cnt, h->d_blk_q, want_q);
-    launch_scan(st, h->d_cell_cnt, h->d_cell_start, h->ncell, a.step_dev, a.step, h->d_cur_step);
-    launch_scatter(st, n, h->d_cid, h->d_rank, h->d_cell_start, mixed ? h->d_fx : nullptr,
-                   h->d_spos, mixed ? nullptr : h->d_fx64, h->d_spos64, h->d_perm);
-    launch_cell_fixup(st, h->ncell, h->d_cell_start, mixed ? h->d_spos : nullptr,
-                      mixed ? nullptr : h->d_spos64, h->d_perm);
+    const bool prof = h->prof_on && st == h->stream;
+    bool used[RBE_K_COUNT] = {};
+    int count = 0;
+    auto run = [&](int kid, auto&& launch) {
+        if (prof) cudaEventRecord(h->ev_beg[kid], st);
+        launch();
+        if (prof) {
+            cudaEventRecord(h->ev_end[kid], st);
+            used[kid] = true;
+        }
+        ++count;
+    };
+    run(RBE_K_PREP, [&] {
+        if (mixed)
+            launch_prep_mixed(st, h->d_sys, h->d_pblk, h->npblk, a.pos, h->d_fx, h->d_cid,
+                              h->d_rank, h->d_cell_cnt, h->d_blk_q, want_q);
+        else
+            launch_prep_f64(st, h->d_sys, h->d_pblk, h->npblk, a.pos64, h->d_fx64, h->d_cid,
+                            h->d_rank, h->d_cell_cnt, h->d_blk_q, want_q);
+    });
+    run(RBE_K_SCAN, [&] {
+        launch_scan(st, h->d_cell_cnt, h->d_cell_start, h->ncell, a.step_dev, a.step,
+                    h->d_cur_step);
+    });
+    run(RBE_K_SCATTER, [&] {
+        launch_scatter(st, n, h->d_cid, h->d_rank, h->d_cell_start, mixed ? h->d_fx : nullptr,
+                       h->d_spos, mixed ? nullptr : h->d_fx64, h->d_spos64, h->d_perm);
+    });
+    run(RBE_K_CELL_ORDER, [&] {
+        launch_cell_fixup(st, h->ncell, h->d_cell_start, mixed ? h->d_spos : nullptr,
+                          mixed ? nullptr : h->d_spos64, h->d_perm);
+    });
     const int ltiles = (h->pmax + kLTile - 1) / kLTile;
     if (fourier) {
         if (mixed) {
-            launch_rho_mixed(st, h->d_sys, h->d_chunks, h->nchunks, ltiles, h->d_table,
-                             h->d_cur_step, h->d_spos, h->d_part, h->d_ksamp, h->d_err);
-            launch_finalize(st, h->d_sys, h->nsys, h->ktot, h->d_kstart, h->d_part, nullptr,
-                            h->d_ksamp, h->d_rho, h->d_kab, nullptr, h->d_eterm,
-                            want_q ? h->d_blk_q : nullptr, h->d_qsum);
-            launch_fourier_force_mixed(st, h->d_sys, h->split == 1 ? h->d_pblk : h->d_fblk,
-                                       h->split == 1 ? h->npblk : h->nfblk, h->split, h->d_spos,
-                                       h->d_ksamp, h->d_kab, h->d_fs);
+            run(RBE_K_RHO, [&] {
+                launch_rho_mixed(st, h->d_sys, h->d_chunks, h->nchunks, ltiles, h->d_table,
+                                 h->d_cur_step, h->d_spos, h->d_part, h->d_ksamp, h->d_err);
+            });
+            run(RBE_K_FINALIZE, [&] {
+                launch_finalize(st, h->d_sys, h->nsys, h->ktot, h->d_kstart, h->d_part, nullptr,
+                                h->d_ksamp, h->d_rho, h->d_kab, nullptr, h->d_eterm,
+                                want_q ? h->d_blk_q : nullptr, h->d_qsum);
+            });
+            run(RBE_K_FOURIER_FORCE, [&] {
+                launch_fourier_force_mixed(st, h->d_sys, h->split == 1 ? h->d_pblk : h->d_fblk,
+                                           h->split == 1 ? h->npblk : h->nfblk, h->split,
+                                           h->d_spos, h->d_ksamp, h->d_kab, h->d_fs);
+            });
         } else {
-            launch_rho_f64(st, h->d_sys, h->d_chunks, h->nchunks, ltiles, h->d_table,
-                           h->d_cur_step, h->d_spos64, h->d_part64, h->d_ksamp, h->d_err);
-            launch_finalize(st, h->d_sys, h->nsys, h->ktot, h->d_kstart, nullptr, h->d_part64,
-                            h->d_ksamp, h->d_rho, nullptr, h->d_kab64, h->d_eterm,
-                            want_q ? h->d_blk_q : nullptr, h->d_qsum);
-            launch_fourier_force_f64(st, h->d_sys, h->d_pblk, h->npblk, h->d_spos64, h->d_ksamp,
-                                     h->d_kab64, h->d_fs64);
+            run(RBE_K_RHO, [&] {
+                launch_rho_f64(st, h->d_sys, h->d_chunks, h->nchunks, ltiles, h->d_table,
+                               h->d_cur_step, h->d_spos64, h->d_part64, h->d_ksamp, h->d_err);
+            });
+            run(RBE_K_FINALIZE, [&] {
+                launch_finalize(st, h->d_sys, h->nsys, h->ktot, h->d_kstart, nullptr,
+                                h->d_part64, h->d_ksamp, h->d_rho, nullptr, h->d_kab64,
+                                h->d_eterm, want_q ? h->d_blk_q : nullptr, h->d_qsum);
+            });
+            run(RBE_K_FOURIER_FORCE, [&] {
+                launch_fourier_force_f64(st, h->d_sys, h->d_pblk, h->npblk, h->d_spos64,
+                                         h->d_ksamp, h->d_kab64, h->d_fs64);
+            });
         }
     }
     RealArgs r{};
@@ -536,8 +584,26 @@ void enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     r.md_pos64 = a.md_pos64;
     r.md_vel64 = a.md_vel64;
     r.blk_e = a.E ? h->d_blk_e : nullptr;
-    if (mixed) launch_real_mixed(st, r); else launch_real_f64(st, r);
-    if (a.E) launch_energy(st, h->d_sys, h->nsys, h->d_eterm, h->d_blk_e, h->d_qsum, a.parts, a.E);
+    run(RBE_K_REAL, [&] {
+        if (mixed) launch_real_mixed(st, r); else launch_real_f64(st, r);
+    });
+    if (a.E)
+        run(RBE_K_ENERGY, [&] {
+            launch_energy(st, h->d_sys, h->nsys, h->d_eterm, h->d_blk_e, h->d_qsum, a.parts, a.E);
+        });
+    if (prof) {
+        cudaEventSynchronize(h->ev_end[a.E ? RBE_K_ENERGY : RBE_K_REAL]);
+        for (int k = 0; k < RBE_K_COUNT; ++k) {
+            if (!used[k]) continue;
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, h->ev_beg[k], h->ev_end[k]) == cudaSuccess) {
+                h->prof_ms[k] += ms;
+                h->prof_cnt[k] += 1;
+            }
+        }
+    }
+    if (st == h->stream) h->kernel_count += count;
+    return count;
 }
 
 rbe_status check_n(rbe_ctx* h, int n) {
@@ -604,27 +670,32 @@ rbe_status step_impl(rbe_ctx* h, int n, int prec, void* pos, void* vel, int nste
         a.md_pos64 = (double4*)pos;
         a.md_vel64 = (double4*)vel;
     }
-    if (!h->use_graph) {
+    if (!h->use_graph || h->prof_on) {
         for (int k = 0; k < nsteps; ++k) enqueue_eval(h, h->stream, a);
         return finish(h, "rbe_step");
     }
     cudaGraphExec_t exec = nullptr;
+    int kernels = 0;
     for (auto& g : h->graphs)
-        if (g.n == n && g.pos == pos && g.vel == vel && g.step == step_dev && g.prec == prec) exec = g.exec;
+        if (g.n == n && g.pos == pos && g.vel == vel && g.step == step_dev && g.prec == prec) {
+            exec = g.exec;
+            kernels = g.kernels;
+        }
     if (!exec) {
         // Capture on the handle's private stream, then replay on the caller's.
         RBE_CUDA(h, cudaStreamSynchronize(h->stream));
         RBE_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-        enqueue_eval(h, h->cap_stream, a);
+        kernels = enqueue_eval(h, h->cap_stream, a);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
-        h->graphs.push_back(GraphEntry{n, pos, vel, step_dev, prec, exec});
+        h->graphs.push_back(GraphEntry{n, pos, vel, step_dev, prec, exec, kernels});
     }
     for (int k = 0; k < nsteps; ++k) RBE_CUDA(h, cudaGraphLaunch(exec, h->stream));
+    h->kernel_count += (int64_t)kernels * nsteps;
     return finish(h, "rbe_step");
 }
 
@@ -866,6 +937,35 @@ rbe_status rbe_autotune(rbe_handle h, int32_t n, const float* pos_q, int32_t* rh
     if (rho_chunk) *rho_chunk = best_chunk;
     if (force_split) *force_split = best_split;
     return finish(h, "rbe_autotune");
+}
+
+rbe_status rbe_profile(rbe_handle h, int32_t enable) {
+    if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
+    if (enable && !h->ev_beg[0]) {
+        for (int k = 0; k < RBE_K_COUNT; ++k) {
+            RBE_CUDA(h, cudaEventCreate(&h->ev_beg[k]));
+            RBE_CUDA(h, cudaEventCreate(&h->ev_end[k]));
+        }
+    }
+    h->prof_on = enable != 0;
+    return RBE_OK;
+}
+
+rbe_status rbe_profile_read(rbe_handle h, double* ms, int64_t* launches) {
+    if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
+    for (int k = 0; k < RBE_K_COUNT; ++k) {
+        if (ms) ms[k] = h->prof_ms[k];
+        if (launches) launches[k] = h->prof_cnt[k];
+        h->prof_ms[k] = 0.0;
+        h->prof_cnt[k] = 0;
+    }
+    return RBE_OK;
+}
+
+rbe_status rbe_launch_count(rbe_handle h, int64_t* count) {
+    if (!h || !count) return fail(h, RBE_ERR_ARG, "null argument");
+    *count = h->kernel_count;
+    return RBE_OK;
 }
 
 }  // extern "C"
