@@ -233,6 +233,38 @@ rbe_status rbe_profile_read(rbe_handle h, double *ms, int64_t *launches);
  * kernels of the replayed step). */
 rbe_status rbe_launch_count(rbe_handle h, int64_t *count);
 
+/* Fourier part of one RBE evaluation without any device allocation, for
+ * callers that cannot call cudaMalloc: an MD engine whose memory pool owns all
+ * device memory and forbids plugins to allocate, an application that records
+ * its whole time step into a CUDA graph (allocation is not allowed inside the
+ * capture region), or a latency-bound loop that cannot afford cudaMalloc's
+ * implicit device synchronisation.  The paper has no counterpart: this is an
+ * interface variant of rbe_forces_ex(..., RBE_PART_FOURIER, ...) that needs no
+ * handle.
+ *
+ * p: system parameters (box, alpha, P, seed, stream, coulomb_prefactor are
+ * used).  pos_q: device float4[n] (x, y, z, q), caller-owned.  F_out: device
+ * float4[n] receives the RBE Fourier force (caller's order).  E_out (device,
+ * nullable): one double, the Fourier energy including self and background
+ * terms.  cuda_stream: a cudaStream_t or NULL.  The k-batch of `step` is the
+ * same one rbe_forces draws for the same parameters.
+ *
+ * Scratch: a 4 MiB file-scope device array inside librbe, held by every GPU
+ * that loads the library until the process exits.  Limits, checked on the host
+ * (RBE_ERR_ARG with a message from rbe_last_error(NULL)): 1 <= P <= 1024, a
+ * sampling table of at most 4096 entries, and n * P small enough that the
+ * per-chunk partial sums fit (chunks of up to 65536 particles; e.g. n = 2^20
+ * with P = 500 fits).  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call shares the array and
+ * overwrites what it reads, so no state carries over between calls, but calls
+ * that overlap on the GPU (e.g. on two streams) race on it and must be
+ * serialised.  The call synchronises cuda_stream before returning.  It calls
+ * no cudaMalloc, cudaFree or other allocating routine. */
+rbe_status rbe_fourier_forces_noalloc(const rbe_params *p, int32_t n, const float *pos_q,
+                                      uint64_t step, float *F_out, double *E_out,
+                                      void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -71,6 +71,8 @@ _SIGS = {
     "rbe_profile": ([_H, ctypes.c_int32], ctypes.c_int),
     "rbe_profile_read": ([_H, _P, _P], ctypes.c_int),
     "rbe_launch_count": ([_H, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "rbe_fourier_forces_noalloc": ([ctypes.POINTER(rbe_params), ctypes.c_int32, _P,
+                                    ctypes.c_uint64, _P, _P, _P], ctypes.c_int),
 }
 
 #: kernel names in RBE_K_* order

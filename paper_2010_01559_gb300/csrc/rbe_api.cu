@@ -969,3 +969,9 @@ rbe_status rbe_launch_count(rbe_handle h, int64_t* count) {
 }
 
 }  // extern "C"
+
+namespace rbe {
+// Lets other translation units of the library report a message through
+// rbe_last_error(NULL).
+void set_last_error_message(const char* msg) { g_last_error = msg ? msg : ""; }
+}  // namespace rbe
