@@ -194,16 +194,26 @@ rbe_status rbe_step_host(rbe_handle h, int32_t n, float *pos_q, float *vel, int3
  * (RBE_ERR_SAMPLER) and asynchronous CUDA errors.  Clears the latch. */
 rbe_status rbe_sync(rbe_handle h);
 
-/* Tuning of the Fourier kernels: particles per structure-factor chunk
- * (power of two, 32..8192; 0 = automatic) and threads cooperating on one
- * particle in the force pass (1, 2, 4 or 8; 0 = automatic). */
-rbe_status rbe_set_tuning(rbe_handle h, int32_t rho_chunk, int32_t force_split);
+/* Launch shapes of the per-particle kernels (0 = automatic for every field). */
+typedef struct {
+    int32_t rho_chunk;     /* particles per structure-factor chunk: power of two in [32, 8192] */
+    int32_t force_split;   /* threads per particle in the Fourier-force pass: 1, 2, 4 or 8     */
+    int32_t real_split;    /* threads per particle in the real-space pass: 1..32, power of two  */
+    int32_t reserved;      /* must be 0                                                         */
+} rbe_tuning;
 
-/* Time the candidate tunings on the given input (device pos_q, n particles)
- * with CUDA events and keep the fastest; returns it in *rho_chunk and
- * *force_split (nullable). */
-rbe_status rbe_autotune(rbe_handle h, int32_t n, const float *pos_q, int32_t *rho_chunk,
-                        int32_t *force_split);
+/* Set the launch shapes (results change only by floating-point summation
+ * order).  RBE_ERR_ARG for a value out of range. */
+rbe_status rbe_set_tuning(rbe_handle h, const rbe_tuning *t);
+
+/* The launch shapes in effect for the last prepared particle count (automatic
+ * choices resolved). */
+rbe_status rbe_get_tuning(rbe_handle h, rbe_tuning *t);
+
+/* Time the candidate launch shapes of each tunable kernel on the given input
+ * (device pos_q, n particles) with CUDA events, keep the fastest and return
+ * them in *out (nullable). */
+rbe_status rbe_autotune(rbe_handle h, int32_t n, const float *pos_q, rbe_tuning *out);
 
 /* Kernels of one evaluation, in launch order (per-kernel profile indices). */
 enum {

@@ -103,15 +103,23 @@ class _HandleBase:
     def sync(self):
         capi.check(self.lib.rbe_sync(self._h), self._h)
 
-    def set_tuning(self, rho_chunk=0, force_split=0):
-        capi.check(self.lib.rbe_set_tuning(self._h, rho_chunk, force_split), self._h)
+    def set_tuning(self, rho_chunk=0, force_split=0, real_split=0):
+        t = capi.rbe_tuning(rho_chunk, force_split, real_split, 0)
+        capi.check(self.lib.rbe_set_tuning(self._h, ctypes.byref(t)), self._h)
+
+    def get_tuning(self):
+        """(rho_chunk, force_split, real_split) in effect."""
+        t = capi.rbe_tuning()
+        capi.check(self.lib.rbe_get_tuning(self._h, ctypes.byref(t)), self._h)
+        return t.rho_chunk, t.force_split, t.real_split
 
     def autotune(self, pos_q):
-        a, b = ctypes.c_int32(), ctypes.c_int32()
+        """Pick the fastest launch shapes on this input; returns them."""
+        t = capi.rbe_tuning()
         self._stream()
-        capi.check(self.lib.rbe_autotune(self._h, pos_q.shape[0], _ptr(pos_q), ctypes.byref(a),
-                                         ctypes.byref(b)), self._h)
-        return a.value, b.value
+        capi.check(self.lib.rbe_autotune(self._h, pos_q.shape[0], _ptr(pos_q), ctypes.byref(t)),
+                   self._h)
+        return t.rho_chunk, t.force_split, t.real_split
 
     def profile(self, on=True):
         capi.check(self.lib.rbe_profile(self._h, 1 if on else 0), self._h)

@@ -33,6 +33,11 @@ class rbe_params(ctypes.Structure):
                 ("P", ctypes.c_int32), ("n_max", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
+class rbe_tuning(ctypes.Structure):
+    _fields_ = [("rho_chunk", ctypes.c_int32), ("force_split", ctypes.c_int32),
+                ("real_split", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class rbe_info(ctypes.Structure):
     _fields_ = [("H", ctypes.c_double), ("S", ctypes.c_double), ("M", ctypes.c_int32),
                 ("n_cells_dim", ctypes.c_int32), ("n", ctypes.c_int32), ("P", ctypes.c_int32),
@@ -65,9 +70,9 @@ _SIGS = {
     "rbe_forces_host": ([_H, ctypes.c_int32, _P, ctypes.c_uint64, _P, _P], ctypes.c_int),
     "rbe_step_host": ([_H, ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_uint64], ctypes.c_int),
     "rbe_sync": ([_H], ctypes.c_int),
-    "rbe_set_tuning": ([_H, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
-    "rbe_autotune": ([_H, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_int32),
-                      ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "rbe_set_tuning": ([_H, ctypes.POINTER(rbe_tuning)], ctypes.c_int),
+    "rbe_get_tuning": ([_H, ctypes.POINTER(rbe_tuning)], ctypes.c_int),
+    "rbe_autotune": ([_H, ctypes.c_int32, _P, ctypes.POINTER(rbe_tuning)], ctypes.c_int),
     "rbe_profile": ([_H, ctypes.c_int32], ctypes.c_int),
     "rbe_profile_read": ([_H, _P, _P], ctypes.c_int),
     "rbe_launch_count": ([_H, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),

@@ -110,10 +110,11 @@ struct rbe_ctx {
     std::vector<SysDev> sysdev;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
-    int rho_chunk = 0, force_split = 0;      // 0 = automatic
-    int cur_n = -1, cur_chunk = -1, cur_split = -1;
-    int npblk = 0, nfblk = 0, nchunks = 0, split = 1;
-    int max_pblk = 0, max_fblk = 0, max_chunks = 0;
+    int rho_chunk = 0, force_split = 0, real_split = 0;   // requested; 0 = automatic
+    int cur_n = -1, cur_chunk = -1, cur_split = -1, cur_rsplit = -1;
+    int npblk = 0, nfblk = 0, nrblk = 0, nchunks = 0, split = 1, rsplit = 1;
+    int max_pblk = 0, max_fblk = 0, max_rblk = 0, max_chunks = 0;
+    int tab_smem = 0;                        // table entries staged in shared memory
     size_t max_part = 0;
     bool use_graph = false;
     std::vector<GraphEntry> graphs;
@@ -129,6 +130,7 @@ struct rbe_ctx {
     SysDev* d_sys = nullptr;
     Tile* d_pblk = nullptr;
     Tile* d_fblk = nullptr;
+    Tile* d_rblk = nullptr;
     Tile* d_chunks = nullptr;
     int* d_kstart = nullptr;
     uint64_t* d_table = nullptr;
@@ -139,6 +141,7 @@ struct rbe_ctx {
     int* d_cid = nullptr;
     int* d_rank = nullptr;
     int* d_perm = nullptr;
+    int* d_perm_tmp = nullptr;
     float4* d_fs = nullptr;
     double4* d_fs64 = nullptr;
     int* d_cell_cnt = nullptr;
@@ -248,6 +251,8 @@ void fill_sysdev(const SysHost& s, SysDev& d) {
     d.nchunk = 0;
     d.off_b = 0;
     d.nb = 0;
+    d.off_rb = 0;
+    d.nrb = 0;
 }
 
 int auto_chunk(const rbe_ctx* h, long long ntot) {
@@ -266,15 +271,26 @@ int auto_split(long long ntot) {
     return s;
 }
 
+int auto_real_split(long long ntot) {
+    const long long target_threads = 152LL * 2048;
+    int s = 1;
+    while (s < 16 && ntot * s * 2 <= target_threads) s <<= 1;
+    return s;
+}
+
 // (Re)build the work tables for the current particle counts and tuning.
 rbe_status prepare(rbe_ctx* h, int n) {
     if (!h->batch) h->sys[0].n = n;
     const long long ntot = h->batch ? h->ntot : n;
     const int chunk = h->rho_chunk > 0 ? h->rho_chunk : auto_chunk(h, ntot);
     const int split = h->force_split > 0 ? h->force_split : auto_split(ntot);
-    if (h->cur_n == n && h->cur_chunk == chunk && h->cur_split == split) return RBE_OK;
-    std::vector<Tile> pblk, fblk, chunks;
+    const int rsplit = h->real_split > 0 ? h->real_split : auto_real_split(ntot);
+    if (h->cur_n == n && h->cur_chunk == chunk && h->cur_split == split &&
+        h->cur_rsplit == rsplit)
+        return RBE_OK;
+    std::vector<Tile> pblk, fblk, rblk, chunks;
     const int ftile = kBlockP / split;
+    const int rtile = kBlockP / rsplit;
     int off_part = 0;
     for (int s = 0; s < h->nsys; ++s) {
         SysHost& sh = h->sys[s];
@@ -292,6 +308,14 @@ rbe_status prepare(rbe_ctx* h, int n) {
             fblk.push_back(Tile{s, sh.off_p + f, std::max(0, std::min(ftile, sh.n - f)), 0});
             if (sh.n == 0) break;
         }
+        d.off_rb = (int)rblk.size();
+        int nrb = 0;
+        for (int f = 0; f < sh.n || f == 0; f += rtile) {
+            rblk.push_back(Tile{s, sh.off_p + f, std::max(0, std::min(rtile, sh.n - f)), 0});
+            ++nrb;
+            if (sh.n == 0) break;
+        }
+        d.nrb = nrb;
         d.off_part = off_part;
         int nc = 0;
         for (int f = 0; f < sh.n || f == 0; f += chunk) {
@@ -304,7 +328,8 @@ rbe_status prepare(rbe_ctx* h, int n) {
         off_part += nc * sh.p.P;
     }
     if ((int)pblk.size() > h->max_pblk || (int)fblk.size() > h->max_fblk ||
-        (int)chunks.size() > h->max_chunks || (size_t)off_part > h->max_part)
+        (int)rblk.size() > h->max_rblk || (int)chunks.size() > h->max_chunks ||
+        (size_t)off_part > h->max_part)
         return fail(h, RBE_ERR_ARG, "work tables exceed the workspace (n > capacity?)");
     RBE_CUDA(h, cudaMemcpyAsync(h->d_sys, h->sysdev.data(), sizeof(SysDev) * h->nsys,
                                 cudaMemcpyHostToDevice, h->stream));
@@ -312,32 +337,39 @@ rbe_status prepare(rbe_ctx* h, int n) {
                                 cudaMemcpyHostToDevice, h->stream));
     RBE_CUDA(h, cudaMemcpyAsync(h->d_fblk, fblk.data(), sizeof(Tile) * fblk.size(),
                                 cudaMemcpyHostToDevice, h->stream));
+    RBE_CUDA(h, cudaMemcpyAsync(h->d_rblk, rblk.data(), sizeof(Tile) * rblk.size(),
+                                cudaMemcpyHostToDevice, h->stream));
     RBE_CUDA(h, cudaMemcpyAsync(h->d_chunks, chunks.data(), sizeof(Tile) * chunks.size(),
                                 cudaMemcpyHostToDevice, h->stream));
     RBE_CUDA(h, cudaStreamSynchronize(h->stream));
     h->npblk = (int)pblk.size();
     h->nfblk = (int)fblk.size();
+    h->nrblk = (int)rblk.size();
     h->nchunks = (int)chunks.size();
     h->split = split;
+    h->rsplit = rsplit;
     h->cur_n = n;
     h->cur_chunk = chunk;
     h->cur_split = split;
+    h->cur_rsplit = rsplit;
     return RBE_OK;
 }
 
 rbe_status allocate(rbe_ctx* h) {
     // capacities (chunks as small as 32 particles, force tiles as small as 16)
-    long long pb = 0, fb = 0, ch = 0, part = 0;
+    long long pb = 0, fb = 0, rb = 0, ch = 0, part = 0;
     for (auto& s : h->sys) {
         const long long n = h->batch ? s.n : s.p.n_max;
         pb += (n + kBlockP - 1) / kBlockP + 1;
         fb += (n + 15) / 16 + 1;
+        rb += (n + 3) / 4 + 1;
         const long long c = (n + 31) / 32 + 1;
         ch += c;
         part += c * s.p.P;
     }
     h->max_pblk = (int)pb;
     h->max_fblk = (int)fb;
+    h->max_rblk = (int)rb;
     h->max_chunks = (int)ch;
     h->max_part = (size_t)part;
     const size_t N = (size_t)std::max(h->ntot, 1);
@@ -347,6 +379,7 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_ALLOC(h->d_sys, h->nsys);
     RBE_ALLOC(h->d_pblk, pb);
     RBE_ALLOC(h->d_fblk, fb);
+    RBE_ALLOC(h->d_rblk, rb);
     RBE_ALLOC(h->d_chunks, ch);
     RBE_ALLOC(h->d_kstart, h->nsys + 1);
     RBE_ALLOC(h->d_table, h->ttot);
@@ -357,6 +390,7 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_ALLOC(h->d_cid, N);
     RBE_ALLOC(h->d_rank, N);
     RBE_ALLOC(h->d_perm, N);
+    RBE_ALLOC(h->d_perm_tmp, N);
     RBE_ALLOC(h->d_fs, N);
     RBE_ALLOC(h->d_fs64, N);
     RBE_ALLOC(h->d_cell_cnt, h->ncell + 1);
@@ -368,7 +402,7 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_ALLOC(h->d_kab64, h->ktot);
     RBE_ALLOC(h->d_rho, h->ktot);
     RBE_ALLOC(h->d_eterm, h->ktot);
-    RBE_ALLOC(h->d_blk_e, pb);
+    RBE_ALLOC(h->d_blk_e, rb);
     RBE_ALLOC(h->d_blk_q, pb);
     RBE_ALLOC(h->d_qsum, h->nsys);
     RBE_ALLOC(h->d_cur_step, 1);
@@ -401,9 +435,9 @@ void release(rbe_ctx* h) {
     if (!h) return;
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
-    void* ptrs[] = {h->d_sys, h->d_pblk, h->d_fblk, h->d_chunks, h->d_kstart, h->d_table,
-                    h->d_fx, h->d_spos, h->d_fx64, h->d_spos64, h->d_cid, h->d_rank,
-                    h->d_perm, h->d_fs, h->d_fs64, h->d_cell_cnt, h->d_cell_start, h->d_part,
+    void* ptrs[] = {h->d_sys, h->d_pblk, h->d_fblk, h->d_rblk, h->d_chunks, h->d_kstart,
+                    h->d_table, h->d_fx, h->d_spos, h->d_fx64, h->d_spos64, h->d_cid, h->d_rank,
+                    h->d_perm, h->d_perm_tmp, h->d_fs, h->d_fs64, h->d_cell_cnt, h->d_cell_start, h->d_part,
                     h->d_part64, h->d_ksamp, h->d_kab, h->d_kab64, h->d_rho, h->d_eterm,
                     h->d_blk_e, h->d_blk_q, h->d_qsum, h->d_cur_step, h->d_stage_step,
                     h->d_err, h->d_stage_pos, h->d_stage_vel, h->d_stage_F, h->d_stage_E};
@@ -457,6 +491,11 @@ rbe_status create_common(const rbe_params* ps, const int32_t* ns, int nsys, bool
     }
     h->ntot = off_p;
     h->ncell = off_c;
+    {
+        int tmax = 0;
+        for (auto& sh : h->sys) tmax = std::max(tmax, 2 * sh.M);
+        h->tab_smem = tmax <= 8192 ? tmax : 0;
+    }
     h->ktot = off_k;
     h->ttot = off_t;
     rbe_status st = allocate(h);
@@ -522,19 +561,19 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
                     h->d_cur_step);
     });
     run(RBE_K_SCATTER, [&] {
-        launch_scatter(st, n, h->d_cid, h->d_rank, h->d_cell_start, mixed ? h->d_fx : nullptr,
-                       h->d_spos, mixed ? nullptr : h->d_fx64, h->d_spos64, h->d_perm);
+        launch_scatter(st, n, h->d_cid, h->d_rank, h->d_cell_start, h->d_perm_tmp);
     });
     run(RBE_K_CELL_ORDER, [&] {
-        launch_cell_fixup(st, h->ncell, h->d_cell_start, mixed ? h->d_spos : nullptr,
-                          mixed ? nullptr : h->d_spos64, h->d_perm);
+        launch_order(st, n, h->d_cid, h->d_cell_start, h->d_perm_tmp, mixed ? h->d_fx : nullptr,
+                     h->d_spos, mixed ? nullptr : h->d_fx64, h->d_spos64, h->d_perm);
     });
     const int ltiles = (h->pmax + kLTile - 1) / kLTile;
     if (fourier) {
         if (mixed) {
             run(RBE_K_RHO, [&] {
-                launch_rho_mixed(st, h->d_sys, h->d_chunks, h->nchunks, ltiles, h->d_table,
-                                 h->d_cur_step, h->d_spos, h->d_part, h->d_ksamp, h->d_err);
+                launch_rho_mixed(st, h->d_sys, h->d_chunks, h->nchunks, ltiles, h->tab_smem,
+                                 h->d_table, h->d_cur_step, h->d_spos, h->d_part, h->d_ksamp,
+                                 h->d_err);
             });
             run(RBE_K_FINALIZE, [&] {
                 launch_finalize(st, h->d_sys, h->nsys, h->ktot, h->d_kstart, h->d_part, nullptr,
@@ -548,8 +587,9 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
             });
         } else {
             run(RBE_K_RHO, [&] {
-                launch_rho_f64(st, h->d_sys, h->d_chunks, h->nchunks, ltiles, h->d_table,
-                               h->d_cur_step, h->d_spos64, h->d_part64, h->d_ksamp, h->d_err);
+                launch_rho_f64(st, h->d_sys, h->d_chunks, h->nchunks, ltiles, h->tab_smem,
+                               h->d_table, h->d_cur_step, h->d_spos64, h->d_part64, h->d_ksamp,
+                               h->d_err);
             });
             run(RBE_K_FINALIZE, [&] {
                 launch_finalize(st, h->d_sys, h->nsys, h->ktot, h->d_kstart, nullptr,
@@ -564,8 +604,9 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     }
     RealArgs r{};
     r.sys = h->d_sys;
-    r.pblk = h->d_pblk;
-    r.npblk = h->npblk;
+    r.rblk = h->d_rblk;
+    r.nrblk = h->nrblk;
+    r.split = h->rsplit;
     r.parts = a.parts;
     r.cell_start = h->d_cell_start;
     r.perm = h->d_perm;
@@ -699,6 +740,24 @@ rbe_status step_impl(rbe_ctx* h, int n, int prec, void* pos, void* vel, int nste
     return finish(h, "rbe_step");
 }
 
+}  // namespace
+
+namespace {
+// Device time of `reps` launches of one kernel (the first, a warm-up, dropped).
+template <class F>
+float time_kernel(rbe_ctx* h, cudaEvent_t e0, cudaEvent_t e1, F&& launch) {
+    float tot = 0.f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, h->stream);
+        launch();
+        cudaEventRecord(e1, h->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) tot += ms;
+    }
+    return tot;
+}
 }  // namespace
 
 // ===================================================================== C ABI
@@ -857,22 +916,39 @@ rbe_status rbe_sync(rbe_handle h) {
     return finish(h, "rbe_sync");
 }
 
-rbe_status rbe_set_tuning(rbe_handle h, int32_t rho_chunk, int32_t force_split) {
-    if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
-    if (rho_chunk != 0 && (rho_chunk < 32 || rho_chunk > 8192 || (rho_chunk & (rho_chunk - 1))))
+rbe_status rbe_set_tuning(rbe_handle h, const rbe_tuning* t) {
+    if (!h || !t) return fail(h, RBE_ERR_ARG, "null argument");
+    const int c = t->rho_chunk, f = t->force_split, r = t->real_split;
+    if (c != 0 && (c < 32 || c > 8192 || (c & (c - 1))))
         return fail(h, RBE_ERR_ARG, "rho_chunk must be 0 or a power of two in [32, 8192]");
-    if (force_split != 0 && force_split != 1 && force_split != 2 && force_split != 4 &&
-        force_split != 8)
+    if (f != 0 && f != 1 && f != 2 && f != 4 && f != 8)
         return fail(h, RBE_ERR_ARG, "force_split must be 0, 1, 2, 4 or 8");
-    h->rho_chunk = rho_chunk;
-    h->force_split = force_split;
+    if (r != 0 && (r < 1 || r > 32 || (r & (r - 1))))
+        return fail(h, RBE_ERR_ARG, "real_split must be 0 or a power of two in [1, 32]");
+    if (t->reserved != 0) return fail(h, RBE_ERR_ARG, "reserved must be 0");
+    h->rho_chunk = c;
+    h->force_split = f;
+    h->real_split = r;
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
     return RBE_OK;
 }
 
-rbe_status rbe_autotune(rbe_handle h, int32_t n, const float* pos_q, int32_t* rho_chunk,
-                        int32_t* force_split) {
+rbe_status rbe_get_tuning(rbe_handle h, rbe_tuning* t) {
+    if (!h || !t) return fail(h, RBE_ERR_ARG, "null argument");
+    const long long ntot = h->batch ? h->ntot : std::max(h->cur_n, 0);
+    t->rho_chunk = h->cur_chunk > 0 ? h->cur_chunk
+                                    : (h->rho_chunk > 0 ? h->rho_chunk : auto_chunk(h, ntot));
+    t->force_split = h->cur_split > 0 ? h->cur_split
+                                      : (h->force_split > 0 ? h->force_split : auto_split(ntot));
+    t->real_split = h->cur_rsplit > 0 ? h->cur_rsplit
+                                      : (h->real_split > 0 ? h->real_split : auto_real_split(ntot));
+    t->reserved = 0;
+    return RBE_OK;
+}
+
+
+rbe_status rbe_autotune(rbe_handle h, int32_t n, const float* pos_q, rbe_tuning* out) {
     if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
     rbe_status s = check_n(h, n);
     if (s != RBE_OK) return s;
@@ -881,61 +957,80 @@ rbe_status rbe_autotune(rbe_handle h, int32_t n, const float* pos_q, int32_t* rh
     RBE_CUDA(h, cudaEventCreate(&e0));
     RBE_CUDA(h, cudaEventCreate(&e1));
     const int ltiles = (h->pmax + kLTile - 1) / kLTile;
-    const int chunks[] = {32, 64, 128, 256, 512, 1024, 2048, 4096};
-    const int splits[] = {1, 2, 4, 8};
-    float best = 1e30f;
-    int best_chunk = 0, best_split = 0;
     EvalArgs a{};
     a.prec = RBE_MIXED;
     a.parts = RBE_PART_ALL;
     a.pos = (const float4*)pos_q;
     a.F = h->d_stage_F;
+    const bool prof = h->prof_on;
+    h->prof_on = false;
     // structure-factor chunk
-    for (int c : chunks) {
+    float best = 1e30f;
+    int best_chunk = 32;
+    for (int c = 32; c <= 4096; c <<= 1) {
         h->rho_chunk = c;
-        if ((s = prepare(h, n)) != RBE_OK) return s;
-        enqueue_eval(h, h->stream, a);   // builds the sorted order and k data
-        float tot = 0.f;
-        for (int rep = 0; rep < 3; ++rep) {
-            cudaEventRecord(e0, h->stream);
-            launch_rho_mixed(h->stream, h->d_sys, h->d_chunks, h->nchunks, ltiles, h->d_table,
-                             h->d_cur_step, h->d_spos, h->d_part, h->d_ksamp, h->d_err);
-            cudaEventRecord(e1, h->stream);
-            RBE_CUDA(h, cudaEventSynchronize(e1));
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) tot += ms;
-        }
-        if (tot < best) { best = tot; best_chunk = c; }
+        if ((s = prepare(h, n)) != RBE_OK) break;
+        enqueue_eval(h, h->stream, a);
+        const float t = time_kernel(h, e0, e1, [&] {
+            launch_rho_mixed(h->stream, h->d_sys, h->d_chunks, h->nchunks, ltiles, h->tab_smem,
+                             h->d_table, h->d_cur_step, h->d_spos, h->d_part, h->d_ksamp,
+                             h->d_err);
+        });
+        if (t < best) { best = t; best_chunk = c; }
     }
     h->rho_chunk = best_chunk;
+    // Fourier-force split
     best = 1e30f;
-    for (int sp : splits) {
+    int best_split = 1;
+    for (int sp = 1; sp <= 8 && s == RBE_OK; sp <<= 1) {
         h->force_split = sp;
-        if ((s = prepare(h, n)) != RBE_OK) return s;
+        if ((s = prepare(h, n)) != RBE_OK) break;
         enqueue_eval(h, h->stream, a);
-        float tot = 0.f;
-        for (int rep = 0; rep < 3; ++rep) {
-            cudaEventRecord(e0, h->stream);
+        const float t = time_kernel(h, e0, e1, [&] {
             launch_fourier_force_mixed(h->stream, h->d_sys, h->split == 1 ? h->d_pblk : h->d_fblk,
                                        h->split == 1 ? h->npblk : h->nfblk, h->split, h->d_spos,
                                        h->d_ksamp, h->d_kab, h->d_fs);
-            cudaEventRecord(e1, h->stream);
-            RBE_CUDA(h, cudaEventSynchronize(e1));
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) tot += ms;
-        }
-        if (tot < best) { best = tot; best_split = sp; }
+        });
+        if (t < best) { best = t; best_split = sp; }
     }
     h->force_split = best_split;
+    // real-space split
+    best = 1e30f;
+    int best_rsplit = 1;
+    for (int sp = 1; sp <= 32 && s == RBE_OK; sp <<= 1) {
+        h->real_split = sp;
+        if ((s = prepare(h, n)) != RBE_OK) break;
+        enqueue_eval(h, h->stream, a);
+        RealArgs r{};
+        r.sys = h->d_sys;
+        r.rblk = h->d_rblk;
+        r.nrblk = h->nrblk;
+        r.split = h->rsplit;
+        r.parts = RBE_PART_ALL;
+        r.cell_start = h->d_cell_start;
+        r.perm = h->d_perm;
+        r.cur_step = h->d_cur_step;
+        r.qsum = h->d_qsum;
+        r.spos = h->d_spos;
+        r.fs = h->d_fs;
+        r.F_out = h->d_stage_F;
+        const float t = time_kernel(h, e0, e1, [&] { launch_real_mixed(h->stream, r); });
+        if (t < best) { best = t; best_rsplit = sp; }
+    }
+    h->real_split = best_rsplit;
+    h->prof_on = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (s != RBE_OK) return s;
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
     if ((s = prepare(h, n)) != RBE_OK) return s;
-    if (rho_chunk) *rho_chunk = best_chunk;
-    if (force_split) *force_split = best_split;
+    if (out) {
+        out->rho_chunk = best_chunk;
+        out->force_split = best_split;
+        out->real_split = best_rsplit;
+        out->reserved = 0;
+    }
     return finish(h, "rbe_autotune");
 }
 

@@ -197,44 +197,33 @@ k_scan(int* __restrict__ cell_cnt, int* __restrict__ cell_start, int ncell,
     if (threadIdx.x == 0) cell_start[ncell] = carry_s;
 }
 
+// Scatter of the caller's indices to their atomic slots (arbitrary order
+// inside each cell).
 __global__ void k_scatter(int n, const int* __restrict__ cid, const int* __restrict__ rank,
-                          const int* __restrict__ cell_start, const uint4* __restrict__ fx,
-                          uint4* __restrict__ spos, const double4* __restrict__ fx64,
-                          double4* __restrict__ spos64, int* __restrict__ perm) {
+                          const int* __restrict__ cell_start, int* __restrict__ perm_tmp) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int dst = cell_start[cid[i]] + rank[i];
-    if (fx) spos[dst] = fx[i];
-    if (fx64) spos64[dst] = fx64[i];
-    perm[dst] = i;
+    perm_tmp[cell_start[cid[i]] + rank[i]] = i;
 }
 
-// Order each cell's members by original index (insertion sort; cells hold a
-// handful of particles at the densities of interest).
-__global__ void k_cell_fixup(int ncell, const int* __restrict__ cell_start,
-                             uint4* __restrict__ spos, double4* __restrict__ spos64,
-                             int* __restrict__ perm) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    const int s = cell_start[c], e = cell_start[c + 1];
-    for (int k = s + 1; k < e; ++k) {
-        const int key = perm[k];
-        int j = k - 1;
-        if (perm[j] <= key) continue;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        double4 v64 = make_double4(0, 0, 0, 0);
-        if (spos) v = spos[k];
-        if (spos64) v64 = spos64[k];
-        while (j >= s && perm[j] > key) {
-            perm[j + 1] = perm[j];
-            if (spos) spos[j + 1] = spos[j];
-            if (spos64) spos64[j + 1] = spos64[j];
-            --j;
-        }
-        perm[j + 1] = key;
-        if (spos) spos[j + 1] = v;
-        if (spos64) spos64[j + 1] = v64;
-    }
+// Canonical order inside each cell: the particle at atomic slot s goes to
+// cell_start + (number of members of its cell with a smaller caller index).
+// One thread per particle; cells hold a handful of particles.
+__global__ void k_order(int n, const int* __restrict__ cid, const int* __restrict__ cell_start,
+                        const int* __restrict__ perm_tmp, const uint4* __restrict__ fx,
+                        uint4* __restrict__ spos, const double4* __restrict__ fx64,
+                        double4* __restrict__ spos64, int* __restrict__ perm) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int i = perm_tmp[s];
+    const int c = cid[i];
+    const int b = cell_start[c], e = cell_start[c + 1];
+    int r = 0;
+    for (int k = b; k < e; ++k) r += (__ldg(perm_tmp + k) < i) ? 1 : 0;
+    const int dst = b + r;
+    perm[dst] = i;
+    if (fx) spos[dst] = fx[i];
+    if (fx64) spos64[dst] = fx64[i];
 }
 
 // ------------------------------------------------------------- launchers
@@ -260,17 +249,17 @@ void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell,
 }
 
 void launch_scatter(cudaStream_t st, int n, const int* cid, const int* rank,
-                    const int* cell_start, const uint4* fx, uint4* spos, const double4* fx64,
-                    double4* spos64, int* perm) {
+                    const int* cell_start, int* perm_tmp) {
     if (n <= 0) return;
-    k_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, cid, rank, cell_start, fx, spos, fx64, spos64,
-                                               perm);
+    k_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, cid, rank, cell_start, perm_tmp);
 }
 
-void launch_cell_fixup(cudaStream_t st, int ncell, const int* cell_start, uint4* spos,
-                       double4* spos64, int* perm) {
-    if (ncell <= 0) return;
-    k_cell_fixup<<<(ncell + 127) / 128, 128, 0, st>>>(ncell, cell_start, spos, spos64, perm);
+void launch_order(cudaStream_t st, int n, const int* cid, const int* cell_start,
+                  const int* perm_tmp, const uint4* fx, uint4* spos, const double4* fx64,
+                  double4* spos64, int* perm) {
+    if (n <= 0) return;
+    k_order<<<(n + 255) / 256, 256, 0, st>>>(n, cid, cell_start, perm_tmp, fx, spos, fx64, spos64,
+                                             perm);
 }
 
 }  // namespace rbe

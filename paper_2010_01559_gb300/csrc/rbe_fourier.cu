@@ -54,6 +54,37 @@ __device__ __forceinline__ int4 sample_one(const SysDev& S, const uint64_t* __re
     return make_int4(1, 0, 0, kMaxAttempts + 1);   // keeps later arithmetic finite
 }
 
+// As sample_one, with the table's first 2M entries staged in shared memory as
+// 32-bit words (entry 2M = 2^32 is implicit).
+__device__ __forceinline__ int4 sample_one_smem(const SysDev& S, const uint32_t* __restrict__ T,
+                                                int l, uint64_t step, int* err) {
+    const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
+    const int last = 2 * S.M;
+    auto lookup = [&](uint32_t w) {
+        int lo = 0, hi = last;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (w < T[mid]) hi = mid; else lo = mid + 1;
+        }
+        return lo - S.M;
+    };
+    for (int a = 0; a < kMaxAttempts; ++a) {
+        const uint4 w = philox4x32_10(
+            make_uint4((uint32_t)l, (uint32_t)a, (uint32_t)step, (S.stream << 8) | 0x01u), key);
+        const int mx = lookup(w.x), my = lookup(w.y), mz = lookup(w.z);
+        if (mx != 0 || my != 0 || mz != 0) return make_int4(mx, my, mz, a + 1);
+    }
+    atomicOr(err, kErrSampler);
+    return make_int4(1, 0, 0, kMaxAttempts + 1);
+}
+
+// Stage the first 2M table entries of system S into shared memory.
+__device__ __forceinline__ void stage_table(const SysDev& S, const uint64_t* __restrict__ table,
+                                            uint32_t* s_tab) {
+    const uint64_t* T = table + S.off_t;
+    for (int j = threadIdx.x; j < 2 * S.M; j += blockDim.x) s_tab[j] = (uint32_t)__ldg(T + j);
+}
+
 __global__ void k_sample(const SysDev* __restrict__ sysv, int nsys, int ktot,
                          const int* __restrict__ kstart, const uint64_t* __restrict__ table,
                          const uint64_t* __restrict__ cur_step, int4* __restrict__ ksamp,
@@ -67,19 +98,25 @@ __global__ void k_sample(const SysDev* __restrict__ sysv, int nsys, int ktot,
 
 // ----------------------------------------------------------------- rho (mixed)
 __global__ void __launch_bounds__(kLTile)
-k_rho_mixed(const SysDev* __restrict__ sysv, const Tile* __restrict__ chunks,
+k_rho_mixed(const SysDev* __restrict__ sysv, const Tile* __restrict__ chunks, int tab_smem,
             const uint64_t* __restrict__ table, const uint64_t* __restrict__ cur_step,
             const uint4* __restrict__ spos, float2* __restrict__ part, int4* __restrict__ ksamp,
             int* __restrict__ err) {
     __shared__ uint4 sp[kStage];
+    extern __shared__ uint32_t s_tab[];
     const Tile ch = chunks[blockIdx.x];
     const SysDev& S = sysv[ch.sys];
     const int l = blockIdx.y * kLTile + threadIdx.x;
     if (blockIdx.y * kLTile >= S.P) return;          // whole block beyond this system's P
     const bool active = l < S.P;
+    if (tab_smem) {
+        stage_table(S, table, s_tab);
+        __syncthreads();
+    }
     int4 m = make_int4(0, 0, 0, 0);
     if (active) {
-        m = sample_one(S, table + S.off_t, l, *cur_step, err);
+        m = tab_smem ? sample_one_smem(S, s_tab, l, *cur_step, err)
+                     : sample_one(S, table + S.off_t, l, *cur_step, err);
         if (ch.aux == S.off_part) ksamp[S.off_k + l] = m;
     }
     const uint32_t mx = (uint32_t)m.x, my = (uint32_t)m.y, mz = (uint32_t)m.z;
@@ -108,19 +145,25 @@ k_rho_mixed(const SysDev* __restrict__ sysv, const Tile* __restrict__ chunks,
 
 // ----------------------------------------------------------------- rho (FP64)
 __global__ void __launch_bounds__(kLTile)
-k_rho_f64(const SysDev* __restrict__ sysv, const Tile* __restrict__ chunks,
+k_rho_f64(const SysDev* __restrict__ sysv, const Tile* __restrict__ chunks, int tab_smem,
           const uint64_t* __restrict__ table, const uint64_t* __restrict__ cur_step,
           const double4* __restrict__ spos64, double2* __restrict__ part64,
           int4* __restrict__ ksamp, int* __restrict__ err) {
     __shared__ double4 sp[kStage / 2];
+    extern __shared__ uint32_t s_tab[];
     const Tile ch = chunks[blockIdx.x];
     const SysDev& S = sysv[ch.sys];
     const int l = blockIdx.y * kLTile + threadIdx.x;
     if (blockIdx.y * kLTile >= S.P) return;
     const bool active = l < S.P;
+    if (tab_smem) {
+        stage_table(S, table, s_tab);
+        __syncthreads();
+    }
     int4 m = make_int4(0, 0, 0, 0);
     if (active) {
-        m = sample_one(S, table + S.off_t, l, *cur_step, err);
+        m = tab_smem ? sample_one_smem(S, s_tab, l, *cur_step, err)
+                     : sample_one(S, table + S.off_t, l, *cur_step, err);
         if (ch.aux == S.off_part) ksamp[S.off_k + l] = m;
     }
     const double tp = 2.0 * M_PI * S.invL;
@@ -330,20 +373,24 @@ void launch_sample(cudaStream_t st, const SysDev* sys, int nsys, int ktot, const
                                                  err);
 }
 
+// tab_smem: number of 32-bit table entries to stage per block (max 2M over the
+// systems), 0 to search the table in global memory.
 void launch_rho_mixed(cudaStream_t st, const SysDev* sys, const Tile* chunks, int nchunks,
-                      int ltiles, const uint64_t* table, const uint64_t* cur_step,
+                      int ltiles, int tab_smem, const uint64_t* table, const uint64_t* cur_step,
                       const uint4* spos, float2* part, int4* ksamp, int* err) {
     if (nchunks <= 0 || ltiles <= 0) return;
     dim3 grid(nchunks, ltiles);
-    k_rho_mixed<<<grid, kLTile, 0, st>>>(sys, chunks, table, cur_step, spos, part, ksamp, err);
+    k_rho_mixed<<<grid, kLTile, sizeof(uint32_t) * tab_smem, st>>>(
+        sys, chunks, tab_smem > 0 ? 1 : 0, table, cur_step, spos, part, ksamp, err);
 }
 
 void launch_rho_f64(cudaStream_t st, const SysDev* sys, const Tile* chunks, int nchunks,
-                    int ltiles, const uint64_t* table, const uint64_t* cur_step,
+                    int ltiles, int tab_smem, const uint64_t* table, const uint64_t* cur_step,
                     const double4* spos64, double2* part64, int4* ksamp, int* err) {
     if (nchunks <= 0 || ltiles <= 0) return;
     dim3 grid(nchunks, ltiles);
-    k_rho_f64<<<grid, kLTile, 0, st>>>(sys, chunks, table, cur_step, spos64, part64, ksamp, err);
+    k_rho_f64<<<grid, kLTile, sizeof(uint32_t) * tab_smem, st>>>(
+        sys, chunks, tab_smem > 0 ? 1 : 0, table, cur_step, spos64, part64, ksamp, err);
 }
 
 void launch_finalize(cudaStream_t st, const SysDev* sys, int nsys, int ktot, const int* kstart,
@@ -352,7 +399,7 @@ void launch_finalize(cudaStream_t st, const SysDev* sys, int nsys, int ktot, con
                      const double2* blk_q, double2* qsum) {
     const int warps = ktot + nsys;
     if (warps <= 0) return;
-    const int threads = 256;
+    const int threads = 64;          // few warps per block: spread the FP64 sums over all SMs
     const int blocks = (warps * 32 + threads - 1) / threads;
     k_finalize<<<blocks, threads, 0, st>>>(sys, nsys, ktot, kstart, part, part64, ksamp, rho,
                                            kab, kab64, eterm, blk_q, qsum);

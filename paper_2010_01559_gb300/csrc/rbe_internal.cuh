@@ -8,8 +8,10 @@
 // HBM layout (per handle, sized at create for the total particle count N):
 //   fx     uint4 [N]   unsorted 32-bit fixed-point fractional coordinates
 //                      (x/L, y/L, z/L mod 1, scaled by 2^32) and the charge bits
-//   cid    int   [N]   global cell index;   rank int [N]: slot within the cell
-//   spos   uint4 [N]   fx sorted by cell (the order all later kernels use)
+//   cid    int   [N]   global cell index;   rank int [N]: atomic slot within the cell
+//   perm_tmp int [N]   caller's index at its atomic slot (arbitrary in-cell order)
+//   spos   uint4 [N]   fx sorted by cell, in-cell by caller's index (the order all
+//                      later kernels use)
 //   perm   int   [N]   sorted index -> caller's index
 //   fs     float4[N]   Fourier force (xyz) and Fourier dE/dq (w), sorted order
 //   cell_cnt / cell_start  int [C + 1] over all systems' cells
@@ -50,7 +52,8 @@ struct SysDev {
     int off_t;              // first table entry
     int off_part;           // first partial of the structure-factor chunks
     int nchunk;             // structure-factor chunks of this system
-    int off_b, nb;          // first per-particle block and block count
+    int off_b, nb;          // first per-particle block and block count (prep)
+    int off_rb, nrb;        // first real-space block and block count
 };
 
 // A tile of particles of one system: (system, first particle, count, aux).
@@ -96,19 +99,19 @@ void launch_prep_f64(cudaStream_t st, const SysDev* sys, const Tile* pblk, int n
 void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell,
                  uint64_t* step_dev, uint64_t step_arg, uint64_t* cur_step);
 void launch_scatter(cudaStream_t st, int n, const int* cid, const int* rank,
-                    const int* cell_start, const uint4* fx, uint4* spos, const double4* fx64,
-                    double4* spos64, int* perm);
-void launch_cell_fixup(cudaStream_t st, int ncell, const int* cell_start, uint4* spos,
-                       double4* spos64, int* perm);
+                    const int* cell_start, int* perm_tmp);
+void launch_order(cudaStream_t st, int n, const int* cid, const int* cell_start,
+                  const int* perm_tmp, const uint4* fx, uint4* spos, const double4* fx64,
+                  double4* spos64, int* perm);
 
 // Fourier part (rbe_fourier.cu)
 void launch_sample(cudaStream_t st, const SysDev* sys, int nsys, int ktot, const int* kstart,
                    const uint64_t* table, const uint64_t* cur_step, int4* ksamp, int* err);
 void launch_rho_mixed(cudaStream_t st, const SysDev* sys, const Tile* chunks, int nchunks,
-                      int ltiles, const uint64_t* table, const uint64_t* cur_step,
+                      int ltiles, int tab_smem, const uint64_t* table, const uint64_t* cur_step,
                       const uint4* spos, float2* part, int4* ksamp, int* err);
 void launch_rho_f64(cudaStream_t st, const SysDev* sys, const Tile* chunks, int nchunks,
-                    int ltiles, const uint64_t* table, const uint64_t* cur_step,
+                    int ltiles, int tab_smem, const uint64_t* table, const uint64_t* cur_step,
                     const double4* spos64, double2* part64, int4* ksamp, int* err);
 void launch_finalize(cudaStream_t st, const SysDev* sys, int nsys, int ktot, const int* kstart,
                      const float2* part, const double2* part64, const int4* ksamp,
@@ -124,8 +127,9 @@ void launch_fourier_force_f64(cudaStream_t st, const SysDev* sys, const Tile* pb
 // real space, LJ, Langevin, energies (rbe_real.cu)
 struct RealArgs {
     const SysDev* sys;
-    const Tile* pblk;
-    int npblk;
+    const Tile* rblk;        // real-space tiles of kBlockP / split particles
+    int nrblk;
+    int split;               // threads per particle
     int parts;               // RBE_PART_* mask
     const int* cell_start;
     const int* perm;

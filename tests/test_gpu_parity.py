@@ -234,9 +234,14 @@ def test_tuning_does_not_change_results_beyond_rounding(rbe, c2):
     h = _handle(rbe, c2)
     x = _dev(c2)
     ref = oracle_eval(c2, 6)
-    for chunk, split in ((32, 1), (256, 2), (4096, 8), (0, 0)):
-        h.set_tuning(chunk, split)
-        F, _, _ = h.forces(x, 6)
-        assert rel_rms(F[:, :3].cpu().numpy(), ref["F"]) <= TOL_MIXED, (chunk, split)
-    c, s = h.autotune(x)
-    assert c >= 32 and s in (1, 2, 4, 8)
+    for chunk, split, rsplit in ((32, 1, 1), (256, 2, 4), (4096, 8, 32), (64, 4, 16),
+                                 (0, 0, 0)):
+        h.set_tuning(chunk, split, rsplit)
+        F, E, phi = h.forces(x, 6, phi=True)
+        assert rel_rms(F[:, :3].cpu().numpy(), ref["F"]) <= TOL_MIXED, (chunk, split, rsplit)
+        assert energy_rel(E.cpu().numpy()[0], ref["E"]) <= TOL_E_MIXED
+        if chunk:
+            assert h.get_tuning() == (chunk, split, rsplit)
+    c, s, r = h.autotune(x)
+    assert c >= 32 and s in (1, 2, 4, 8) and r in (1, 2, 4, 8, 16, 32)
+    assert h.get_tuning() == (c, s, r)
