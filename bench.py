@@ -17,6 +17,9 @@ Printed as one JSON line (rank 0):
   cpu_baseline  the FP64 CPU oracle on a bounded sample, host cores
   fp64_path   the plain FP64 GPU path on the same steps; speedup_vs_fp64
   accuracy    rel-RMS of the mixed forces against the FP64 GPU forces
+  large_system  the same measurements for the 1:1 electrolyte of 2^20 ions
+              (density 0.064, alpha = 0.3, r_c = 5, P = 500), where the Fourier
+              kernels dominate
 ``--impl reference`` times the FP64 CPU oracle instead (the reference arm).
 """
 from __future__ import annotations
@@ -53,6 +56,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="budget of the CPU-oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--large", dest="large", action="store_true", default=True,
+                    help="also measure the 2^20-particle system (default)")
+    ap.add_argument("--no-large", dest="large", action="store_false")
     return ap.parse_args()
 
 
@@ -211,7 +217,53 @@ def traffic_for(kernel, workload_name):
     return e.get("dram_bytes_per_launch")
 
 
-def roofline(prof, wl, peaks, clocks):
+FP32_LANES_PER_SM = 128
+# FP32-pipe operations the real-space pass needs: the distance test of a
+# candidate (3 subtractions, 1 multiply, 2 fused multiply-adds) and the terms
+# of a pair inside the cutoff (erfc by the 5-term rational form, Gaussian,
+# G(r)/r, force, potential and energy accumulation: 25 operations, plus three
+# special-function operations counted separately).
+REAL_OPS_PER_CANDIDATE = 6
+REAL_OPS_PER_PAIR = 25
+
+
+def pair_counts(wl):
+    """(candidates, pairs within r_c) of the real-space pass, counted on the host
+    from the cell occupancy and a k-d tree (ordered pairs, as the kernel visits them)."""
+    import numpy as np
+    from scipy.spatial import cKDTree
+    p = wl.params
+    L = p.box
+    ncd = min(256, int(L // p.r_c))
+    pos = wl.pos.astype(np.float64)
+    cell = np.minimum((pos / L * ncd).astype(int), ncd - 1)
+    cid = (cell[:, 2] * ncd + cell[:, 1]) * ncd + cell[:, 0]
+    occ = np.bincount(cid, minlength=ncd ** 3).reshape(ncd, ncd, ncd)
+    nb = sum(np.roll(occ, (dz, dy, dx), axis=(0, 1, 2))
+             for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1))
+    candidates = int((occ * nb).sum() - wl.n)
+    tree = cKDTree(pos, boxsize=L)
+    pairs = int(tree.count_neighbors(tree, p.r_c)) - wl.n        # ordered pairs, self excluded
+    return candidates, pairs
+
+
+def fourier_rooflines(prof, wl):
+    """SFU roofline of both Fourier kernels (one sine and one cosine per pair)."""
+    out = {}
+    peak = SM_COUNT * SFU_PER_SM_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    for name in ("rho", "fourier_force"):
+        ms, cnt = prof.get(name, (0.0, 0))
+        if not cnt:
+            continue
+        avg_s = ms / cnt / 1e3
+        achieved = 2.0 * wl.n * wl.params.P / avg_s / 1e12
+        out[name] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tsfu/s",
+                     "frac": achieved / peak, "avg_launch_us": avg_s * 1e6,
+                     "traffic": traffic_for(name, wl.name)}
+    return out
+
+
+def roofline(prof, wl, peaks, clocks, counts=None):
     """Dominant kernel of the profiled pass against its bound."""
     name, (ms, cnt) = max(prof.items(), key=lambda kv: kv[1][0])
     avg_s = ms / max(cnt, 1) / 1e3
@@ -225,11 +277,20 @@ def roofline(prof, wl, peaks, clocks):
                "unit": "Tsfu/s", "frac": achieved / peak,
                "peak_basis": "152 SMs x 16 sin/cos per clock x 2070 MHz (max SM clock)",
                "algorithmic": f"2 SFU ops per (particle, k) pair x {N} x {P}"}
+    elif name == "real" and counts is not None:
+        cand, pairs = counts
+        work = REAL_OPS_PER_CANDIDATE * cand + REAL_OPS_PER_PAIR * pairs
+        peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+        achieved = work / avg_s / 1e12
+        out = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
+               "unit": "Tops/s", "frac": achieved / peak,
+               "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz (max SM clock)",
+               "algorithmic": f"{REAL_OPS_PER_CANDIDATE} ops x {cand} candidates + "
+                              f"{REAL_OPS_PER_PAIR} ops x {pairs} pairs within r_c"}
     else:
         # bytes the kernel must move: records read/written per particle
-        per_particle = {"prep": 16 + 16 + 4 + 4, "scatter": 16 + 4 + 4 + 16 + 4,
-                        "cell_order": 0, "real": 16 + 16 + 4 + 16 + 32,
-                        "scan": 0, "finalize": 0, "energy": 0}.get(name, 0)
+        per_particle = {"prep": 16 + 16 + 4 + 4, "scatter": 4 + 4 + 4 + 4,
+                        "cell_order": 4 + 16 + 4 + 16 + 4, "scan": 0, "energy": 0}.get(name, 0)
         bytes_ = per_particle * N
         peak = peaks.get("hbm_gbs", 6800.0)
         achieved = bytes_ / avg_s / 1e9
@@ -287,6 +348,7 @@ def run_ours(args):
 
     # ---------------------------------------------------------------- mixed path
     with torch.cuda.stream(stream):
+        tuning = h.autotune(pos0)            # the library's own launch-shape tuner
         pos = pos0.clone()
         vel = vel0.clone()
         step_dev = torch.zeros(1, dtype=torch.int64, device=dev)
@@ -352,9 +414,14 @@ def run_ours(args):
     e2e_value = n_all * K / e2e_t
     bytes_io = 2 * 16 * wl.n
 
+    large = None
+    if args.large and rank == 0:
+        from paper_2010_01559_gb300 import workloads as wls
+        large = measure_system(rbe, torch, wls.config_large(), dev, stream, 50, 3, flush, peaks)
+
     result = None
     if rank == 0:
-        rl = roofline(prof, wl, peaks, clk)
+        rl = roofline(prof, wl, peaks, clk, counts=pair_counts(wl))
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -364,10 +431,13 @@ def run_ours(args):
                        "box": round(wl.params.box, 4), "path": "mixed (FP32 phases/forces, "
                        "FP64 rho(k) and energy sums)", "graph": True,
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
+                       "tuning": {"rho_chunk": tuning[0], "force_split": tuning[1],
+                                  "real_split": tuning[2]},
                        "parallelism": f"replicas x{world}"},
             "force_evals_per_s": value / wl.n,
             "clocks": clk,
             "roofline": rl,
+            "fourier_rooflines": fourier_rooflines(prof, wl),
             "kernels_avg_us": kernels_us,
             "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_io,
@@ -378,6 +448,8 @@ def run_ours(args):
             "speedup_vs_fp64": value / value64,
             "accuracy": {"force_rel_rms_mixed_vs_fp64_gpu": acc, "target": 1e-5},
         }
+        if large is not None:
+            result["large_system"] = large
         if not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
         print(json.dumps(result), flush=True)
@@ -386,6 +458,69 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return result
+
+
+def measure_system(rbe, torch, wl, dev, stream, K, W, flush, peaks):
+    """Timed MD steps (mixed, graph replay, L2 flushed between steps), a
+    profiled pass, the FP64 path and the mixed-vs-FP64 force agreement."""
+    h = rbe.RBE(rbe.params_from(wl.params, n_max=wl.n))
+    pos0 = torch.from_numpy(wl.pos_q()).to(dev)
+    vel0 = torch.zeros((wl.n, 4), dtype=torch.float32, device=dev)
+    vel0[:, :3] = torch.from_numpy(wl.vel).to(dev)
+
+    def timed(pos, vel, step_dev, nsteps, profile=False):
+        evs = []
+        h.profile(profile)
+        with torch.cuda.stream(stream):
+            for k in range(nsteps):
+                flush.fill_(k & 0xFF)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h.step(pos, vel, 1, step_dev)
+                e1.record(stream)
+                evs.append((e0, e1))
+        stream.synchronize()
+        h.profile(False)
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    with torch.cuda.stream(stream):
+        tuning = h.autotune(pos0)
+        pos, vel = pos0.clone(), vel0.clone()
+        step_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+        h.set_graph(True)
+        for _ in range(W):
+            h.step(pos, vel, 1, step_dev)
+    stream.synchronize()
+    ms = timed(pos, vel, step_dev, K)
+    timed(pos, vel, step_dev, max(3, K // 4), profile=True)
+    prof = h.profile_read()
+    with torch.cuda.stream(stream):
+        F32, _, _ = h.forces(pos0, 0, energy=False)
+        F64, _, _ = h.forces_f64(pos0.double().contiguous(), 0, energy=False)
+    stream.synchronize()
+    acc = ((F32[:, :3].double() - F64[:, :3]).norm() / F64[:, :3].norm()).item()
+    K64 = 3
+    with torch.cuda.stream(stream):
+        p64, v64 = pos0.double().contiguous(), vel0.double().contiguous()
+        s64 = torch.zeros(1, dtype=torch.int64, device=dev)
+        h.step(p64, v64, 1, s64)
+    stream.synchronize()
+    ms64 = timed(p64, v64, s64, K64)
+    value = wl.n * K / (ms / 1e3)
+    value64 = wl.n * K64 / (ms64 / 1e3)
+    out = {"workload": wl.name, "N": wl.n, "P": wl.params.P, "alpha": wl.params.alpha,
+           "r_c": wl.params.r_c, "value": value, "unit": UNIT, "steps": K,
+           "ms_per_step": ms / K, "force_evals_per_s": K / (ms / 1e3),
+           "tuning": {"rho_chunk": tuning[0], "force_split": tuning[1], "real_split": tuning[2]},
+           "kernels_avg_us": {k: (t / c * 1e3 if c else 0.0) for k, (t, c) in prof.items()},
+           "roofline": roofline(prof, wl, peaks, None, counts=pair_counts(wl)),
+           "fourier_rooflines": fourier_rooflines(prof, wl),
+           "fp64_path": {"value": value64, "unit": UNIT, "steps": K64, "ms_per_step": ms64 / K64},
+           "speedup_vs_fp64": value / value64,
+           "accuracy": {"force_rel_rms_mixed_vs_fp64_gpu": acc, "target": 1e-5}}
+    h.close()
+    return out
 
 
 # --------------------------------------------------------------------- reference arm

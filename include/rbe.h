@@ -199,7 +199,7 @@ typedef struct {
     int32_t rho_chunk;     /* particles per structure-factor chunk: power of two in [32, 8192] */
     int32_t force_split;   /* threads per particle in the Fourier-force pass: 1, 2, 4 or 8     */
     int32_t real_split;    /* threads per particle in the real-space pass: 1..32, power of two  */
-    int32_t reserved;      /* must be 0                                                         */
+    int32_t real_seg;      /* cells along x per real-space block: 1 .. cells per edge           */
 } rbe_tuning;
 
 /* Set the launch shapes (results change only by floating-point summation
@@ -221,8 +221,10 @@ enum {
     RBE_K_SCAN = 1,          /* exclusive scan of cell counts, step latch           */
     RBE_K_SCATTER = 2,       /* counting-sort scatter                               */
     RBE_K_CELL_ORDER = 3,    /* order inside each cell by original index            */
-    RBE_K_RHO = 4,           /* k-sampling + per-chunk structure factors            */
-    RBE_K_FINALIZE = 5,      /* FP64 rho(k), energy terms, force coefficients       */
+    RBE_K_RHO = 4,           /* k-sampling, per-chunk structure factors, and (last
+                                block of each k-tile) FP64 rho(k), energy terms,
+                                force coefficients                                */
+    RBE_K_FINALIZE = 5,      /* reserved (finalisation is fused into RBE_K_RHO)     */
     RBE_K_FOURIER_FORCE = 6, /* RBE Fourier force and dE/dq (Eq. rbmapprox)         */
     RBE_K_REAL = 7,          /* real space + LJ + assembly (+ Langevin)             */
     RBE_K_ENERGY = 8,        /* FP64 energy reduction                               */

@@ -103,15 +103,15 @@ class _HandleBase:
     def sync(self):
         capi.check(self.lib.rbe_sync(self._h), self._h)
 
-    def set_tuning(self, rho_chunk=0, force_split=0, real_split=0):
-        t = capi.rbe_tuning(rho_chunk, force_split, real_split, 0)
+    def set_tuning(self, rho_chunk=0, force_split=0, real_split=0, real_seg=0):
+        t = capi.rbe_tuning(rho_chunk, force_split, real_split, real_seg)
         capi.check(self.lib.rbe_set_tuning(self._h, ctypes.byref(t)), self._h)
 
     def get_tuning(self):
-        """(rho_chunk, force_split, real_split) in effect."""
+        """(rho_chunk, force_split, real_split, real_seg) in effect."""
         t = capi.rbe_tuning()
         capi.check(self.lib.rbe_get_tuning(self._h, ctypes.byref(t)), self._h)
-        return t.rho_chunk, t.force_split, t.real_split
+        return t.rho_chunk, t.force_split, t.real_split, t.real_seg
 
     def autotune(self, pos_q):
         """Pick the fastest launch shapes on this input; returns them."""
@@ -119,7 +119,7 @@ class _HandleBase:
         self._stream()
         capi.check(self.lib.rbe_autotune(self._h, pos_q.shape[0], _ptr(pos_q), ctypes.byref(t)),
                    self._h)
-        return t.rho_chunk, t.force_split, t.real_split
+        return t.rho_chunk, t.force_split, t.real_split, t.real_seg
 
     def profile(self, on=True):
         capi.check(self.lib.rbe_profile(self._h, 1 if on else 0), self._h)

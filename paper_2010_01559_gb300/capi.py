@@ -35,7 +35,7 @@ class rbe_params(ctypes.Structure):
 
 class rbe_tuning(ctypes.Structure):
     _fields_ = [("rho_chunk", ctypes.c_int32), ("force_split", ctypes.c_int32),
-                ("real_split", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("real_split", ctypes.c_int32), ("real_seg", ctypes.c_int32)]
 
 
 class rbe_info(ctypes.Structure):

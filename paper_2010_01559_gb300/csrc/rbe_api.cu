@@ -110,10 +110,13 @@ struct rbe_ctx {
     std::vector<SysDev> sysdev;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
-    int rho_chunk = 0, force_split = 0, real_split = 0;   // requested; 0 = automatic
-    int cur_n = -1, cur_chunk = -1, cur_split = -1, cur_rsplit = -1;
+    cudaStream_t stream2 = nullptr;          // Fourier branch of each evaluation
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int rho_chunk = 0, force_split = 0, real_split = 0, real_seg = 0;   // 0 = automatic
+    int cur_n = -1, cur_chunk = -1, cur_split = -1, cur_rsplit = -1, cur_seg = -1;
     int npblk = 0, nfblk = 0, nrblk = 0, nchunks = 0, split = 1, rsplit = 1;
-    int max_pblk = 0, max_fblk = 0, max_rblk = 0, max_chunks = 0;
+    int nseg = 0, seg_max = 1, stage_cap = 0, seg_threads = 64;
+    int max_pblk = 0, max_fblk = 0, max_rblk = 0, max_chunks = 0, max_seg = 0;
     int tab_smem = 0;                        // table entries staged in shared memory
     size_t max_part = 0;
     bool use_graph = false;
@@ -131,8 +134,10 @@ struct rbe_ctx {
     Tile* d_pblk = nullptr;
     Tile* d_fblk = nullptr;
     Tile* d_rblk = nullptr;
+    Tile* d_segs = nullptr;
     Tile* d_chunks = nullptr;
     int* d_kstart = nullptr;
+    int* d_cstart = nullptr;
     uint64_t* d_table = nullptr;
     uint4* d_fx = nullptr;
     uint4* d_spos = nullptr;
@@ -146,16 +151,11 @@ struct rbe_ctx {
     double4* d_fs64 = nullptr;
     int* d_cell_cnt = nullptr;
     int* d_cell_start = nullptr;
-    float2* d_part = nullptr;
-    double2* d_part64 = nullptr;
     int4* d_ksamp = nullptr;
-    float2* d_kab = nullptr;
-    double2* d_kab64 = nullptr;
-    double2* d_rho = nullptr;
-    double* d_eterm = nullptr;
+    unsigned long long* d_rho_fx = nullptr;   // rho(k) accumulators (fixed point)
+    unsigned long long* d_qsum_fx = nullptr;  // sum q per system (fixed point)
     double2* d_blk_e = nullptr;
     double2* d_blk_q = nullptr;
-    double2* d_qsum = nullptr;
     uint64_t* d_cur_step = nullptr;
     uint64_t* d_stage_step = nullptr;
     int* d_err = nullptr;
@@ -253,6 +253,15 @@ void fill_sysdev(const SysHost& s, SysDev& d) {
     d.nb = 0;
     d.off_rb = 0;
     d.nrb = 0;
+    d.off_sg = 0;
+    d.nsg = 0;
+    // rho(k) accumulators: |rho| <= sum |q| <= 4 n is assumed; the largest
+    // power of two (at most 2^52) that keeps 4 n * scale below 2^62.
+    int e = 52;
+    const double bound = 4.0 * std::max(1, s.n);
+    while (e > 20 && bound * std::ldexp(1.0, e) >= std::ldexp(1.0, 62)) --e;
+    d.rho_scale = std::ldexp(1.0, e);
+    d.rho_inv_scale = std::ldexp(1.0, -e);
 }
 
 int auto_chunk(const rbe_ctx* h, long long ntot) {
@@ -271,11 +280,26 @@ int auto_split(long long ntot) {
     return s;
 }
 
-int auto_real_split(long long ntot) {
+// Threads per particle of the real-space pass: the mixed path runs one block
+// of 64 threads per cell, so give each particle of an average cell
+// 64 / (next power of two of the mean occupancy) threads.
+int auto_real_split(long long ntot, long long ncell) {
+    // at least a few candidates per lane; more lanes when there are few particles
     const long long target_threads = 152LL * 2048;
     int s = 1;
-    while (s < 16 && ntot * s * 2 <= target_threads) s <<= 1;
+    while (s < 8 && ntot * s * 2 <= target_threads) s <<= 1;
+    (void)ncell;
     return s;
+}
+
+// Cells along x per real-space block: enough blocks to fill the GPU, and a
+// staged neighbourhood (9 rows of seg + 2 cells) of about 2500 records.
+int auto_real_seg(long long ntot, long long ncell, int ncd) {
+    const double occ = ncell > 0 ? (double)ntot / (double)ncell : 1.0;
+    int seg = (int)std::floor(2500.0 / (9.0 * std::max(occ, 0.5)) - 2.0);
+    const long long min_blocks = 152LL * 4;
+    seg = std::min(seg, (int)std::max(1LL, ncell / min_blocks));
+    return std::max(1, std::min(seg, ncd));
 }
 
 // (Re)build the work tables for the current particle counts and tuning.
@@ -284,10 +308,17 @@ rbe_status prepare(rbe_ctx* h, int n) {
     const long long ntot = h->batch ? h->ntot : n;
     const int chunk = h->rho_chunk > 0 ? h->rho_chunk : auto_chunk(h, ntot);
     const int split = h->force_split > 0 ? h->force_split : auto_split(ntot);
-    const int rsplit = h->real_split > 0 ? h->real_split : auto_real_split(ntot);
+    const int rsplit = h->real_split > 0 ? h->real_split : auto_real_split(ntot, h->ncell);
+    int ncd_max = 3;
+    for (auto& sh : h->sys) ncd_max = std::max(ncd_max, sh.ncd);
+    const int rseg = h->real_seg > 0 ? std::min(h->real_seg, ncd_max)
+                                     : auto_real_seg(ntot, h->ncell, ncd_max);
     if (h->cur_n == n && h->cur_chunk == chunk && h->cur_split == split &&
-        h->cur_rsplit == rsplit)
+        h->cur_rsplit == rsplit && h->cur_seg == rseg)
         return RBE_OK;
+    std::vector<Tile> segs;
+    int seg_max = 1;
+    double stage_need = 0.0;
     std::vector<Tile> pblk, fblk, rblk, chunks;
     const int ftile = kBlockP / split;
     const int rtile = kBlockP / rsplit;
@@ -316,11 +347,26 @@ rbe_status prepare(rbe_ctx* h, int n) {
             if (sh.n == 0) break;
         }
         d.nrb = nrb;
+        d.off_sg = (int)segs.size();
+        {
+            const int ncd = sh.ncd, seg = std::min(rseg, ncd);
+            for (int z = 0; z < ncd; ++z)
+                for (int y = 0; y < ncd; ++y)
+                    for (int x0 = 0; x0 < ncd; x0 += seg) {
+                        const int cnt = std::min(seg, ncd - x0);
+                        segs.push_back(Tile{s, sh.off_c + (z * ncd + y) * ncd + x0, cnt,
+                                            x0 | (y << 10) | (z << 20)});
+                        seg_max = std::max(seg_max, cnt);
+                    }
+            const double occ = (double)sh.n / ((double)ncd * ncd * ncd);
+            const double mean = 9.0 * (seg + 2) * occ;
+            stage_need = std::max(stage_need, mean + 6.0 * std::sqrt(mean) + 64.0);
+        }
+        d.nsg = (int)segs.size() - d.off_sg;
         d.off_part = off_part;
         int nc = 0;
         for (int f = 0; f < sh.n || f == 0; f += chunk) {
-            chunks.push_back(Tile{s, sh.off_p + f, std::max(0, std::min(chunk, sh.n - f)),
-                                  off_part + nc * sh.p.P});
+            chunks.push_back(Tile{s, sh.off_p + f, std::max(0, std::min(chunk, sh.n - f)), nc});
             ++nc;
             if (sh.n == 0) break;
         }
@@ -329,6 +375,7 @@ rbe_status prepare(rbe_ctx* h, int n) {
     }
     if ((int)pblk.size() > h->max_pblk || (int)fblk.size() > h->max_fblk ||
         (int)rblk.size() > h->max_rblk || (int)chunks.size() > h->max_chunks ||
+        (int)segs.size() > h->max_seg ||
         (size_t)off_part > h->max_part)
         return fail(h, RBE_ERR_ARG, "work tables exceed the workspace (n > capacity?)");
     RBE_CUDA(h, cudaMemcpyAsync(h->d_sys, h->sysdev.data(), sizeof(SysDev) * h->nsys,
@@ -339,6 +386,8 @@ rbe_status prepare(rbe_ctx* h, int n) {
                                 cudaMemcpyHostToDevice, h->stream));
     RBE_CUDA(h, cudaMemcpyAsync(h->d_rblk, rblk.data(), sizeof(Tile) * rblk.size(),
                                 cudaMemcpyHostToDevice, h->stream));
+    RBE_CUDA(h, cudaMemcpyAsync(h->d_segs, segs.data(), sizeof(Tile) * segs.size(),
+                                cudaMemcpyHostToDevice, h->stream));
     RBE_CUDA(h, cudaMemcpyAsync(h->d_chunks, chunks.data(), sizeof(Tile) * chunks.size(),
                                 cudaMemcpyHostToDevice, h->stream));
     RBE_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -348,6 +397,19 @@ rbe_status prepare(rbe_ctx* h, int n) {
     h->nchunks = (int)chunks.size();
     h->split = split;
     h->rsplit = rsplit;
+    h->nseg = (int)segs.size();
+    h->seg_max = seg_max;
+    // staged records per segment block: the expected neighbourhood plus six
+    // standard deviations, within a 96 KB budget (larger ones read global memory)
+    h->stage_cap = (int)std::min(6144.0, std::ceil(stage_need));
+    {
+        // about one group of rsplit threads per particle of a segment
+        const double per_seg = (double)std::max<long long>(ntot, 1) * seg_max /
+                               std::max(1, h->ncell);
+        const double want = per_seg * rsplit;
+        h->seg_threads = want > 160 ? 256 : (want > 80 ? 128 : 64);
+    }
+    h->cur_seg = rseg;
     h->cur_n = n;
     h->cur_chunk = chunk;
     h->cur_split = split;
@@ -370,6 +432,7 @@ rbe_status allocate(rbe_ctx* h) {
     h->max_pblk = (int)pb;
     h->max_fblk = (int)fb;
     h->max_rblk = (int)rb;
+    h->max_seg = std::max(1, h->ncell);
     h->max_chunks = (int)ch;
     h->max_part = (size_t)part;
     const size_t N = (size_t)std::max(h->ntot, 1);
@@ -380,8 +443,10 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_ALLOC(h->d_pblk, pb);
     RBE_ALLOC(h->d_fblk, fb);
     RBE_ALLOC(h->d_rblk, rb);
+    RBE_ALLOC(h->d_segs, std::max(1, h->ncell));
     RBE_ALLOC(h->d_chunks, ch);
     RBE_ALLOC(h->d_kstart, h->nsys + 1);
+    RBE_ALLOC(h->d_cstart, h->nsys + 1);
     RBE_ALLOC(h->d_table, h->ttot);
     RBE_ALLOC(h->d_fx, N);
     RBE_ALLOC(h->d_spos, N);
@@ -395,16 +460,11 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_ALLOC(h->d_fs64, N);
     RBE_ALLOC(h->d_cell_cnt, h->ncell + 1);
     RBE_ALLOC(h->d_cell_start, h->ncell + 1);
-    RBE_ALLOC(h->d_part, part);
-    RBE_ALLOC(h->d_part64, part);
     RBE_ALLOC(h->d_ksamp, h->ktot);
-    RBE_ALLOC(h->d_kab, h->ktot);
-    RBE_ALLOC(h->d_kab64, h->ktot);
-    RBE_ALLOC(h->d_rho, h->ktot);
-    RBE_ALLOC(h->d_eterm, h->ktot);
-    RBE_ALLOC(h->d_blk_e, rb);
+    RBE_ALLOC(h->d_rho_fx, 2 * (size_t)h->ktot);
+    RBE_ALLOC(h->d_qsum_fx, h->nsys);
+    RBE_ALLOC(h->d_blk_e, std::max<long long>(rb, h->ncell + 1));
     RBE_ALLOC(h->d_blk_q, pb);
-    RBE_ALLOC(h->d_qsum, h->nsys);
     RBE_ALLOC(h->d_cur_step, 1);
     RBE_ALLOC(h->d_stage_step, 1);
     RBE_ALLOC(h->d_err, 1);
@@ -415,19 +475,27 @@ rbe_status allocate(rbe_ctx* h) {
 #undef RBE_ALLOC
     RBE_CUDA(h, cudaMemset(h->d_cell_cnt, 0, sizeof(int) * (h->ncell + 1)));
     RBE_CUDA(h, cudaMemset(h->d_err, 0, sizeof(int)));
-    RBE_CUDA(h, cudaMemset(h->d_qsum, 0, sizeof(double2) * h->nsys));
+    RBE_CUDA(h, cudaMemset(h->d_qsum_fx, 0, sizeof(unsigned long long) * h->nsys));
+    RBE_CUDA(h, cudaMemset(h->d_rho_fx, 0, sizeof(unsigned long long) * 2 * h->ktot));
     std::vector<uint64_t> tab;
-    std::vector<int> kstart;
+    std::vector<int> kstart, cstart;
     for (auto& s : h->sys) {
         tab.insert(tab.end(), s.table.begin(), s.table.end());
         kstart.push_back(s.off_k);
+        cstart.push_back(s.off_c);
     }
     kstart.push_back(h->ktot);
+    cstart.push_back(h->ncell);
+    RBE_CUDA(h, cudaMemcpy(h->d_cstart, cstart.data(), sizeof(int) * cstart.size(),
+                           cudaMemcpyHostToDevice));
     RBE_CUDA(h, cudaMemcpy(h->d_table, tab.data(), sizeof(uint64_t) * tab.size(),
                            cudaMemcpyHostToDevice));
     RBE_CUDA(h, cudaMemcpy(h->d_kstart, kstart.data(), sizeof(int) * kstart.size(),
                            cudaMemcpyHostToDevice));
     RBE_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    RBE_CUDA(h, cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking));
+    RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     return RBE_OK;
 }
 
@@ -435,15 +503,20 @@ void release(rbe_ctx* h) {
     if (!h) return;
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
-    void* ptrs[] = {h->d_sys, h->d_pblk, h->d_fblk, h->d_rblk, h->d_chunks, h->d_kstart,
+    void* ptrs[] = {h->d_sys, h->d_pblk, h->d_fblk, h->d_rblk, h->d_segs, h->d_chunks,
+                    h->d_kstart,
+                    h->d_cstart,
                     h->d_table, h->d_fx, h->d_spos, h->d_fx64, h->d_spos64, h->d_cid, h->d_rank,
-                    h->d_perm, h->d_perm_tmp, h->d_fs, h->d_fs64, h->d_cell_cnt, h->d_cell_start, h->d_part,
-                    h->d_part64, h->d_ksamp, h->d_kab, h->d_kab64, h->d_rho, h->d_eterm,
-                    h->d_blk_e, h->d_blk_q, h->d_qsum, h->d_cur_step, h->d_stage_step,
+                    h->d_perm, h->d_perm_tmp, h->d_fs, h->d_fs64, h->d_cell_cnt,
+                    h->d_cell_start, h->d_ksamp, h->d_rho_fx, h->d_qsum_fx,
+                    h->d_blk_e, h->d_blk_q, h->d_cur_step, h->d_stage_step,
                     h->d_err, h->d_stage_pos, h->d_stage_vel, h->d_stage_F, h->d_stage_E};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->stream2) cudaStreamDestroy(h->stream2);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     for (int k = 0; k < RBE_K_COUNT; ++k) {
         if (h->ev_beg[k]) cudaEventDestroy(h->ev_beg[k]);
         if (h->ev_end[k]) cudaEventDestroy(h->ev_end[k]);
@@ -528,109 +601,150 @@ struct EvalArgs {
     double4* md_vel64;
 };
 
-// Returns the number of kernels enqueued.  With profiling on (and st the
-// handle's own stream, i.e. not capturing) every kernel is bracketed by events
-// and the per-kernel device times are accumulated after the last one.
+// Kernel work descriptor: tables for a batch, by-value constants and a tile
+// size for a single system.
+Work make_work(const rbe_ctx* h, const Tile* tiles, int tile, int aux_stride) {
+    Work w{};
+    if (h->batch) {
+        w.sysv = h->d_sys;
+        w.tiles = tiles;
+    } else {
+        w.tile = tile;
+        w.aux_stride = aux_stride;
+        w.one = h->sysdev[0];
+    }
+    return w;
+}
+
+RealArgs make_real_args(const rbe_ctx* h, int parts) {
+    RealArgs r{};
+    r.w = make_work(h, h->d_rblk, kBlockP / h->rsplit, 0);
+    r.nrblk = h->nrblk;
+    r.split = h->rsplit;
+    r.ncell = h->ncell;
+    r.nsys = h->nsys;
+    r.cstart = h->d_cstart;
+    r.segs = h->d_segs;
+    r.nseg = h->nseg;
+    r.seg_max = h->seg_max;
+    r.stage_cap = h->stage_cap;
+    r.seg_threads = h->seg_threads;
+    r.parts = parts;
+    r.cell_start = h->d_cell_start;
+    r.perm = h->d_perm;
+    r.cur_step = h->d_cur_step;
+    r.qsum_fx = h->d_qsum_fx;
+    r.spos = h->d_spos;
+    r.fs = h->d_fs;
+    r.spos64 = h->d_spos64;
+    r.fs64 = h->d_fs64;
+    return r;
+}
+
+// Structure factors: per-chunk partials added to the fixed-point rho(k).
+void launch_rho(const rbe_ctx* h, cudaStream_t st, bool mixed) {
+    const bool one = !h->batch;
+    const int ltiles = (h->pmax + kLTile - 1) / kLTile;
+    const Work w = make_work(h, h->d_chunks, h->cur_chunk, 1);
+    if (mixed)
+        launch_rho_mixed(st, one, w, h->nchunks, ltiles, h->tab_smem, h->d_table, h->d_cur_step,
+                         h->d_fx, h->d_rho_fx, h->d_ksamp, h->d_err);
+    else
+        launch_rho_f64(st, one, w, h->nchunks, ltiles, h->tab_smem, h->d_table, h->d_cur_step,
+                       h->d_fx64, h->d_rho_fx, h->d_ksamp, h->d_err);
+}
+
+void launch_force(const rbe_ctx* h, cudaStream_t st, bool mixed) {
+    const bool one = !h->batch;
+    if (mixed) {
+        const Work w = make_work(h, h->split == 1 ? h->d_pblk : h->d_fblk, kBlockP / h->split, 0);
+        launch_fourier_force_mixed(st, one, w, h->split == 1 ? h->npblk : h->nfblk, h->split,
+                                   h->d_fx, h->d_ksamp, h->d_rho_fx, h->d_fs);
+    } else {
+        const Work w = make_work(h, h->d_pblk, kBlockP, 0);
+        launch_fourier_force_f64(st, one, w, h->npblk, h->d_fx64, h->d_ksamp, h->d_rho_fx,
+                                 h->d_fs64);
+    }
+}
+
+// Returns the number of kernels enqueued.  The Fourier branch (structure
+// factors -> finalize -> Fourier force, on the unsorted records) runs on a
+// second stream concurrently with the cell-list branch (scan -> scatter ->
+// order); both join before the real-space kernel.  With profiling on (and st
+// the handle's own stream, i.e. not capturing) every kernel is bracketed by
+// events and the per-kernel device times are accumulated after the last one.
 int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     const bool mixed = a.prec == RBE_MIXED;
+    const bool one = !h->batch;
     const bool fourier = (a.parts & RBE_PART_FOURIER) != 0;
     const int want_q = (fourier && (a.E || a.phi || a.phi64)) ? 1 : 0;
     const int n = h->batch ? h->ntot : h->cur_n;
     const bool prof = h->prof_on && st == h->stream;
+    cudaStream_t st2 = h->stream2;
     bool used[RBE_K_COUNT] = {};
     int count = 0;
-    auto run = [&](int kid, auto&& launch) {
-        if (prof) cudaEventRecord(h->ev_beg[kid], st);
+    auto run = [&](int kid, cudaStream_t s, auto&& launch) {
+        if (prof) cudaEventRecord(h->ev_beg[kid], s);
         launch();
         if (prof) {
-            cudaEventRecord(h->ev_end[kid], st);
+            cudaEventRecord(h->ev_end[kid], s);
             used[kid] = true;
         }
         ++count;
     };
-    run(RBE_K_PREP, [&] {
+    const Work wp = make_work(h, h->d_pblk, kBlockP, 0);
+    PrepArgs pa{};
+    pa.blk_q = h->d_blk_q;
+    pa.want_q = want_q;
+    pa.qsum_fx = h->d_qsum_fx;
+    pa.rho_fx = h->d_rho_fx;
+    pa.nrho = h->ktot;
+    pa.step_dev = a.step_dev;
+    pa.step_arg = a.step;
+    pa.cur_step = h->d_cur_step;
+    if (want_q)
+        cudaMemsetAsync(h->d_qsum_fx, 0, sizeof(unsigned long long) * h->nsys, st);
+    run(RBE_K_PREP, st, [&] {
         if (mixed)
-            launch_prep_mixed(st, h->d_sys, h->d_pblk, h->npblk, a.pos, h->d_fx, h->d_cid,
-                              h->d_rank, h->d_cell_cnt, h->d_blk_q, want_q);
+            launch_prep_mixed(st, one, wp, h->npblk, a.pos, h->d_fx, h->d_cid, h->d_rank,
+                              h->d_cell_cnt, pa);
         else
-            launch_prep_f64(st, h->d_sys, h->d_pblk, h->npblk, a.pos64, h->d_fx64, h->d_cid,
-                            h->d_rank, h->d_cell_cnt, h->d_blk_q, want_q);
+            launch_prep_f64(st, one, wp, h->npblk, a.pos64, h->d_fx64, h->d_cid, h->d_rank,
+                            h->d_cell_cnt, pa);
     });
-    run(RBE_K_SCAN, [&] {
-        launch_scan(st, h->d_cell_cnt, h->d_cell_start, h->ncell, a.step_dev, a.step,
-                    h->d_cur_step);
-    });
-    run(RBE_K_SCATTER, [&] {
+    if (fourier) {
+        cudaEventRecord(h->ev_fork, st);
+        cudaStreamWaitEvent(st2, h->ev_fork, 0);
+        run(RBE_K_RHO, st2, [&] { launch_rho(h, st2, mixed); });
+        run(RBE_K_FOURIER_FORCE, st2, [&] { launch_force(h, st2, mixed); });
+        cudaEventRecord(h->ev_join, st2);
+    }
+    run(RBE_K_SCAN, st, [&] { launch_scan(st, h->d_cell_cnt, h->d_cell_start, h->ncell); });
+    run(RBE_K_SCATTER, st, [&] {
         launch_scatter(st, n, h->d_cid, h->d_rank, h->d_cell_start, h->d_perm_tmp);
     });
-    run(RBE_K_CELL_ORDER, [&] {
+    run(RBE_K_CELL_ORDER, st, [&] {
         launch_order(st, n, h->d_cid, h->d_cell_start, h->d_perm_tmp, mixed ? h->d_fx : nullptr,
                      h->d_spos, mixed ? nullptr : h->d_fx64, h->d_spos64, h->d_perm);
     });
-    const int ltiles = (h->pmax + kLTile - 1) / kLTile;
-    if (fourier) {
-        if (mixed) {
-            run(RBE_K_RHO, [&] {
-                launch_rho_mixed(st, h->d_sys, h->d_chunks, h->nchunks, ltiles, h->tab_smem,
-                                 h->d_table, h->d_cur_step, h->d_spos, h->d_part, h->d_ksamp,
-                                 h->d_err);
-            });
-            run(RBE_K_FINALIZE, [&] {
-                launch_finalize(st, h->d_sys, h->nsys, h->ktot, h->d_kstart, h->d_part, nullptr,
-                                h->d_ksamp, h->d_rho, h->d_kab, nullptr, h->d_eterm,
-                                want_q ? h->d_blk_q : nullptr, h->d_qsum);
-            });
-            run(RBE_K_FOURIER_FORCE, [&] {
-                launch_fourier_force_mixed(st, h->d_sys, h->split == 1 ? h->d_pblk : h->d_fblk,
-                                           h->split == 1 ? h->npblk : h->nfblk, h->split,
-                                           h->d_spos, h->d_ksamp, h->d_kab, h->d_fs);
-            });
-        } else {
-            run(RBE_K_RHO, [&] {
-                launch_rho_f64(st, h->d_sys, h->d_chunks, h->nchunks, ltiles, h->tab_smem,
-                               h->d_table, h->d_cur_step, h->d_spos64, h->d_part64, h->d_ksamp,
-                               h->d_err);
-            });
-            run(RBE_K_FINALIZE, [&] {
-                launch_finalize(st, h->d_sys, h->nsys, h->ktot, h->d_kstart, nullptr,
-                                h->d_part64, h->d_ksamp, h->d_rho, nullptr, h->d_kab64,
-                                h->d_eterm, want_q ? h->d_blk_q : nullptr, h->d_qsum);
-            });
-            run(RBE_K_FOURIER_FORCE, [&] {
-                launch_fourier_force_f64(st, h->d_sys, h->d_pblk, h->npblk, h->d_spos64,
-                                         h->d_ksamp, h->d_kab64, h->d_fs64);
-            });
-        }
-    }
-    RealArgs r{};
-    r.sys = h->d_sys;
-    r.rblk = h->d_rblk;
-    r.nrblk = h->nrblk;
-    r.split = h->rsplit;
-    r.parts = a.parts;
-    r.cell_start = h->d_cell_start;
-    r.perm = h->d_perm;
-    r.cur_step = h->d_cur_step;
-    r.qsum = h->d_qsum;
-    r.spos = h->d_spos;
-    r.fs = h->d_fs;
+    if (fourier) cudaStreamWaitEvent(st, h->ev_join, 0);
+    RealArgs r = make_real_args(h, a.parts);
     r.F_out = a.F;
     r.phi_out = a.phi;
     r.md_pos = a.md_pos;
     r.md_vel = a.md_vel;
-    r.spos64 = h->d_spos64;
-    r.fs64 = h->d_fs64;
     r.F_out64 = a.F64;
     r.phi_out64 = a.phi64;
     r.md_pos64 = a.md_pos64;
     r.md_vel64 = a.md_vel64;
     r.blk_e = a.E ? h->d_blk_e : nullptr;
-    run(RBE_K_REAL, [&] {
-        if (mixed) launch_real_mixed(st, r); else launch_real_f64(st, r);
+    run(RBE_K_REAL, st, [&] {
+        if (mixed) launch_real_mixed(st, one, r); else launch_real_f64(st, one, r);
     });
     if (a.E)
-        run(RBE_K_ENERGY, [&] {
-            launch_energy(st, h->d_sys, h->nsys, h->d_eterm, h->d_blk_e, h->d_qsum, a.parts, a.E);
+        run(RBE_K_ENERGY, st, [&] {
+            launch_energy(st, one, make_work(h, nullptr, 0, 0), h->nsys, h->d_ksamp, h->d_rho_fx,
+                          h->d_blk_e, h->d_blk_q, a.parts, mixed ? 1 : 0, a.E);
         });
     if (prof) {
         cudaEventSynchronize(h->ev_end[a.E ? RBE_K_ENERGY : RBE_K_REAL]);
@@ -918,17 +1032,18 @@ rbe_status rbe_sync(rbe_handle h) {
 
 rbe_status rbe_set_tuning(rbe_handle h, const rbe_tuning* t) {
     if (!h || !t) return fail(h, RBE_ERR_ARG, "null argument");
-    const int c = t->rho_chunk, f = t->force_split, r = t->real_split;
+    const int c = t->rho_chunk, f = t->force_split, r = t->real_split, sg = t->real_seg;
     if (c != 0 && (c < 32 || c > 8192 || (c & (c - 1))))
         return fail(h, RBE_ERR_ARG, "rho_chunk must be 0 or a power of two in [32, 8192]");
     if (f != 0 && f != 1 && f != 2 && f != 4 && f != 8)
         return fail(h, RBE_ERR_ARG, "force_split must be 0, 1, 2, 4 or 8");
     if (r != 0 && (r < 1 || r > 32 || (r & (r - 1))))
         return fail(h, RBE_ERR_ARG, "real_split must be 0 or a power of two in [1, 32]");
-    if (t->reserved != 0) return fail(h, RBE_ERR_ARG, "reserved must be 0");
+    if (sg < 0 || sg > 256) return fail(h, RBE_ERR_ARG, "real_seg must be in [0, 256]");
     h->rho_chunk = c;
     h->force_split = f;
     h->real_split = r;
+    h->real_seg = sg;
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
     return RBE_OK;
@@ -942,8 +1057,13 @@ rbe_status rbe_get_tuning(rbe_handle h, rbe_tuning* t) {
     t->force_split = h->cur_split > 0 ? h->cur_split
                                       : (h->force_split > 0 ? h->force_split : auto_split(ntot));
     t->real_split = h->cur_rsplit > 0 ? h->cur_rsplit
-                                      : (h->real_split > 0 ? h->real_split : auto_real_split(ntot));
-    t->reserved = 0;
+                                      : (h->real_split > 0 ? h->real_split
+                                                           : auto_real_split(ntot, h->ncell));
+    int ncd_max = 3;
+    for (auto& sh : h->sys) ncd_max = std::max(ncd_max, sh.ncd);
+    t->real_seg = h->cur_seg > 0 ? h->cur_seg
+                                 : (h->real_seg > 0 ? std::min(h->real_seg, ncd_max)
+                                                    : auto_real_seg(ntot, h->ncell, ncd_max));
     return RBE_OK;
 }
 
@@ -956,7 +1076,6 @@ rbe_status rbe_autotune(rbe_handle h, int32_t n, const float* pos_q, rbe_tuning*
     cudaEvent_t e0, e1;
     RBE_CUDA(h, cudaEventCreate(&e0));
     RBE_CUDA(h, cudaEventCreate(&e1));
-    const int ltiles = (h->pmax + kLTile - 1) / kLTile;
     EvalArgs a{};
     a.prec = RBE_MIXED;
     a.parts = RBE_PART_ALL;
@@ -971,11 +1090,7 @@ rbe_status rbe_autotune(rbe_handle h, int32_t n, const float* pos_q, rbe_tuning*
         h->rho_chunk = c;
         if ((s = prepare(h, n)) != RBE_OK) break;
         enqueue_eval(h, h->stream, a);
-        const float t = time_kernel(h, e0, e1, [&] {
-            launch_rho_mixed(h->stream, h->d_sys, h->d_chunks, h->nchunks, ltiles, h->tab_smem,
-                             h->d_table, h->d_cur_step, h->d_spos, h->d_part, h->d_ksamp,
-                             h->d_err);
-        });
+        const float t = time_kernel(h, e0, e1, [&] { launch_rho(h, h->stream, true); });
         if (t < best) { best = t; best_chunk = c; }
     }
     h->rho_chunk = best_chunk;
@@ -986,38 +1101,33 @@ rbe_status rbe_autotune(rbe_handle h, int32_t n, const float* pos_q, rbe_tuning*
         h->force_split = sp;
         if ((s = prepare(h, n)) != RBE_OK) break;
         enqueue_eval(h, h->stream, a);
-        const float t = time_kernel(h, e0, e1, [&] {
-            launch_fourier_force_mixed(h->stream, h->d_sys, h->split == 1 ? h->d_pblk : h->d_fblk,
-                                       h->split == 1 ? h->npblk : h->nfblk, h->split, h->d_spos,
-                                       h->d_ksamp, h->d_kab, h->d_fs);
-        });
+        const float t = time_kernel(h, e0, e1, [&] { launch_force(h, h->stream, true); });
         if (t < best) { best = t; best_split = sp; }
     }
     h->force_split = best_split;
-    // real-space split
+    // real-space segment length and split
     best = 1e30f;
-    int best_rsplit = 1;
-    for (int sp = 1; sp <= 32 && s == RBE_OK; sp <<= 1) {
-        h->real_split = sp;
-        if ((s = prepare(h, n)) != RBE_OK) break;
-        enqueue_eval(h, h->stream, a);
-        RealArgs r{};
-        r.sys = h->d_sys;
-        r.rblk = h->d_rblk;
-        r.nrblk = h->nrblk;
-        r.split = h->rsplit;
-        r.parts = RBE_PART_ALL;
-        r.cell_start = h->d_cell_start;
-        r.perm = h->d_perm;
-        r.cur_step = h->d_cur_step;
-        r.qsum = h->d_qsum;
-        r.spos = h->d_spos;
-        r.fs = h->d_fs;
-        r.F_out = h->d_stage_F;
-        const float t = time_kernel(h, e0, e1, [&] { launch_real_mixed(h->stream, r); });
-        if (t < best) { best = t; best_rsplit = sp; }
+    int best_rsplit = 1, best_seg = 1;
+    int ncd_max = 3;
+    for (auto& sh : h->sys) ncd_max = std::max(ncd_max, sh.ncd);
+    std::vector<int> segs_try;
+    for (int sg = 1; sg <= ncd_max; sg = sg < 4 ? sg + 1 : sg * 2) segs_try.push_back(sg);
+    if (segs_try.back() != ncd_max) segs_try.push_back(ncd_max);
+    for (int sg : segs_try) {
+        for (int sp = 1; sp <= 8 && s == RBE_OK; sp <<= 1) {
+            h->real_split = sp;
+            h->real_seg = sg;
+            if ((s = prepare(h, n)) != RBE_OK) break;
+            if ((long long)h->nseg * 2 < 152 && sg > 1) continue;   // too few blocks
+            enqueue_eval(h, h->stream, a);
+            RealArgs r = make_real_args(h, RBE_PART_ALL);
+            r.F_out = h->d_stage_F;
+            const float t = time_kernel(h, e0, e1, [&] { launch_real_mixed(h->stream, !h->batch, r); });
+            if (t < best) { best = t; best_rsplit = sp; best_seg = sg; }
+        }
     }
     h->real_split = best_rsplit;
+    h->real_seg = best_seg;
     h->prof_on = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1029,7 +1139,7 @@ rbe_status rbe_autotune(rbe_handle h, int32_t n, const float* pos_q, rbe_tuning*
         out->rho_chunk = best_chunk;
         out->force_split = best_split;
         out->real_split = best_rsplit;
-        out->reserved = 0;
+        out->real_seg = best_seg;
     }
     return finish(h, "rbe_autotune");
 }

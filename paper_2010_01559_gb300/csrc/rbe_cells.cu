@@ -53,13 +53,36 @@ __device__ __forceinline__ double2 block_sum2(double a, double b) {
     return r;
 }
 
+// Thread 0 of block 0 latches the step index of this evaluation: the
+// caller's device counter (incremented here, once per step) or the host value.
+__device__ __forceinline__ void latch_step(uint64_t* step_dev, uint64_t step_arg,
+                                          uint64_t* cur_step) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (step_dev) {
+            const uint64_t s = *step_dev;
+            *cur_step = s;
+            *step_dev = s + 1;
+        } else {
+            *cur_step = step_arg;
+        }
+    }
+}
+
+// Zero the rho(k) accumulators for this evaluation (grid-stride).
+__device__ __forceinline__ void clear_rho(unsigned long long* rho_fx, int nrho) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 2 * nrho; k += gridDim.x * blockDim.x)
+        rho_fx[k] = 0ull;
+}
+
+template <bool ONE>
 __global__ void __launch_bounds__(kBlockP)
-k_prep_mixed(const SysDev* __restrict__ sysv, const Tile* __restrict__ pblk,
-             const float4* __restrict__ pos_q, uint4* __restrict__ fx, int* __restrict__ cid,
-             int* __restrict__ rank, int* __restrict__ cell_cnt, double2* __restrict__ blk_q,
-             int want_q) {
-    const Tile tl = pblk[blockIdx.x];
-    const SysDev& S = sysv[tl.sys];
+k_prep_mixed(const __grid_constant__ Work w, const float4* __restrict__ pos_q,
+             uint4* __restrict__ fx, int* __restrict__ cid, int* __restrict__ rank,
+             int* __restrict__ cell_cnt, const __grid_constant__ PrepArgs pa) {
+    latch_step(pa.step_dev, pa.step_arg, pa.cur_step);
+    clear_rho(pa.rho_fx, pa.nrho);
+    const Tile tl = tile_of<ONE>(w);
+    const SysDev& S = sys_of<ONE>(w, tl.sys);
     const int t = threadIdx.x;
     double qs = 0.0, q2s = 0.0;
     if (t < tl.count) {
@@ -77,9 +100,12 @@ k_prep_mixed(const SysDev* __restrict__ sysv, const Tile* __restrict__ pblk,
         qs = (double)p.w;
         q2s = (double)p.w * (double)p.w;
     }
-    if (want_q) {
+    if (pa.want_q) {
         const double2 r = block_sum2(qs, q2s);
-        if (t == 0) blk_q[blockIdx.x] = r;
+        if (t == 0) {
+            pa.blk_q[blockIdx.x] = r;
+            atomicAdd(pa.qsum_fx + tl.sys, (unsigned long long)__double2ll_rn(r.x * kQScale));
+        }
     }
 }
 
@@ -96,13 +122,15 @@ __device__ __forceinline__ int cell_of_f64(double w, double invL, int ncd) {
     return c;
 }
 
+template <bool ONE>
 __global__ void __launch_bounds__(kBlockP)
-k_prep_f64(const SysDev* __restrict__ sysv, const Tile* __restrict__ pblk,
-           const double4* __restrict__ pos_q, double4* __restrict__ fx64, int* __restrict__ cid,
-           int* __restrict__ rank, int* __restrict__ cell_cnt, double2* __restrict__ blk_q,
-           int want_q) {
-    const Tile tl = pblk[blockIdx.x];
-    const SysDev& S = sysv[tl.sys];
+k_prep_f64(const __grid_constant__ Work w, const double4* __restrict__ pos_q,
+           double4* __restrict__ fx64, int* __restrict__ cid, int* __restrict__ rank,
+           int* __restrict__ cell_cnt, const __grid_constant__ PrepArgs pa) {
+    latch_step(pa.step_dev, pa.step_arg, pa.cur_step);
+    clear_rho(pa.rho_fx, pa.nrho);
+    const Tile tl = tile_of<ONE>(w);
+    const SysDev& S = sys_of<ONE>(w, tl.sys);
     const int t = threadIdx.x;
     double qs = 0.0, q2s = 0.0;
     if (t < tl.count) {
@@ -121,33 +149,25 @@ k_prep_f64(const SysDev* __restrict__ sysv, const Tile* __restrict__ pblk,
         qs = p.w;
         q2s = p.w * p.w;
     }
-    if (want_q) {
+    if (pa.want_q) {
         const double2 r = block_sum2(qs, q2s);
-        if (t == 0) blk_q[blockIdx.x] = r;
+        if (t == 0) {
+            pa.blk_q[blockIdx.x] = r;
+            atomicAdd(pa.qsum_fx + tl.sys, (unsigned long long)__double2ll_rn(r.x * kQScale));
+        }
     }
 }
 
 // Exclusive scan of the cell counts (one block), zeroing the counts for the
-// next call.  Thread 0 also latches the step index of this evaluation: the
-// caller's device counter (incremented here, once per step) or the host value.
+// next call.
 constexpr int kScanThreads = 1024;
 constexpr int kScanPer = 4;
 
 __global__ void __launch_bounds__(kScanThreads)
-k_scan(int* __restrict__ cell_cnt, int* __restrict__ cell_start, int ncell,
-       uint64_t* __restrict__ step_dev, uint64_t step_arg, uint64_t* __restrict__ cur_step) {
+k_scan(int* __restrict__ cell_cnt, int* __restrict__ cell_start, int ncell) {
     __shared__ int warp_tot[kScanThreads / 32];
     __shared__ int carry_s;
-    if (threadIdx.x == 0) {
-        carry_s = 0;
-        if (step_dev) {
-            const uint64_t s = *step_dev;
-            *cur_step = s;
-            *step_dev = s + 1;
-        } else {
-            *cur_step = step_arg;
-        }
-    }
+    if (threadIdx.x == 0) carry_s = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int base = 0; base < ncell; base += kScanThreads * kScanPer) {
@@ -227,25 +247,26 @@ __global__ void k_order(int n, const int* __restrict__ cid, const int* __restric
 }
 
 // ------------------------------------------------------------- launchers
-void launch_prep_mixed(cudaStream_t st, const SysDev* sys, const Tile* pblk, int npblk,
-                       const float4* pos_q, uint4* fx, int* cid, int* rank, int* cell_cnt,
-                       double2* blk_q, int want_q) {
-    if (npblk <= 0) return;
-    k_prep_mixed<<<npblk, kBlockP, 0, st>>>(sys, pblk, pos_q, fx, cid, rank, cell_cnt, blk_q,
-                                            want_q);
+void launch_prep_mixed(cudaStream_t st, bool one, const Work& w, int nblk, const float4* pos_q,
+                       uint4* fx, int* cid, int* rank, int* cell_cnt, const PrepArgs& pa) {
+    if (nblk <= 0) return;
+    if (one)
+        k_prep_mixed<true><<<nblk, kBlockP, 0, st>>>(w, pos_q, fx, cid, rank, cell_cnt, pa);
+    else
+        k_prep_mixed<false><<<nblk, kBlockP, 0, st>>>(w, pos_q, fx, cid, rank, cell_cnt, pa);
 }
 
-void launch_prep_f64(cudaStream_t st, const SysDev* sys, const Tile* pblk, int npblk,
-                     const double4* pos_q, double4* fx64, int* cid, int* rank, int* cell_cnt,
-                     double2* blk_q, int want_q) {
-    if (npblk <= 0) return;
-    k_prep_f64<<<npblk, kBlockP, 0, st>>>(sys, pblk, pos_q, fx64, cid, rank, cell_cnt, blk_q,
-                                          want_q);
+void launch_prep_f64(cudaStream_t st, bool one, const Work& w, int nblk, const double4* pos_q,
+                     double4* fx64, int* cid, int* rank, int* cell_cnt, const PrepArgs& pa) {
+    if (nblk <= 0) return;
+    if (one)
+        k_prep_f64<true><<<nblk, kBlockP, 0, st>>>(w, pos_q, fx64, cid, rank, cell_cnt, pa);
+    else
+        k_prep_f64<false><<<nblk, kBlockP, 0, st>>>(w, pos_q, fx64, cid, rank, cell_cnt, pa);
 }
 
-void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell,
-                 uint64_t* step_dev, uint64_t step_arg, uint64_t* cur_step) {
-    k_scan<<<1, kScanThreads, 0, st>>>(cell_cnt, cell_start, ncell, step_dev, step_arg, cur_step);
+void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell) {
+    k_scan<<<1, kScanThreads, 0, st>>>(cell_cnt, cell_start, ncell);
 }
 
 void launch_scatter(cudaStream_t st, int n, const int* cid, const int* rank,

@@ -4,14 +4,17 @@
 //               by a per-axis integer inverse-CDF table indexed with Philox words;
 //  k_rho        per-chunk partial structure factors
 //                 rho_chunk(k_l) = sum_{j in chunk} q_j exp(i k_l . r_j)          (Sec. 2)
-//               one thread per wave vector, particles staged in shared memory and
-//               read as broadcasts; the k-batch is drawn by the same blocks;
-//  k_finalize   FP64 sum of the chunk partials in a fixed order -> rho(k_l), the
-//               estimator's energy terms (S/P) 2 pi |rho|^2 / (V k^2) and the
-//               per-k force coefficients (S/P) 4 pi / (V k^2) * (Im rho, Re rho);
+//               one thread per wave vector, particles (caller's order, so this
+//               branch does not wait for the cell sort) staged in shared memory
+//               and read as broadcasts; the k-batch is drawn by the same blocks;
+//               Each block adds its chunk's partial to rho(k_l) with 64-bit
+//               fixed-point atomics: integer addition is associative, so the
+//               cross-block sum is bitwise reproducible, with no separate
+//               reduction pass;
 //  k_force      per particle: F*_i = -q_i sum_l coef_l k_l Im(e^{-i k_l.r_i} rho_l)
 //               (Eq. rbmapprox) and the Fourier part of dE/dq_i, with the k-batch
-//               staged in shared memory.
+//               and coef_l (Im rho, Re rho), coef_l = (S/P) 4 pi / (V k^2) formed
+//               in FP64, staged in shared memory.
 //
 // Mixed path phases: theta = 2 pi (m . s mod 1) with s the 32-bit fixed-point
 // fraction of the position; the product is exact in 32-bit integer arithmetic,
@@ -97,15 +100,16 @@ __global__ void k_sample(const SysDev* __restrict__ sysv, int nsys, int ktot,
 }
 
 // ----------------------------------------------------------------- rho (mixed)
+template <bool ONE>
 __global__ void __launch_bounds__(kLTile)
-k_rho_mixed(const SysDev* __restrict__ sysv, const Tile* __restrict__ chunks, int tab_smem,
-            const uint64_t* __restrict__ table, const uint64_t* __restrict__ cur_step,
-            const uint4* __restrict__ spos, float2* __restrict__ part, int4* __restrict__ ksamp,
+k_rho_mixed(const __grid_constant__ Work w, int tab_smem, const uint64_t* __restrict__ table,
+            const uint64_t* __restrict__ cur_step, const uint4* __restrict__ fx,
+            unsigned long long* __restrict__ rho_fx, int4* __restrict__ ksamp,
             int* __restrict__ err) {
     __shared__ uint4 sp[kStage];
     extern __shared__ uint32_t s_tab[];
-    const Tile ch = chunks[blockIdx.x];
-    const SysDev& S = sysv[ch.sys];
+    const Tile ch = tile_of<ONE>(w);
+    const SysDev& S = sys_of<ONE>(w, ch.sys);
     const int l = blockIdx.y * kLTile + threadIdx.x;
     if (blockIdx.y * kLTile >= S.P) return;          // whole block beyond this system's P
     const bool active = l < S.P;
@@ -117,14 +121,14 @@ k_rho_mixed(const SysDev* __restrict__ sysv, const Tile* __restrict__ chunks, in
     if (active) {
         m = tab_smem ? sample_one_smem(S, s_tab, l, *cur_step, err)
                      : sample_one(S, table + S.off_t, l, *cur_step, err);
-        if (ch.aux == S.off_part) ksamp[S.off_k + l] = m;
+        if (ch.aux == 0) ksamp[S.off_k + l] = m;
     }
     const uint32_t mx = (uint32_t)m.x, my = (uint32_t)m.y, mz = (uint32_t)m.z;
     float re = 0.f, im = 0.f;
     for (int base = 0; base < ch.count; base += kStage) {
         const int cnt = min(kStage, ch.count - base);
         __syncthreads();
-        for (int t = threadIdx.x; t < cnt; t += blockDim.x) sp[t] = spos[ch.first + base + t];
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) sp[t] = fx[ch.first + base + t];
         __syncthreads();
         if (active) {
 #pragma unroll 4
@@ -140,19 +144,20 @@ k_rho_mixed(const SysDev* __restrict__ sysv, const Tile* __restrict__ chunks, in
             }
         }
     }
-    if (active) part[ch.aux + l] = make_float2(re, im);
+    if (active) rho_accumulate(rho_fx + 2 * (S.off_k + l), (double)re, (double)im, S.rho_scale);
 }
 
 // ----------------------------------------------------------------- rho (FP64)
+template <bool ONE>
 __global__ void __launch_bounds__(kLTile)
-k_rho_f64(const SysDev* __restrict__ sysv, const Tile* __restrict__ chunks, int tab_smem,
-          const uint64_t* __restrict__ table, const uint64_t* __restrict__ cur_step,
-          const double4* __restrict__ spos64, double2* __restrict__ part64,
-          int4* __restrict__ ksamp, int* __restrict__ err) {
+k_rho_f64(const __grid_constant__ Work w, int tab_smem, const uint64_t* __restrict__ table,
+          const uint64_t* __restrict__ cur_step, const double4* __restrict__ fx64,
+          unsigned long long* __restrict__ rho_fx, int4* __restrict__ ksamp,
+          int* __restrict__ err) {
     __shared__ double4 sp[kStage / 2];
     extern __shared__ uint32_t s_tab[];
-    const Tile ch = chunks[blockIdx.x];
-    const SysDev& S = sysv[ch.sys];
+    const Tile ch = tile_of<ONE>(w);
+    const SysDev& S = sys_of<ONE>(w, ch.sys);
     const int l = blockIdx.y * kLTile + threadIdx.x;
     if (blockIdx.y * kLTile >= S.P) return;
     const bool active = l < S.P;
@@ -164,7 +169,7 @@ k_rho_f64(const SysDev* __restrict__ sysv, const Tile* __restrict__ chunks, int 
     if (active) {
         m = tab_smem ? sample_one_smem(S, s_tab, l, *cur_step, err)
                      : sample_one(S, table + S.off_t, l, *cur_step, err);
-        if (ch.aux == S.off_part) ksamp[S.off_k + l] = m;
+        if (ch.aux == 0) ksamp[S.off_k + l] = m;
     }
     const double tp = 2.0 * M_PI * S.invL;
     const double kx = tp * m.x, ky = tp * m.y, kz = tp * m.z;
@@ -172,7 +177,7 @@ k_rho_f64(const SysDev* __restrict__ sysv, const Tile* __restrict__ chunks, int 
     for (int base = 0; base < ch.count; base += kStage / 2) {
         const int cnt = min(kStage / 2, ch.count - base);
         __syncthreads();
-        for (int t = threadIdx.x; t < cnt; t += blockDim.x) sp[t] = spos64[ch.first + base + t];
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) sp[t] = fx64[ch.first + base + t];
         __syncthreads();
         if (active) {
             for (int j = 0; j < cnt; ++j) {
@@ -185,73 +190,18 @@ k_rho_f64(const SysDev* __restrict__ sysv, const Tile* __restrict__ chunks, int 
             }
         }
     }
-    if (active) part64[ch.aux + l] = make_double2(re, im);
+    if (active) rho_accumulate(rho_fx + 2 * (S.off_k + l), re, im, S.rho_scale);
 }
 
-// ----------------------------------------------------------------- finalize
-// One warp per (system, l): FP64 sum of the system's chunk partials in a fixed
-// order; lane 0 writes rho, the energy term and the force coefficients.  The
-// last nsys warps sum the per-block (sum q, sum q^2) partials of each system.
-__global__ void k_finalize(const SysDev* __restrict__ sysv, int nsys, int ktot,
-                           const int* __restrict__ kstart, const float2* __restrict__ part,
-                           const double2* __restrict__ part64, const int4* __restrict__ ksamp,
-                           double2* __restrict__ rho, float2* __restrict__ kab,
-                           double2* __restrict__ kab64, double* __restrict__ eterm,
-                           const double2* __restrict__ blk_q, double2* __restrict__ qsum) {
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w < ktot) {
-        const int s = find_sys(kstart, nsys, w);
-        const SysDev& S = sysv[s];
-        const int l = w - S.off_k;
-        double re = 0.0, im = 0.0;
-        if (part) {
-            for (int c = lane; c < S.nchunk; c += 32) {
-                const float2 v = part[S.off_part + c * S.P + l];
-                re += (double)v.x;
-                im += (double)v.y;
-            }
-        } else {
-            for (int c = lane; c < S.nchunk; c += 32) {
-                const double2 v = part64[S.off_part + c * S.P + l];
-                re += v.x;
-                im += v.y;
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            re += __shfl_down_sync(0xffffffffu, re, o);
-            im += __shfl_down_sync(0xffffffffu, im, o);
-        }
-        if (lane == 0) {
-            const int4 m = ksamp[w];
-            const double m2 = (double)m.x * m.x + (double)m.y * m.y + (double)m.z * m.z;
-            const double tp = 2.0 * M_PI * S.invL;
-            const double k2 = tp * tp * m2;
-            const double coef = S.coef_scale / k2;        // lB (S/P) 4 pi / (V k^2)
-            rho[w] = make_double2(re, im);
-            eterm[w] = 0.5 * coef * (re * re + im * im);  // lB (S/P) 2 pi |rho|^2 / (V k^2)
-            if (kab) kab[w] = make_float2((float)(coef * im), (float)(coef * re));
-            if (kab64) kab64[w] = make_double2(coef * im, coef * re);
-        }
-    } else if (w < ktot + nsys) {
-        const int s = w - ktot;
-        const SysDev& S = sysv[s];
-        double a = 0.0, b = 0.0;
-        if (blk_q) {
-            for (int k = lane; k < S.nb; k += 32) {
-                const double2 v = blk_q[S.off_b + k];
-                a += v.x;
-                b += v.y;
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_down_sync(0xffffffffu, a, o);
-            b += __shfl_down_sync(0xffffffffu, b, o);
-        }
-        if (lane == 0) qsum[s] = make_double2(a, b);
-    }
+// Force coefficients of wave vector m: coef = lB (S/P) 4 pi / (V k^2) times
+// (Im rho, Re rho), from the fixed-point rho(k) accumulator, in FP64.
+__device__ __forceinline__ double2 kcoef(const SysDev& S, int4 m,
+                                         const unsigned long long* __restrict__ rho) {
+    const double2 r = rho_read(rho, S.rho_inv_scale);
+    const double tp = 2.0 * M_PI * S.invL;
+    const double k2 = tp * tp * ((double)m.x * m.x + (double)m.y * m.y + (double)m.z * m.z);
+    const double coef = S.coef_scale / k2;
+    return make_double2(coef * r.y, coef * r.x);
 }
 
 // ----------------------------------------------------------------- force (mixed)
@@ -260,34 +210,33 @@ __global__ void k_finalize(const SysDev* __restrict__ sysv, int nsys, int ktot,
 struct KPhase { uint32_t mx, my, mz, pad; };
 struct KForce { float mx, my, mz, A; };
 
-template <int SPLIT>
+template <int SPLIT, bool ONE>
 __global__ void __launch_bounds__(kBlockP)
-k_force_mixed(const SysDev* __restrict__ sysv, const Tile* __restrict__ pblk,
-              const uint4* __restrict__ spos, const int4* __restrict__ ksamp,
-              const float2* __restrict__ kab, float4* __restrict__ fs) {
+k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
+              const int4* __restrict__ ksamp, const unsigned long long* __restrict__ rho_fx,
+              float4* __restrict__ fs) {
     constexpr int kKT = 256;                        // wave vectors staged per pass
     __shared__ KPhase kp[kKT];
     __shared__ KForce kf[kKT];
     __shared__ float kb[kKT];
-    constexpr int PER_BLOCK = kBlockP / SPLIT;      // particles per block
-    const Tile tl = pblk[blockIdx.x];
-    const SysDev& S = sysv[tl.sys];
+    const Tile tl = tile_of<ONE>(w);
+    const SysDev& S = sys_of<ONE>(w, tl.sys);
     const int sub = threadIdx.x % SPLIT;            // lane within the particle's group
     const int t = threadIdx.x / SPLIT;
     const int i = tl.first + min(t, max(tl.count - 1, 0));
     const bool active = t < tl.count;
     uint4 p = make_uint4(0, 0, 0, 0);
-    if (tl.count > 0) p = spos[i];
+    if (tl.count > 0) p = rec[i];
     float fx = 0.f, fy = 0.f, fz = 0.f, ph = 0.f;
     for (int base = 0; base < S.P; base += kKT) {
         const int cnt = min(kKT, S.P - base);
         __syncthreads();
         for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
             const int4 m = ksamp[S.off_k + base + k];
-            const float2 ab = kab[S.off_k + base + k];
+            const double2 ab = kcoef(S, m, rho_fx + 2 * (S.off_k + base + k));
             kp[k] = KPhase{(uint32_t)m.x, (uint32_t)m.y, (uint32_t)m.z, 0u};
-            kf[k] = KForce{(float)m.x, (float)m.y, (float)m.z, ab.x};
-            kb[k] = ab.y;
+            kf[k] = KForce{(float)m.x, (float)m.y, (float)m.z, (float)ab.x};
+            kb[k] = (float)ab.y;
         }
         __syncthreads();
 #pragma unroll 4
@@ -313,7 +262,6 @@ k_force_mixed(const SysDev* __restrict__ sysv, const Tile* __restrict__ pblk,
         fz += __shfl_down_sync(0xffffffffu, fz, o, SPLIT);
         ph += __shfl_down_sync(0xffffffffu, ph, o, SPLIT);
     }
-    (void)PER_BLOCK;
     if (active && sub == 0) {
         const float q = __uint_as_float(p.w);
         const float sc = -q * (float)(2.0 * M_PI) * (float)S.invL;
@@ -322,19 +270,20 @@ k_force_mixed(const SysDev* __restrict__ sysv, const Tile* __restrict__ pblk,
 }
 
 // ----------------------------------------------------------------- force (FP64)
+template <bool ONE>
 __global__ void __launch_bounds__(kBlockP)
-k_force_f64(const SysDev* __restrict__ sysv, const Tile* __restrict__ pblk,
-            const double4* __restrict__ spos64, const int4* __restrict__ ksamp,
-            const double2* __restrict__ kab64, double4* __restrict__ fs64) {
+k_force_f64(const __grid_constant__ Work w, const double4* __restrict__ rec64,
+            const int4* __restrict__ ksamp, const unsigned long long* __restrict__ rho_fx,
+            double4* __restrict__ fs64) {
     constexpr int kKT = 256;
     __shared__ double4 kk[kKT];     // kx, ky, kz, A
     __shared__ double kb[kKT];      // B
-    const Tile tl = pblk[blockIdx.x];
-    const SysDev& S = sysv[tl.sys];
+    const Tile tl = tile_of<ONE>(w);
+    const SysDev& S = sys_of<ONE>(w, tl.sys);
     const int t = threadIdx.x;
     const bool active = t < tl.count;
     double4 p = make_double4(0, 0, 0, 0);
-    if (active) p = spos64[tl.first + t];
+    if (active) p = rec64[tl.first + t];
     const double tp = 2.0 * M_PI * S.invL;
     double fx = 0, fy = 0, fz = 0, ph = 0;
     for (int base = 0; base < S.P; base += kKT) {
@@ -342,7 +291,7 @@ k_force_f64(const SysDev* __restrict__ sysv, const Tile* __restrict__ pblk,
         __syncthreads();
         for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
             const int4 m = ksamp[S.off_k + base + k];
-            const double2 ab = kab64[S.off_k + base + k];
+            const double2 ab = kcoef(S, m, rho_fx + 2 * (S.off_k + base + k));
             kk[k] = make_double4(tp * m.x, tp * m.y, tp * m.z, ab.x);
             kb[k] = ab.y;
         }
@@ -375,53 +324,63 @@ void launch_sample(cudaStream_t st, const SysDev* sys, int nsys, int ktot, const
 
 // tab_smem: number of 32-bit table entries to stage per block (max 2M over the
 // systems), 0 to search the table in global memory.
-void launch_rho_mixed(cudaStream_t st, const SysDev* sys, const Tile* chunks, int nchunks,
-                      int ltiles, int tab_smem, const uint64_t* table, const uint64_t* cur_step,
-                      const uint4* spos, float2* part, int4* ksamp, int* err) {
+void launch_rho_mixed(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
+                      int tab_smem, const uint64_t* table, const uint64_t* cur_step,
+                      const uint4* fx, unsigned long long* rho_fx, int4* ksamp, int* err) {
     if (nchunks <= 0 || ltiles <= 0) return;
     dim3 grid(nchunks, ltiles);
-    k_rho_mixed<<<grid, kLTile, sizeof(uint32_t) * tab_smem, st>>>(
-        sys, chunks, tab_smem > 0 ? 1 : 0, table, cur_step, spos, part, ksamp, err);
+    const size_t smem = sizeof(uint32_t) * tab_smem;
+    if (one)
+        k_rho_mixed<true><<<grid, kLTile, smem, st>>>(w, tab_smem > 0, table, cur_step, fx,
+                                                      rho_fx, ksamp, err);
+    else
+        k_rho_mixed<false><<<grid, kLTile, smem, st>>>(w, tab_smem > 0, table, cur_step, fx,
+                                                       rho_fx, ksamp, err);
 }
 
-void launch_rho_f64(cudaStream_t st, const SysDev* sys, const Tile* chunks, int nchunks,
-                    int ltiles, int tab_smem, const uint64_t* table, const uint64_t* cur_step,
-                    const double4* spos64, double2* part64, int4* ksamp, int* err) {
+void launch_rho_f64(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
+                    int tab_smem, const uint64_t* table, const uint64_t* cur_step,
+                    const double4* fx64, unsigned long long* rho_fx, int4* ksamp, int* err) {
     if (nchunks <= 0 || ltiles <= 0) return;
     dim3 grid(nchunks, ltiles);
-    k_rho_f64<<<grid, kLTile, sizeof(uint32_t) * tab_smem, st>>>(
-        sys, chunks, tab_smem > 0 ? 1 : 0, table, cur_step, spos64, part64, ksamp, err);
+    const size_t smem = sizeof(uint32_t) * tab_smem;
+    if (one)
+        k_rho_f64<true><<<grid, kLTile, smem, st>>>(w, tab_smem > 0, table, cur_step, fx64,
+                                                    rho_fx, ksamp, err);
+    else
+        k_rho_f64<false><<<grid, kLTile, smem, st>>>(w, tab_smem > 0, table, cur_step, fx64,
+                                                     rho_fx, ksamp, err);
 }
 
-void launch_finalize(cudaStream_t st, const SysDev* sys, int nsys, int ktot, const int* kstart,
-                     const float2* part, const double2* part64, const int4* ksamp,
-                     double2* rho, float2* kab, double2* kab64, double* eterm,
-                     const double2* blk_q, double2* qsum) {
-    const int warps = ktot + nsys;
-    if (warps <= 0) return;
-    const int threads = 64;          // few warps per block: spread the FP64 sums over all SMs
-    const int blocks = (warps * 32 + threads - 1) / threads;
-    k_finalize<<<blocks, threads, 0, st>>>(sys, nsys, ktot, kstart, part, part64, ksamp, rho,
-                                           kab, kab64, eterm, blk_q, qsum);
+template <int SPLIT>
+static void force_mixed_split(cudaStream_t st, bool one, const Work& w, int nblk, const uint4* fx,
+                              const int4* ksamp, const unsigned long long* rho_fx, float4* fs) {
+    if (one)
+        k_force_mixed<SPLIT, true><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, rho_fx, fs);
+    else
+        k_force_mixed<SPLIT, false><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, rho_fx, fs);
 }
 
-void launch_fourier_force_mixed(cudaStream_t st, const SysDev* sys, const Tile* pblk, int npblk,
-                                int split, const uint4* spos, const int4* ksamp,
-                                const float2* kab, float4* fs) {
-    if (npblk <= 0) return;
+void launch_fourier_force_mixed(cudaStream_t st, bool one, const Work& w, int nblk, int split,
+                                const uint4* fx, const int4* ksamp,
+                                const unsigned long long* rho_fx, float4* fs) {
+    if (nblk <= 0) return;
     switch (split) {
-        case 2: k_force_mixed<2><<<npblk, kBlockP, 0, st>>>(sys, pblk, spos, ksamp, kab, fs); break;
-        case 4: k_force_mixed<4><<<npblk, kBlockP, 0, st>>>(sys, pblk, spos, ksamp, kab, fs); break;
-        case 8: k_force_mixed<8><<<npblk, kBlockP, 0, st>>>(sys, pblk, spos, ksamp, kab, fs); break;
-        default: k_force_mixed<1><<<npblk, kBlockP, 0, st>>>(sys, pblk, spos, ksamp, kab, fs); break;
+        case 2: force_mixed_split<2>(st, one, w, nblk, fx, ksamp, rho_fx, fs); break;
+        case 4: force_mixed_split<4>(st, one, w, nblk, fx, ksamp, rho_fx, fs); break;
+        case 8: force_mixed_split<8>(st, one, w, nblk, fx, ksamp, rho_fx, fs); break;
+        default: force_mixed_split<1>(st, one, w, nblk, fx, ksamp, rho_fx, fs); break;
     }
 }
 
-void launch_fourier_force_f64(cudaStream_t st, const SysDev* sys, const Tile* pblk, int npblk,
-                              const double4* spos64, const int4* ksamp, const double2* kab64,
-                              double4* fs64) {
-    if (npblk <= 0) return;
-    k_force_f64<<<npblk, kBlockP, 0, st>>>(sys, pblk, spos64, ksamp, kab64, fs64);
+void launch_fourier_force_f64(cudaStream_t st, bool one, const Work& w, int nblk,
+                              const double4* fx64, const int4* ksamp,
+                              const unsigned long long* rho_fx, double4* fs64) {
+    if (nblk <= 0) return;
+    if (one)
+        k_force_f64<true><<<nblk, kBlockP, 0, st>>>(w, fx64, ksamp, rho_fx, fs64);
+    else
+        k_force_f64<false><<<nblk, kBlockP, 0, st>>>(w, fx64, ksamp, rho_fx, fs64);
 }
 
 }  // namespace rbe

@@ -13,12 +13,13 @@
 //   spos   uint4 [N]   fx sorted by cell, in-cell by caller's index (the order all
 //                      later kernels use)
 //   perm   int   [N]   sorted index -> caller's index
-//   fs     float4[N]   Fourier force (xyz) and Fourier dE/dq (w), sorted order
+//   fs     float4[N]   Fourier force (xyz) and Fourier dE/dq (w), caller's order
 //   cell_cnt / cell_start  int [C + 1] over all systems' cells
-//   part   float2 [sum_s nchunk_s * P_s]  per-chunk partial rho(k_l)
-//   ksamp  int4   [K] (m_x, m_y, m_z, attempts)   K = sum_s P_s
-//   kab    float2 [K] (coef * Im rho, coef * Re rho)
-//   rho    double2[K], eterm double [K]
+//   rho_fx int64 [2K]  rho(k_l) = (Re, Im) accumulated over all chunks with 64-bit
+//                      fixed-point atomics (integer addition is associative, so
+//                      the sum is bitwise reproducible), K = sum_s P_s
+//   ksamp  int4   [K] (m_x, m_y, m_z, attempts)
+//   qsum_fx int64 [nsys] sum q in fixed point (for dE/dq)
 //   blk_e  double2[nblk] per-block (E_coul, E_lj); blk_q double2[nblk] (sum q, sum q^2)
 // and the same with double4 / double2 records for the FP64 path.
 #pragma once
@@ -32,6 +33,7 @@ constexpr int kBlockP = 128;      // particles per block of the per-particle ker
 constexpr int kLTile = 128;       // wave vectors per block of the structure-factor kernel
 constexpr int kMaxAttempts = 32;  // bound on the (0,0,0) rejection loop
 constexpr int kErrSampler = 1;    // bit in the device error word
+constexpr double kQScale = 4294967296.0;           // 2^32: fixed point of sum q
 
 // Per-system constants (device copy).  All derived in FP64 on the host.
 struct SysDev {
@@ -52,8 +54,11 @@ struct SysDev {
     int off_t;              // first table entry
     int off_part;           // first partial of the structure-factor chunks
     int nchunk;             // structure-factor chunks of this system
+    double rho_scale;       // 64-bit fixed-point scale of the rho(k) accumulators
+    double rho_inv_scale;
     int off_b, nb;          // first per-particle block and block count (prep)
-    int off_rb, nrb;        // first real-space block and block count
+    int off_rb, nrb;        // first real-space block and block count (FP64 path)
+    int off_sg, nsg;        // first real-space segment and segment count (mixed path)
 };
 
 // A tile of particles of one system: (system, first particle, count, aux).
@@ -78,66 +83,121 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     return c;
 }
 
-// Index of the system owning global particle i (pstart has nsys + 1 entries).
-__device__ __forceinline__ int find_sys(const int* __restrict__ pstart, int nsys, int i) {
+// Where a kernel finds its tile of work and its system.  Batch handles pass
+// tables (tiles[blockIdx.x], then sysv[tile.sys]); single-system handles pass
+// the system's constants by value and the tile size, so a block finds both
+// without touching memory (every step starts with cold caches otherwise).
+struct Work {
+    const SysDev* sysv;   // batch: per-system constants (null for one system)
+    const Tile* tiles;    // batch: one tile per block
+    int tile;             // one system: particles per block
+    int aux_stride;       // one system: tile.aux = blockIdx.x * aux_stride
+    SysDev one;           // one system: its constants
+};
+
+template <bool ONE>
+__device__ __forceinline__ Tile tile_of(const Work& w) {
+    if constexpr (ONE) {
+        const int first = blockIdx.x * w.tile;
+        return Tile{0, first, max(0, min(w.tile, w.one.n - first)),
+                    (int)blockIdx.x * w.aux_stride};
+    } else {
+        return w.tiles[blockIdx.x];
+    }
+}
+
+template <bool ONE>
+__device__ __forceinline__ const SysDev& sys_of(const Work& w, int s) {
+    if constexpr (ONE) return w.one;
+    else return w.sysv[s];
+}
+
+// Index of the system owning global item i (start has nsys + 1 entries).
+__device__ __forceinline__ int find_sys(const int* __restrict__ start, int nsys, int i) {
     int lo = 0, hi = nsys - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        if (__ldg(pstart + mid) <= i) lo = mid; else hi = mid - 1;
+        if (__ldg(start + mid) <= i) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
 
 // ------------------------------------------------------------- launchers
+// `one` selects the single-system kernels (Work.one / Work.tile), else tables.
 // cells / sorting (rbe_cells.cu)
-void launch_prep_mixed(cudaStream_t st, const SysDev* sys, const Tile* pblk, int npblk,
-                       const float4* pos_q, uint4* fx, int* cid, int* rank, int* cell_cnt,
-                       double2* blk_q, int want_q);
-void launch_prep_f64(cudaStream_t st, const SysDev* sys, const Tile* pblk, int npblk,
-                     const double4* pos_q, double4* fx64, int* cid, int* rank, int* cell_cnt,
-                     double2* blk_q, int want_q);
-void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell,
-                 uint64_t* step_dev, uint64_t step_arg, uint64_t* cur_step);
+// The prep kernels also clear the rho(k) accumulators (2 * nrho words) and,
+// with want_q, add each system's charges to qsum_fx (cleared by the caller).
+struct PrepArgs {
+    double2* blk_q;
+    int want_q;
+    unsigned long long* qsum_fx;
+    unsigned long long* rho_fx;
+    int nrho;
+    uint64_t* step_dev;
+    uint64_t step_arg;
+    uint64_t* cur_step;
+};
+void launch_prep_mixed(cudaStream_t st, bool one, const Work& w, int nblk, const float4* pos_q,
+                       uint4* fx, int* cid, int* rank, int* cell_cnt, const PrepArgs& pa);
+void launch_prep_f64(cudaStream_t st, bool one, const Work& w, int nblk, const double4* pos_q,
+                     double4* fx64, int* cid, int* rank, int* cell_cnt, const PrepArgs& pa);
+void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell);
 void launch_scatter(cudaStream_t st, int n, const int* cid, const int* rank,
                     const int* cell_start, int* perm_tmp);
 void launch_order(cudaStream_t st, int n, const int* cid, const int* cell_start,
                   const int* perm_tmp, const uint4* fx, uint4* spos, const double4* fx64,
                   double4* spos64, int* perm);
 
-// Fourier part (rbe_fourier.cu)
+// Fourier part (rbe_fourier.cu).  The structure factors and the Fourier force
+// run over the unsorted fixed-point records (caller's order).
 void launch_sample(cudaStream_t st, const SysDev* sys, int nsys, int ktot, const int* kstart,
                    const uint64_t* table, const uint64_t* cur_step, int4* ksamp, int* err);
-void launch_rho_mixed(cudaStream_t st, const SysDev* sys, const Tile* chunks, int nchunks,
-                      int ltiles, int tab_smem, const uint64_t* table, const uint64_t* cur_step,
-                      const uint4* spos, float2* part, int4* ksamp, int* err);
-void launch_rho_f64(cudaStream_t st, const SysDev* sys, const Tile* chunks, int nchunks,
-                    int ltiles, int tab_smem, const uint64_t* table, const uint64_t* cur_step,
-                    const double4* spos64, double2* part64, int4* ksamp, int* err);
-void launch_finalize(cudaStream_t st, const SysDev* sys, int nsys, int ktot, const int* kstart,
-                     const float2* part, const double2* part64, const int4* ksamp,
-                     double2* rho, float2* kab, double2* kab64, double* eterm,
-                     const double2* blk_q, double2* qsum);
-void launch_fourier_force_mixed(cudaStream_t st, const SysDev* sys, const Tile* pblk, int npblk,
-                                int split, const uint4* spos, const int4* ksamp,
-                                const float2* kab, float4* fs);
-void launch_fourier_force_f64(cudaStream_t st, const SysDev* sys, const Tile* pblk, int npblk,
-                              const double4* spos64, const int4* ksamp, const double2* kab64,
-                              double4* fs64);
+// rho(k) accumulators: 64-bit two's-complement fixed point, scale per system.
+__device__ __forceinline__ void rho_accumulate(unsigned long long* dst, double re, double im,
+                                               double scale) {
+    atomicAdd(dst, (unsigned long long)__double2ll_rn(re * scale));
+    atomicAdd(dst + 1, (unsigned long long)__double2ll_rn(im * scale));
+}
+
+__device__ __forceinline__ double2 rho_read(const unsigned long long* src, double inv_scale) {
+    return make_double2((double)(long long)__ldcg(src) * inv_scale,
+                        (double)(long long)__ldcg(src + 1) * inv_scale);
+}
+
+void launch_rho_mixed(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
+                      int tab_smem, const uint64_t* table, const uint64_t* cur_step,
+                      const uint4* fx, unsigned long long* rho_fx, int4* ksamp, int* err);
+void launch_rho_f64(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
+                    int tab_smem, const uint64_t* table, const uint64_t* cur_step,
+                    const double4* fx64, unsigned long long* rho_fx, int4* ksamp, int* err);
+void launch_fourier_force_mixed(cudaStream_t st, bool one, const Work& w, int nblk, int split,
+                                const uint4* fx, const int4* ksamp,
+                                const unsigned long long* rho_fx, float4* fs);
+void launch_fourier_force_f64(cudaStream_t st, bool one, const Work& w, int nblk,
+                              const double4* fx64, const int4* ksamp,
+                              const unsigned long long* rho_fx, double4* fs64);
 
 // real space, LJ, Langevin, energies (rbe_real.cu)
 struct RealArgs {
-    const SysDev* sys;
-    const Tile* rblk;        // real-space tiles of kBlockP / split particles
+    Work w;                  // real-space tiles of kBlockP / split particles (FP64 path)
     int nrblk;
     int split;               // threads per particle
+    int ncell;               // cells over all systems
+    int nsys;
+    const int* cstart;       // first cell of each system (nsys + 1), batch only
+    const Tile* segs;        // mixed path: (system, first cell, cells, packed x0|y<<10|z<<20)
+    int nseg;
+    int seg_max;             // most cells in one segment
+    int stage_cap;           // staged records per segment block
+    int seg_threads;         // threads per segment block (64, 128 or 256)
     int parts;               // RBE_PART_* mask
     const int* cell_start;
     const int* perm;
     const uint64_t* cur_step;
-    const double2* qsum;     // per system (sum q, sum q^2)
+    const unsigned long long* qsum_fx;   // per system sum q (fixed point 2^32)
     // mixed
     const uint4* spos;
-    const float4* fs;
+    const float4* fs;        // Fourier force and dE/dq, caller's order
     float4* F_out;
     float* phi_out;
     float4* md_pos;          // non-null: Langevin update in place
@@ -151,9 +211,10 @@ struct RealArgs {
     double4* md_vel64;
     double2* blk_e;          // per block (E_coul, E_lj), nullable
 };
-void launch_real_mixed(cudaStream_t st, const RealArgs& a);
-void launch_real_f64(cudaStream_t st, const RealArgs& a);
-void launch_energy(cudaStream_t st, const SysDev* sys, int nsys, const double* eterm,
-                   const double2* blk_e, const double2* qsum, int parts, double* E_out);
+void launch_real_mixed(cudaStream_t st, bool one, const RealArgs& a);
+void launch_real_f64(cudaStream_t st, bool one, const RealArgs& a);
+void launch_energy(cudaStream_t st, bool one, const Work& w, int nsys, const int4* ksamp,
+                   const unsigned long long* rho_fx, const double2* blk_e,
+                   const double2* blk_q, int parts, int per_cell, double* E_out);
 
 }  // namespace rbe

@@ -3,11 +3,12 @@
 // total force / dE/dq, the Langevin update of Sec. 3.3, and the FP64 energy
 // reduction.
 //
-// G threads per particle (G = 1 .. 32, a tuning choice) in cell order walk the
-// 27 cells around the particle's own (cells have side >= r_c, at least 3 per
-// edge, so every pair within r_c is met exactly once, as the minimum image).
-// Neighbouring particles share most neighbour records, so they are served
-// from L1.
+// Cells have side >= r_c and there are at least 3 per edge, so every pair
+// within r_c is met exactly once, as the minimum image, among the 27 cells
+// around a particle's own.  Mixed path: one block per segment of x-adjacent
+// cells with the neighbourhood staged in shared memory and G threads per
+// particle (tuning choices).  FP64 path: G threads per particle reading the
+// neighbours from global memory.
 //
 // Real-space pair terms for r < r_c (r_ij = r_j - r_i):
 //   F_i   += -lB q_i q_j G(r) r_ij / r,  G = erfc(sqrt(a) r)/r^2 + 2 sqrt(a) e^{-a r^2}/(sqrt(pi) r)
@@ -65,149 +66,357 @@ __device__ __forceinline__ void row_ranges(const int* __restrict__ cs, int base,
 }
 
 // ----------------------------------------------------------------- mixed
-// G threads cooperate on one particle: they stride over the candidates of each
-// row, and their partial sums are combined with shuffles.
+// One block per cell.  The block stages the records of the 27 neighbouring
+// cells (9 rows, each one or two contiguous ranges of the cell-sorted records)
+// into shared memory with coalesced loads; then G threads per particle of the
+// cell stride over the staged records and combine their sums with shuffles.
+// Each thread first runs the cheap distance test over its candidates and keeps
+// the indices of those within the cutoff (about one in six) in a list, then
+// evaluates erfc / exp / LJ for the listed ones only: a warp whose lanes would
+// otherwise take the expensive branch at different candidates now runs it
+// densely.  A cell whose neighbourhood exceeds the staging capacity reads the
+// records from global memory instead.
+constexpr int kNbCap = 24;          // entries of each lane's neighbour list
+
+struct PairAcc {
+    float fx, fy, fz, phr, ec, elj;
+};
+
+// erfc(x) for x >= 0 given e = exp(-x^2): the rational approximation of
+// Abramowitz & Stegun, Handbook of Mathematical Functions, formula 7.1.26
+// (after Hastings), |error| <= 1.5e-7.  It reuses the Gaussian the force needs
+// anyway, so erfc costs one reciprocal and five FMAs.
+__device__ __forceinline__ float erfc_as(float e, float x) {
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+    float p = 1.061405429f;
+    p = fmaf(p, t, -1.453152027f);
+    p = fmaf(p, t, 1.421413741f);
+    p = fmaf(p, t, -0.284496736f);
+    p = fmaf(p, t, 0.254829592f);
+    return p * t * e;
+}
+
+// Per-system constants of the pair terms, in registers.
+struct PairConst {
+    float rc2, lj_rc2, alpha, sa, two_sa_spi, lB, lj_s2, lj_eps, lj_shift;
+};
+
+// Pair terms for displacement r_ij = (dx, dy, dz), |r_ij|^2 = r2 > 0.
+__device__ __forceinline__ void pair_terms(float dx, float dy, float dz, float r2, float qj,
+                                           float lbqi, const PairConst& k, PairAcc& acc) {
+    const float inv_r = rsqrtf(r2);
+    if (r2 < k.rc2) {
+        const float x = k.sa * (r2 * inv_r);
+        const float ex = __expf(-k.alpha * r2);                  // exp(-x^2)
+        const float pot = erfc_as(ex, x) * inv_r;                 // erfc(sqrt(a) r) / r
+        const float g_over_r = fmaf(k.two_sa_spi, ex, pot) * inv_r * inv_r;   // G(r) / r
+        const float s_ = -lbqi * qj * g_over_r;
+        acc.fx = fmaf(s_, dx, acc.fx);
+        acc.fy = fmaf(s_, dy, acc.fy);
+        acc.fz = fmaf(s_, dz, acc.fz);
+        acc.phr = fmaf(k.lB * qj, pot, acc.phr);
+        acc.ec = fmaf(0.5f * lbqi * qj, pot, acc.ec);
+    }
+    if (r2 < k.lj_rc2) {
+        const float inv_r2 = inv_r * inv_r;
+        const float sr2 = k.lj_s2 * inv_r2;
+        const float sr6 = sr2 * sr2 * sr2;
+        const float mag = 24.f * k.lj_eps * (2.f * sr6 * sr6 - sr6) * inv_r2;
+        acc.fx = fmaf(-mag, dx, acc.fx);
+        acc.fy = fmaf(-mag, dy, acc.fy);
+        acc.fz = fmaf(-mag, dz, acc.fz);
+        acc.elj += 0.5f * (4.f * k.lj_eps * (sr6 * sr6 - sr6) + k.lj_shift);
+    }
+}
+
 template <int G>
-__global__ void __launch_bounds__(kBlockP)
-k_real_mixed(RealArgs a) {
-    const Tile tl = a.rblk[blockIdx.x];
-    const SysDev& S = a.sys[tl.sys];
-    const int g = threadIdx.x % G;
-    const int t = threadIdx.x / G;
-    const bool active = t < tl.count;
-    const int i = tl.first + (tl.count > 0 ? min(t, tl.count - 1) : 0);
-    uint4 pi = make_uint4(0, 0, 0, 0);
-    if (tl.count > 0) pi = a.spos[i];
-    const float qi = __uint_as_float(pi.w);
+__device__ __forceinline__ float lane_sum(float v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, G);
+    return v;
+}
+
+// Offset of a fixed-point coordinate within its cell, in length units.  The
+// product is rounded explicitly, so a record always maps to the same float and
+// a particle meets itself at distance exactly 0.
+__device__ __forceinline__ float incell(uint32_t s, int ncd, const uint32_t* corner, float Lu) {
+    const int c = (int)(((unsigned long long)s * (unsigned long long)ncd) >> 32);
+    return __fmul_rn((float)(s - corner[c]), Lu);
+}
+
+// Corner-to-corner distance from cell c to cell wrap(c + d), d in {-1, 0, 1}.
+__device__ __forceinline__ float cell_shift(int c, int d, int ncd, const uint32_t* corner,
+                                            float Lu) {
+    const int cn = wrapc(c + d, ncd);
+    return __fmul_rn((float)(int32_t)(corner[cn] - corner[c]), Lu);
+}
+
+// One block per segment: nseg x-adjacent cells of one (y, z) row (the whole row
+// for large systems).  The block stages, for each of the 9 neighbour rows, the
+// segment's cells plus one halo cell on each side, as in-cell offsets with the
+// charge; per-cell boundaries of the staged rows go to a small table.  A
+// particle in cell x then finds its 27 neighbour cells as 9 contiguous windows
+// of three cells, and the displacement to a staged record is its in-cell
+// offset minus the particle's plus the exact corner-to-corner shift of the two
+// cells, so FP32 precision does not depend on where the segment sits in the
+// box.  G threads per particle first run the distance test over their share of
+// the candidates and list the ones within the cutoff, then evaluate erfc / exp
+// / LJ densely for the listed ones.  A segment whose neighbourhood exceeds the
+// staging buffer reads its candidates from global memory instead.
+template <int G, bool ONE, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT)
+k_real_seg(const __grid_constant__ RealArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4* s_rec = (float4*)smem;                                    // [stage_cap]
+    uint32_t* s_nb = (uint32_t*)(s_rec + a.stage_cap);                // [kNbCap][NT]
+    int* s_b = (int*)(s_nb + kNbCap * NT);                            // [9][seg_max + 3]
+    __shared__ uint32_t s_corner[256];
+    __shared__ int s_src[27], s_len[27], s_off[28];
+    const Tile sg = a.segs[blockIdx.x];
+    const int sys = sg.sys;
+    const SysDev& S = sys_of<ONE>(a.w, sys);
+    const int ncd = S.ncd;
+    const int nsc = sg.count;                                         // cells in the segment
+    const int x0 = sg.aux & 1023, cy = (sg.aux >> 10) & 1023, cz = (sg.aux >> 20) & 1023;
+    const int x1 = x0 + nsc - 1;
+    const int bstride = a.seg_max + 3;
+    const int own_s = __ldg(a.cell_start + sg.first), own_e = __ldg(a.cell_start + sg.first + nsc);
+    const int nown = own_e - own_s;
     const bool do_real = (a.parts & kPartReal) != 0;
     const bool do_lj = (a.parts & kPartLJ) != 0 && S.lj_eps != 0.0;
-    float fx = 0.f, fy = 0.f, fz = 0.f, phr = 0.f, ec = 0.f, elj = 0.f;
-    if (active && (do_real || do_lj)) {
-        const int ncd = S.ncd;
-        const int cx = (int)(((unsigned long long)pi.x * ncd) >> 32);
-        const int cy = (int)(((unsigned long long)pi.y * ncd) >> 32);
-        const int cz = (int)(((unsigned long long)pi.z * ncd) >> 32);
-        const float Lu = S.L_over_2_32;
-        const float rc2 = do_real ? (float)(S.r_c * S.r_c) : 0.f;
-        const float alpha = (float)S.alpha, sa = (float)S.sqrt_alpha;
-        const float two_sa_spi = (float)(2.0 * S.sqrt_alpha / sqrt(M_PI));
-        const float lB = (float)S.lB;
-        const float lj_rc2 = do_lj ? (float)S.lj_rcut2 : 0.f, lj_s2 = (float)S.lj_sigma2;
-        const float lj_eps = (float)S.lj_eps, lj_shift = (float)S.lj_shift;
-        const float lbqi = lB * qi;
-        for (int dz = -1; dz <= 1; ++dz) {
-            const int zz = wrapc(cz + dz, ncd);
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int yy = wrapc(cy + dy, ncd);
-                int s0, e0, s1, e1;
-                row_ranges(a.cell_start, S.off_c + (zz * ncd + yy) * ncd, cx, ncd, s0, e0, s1, e1);
+    const bool pairs = nown > 0 && (do_real || do_lj);
+    const float Lu = S.L_over_2_32;
+    for (int c = threadIdx.x; c < ncd; c += blockDim.x)
+        s_corner[c] = (uint32_t)(((unsigned long long)c << 32) / (unsigned long long)ncd);
+    if (pairs && threadIdx.x < 27) {
+        const int r = threadIdx.x / 3, part = threadIdx.x % 3;
+        const int zz = wrapc(cz + r / 3 - 1, ncd), yy = wrapc(cy + r % 3 - 1, ncd);
+        const int row = S.off_c + (zz * ncd + yy) * ncd;
+        int b, e;
+        if (part == 1) {
+            b = __ldg(a.cell_start + row + x0);
+            e = __ldg(a.cell_start + row + x1 + 1);
+        } else {
+            const int xh = wrapc(part == 0 ? x0 - 1 : x1 + 1, ncd);
+            b = __ldg(a.cell_start + row + xh);
+            e = __ldg(a.cell_start + row + xh + 1);
+        }
+        s_src[threadIdx.x] = b;
+        s_len[threadIdx.x] = e - b;
+    }
+    __syncthreads();
+    if (pairs && threadIdx.x < 32) {
+        const int v = threadIdx.x < 27 ? s_len[threadIdx.x] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)threadIdx.x >= o) incl += y;
+        }
+        if (threadIdx.x < 27) s_off[threadIdx.x + 1] = incl;
+        if (threadIdx.x == 0) s_off[0] = 0;
+    }
+    __syncthreads();
+    const int total = pairs ? s_off[27] : 0;
+    const bool staged = total <= a.stage_cap;
+    if (pairs) {
+        // window boundaries: row r, boundary j of cells x0-1 .. x1+1 (j = 0 .. nsc+2)
+        for (int idx = threadIdx.x; idx < 9 * (nsc + 3); idx += blockDim.x) {
+            const int r = idx / (nsc + 3), j = idx - r * (nsc + 3);
+            int v;
+            if (j == 0) {
+                v = s_off[3 * r];
+            } else if (j <= nsc + 1) {
+                const int zz = wrapc(cz + r / 3 - 1, ncd), yy = wrapc(cy + r % 3 - 1, ncd);
+                const int row = S.off_c + (zz * ncd + yy) * ncd;
+                v = s_off[3 * r + 1] + (__ldg(a.cell_start + row + x0 + j - 1) - s_src[3 * r + 1]);
+            } else {
+                v = s_off[3 * r + 3];
+            }
+            s_b[r * bstride + j] = v;
+        }
+        if (staged)
+            // every thread issues its loads at once: staged slot k comes from
+            // range q (binary search over the prefix), consecutive k consecutive
+            for (int k = threadIdx.x; k < total; k += blockDim.x) {
+                int lo = 0, hi = 26;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_off[mid] <= k) lo = mid; else hi = mid - 1;
+                }
+                const uint4 rec = __ldg(a.spos + s_src[lo] + (k - s_off[lo]));
+                s_rec[k] = make_float4(incell(rec.x, ncd, s_corner, Lu),
+                                       incell(rec.y, ncd, s_corner, Lu),
+                                       incell(rec.z, ncd, s_corner, Lu), __uint_as_float(rec.w));
+            }
+    }
+    __syncthreads();
+    PairConst kc;
+    kc.rc2 = do_real ? (float)(S.r_c * S.r_c) : 0.f;
+    kc.lj_rc2 = do_lj ? (float)S.lj_rcut2 : 0.f;
+    kc.alpha = (float)S.alpha;
+    kc.sa = (float)S.sqrt_alpha;
+    kc.two_sa_spi = (float)(2.0 * S.sqrt_alpha / 1.7724538509055160);
+    kc.lB = (float)S.lB;
+    kc.lj_s2 = (float)S.lj_sigma2;
+    kc.lj_eps = (float)S.lj_eps;
+    kc.lj_shift = (float)S.lj_shift;
+    const float cut2 = fmaxf(kc.rc2, kc.lj_rc2);
+    const bool want_phi = a.phi_out != nullptr;
+    const bool want_e = a.blk_e != nullptr;
+    const int g = threadIdx.x % G;
+    const int t = threadIdx.x / G;
+    double ec_own = 0.0, elj_own = 0.0;
+    for (int base = 0; base < nown; base += NT / G) {
+        const bool active = base + t < nown;
+        const int i = own_s + min(base + t, nown - 1);
+        const int o = a.perm[i];                          // issued early: the tail needs it
+        const uint4 rec = a.spos[i];
+        const int cxi = (int)(((unsigned long long)rec.x * (unsigned long long)ncd) >> 32);
+        const float pxo = incell(rec.x, ncd, s_corner, Lu);
+        const float pyo = incell(rec.y, ncd, s_corner, Lu);
+        const float pzo = incell(rec.z, ncd, s_corner, Lu);
+        const float qi = __uint_as_float(rec.w);
+        const float lbqi = kc.lB * qi;
+        // the particle's position relative to the corners of its x-neighbour cells
+        const float px_m = pxo + cell_shift(cxi, -1, ncd, s_corner, Lu) * -1.0f;
+        const float px_p = pxo - cell_shift(cxi, 1, ncd, s_corner, Lu);
+        PairAcc acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (active && pairs) {
+            const int u = cxi - x0;                       // 0 .. nsc-1
+            if (staged) {
+                int cnt = 0;
 #pragma unroll 1
-                for (int r = 0; r < 2; ++r) {
-                    const int s = r ? s1 : s0, e = r ? e1 : e0;
+                for (int r = 0; r < 9; ++r) {
+                    const float py = pyo - cell_shift(cy, r % 3 - 1, ncd, s_corner, Lu);
+                    const float pz = pzo - cell_shift(cz, r / 3 - 1, ncd, s_corner, Lu);
+                    const int* bb = s_b + r * bstride + u;
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {              // cells x-1, x, x+1 of the row
+                        const float px = (m == 0) ? px_m : ((m == 1) ? pxo : px_p);
+                        const int ke = bb[m + 1];
+                        const uint32_t tag = ((uint32_t)r << 24) | ((uint32_t)m << 28);
 #pragma unroll 2
-                    for (int j = s + g; j < e; j += G) {
-                        const uint4 pj = __ldg(a.spos + j);
-                        const float ddx = (float)(int32_t)(pj.x - pi.x) * Lu;
-                        const float ddy = (float)(int32_t)(pj.y - pi.y) * Lu;
-                        const float ddz = (float)(int32_t)(pj.z - pi.z) * Lu;
-                        const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-                        if (j == i) continue;
-                        if (r2 < rc2) {
-                            const float qj = __uint_as_float(pj.w);
-                            const float inv_r = rsqrtf(r2);
-                            const float rr = r2 * inv_r;
-                            const float erfc_v = erfcf(sa * rr);
-                            const float ex = expf(-alpha * r2);
-                            const float pot = erfc_v * inv_r;                 // erfc / r
-                            const float g_over_r = fmaf(two_sa_spi, ex, pot) * inv_r * inv_r;
-                            const float s_ = -lbqi * qj * g_over_r;
-                            fx = fmaf(s_, ddx, fx);
-                            fy = fmaf(s_, ddy, fy);
-                            fz = fmaf(s_, ddz, fz);
-                            phr = fmaf(lB * qj, pot, phr);
-                            ec = fmaf(0.5f * lbqi * qj, pot, ec);
+                        for (int k = bb[m] + g; k < ke; k += G) {
+                            const float4 sj = s_rec[k];
+                            const float dx = sj.x - px, dy = sj.y - py, dz = sj.z - pz;
+                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            if (r2 < cut2 && r2 > 0.f) {
+                                if (cnt < kNbCap)
+                                    s_nb[cnt++ * NT + threadIdx.x] = (uint32_t)k | tag;
+                                else
+                                    pair_terms(dx, dy, dz, r2, sj.w, lbqi, kc, acc);
+                            }
                         }
-                        if (r2 < lj_rc2) {
-                            const float sr2 = lj_s2 / r2;
-                            const float sr6 = sr2 * sr2 * sr2;
-                            const float mag = 24.f * lj_eps * (2.f * sr6 * sr6 - sr6) / r2;
-                            fx = fmaf(-mag, ddx, fx);
-                            fy = fmaf(-mag, ddy, fy);
-                            fz = fmaf(-mag, ddz, fz);
-                            elj += 0.5f * (4.f * lj_eps * (sr6 * sr6 - sr6) + lj_shift);
+                    }
+                }
+                for (int e = 0; e < cnt; ++e) {
+                    const uint32_t ent = s_nb[e * NT + threadIdx.x];
+                    const int k = (int)(ent & 0xFFFFFFu), r = (int)((ent >> 24) & 15u);
+                    const int code = (int)(ent >> 28);
+                    const float4 sj = s_rec[k];
+                    const float px = (code == 0) ? px_m : ((code == 1) ? pxo : px_p);
+                    const float py = pyo - cell_shift(cy, r % 3 - 1, ncd, s_corner, Lu);
+                    const float pz = pzo - cell_shift(cz, r / 3 - 1, ncd, s_corner, Lu);
+                    const float dx = sj.x - px, dy = sj.y - py, dz = sj.z - pz;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    pair_terms(dx, dy, dz, r2, sj.w, lbqi, kc, acc);
+                }
+            } else {
+                // candidates straight from the cell-sorted records
+                for (int r = 0; r < 9; ++r) {
+                    const int dzr = r / 3 - 1, dyr = r % 3 - 1;
+                    const int zz = wrapc(cz + dzr, ncd), yy = wrapc(cy + dyr, ncd);
+                    const int row = S.off_c + (zz * ncd + yy) * ncd;
+                    const float py = pyo - cell_shift(cy, dyr, ncd, s_corner, Lu);
+                    const float pz = pzo - cell_shift(cz, dzr, ncd, s_corner, Lu);
+                    for (int d = -1; d <= 1; ++d) {
+                        const int xn = wrapc(cxi + d, ncd);
+                        const float px = (d < 0) ? px_m : ((d == 0) ? pxo : px_p);
+                        const int cb = __ldg(a.cell_start + row + xn);
+                        const int ce = __ldg(a.cell_start + row + xn + 1);
+                        for (int j = cb + g; j < ce; j += G) {
+                            if (j == i) continue;
+                            const uint4 rj = __ldg(a.spos + j);
+                            const float dx = incell(rj.x, ncd, s_corner, Lu) - px;
+                            const float dy = incell(rj.y, ncd, s_corner, Lu) - py;
+                            const float dz = incell(rj.z, ncd, s_corner, Lu) - pz;
+                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            pair_terms(dx, dy, dz, r2, __uint_as_float(rj.w), lbqi, kc, acc);
                         }
                     }
                 }
             }
         }
-    }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-        fx += __shfl_down_sync(0xffffffffu, fx, o, G);
-        fy += __shfl_down_sync(0xffffffffu, fy, o, G);
-        fz += __shfl_down_sync(0xffffffffu, fz, o, G);
-        phr += __shfl_down_sync(0xffffffffu, phr, o, G);
-        ec += __shfl_down_sync(0xffffffffu, ec, o, G);
-        elj += __shfl_down_sync(0xffffffffu, elj, o, G);
-    }
-    const bool owner = active && g == 0;
-    if (owner) {
-        float phi = phr;
-        if (a.parts & kPartFourier) {
-            const float4 f = a.fs[i];
-            fx += f.x; fy += f.y; fz += f.z;
-            const double2 qs = a.qsum[tl.sys];
-            phi += f.w - (float)(2.0 * S.self_coef * (double)qi + S.bg_coef * qs.x);
+        acc.fx = lane_sum<G>(acc.fx);
+        acc.fy = lane_sum<G>(acc.fy);
+        acc.fz = lane_sum<G>(acc.fz);
+        if (want_phi) acc.phr = lane_sum<G>(acc.phr);
+        if (want_e) {
+            acc.ec = lane_sum<G>(acc.ec);
+            acc.elj = lane_sum<G>(acc.elj);
         }
-        const int o = a.perm[i];
-        if (a.F_out) a.F_out[o] = make_float4(fx, fy, fz, 0.f);
-        if (a.phi_out) a.phi_out[o] = phi;
-        if (a.md_pos) {
-            const uint64_t step = *a.cur_step;
-            const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
-            const uint4 w = philox4x32_10(
-                make_uint4((uint32_t)(o - S.off_p), 0u, (uint32_t)step, (S.stream << 8) | 0x02u),
-                key);
-            const float u1 = (float)((w.x >> 8) + 1u) * 5.9604644775390625e-08f;   // (0, 1]
-            const float u2 = (float)(w.y >> 8) * 5.9604644775390625e-08f;          // [0, 1)
-            const float u3 = (float)((w.z >> 8) + 1u) * 5.9604644775390625e-08f;
-            const float u4 = (float)(w.w >> 8) * 5.9604644775390625e-08f;
-            const float r1 = sqrtf(-2.f * logf(u1)), r3 = sqrtf(-2.f * logf(u3));
-            float s2, c2v, s4, c4;
-            sincospif(2.f * u2, &s2, &c2v);
-            sincospif(2.f * u4, &s4, &c4);
-            const float xi0 = r1 * c2v, xi1 = r1 * s2, xi2 = r3 * c4;
-            const float c1 = (float)S.c1, c2 = (float)S.c2, dtm = (float)S.dt_over_m;
-            const float dt = (float)S.dt;
-            float4 v = a.md_vel[o];
-            float4 rp = a.md_pos[o];
-            v.x = fmaf(c1, fmaf(dtm, fx, v.x), c2 * xi0);
-            v.y = fmaf(c1, fmaf(dtm, fy, v.y), c2 * xi1);
-            v.z = fmaf(c1, fmaf(dtm, fz, v.z), c2 * xi2);
-            const float L = S.Lf, invL = (float)S.invL;
-            rp.x = fmaf(dt, v.x, rp.x); rp.x -= L * floorf(rp.x * invL);
-            rp.y = fmaf(dt, v.y, rp.y); rp.y -= L * floorf(rp.y * invL);
-            rp.z = fmaf(dt, v.z, rp.z); rp.z -= L * floorf(rp.z * invL);
-            // a coordinate just below 0 can round up to exactly L: that is 0
-            if (rp.x >= L) rp.x = 0.f;
-            if (rp.y >= L) rp.y = 0.f;
-            if (rp.z >= L) rp.z = 0.f;
-            a.md_vel[o] = v;
-            a.md_pos[o] = rp;
+        if (active && g == 0) {
+            float fx = acc.fx, fy = acc.fy, fz = acc.fz, phi = acc.phr;
+            ec_own += (double)acc.ec;
+            elj_own += (double)acc.elj;
+            if (a.parts & kPartFourier) {
+                const float4 f = a.fs[o];
+                fx += f.x; fy += f.y; fz += f.z;
+                if (want_phi) {
+                    const double qs = (double)(long long)__ldcg(a.qsum_fx + sys) / kQScale;
+                    phi += f.w - (float)(2.0 * S.self_coef * (double)qi + S.bg_coef * qs);
+                }
+            }
+            if (a.F_out) a.F_out[o] = make_float4(fx, fy, fz, 0.f);
+            if (want_phi) a.phi_out[o] = phi;
+            if (a.md_pos) {
+                const uint64_t step = *a.cur_step;
+                const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
+                const uint4 w = philox4x32_10(make_uint4((uint32_t)(o - S.off_p), 0u,
+                                                         (uint32_t)step, (S.stream << 8) | 0x02u),
+                                              key);
+                const float u1 = (float)((w.x >> 8) + 1u) * 5.9604644775390625e-08f;   // (0, 1]
+                const float u2 = (float)(w.y >> 8) * 5.9604644775390625e-08f;          // [0, 1)
+                const float u3 = (float)((w.z >> 8) + 1u) * 5.9604644775390625e-08f;
+                const float u4 = (float)(w.w >> 8) * 5.9604644775390625e-08f;
+                const float r1 = sqrtf(-2.f * logf(u1)), r3 = sqrtf(-2.f * logf(u3));
+                float s2, c2v, s4, c4;
+                sincospif(2.f * u2, &s2, &c2v);
+                sincospif(2.f * u4, &s4, &c4);
+                const float xi0 = r1 * c2v, xi1 = r1 * s2, xi2 = r3 * c4;
+                const float c1 = (float)S.c1, c2 = (float)S.c2, dtm = (float)S.dt_over_m;
+                const float dt = (float)S.dt;
+                float4 v = a.md_vel[o];
+                float4 rp = a.md_pos[o];
+                v.x = fmaf(c1, fmaf(dtm, fx, v.x), c2 * xi0);
+                v.y = fmaf(c1, fmaf(dtm, fy, v.y), c2 * xi1);
+                v.z = fmaf(c1, fmaf(dtm, fz, v.z), c2 * xi2);
+                const float L = S.Lf, invL = (float)S.invL;
+                rp.x = fmaf(dt, v.x, rp.x); rp.x -= L * floorf(rp.x * invL);
+                rp.y = fmaf(dt, v.y, rp.y); rp.y -= L * floorf(rp.y * invL);
+                rp.z = fmaf(dt, v.z, rp.z); rp.z -= L * floorf(rp.z * invL);
+                // a coordinate just below 0 can round up to exactly L: that is 0
+                if (rp.x >= L) rp.x = 0.f;
+                if (rp.y >= L) rp.y = 0.f;
+                if (rp.z >= L) rp.z = 0.f;
+                a.md_vel[o] = v;
+                a.md_pos[o] = rp;
+            }
         }
     }
-    if (a.blk_e) {
-        const double2 r = block_sum2_real(owner ? (double)ec : 0.0, owner ? (double)elj : 0.0);
+    if (want_e) {
+        const double2 r = block_sum2_real(ec_own, elj_own);
         if (threadIdx.x == 0) a.blk_e[blockIdx.x] = r;
     }
 }
 
 // ----------------------------------------------------------------- FP64
-template <int G>
+template <int G, bool ONE>
 __global__ void __launch_bounds__(kBlockP)
-k_real_f64(RealArgs a) {
-    const Tile tl = a.rblk[blockIdx.x];
-    const SysDev& S = a.sys[tl.sys];
+k_real_f64(const __grid_constant__ RealArgs a) {
+    const Tile tl = tile_of<ONE>(a.w);
+    const SysDev& S = sys_of<ONE>(a.w, tl.sys);
     const int g = threadIdx.x % G;
     const int t = threadIdx.x / G;
     const bool active = t < tl.count;
@@ -278,13 +487,15 @@ k_real_f64(RealArgs a) {
     const bool owner = active && g == 0;
     if (owner) {
         double phi = phr;
-        if (a.parts & kPartFourier) {
-            const double4 f = a.fs64[i];
-            fx += f.x; fy += f.y; fz += f.z;
-            const double2 qs = a.qsum[tl.sys];
-            phi += f.w - 2.0 * S.self_coef * qi - S.bg_coef * qs.x;
-        }
         const int o = a.perm[i];
+        if (a.parts & kPartFourier) {
+            const double4 f = a.fs64[o];
+            fx += f.x; fy += f.y; fz += f.z;
+            if (a.phi_out64) {
+                const double qs = (double)(long long)__ldcg(a.qsum_fx + tl.sys) / kQScale;
+                phi += f.w - 2.0 * S.self_coef * qi - S.bg_coef * qs;
+            }
+        }
         if (a.F_out64) a.F_out64[o] = make_double4(fx, fy, fz, 0.0);
         if (a.phi_out64) a.phi_out64[o] = phi;
         if (a.md_pos64) {
@@ -327,36 +538,57 @@ k_real_f64(RealArgs a) {
 // ----------------------------------------------------------------- energy
 // One block per system: fixed-order FP64 sums of the per-k energy terms and the
 // per-block real-space / LJ partials, plus the self and background terms.
-__global__ void k_energy(const SysDev* __restrict__ sysv, const double* __restrict__ eterm,
-                         const double2* __restrict__ blk_e, const double2* __restrict__ qsum,
-                         int parts, double* __restrict__ E_out) {
-    const SysDev& S = sysv[blockIdx.x];
-    double ef = 0.0, ec = 0.0, elj = 0.0;
-    if (parts & kPartFourier)
-        for (int l = threadIdx.x; l < S.P; l += blockDim.x) ef += eterm[S.off_k + l];
+// One block per system, fixed-order FP64 sums: the estimator's Fourier terms
+// (S/P) 2 pi |rho(k)|^2 / (V k^2) from the fixed-point accumulators, the
+// self and background terms from the per-block charge sums, and the
+// real-space partials (per cell on the mixed path, per block on the FP64 one).
+template <bool ONE>
+__global__ void k_energy(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
+                         const unsigned long long* __restrict__ rho_fx,
+                         const double2* __restrict__ blk_e, const double2* __restrict__ blk_q,
+                         int parts, int per_cell, double* __restrict__ E_out) {
+    const SysDev& S = sys_of<ONE>(w, blockIdx.x);
+    double ef = 0.0, ec = 0.0, elj = 0.0, q1 = 0.0, q2 = 0.0;
+    if (parts & kPartFourier) {
+        const double tp = 2.0 * M_PI * S.invL;
+        for (int l = threadIdx.x; l < S.P; l += blockDim.x) {
+            const int4 m = ksamp[S.off_k + l];
+            const double2 r = rho_read(rho_fx + 2 * (S.off_k + l), S.rho_inv_scale);
+            const double k2 = tp * tp * ((double)m.x * m.x + (double)m.y * m.y + (double)m.z * m.z);
+            ef += 0.5 * (S.coef_scale / k2) * (r.x * r.x + r.y * r.y);
+        }
+        for (int b = threadIdx.x; b < S.nb; b += blockDim.x) {
+            const double2 v = blk_q[S.off_b + b];
+            q1 += v.x;
+            q2 += v.y;
+        }
+    }
+    const int off = per_cell ? S.off_sg : S.off_rb;
+    const int nb = per_cell ? S.nsg : S.nrb;
     if (blk_e)
-        for (int b = threadIdx.x; b < S.nrb; b += blockDim.x) {
-            const double2 v = blk_e[S.off_rb + b];
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            const double2 v = blk_e[off + b];
             ec += v.x;
             elj += v.y;
         }
-    __shared__ double sf[256], sc[256], sl[256];
+    __shared__ double sf[256], sc[256], sl[256], s1[256], s2[256];
     sf[threadIdx.x] = ef; sc[threadIdx.x] = ec; sl[threadIdx.x] = elj;
+    s1[threadIdx.x] = q1; s2[threadIdx.x] = q2;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) {
             sf[threadIdx.x] += sf[threadIdx.x + o];
             sc[threadIdx.x] += sc[threadIdx.x + o];
             sl[threadIdx.x] += sl[threadIdx.x + o];
+            s1[threadIdx.x] += s1[threadIdx.x + o];
+            s2[threadIdx.x] += s2[threadIdx.x + o];
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         double Ef = 0.0;
-        if (parts & kPartFourier) {
-            const double2 qs = qsum[blockIdx.x];
-            Ef = sf[0] - S.self_coef * qs.y - 0.5 * S.bg_coef * qs.x * qs.x;
-        }
+        if (parts & kPartFourier)
+            Ef = sf[0] - S.self_coef * s2[0] - 0.5 * S.bg_coef * s1[0] * s1[0];
         const double Ec = (parts & kPartReal) ? sc[0] : 0.0;
         const double El = (parts & kPartLJ) ? sl[0] : 0.0;
         E_out[4 * blockIdx.x + 0] = Ef + Ec + El;
@@ -366,34 +598,74 @@ __global__ void k_energy(const SysDev* __restrict__ sysv, const double* __restri
     }
 }
 
-void launch_real_mixed(cudaStream_t st, const RealArgs& a) {
-    if (a.nrblk <= 0) return;
-    switch (a.split) {
-        case 2: k_real_mixed<2><<<a.nrblk, kBlockP, 0, st>>>(a); break;
-        case 4: k_real_mixed<4><<<a.nrblk, kBlockP, 0, st>>>(a); break;
-        case 8: k_real_mixed<8><<<a.nrblk, kBlockP, 0, st>>>(a); break;
-        case 16: k_real_mixed<16><<<a.nrblk, kBlockP, 0, st>>>(a); break;
-        case 32: k_real_mixed<32><<<a.nrblk, kBlockP, 0, st>>>(a); break;
-        default: k_real_mixed<1><<<a.nrblk, kBlockP, 0, st>>>(a); break;
+// Dynamic shared memory of the segment kernel for a staging capacity.
+size_t real_seg_smem(int stage_cap, int seg_max, int nt) {
+    return sizeof(float4) * (size_t)stage_cap + sizeof(uint32_t) * kNbCap * (size_t)nt +
+           sizeof(int) * 9 * (size_t)(seg_max + 3);
+}
+
+template <int G, int NT>
+static void real_mixed_gn(cudaStream_t st, bool one, const RealArgs& a) {
+    const size_t smem = real_seg_smem(a.stage_cap, a.seg_max, NT);
+    if (one) {
+        cudaFuncSetAttribute(k_real_seg<G, true, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        k_real_seg<G, true, NT><<<a.nseg, NT, smem, st>>>(a);
+    } else {
+        cudaFuncSetAttribute(k_real_seg<G, false, NT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_real_seg<G, false, NT><<<a.nseg, NT, smem, st>>>(a);
     }
 }
 
-void launch_real_f64(cudaStream_t st, const RealArgs& a) {
-    if (a.nrblk <= 0) return;
+// Block size: about one thread group per particle of a segment, 64 .. 256.
+template <int G>
+static void real_mixed_g(cudaStream_t st, bool one, const RealArgs& a) {
+    if (a.seg_threads >= 256) real_mixed_gn<G, 256>(st, one, a);
+    else if (a.seg_threads >= 128) real_mixed_gn<G, 128>(st, one, a);
+    else real_mixed_gn<G, 64>(st, one, a);
+}
+
+template <int G>
+static void real_f64_g(cudaStream_t st, bool one, const RealArgs& a) {
+    if (one) k_real_f64<G, true><<<a.nrblk, kBlockP, 0, st>>>(a);
+    else k_real_f64<G, false><<<a.nrblk, kBlockP, 0, st>>>(a);
+}
+
+void launch_real_mixed(cudaStream_t st, bool one, const RealArgs& a) {
+    if (a.nseg <= 0) return;
     switch (a.split) {
-        case 2: k_real_f64<2><<<a.nrblk, kBlockP, 0, st>>>(a); break;
-        case 4: k_real_f64<4><<<a.nrblk, kBlockP, 0, st>>>(a); break;
-        case 8: k_real_f64<8><<<a.nrblk, kBlockP, 0, st>>>(a); break;
-        case 16: k_real_f64<16><<<a.nrblk, kBlockP, 0, st>>>(a); break;
-        case 32: k_real_f64<32><<<a.nrblk, kBlockP, 0, st>>>(a); break;
-        default: k_real_f64<1><<<a.nrblk, kBlockP, 0, st>>>(a); break;
+        case 2: real_mixed_g<2>(st, one, a); break;
+        case 4: real_mixed_g<4>(st, one, a); break;
+        case 8: real_mixed_g<8>(st, one, a); break;
+        case 16: real_mixed_g<16>(st, one, a); break;
+        case 32: real_mixed_g<32>(st, one, a); break;
+        default: real_mixed_g<1>(st, one, a); break;
     }
 }
 
-void launch_energy(cudaStream_t st, const SysDev* sys, int nsys, const double* eterm,
-                   const double2* blk_e, const double2* qsum, int parts, double* E_out) {
+void launch_real_f64(cudaStream_t st, bool one, const RealArgs& a) {
+    if (a.nrblk <= 0) return;
+    switch (a.split) {
+        case 2: real_f64_g<2>(st, one, a); break;
+        case 4: real_f64_g<4>(st, one, a); break;
+        case 8: real_f64_g<8>(st, one, a); break;
+        case 16: real_f64_g<16>(st, one, a); break;
+        case 32: real_f64_g<32>(st, one, a); break;
+        default: real_f64_g<1>(st, one, a); break;
+    }
+}
+
+void launch_energy(cudaStream_t st, bool one, const Work& w, int nsys, const int4* ksamp,
+                   const unsigned long long* rho_fx, const double2* blk_e,
+                   const double2* blk_q, int parts, int per_cell, double* E_out) {
     if (nsys <= 0) return;
-    k_energy<<<nsys, 256, 0, st>>>(sys, eterm, blk_e, qsum, parts, E_out);
+    if (one)
+        k_energy<true><<<nsys, 256, 0, st>>>(w, ksamp, rho_fx, blk_e, blk_q, parts, per_cell,
+                                             E_out);
+    else
+        k_energy<false><<<nsys, 256, 0, st>>>(w, ksamp, rho_fx, blk_e, blk_q, parts, per_cell,
+                                              E_out);
 }
 
 }  // namespace rbe

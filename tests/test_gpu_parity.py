@@ -241,7 +241,13 @@ def test_tuning_does_not_change_results_beyond_rounding(rbe, c2):
         assert rel_rms(F[:, :3].cpu().numpy(), ref["F"]) <= TOL_MIXED, (chunk, split, rsplit)
         assert energy_rel(E.cpu().numpy()[0], ref["E"]) <= TOL_E_MIXED
         if chunk:
-            assert h.get_tuning() == (chunk, split, rsplit)
-    c, s, r = h.autotune(x)
-    assert c >= 32 and s in (1, 2, 4, 8) and r in (1, 2, 4, 8, 16, 32)
-    assert h.get_tuning() == (c, s, r)
+            assert h.get_tuning()[:3] == (chunk, split, rsplit)
+    for seg in (1, 2, 9):
+        h.set_tuning(128, 2, 4, seg)
+        F, E, _ = h.forces(x, 6)
+        assert rel_rms(F[:, :3].cpu().numpy(), ref["F"]) <= TOL_MIXED, seg
+        assert energy_rel(E.cpu().numpy()[0], ref["E"]) <= TOL_E_MIXED
+        assert h.get_tuning()[3] == seg
+    c, s, r, sg = h.autotune(x)
+    assert c >= 32 and s in (1, 2, 4, 8) and r in (1, 2, 4, 8, 16, 32) and sg >= 1
+    assert h.get_tuning() == (c, s, r, sg)
