@@ -291,21 +291,20 @@ k_real_seg(const __grid_constant__ RealArgs a) {
                     const float py = pyo - cell_shift(cy, r % 3 - 1, ncd, s_corner, Lu);
                     const float pz = pzo - cell_shift(cz, r / 3 - 1, ncd, s_corner, Lu);
                     const int* bb = s_b + r * bstride + u;
-#pragma unroll
-                    for (int m = 0; m < 3; ++m) {              // cells x-1, x, x+1 of the row
-                        const float px = (m == 0) ? px_m : ((m == 1) ? pxo : px_p);
-                        const int ke = bb[m + 1];
-                        const uint32_t tag = ((uint32_t)r << 24) | ((uint32_t)m << 28);
+                    const int b1 = bb[1], b2 = bb[2], b3 = bb[3];
+                    const uint32_t tag = (uint32_t)r << 24;
 #pragma unroll 2
-                        for (int k = bb[m] + g; k < ke; k += G) {
-                            const float4 sj = s_rec[k];
-                            const float dx = sj.x - px, dy = sj.y - py, dz = sj.z - pz;
-                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            if (r2 < cut2 && r2 > 0.f) {
-                                if (cnt < kNbCap)
-                                    s_nb[cnt++ * NT + threadIdx.x] = (uint32_t)k | tag;
-                                else
-                                    pair_terms(dx, dy, dz, r2, sj.w, lbqi, kc, acc);
+                    for (int k = bb[0] + g; k < b3; k += G) {   // cells x-1, x, x+1 of the row
+                        const float4 sj = s_rec[k];
+                        const float px = (k < b1) ? px_m : ((k < b2) ? pxo : px_p);
+                        const float dx = sj.x - px, dy = sj.y - py, dz = sj.z - pz;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        if (r2 < cut2 && r2 > 0.f) {
+                            if (cnt < kNbCap) {
+                                const uint32_t m = (k < b1) ? 0u : ((k < b2) ? 1u : 2u);
+                                s_nb[cnt++ * NT + threadIdx.x] = (uint32_t)k | tag | (m << 28);
+                            } else {
+                                pair_terms(dx, dy, dz, r2, sj.w, lbqi, kc, acc);
                             }
                         }
                     }
