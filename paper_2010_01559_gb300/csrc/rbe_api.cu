@@ -153,6 +153,8 @@ struct rbe_ctx {
     int* d_cell_start = nullptr;
     int4* d_ksamp = nullptr;
     unsigned long long* d_rho_fx = nullptr;   // rho(k) accumulators (fixed point)
+    int* d_kcnt = nullptr;                    // per k tile: chunks done (rho kernel)
+    float2* d_kab = nullptr;                  // FP32 force coefficients per k
     unsigned long long* d_qsum_fx = nullptr;  // sum q per system (fixed point)
     double2* d_blk_e = nullptr;
     double2* d_blk_q = nullptr;
@@ -262,6 +264,20 @@ void fill_sysdev(const SysHost& s, SysDev& d) {
     while (e > 20 && bound * std::ldexp(1.0, e) >= std::ldexp(1.0, 62)) --e;
     d.rho_scale = std::ldexp(1.0, e);
     d.rho_inv_scale = std::ldexp(1.0, -e);
+    d.f_rc2 = (float)(d.r_c * d.r_c);
+    d.f_lj_rc2 = (float)d.lj_rcut2;
+    d.f_alpha = (float)d.alpha;
+    d.f_sqrt_alpha = (float)d.sqrt_alpha;
+    d.f_two_sa_spi = (float)(2.0 * d.sqrt_alpha / std::sqrt(M_PI));
+    d.f_lB = (float)d.lB;
+    d.f_lj_sigma2 = (float)d.lj_sigma2;
+    d.f_lj_eps = (float)d.lj_eps;
+    d.f_lj_shift = (float)d.lj_shift;
+    d.f_c1 = (float)d.c1;
+    d.f_c2 = (float)d.c2;
+    d.f_dt = (float)d.dt;
+    d.f_dt_over_m = (float)d.dt_over_m;
+    d.f_invL = (float)d.invL;
 }
 
 int auto_chunk(const rbe_ctx* h, long long ntot) {
@@ -462,6 +478,8 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_ALLOC(h->d_cell_start, h->ncell + 1);
     RBE_ALLOC(h->d_ksamp, h->ktot);
     RBE_ALLOC(h->d_rho_fx, 2 * (size_t)h->ktot);
+    RBE_ALLOC(h->d_kcnt, h->ktot);
+    RBE_ALLOC(h->d_kab, h->ktot);
     RBE_ALLOC(h->d_qsum_fx, h->nsys);
     RBE_ALLOC(h->d_blk_e, std::max<long long>(rb, h->ncell + 1));
     RBE_ALLOC(h->d_blk_q, pb);
@@ -477,6 +495,7 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_CUDA(h, cudaMemset(h->d_err, 0, sizeof(int)));
     RBE_CUDA(h, cudaMemset(h->d_qsum_fx, 0, sizeof(unsigned long long) * h->nsys));
     RBE_CUDA(h, cudaMemset(h->d_rho_fx, 0, sizeof(unsigned long long) * 2 * h->ktot));
+    RBE_CUDA(h, cudaMemset(h->d_kcnt, 0, sizeof(int) * h->ktot));
     std::vector<uint64_t> tab;
     std::vector<int> kstart, cstart;
     for (auto& s : h->sys) {
@@ -508,8 +527,8 @@ void release(rbe_ctx* h) {
                     h->d_cstart,
                     h->d_table, h->d_fx, h->d_spos, h->d_fx64, h->d_spos64, h->d_cid, h->d_rank,
                     h->d_perm, h->d_perm_tmp, h->d_fs, h->d_fs64, h->d_cell_cnt,
-                    h->d_cell_start, h->d_ksamp, h->d_rho_fx, h->d_qsum_fx,
-                    h->d_blk_e, h->d_blk_q, h->d_cur_step, h->d_stage_step,
+                    h->d_cell_start, h->d_ksamp, h->d_rho_fx, h->d_kcnt, h->d_kab,
+                    h->d_qsum_fx, h->d_blk_e, h->d_blk_q, h->d_cur_step, h->d_stage_step,
                     h->d_err, h->d_stage_pos, h->d_stage_vel, h->d_stage_F, h->d_stage_E};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -648,7 +667,7 @@ void launch_rho(const rbe_ctx* h, cudaStream_t st, bool mixed) {
     const Work w = make_work(h, h->d_chunks, h->cur_chunk, 1);
     if (mixed)
         launch_rho_mixed(st, one, w, h->nchunks, ltiles, h->tab_smem, h->d_table, h->d_cur_step,
-                         h->d_fx, h->d_rho_fx, h->d_ksamp, h->d_err);
+                         h->d_fx, h->d_rho_fx, h->d_ksamp, h->d_kcnt, h->d_kab, h->d_err);
     else
         launch_rho_f64(st, one, w, h->nchunks, ltiles, h->tab_smem, h->d_table, h->d_cur_step,
                        h->d_fx64, h->d_rho_fx, h->d_ksamp, h->d_err);
@@ -659,7 +678,7 @@ void launch_force(const rbe_ctx* h, cudaStream_t st, bool mixed) {
     if (mixed) {
         const Work w = make_work(h, h->split == 1 ? h->d_pblk : h->d_fblk, kBlockP / h->split, 0);
         launch_fourier_force_mixed(st, one, w, h->split == 1 ? h->npblk : h->nfblk, h->split,
-                                   h->d_fx, h->d_ksamp, h->d_rho_fx, h->d_fs);
+                                   h->d_fx, h->d_ksamp, h->d_kab, h->d_fs);
     } else {
         const Work w = make_work(h, h->d_pblk, kBlockP, 0);
         launch_fourier_force_f64(st, one, w, h->npblk, h->d_fx64, h->d_ksamp, h->d_rho_fx,

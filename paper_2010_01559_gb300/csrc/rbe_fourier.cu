@@ -99,13 +99,24 @@ __global__ void k_sample(const SysDev* __restrict__ sysv, int nsys, int ktot,
     ksamp[g] = sample_one(S, table + S.off_t, g - S.off_k, *cur_step, err);
 }
 
+// Force coefficients of wave vector m: coef = lB (S/P) 4 pi / (V k^2) times
+// (Im rho, Re rho), from the fixed-point rho(k) accumulator, in FP64.
+__device__ __forceinline__ double2 kcoef(const SysDev& S, int4 m,
+                                         const unsigned long long* __restrict__ rho) {
+    const double2 r = rho_read(rho, S.rho_inv_scale);
+    const double tp = 2.0 * M_PI * S.invL;
+    const double k2 = tp * tp * ((double)m.x * m.x + (double)m.y * m.y + (double)m.z * m.z);
+    const double coef = S.coef_scale / k2;
+    return make_double2(coef * r.y, coef * r.x);
+}
+
 // ----------------------------------------------------------------- rho (mixed)
 template <bool ONE>
 __global__ void __launch_bounds__(kLTile)
 k_rho_mixed(const __grid_constant__ Work w, int tab_smem, const uint64_t* __restrict__ table,
             const uint64_t* __restrict__ cur_step, const uint4* __restrict__ fx,
             unsigned long long* __restrict__ rho_fx, int4* __restrict__ ksamp,
-            int* __restrict__ err) {
+            int* __restrict__ kcnt, float2* __restrict__ kab, int* __restrict__ err) {
     __shared__ uint4 sp[kStage];
     extern __shared__ uint32_t s_tab[];
     const Tile ch = tile_of<ONE>(w);
@@ -145,6 +156,25 @@ k_rho_mixed(const __grid_constant__ Work w, int tab_smem, const uint64_t* __rest
         }
     }
     if (active) rho_accumulate(rho_fx + 2 * (S.off_k + l), (double)re, (double)im, S.rho_scale);
+    // The last of the system's chunks to add its partials for this tile of
+    // wave vectors finds rho(k) complete and turns it into the FP32 force
+    // coefficients (A, B) of Eq. rbmapprox, once per k instead of once per
+    // force block.  Fence, then count: every chunk's atomics are visible to
+    // the block that takes the last count (no waiting on other blocks).
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    const int slot = S.off_k + blockIdx.y * kLTile;
+    if (threadIdx.x == 0) s_last = atomicAdd(kcnt + slot, 1) == S.nchunk - 1;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        if (active) {
+            const double2 ab = kcoef(S, m, rho_fx + 2 * (S.off_k + l));
+            kab[S.off_k + l] = make_float2((float)ab.x, (float)ab.y);
+        }
+        if (threadIdx.x == 0) kcnt[slot] = 0;        // ready for the next evaluation
+    }
 }
 
 // ----------------------------------------------------------------- rho (FP64)
@@ -193,17 +223,6 @@ k_rho_f64(const __grid_constant__ Work w, int tab_smem, const uint64_t* __restri
     if (active) rho_accumulate(rho_fx + 2 * (S.off_k + l), re, im, S.rho_scale);
 }
 
-// Force coefficients of wave vector m: coef = lB (S/P) 4 pi / (V k^2) times
-// (Im rho, Re rho), from the fixed-point rho(k) accumulator, in FP64.
-__device__ __forceinline__ double2 kcoef(const SysDev& S, int4 m,
-                                         const unsigned long long* __restrict__ rho) {
-    const double2 r = rho_read(rho, S.rho_inv_scale);
-    const double tp = 2.0 * M_PI * S.invL;
-    const double k2 = tp * tp * ((double)m.x * m.x + (double)m.y * m.y + (double)m.z * m.z);
-    const double coef = S.coef_scale / k2;
-    return make_double2(coef * r.y, coef * r.x);
-}
-
 // ----------------------------------------------------------------- force (mixed)
 // Shared-memory record per wave vector: the integer m (phase) and, as floats,
 // m (direction) with the two coefficients A = coef Im rho, B = coef Re rho.
@@ -213,7 +232,7 @@ struct KForce { float mx, my, mz, A; };
 template <int SPLIT, bool ONE>
 __global__ void __launch_bounds__(kBlockP)
 k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
-              const int4* __restrict__ ksamp, const unsigned long long* __restrict__ rho_fx,
+              const int4* __restrict__ ksamp, const float2* __restrict__ kab,
               float4* __restrict__ fs) {
     constexpr int kKT = 256;                        // wave vectors staged per pass
     __shared__ KPhase kp[kKT];
@@ -233,10 +252,10 @@ k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
         __syncthreads();
         for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
             const int4 m = ksamp[S.off_k + base + k];
-            const double2 ab = kcoef(S, m, rho_fx + 2 * (S.off_k + base + k));
+            const float2 ab = kab[S.off_k + base + k];
             kp[k] = KPhase{(uint32_t)m.x, (uint32_t)m.y, (uint32_t)m.z, 0u};
-            kf[k] = KForce{(float)m.x, (float)m.y, (float)m.z, (float)ab.x};
-            kb[k] = (float)ab.y;
+            kf[k] = KForce{(float)m.x, (float)m.y, (float)m.z, ab.x};
+            kb[k] = ab.y;
         }
         __syncthreads();
 #pragma unroll 4
@@ -264,7 +283,7 @@ k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
     }
     if (active && sub == 0) {
         const float q = __uint_as_float(p.w);
-        const float sc = -q * (float)(2.0 * M_PI) * (float)S.invL;
+        const float sc = -q * (float)(2.0 * M_PI) * S.f_invL;
         fs[i] = make_float4(sc * fx, sc * fy, sc * fz, ph);
     }
 }
@@ -326,16 +345,17 @@ void launch_sample(cudaStream_t st, const SysDev* sys, int nsys, int ktot, const
 // systems), 0 to search the table in global memory.
 void launch_rho_mixed(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
                       int tab_smem, const uint64_t* table, const uint64_t* cur_step,
-                      const uint4* fx, unsigned long long* rho_fx, int4* ksamp, int* err) {
+                      const uint4* fx, unsigned long long* rho_fx, int4* ksamp, int* kcnt,
+                      float2* kab, int* err) {
     if (nchunks <= 0 || ltiles <= 0) return;
     dim3 grid(nchunks, ltiles);
     const size_t smem = sizeof(uint32_t) * tab_smem;
     if (one)
         k_rho_mixed<true><<<grid, kLTile, smem, st>>>(w, tab_smem > 0, table, cur_step, fx,
-                                                      rho_fx, ksamp, err);
+                                                      rho_fx, ksamp, kcnt, kab, err);
     else
         k_rho_mixed<false><<<grid, kLTile, smem, st>>>(w, tab_smem > 0, table, cur_step, fx,
-                                                       rho_fx, ksamp, err);
+                                                       rho_fx, ksamp, kcnt, kab, err);
 }
 
 void launch_rho_f64(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
@@ -354,22 +374,22 @@ void launch_rho_f64(cudaStream_t st, bool one, const Work& w, int nchunks, int l
 
 template <int SPLIT>
 static void force_mixed_split(cudaStream_t st, bool one, const Work& w, int nblk, const uint4* fx,
-                              const int4* ksamp, const unsigned long long* rho_fx, float4* fs) {
+                              const int4* ksamp, const float2* kab, float4* fs) {
     if (one)
-        k_force_mixed<SPLIT, true><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, rho_fx, fs);
+        k_force_mixed<SPLIT, true><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, kab, fs);
     else
-        k_force_mixed<SPLIT, false><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, rho_fx, fs);
+        k_force_mixed<SPLIT, false><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, kab, fs);
 }
 
 void launch_fourier_force_mixed(cudaStream_t st, bool one, const Work& w, int nblk, int split,
-                                const uint4* fx, const int4* ksamp,
-                                const unsigned long long* rho_fx, float4* fs) {
+                                const uint4* fx, const int4* ksamp, const float2* kab,
+                                float4* fs) {
     if (nblk <= 0) return;
     switch (split) {
-        case 2: force_mixed_split<2>(st, one, w, nblk, fx, ksamp, rho_fx, fs); break;
-        case 4: force_mixed_split<4>(st, one, w, nblk, fx, ksamp, rho_fx, fs); break;
-        case 8: force_mixed_split<8>(st, one, w, nblk, fx, ksamp, rho_fx, fs); break;
-        default: force_mixed_split<1>(st, one, w, nblk, fx, ksamp, rho_fx, fs); break;
+        case 2: force_mixed_split<2>(st, one, w, nblk, fx, ksamp, kab, fs); break;
+        case 4: force_mixed_split<4>(st, one, w, nblk, fx, ksamp, kab, fs); break;
+        case 8: force_mixed_split<8>(st, one, w, nblk, fx, ksamp, kab, fs); break;
+        default: force_mixed_split<1>(st, one, w, nblk, fx, ksamp, kab, fs); break;
     }
 }
 

@@ -59,7 +59,27 @@ struct SysDev {
     int off_b, nb;          // first per-particle block and block count (prep)
     int off_rb, nrb;        // first real-space block and block count (FP64 path)
     int off_sg, nsg;        // first real-space segment and segment count (mixed path)
+    // FP32 copies of the pair and Langevin constants, rounded once on the host
+    // (kernels then hold no double-to-float conversions)
+    float f_rc2, f_lj_rc2, f_alpha, f_sqrt_alpha, f_two_sa_spi, f_lB;
+    float f_lj_sigma2, f_lj_eps, f_lj_shift;
+    float f_c1, f_c2, f_dt, f_dt_over_m, f_invL;
 };
+
+// Unsigned 32-bit integer to the nearest float, as (float)x rounds it, on the
+// FP32/integer pipes: each 16-bit half is exact as 2^23 + half - 2^23, and the
+// FMA forms hi * 2^16 + lo exactly before its single rounding.
+__device__ __forceinline__ float u32_to_f32(uint32_t x) {
+    const float hi = __uint_as_float(0x4B000000u | (x >> 16)) - 8388608.0f;
+    const float lo = __uint_as_float(0x4B000000u | (x & 0xFFFFu)) - 8388608.0f;
+    return fmaf(hi, 65536.0f, lo);
+}
+
+// Signed counterpart (|x| < 2^31): round-to-nearest is symmetric in the sign.
+__device__ __forceinline__ float s32_to_f32(int32_t x) {
+    const float a = u32_to_f32(x < 0 ? 0u - (uint32_t)x : (uint32_t)x);
+    return x < 0 ? -a : a;
+}
 
 // A tile of particles of one system: (system, first particle, count, aux).
 // aux = first partial index (chunks) or unused (particle blocks).
@@ -166,13 +186,14 @@ __device__ __forceinline__ double2 rho_read(const unsigned long long* src, doubl
 
 void launch_rho_mixed(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
                       int tab_smem, const uint64_t* table, const uint64_t* cur_step,
-                      const uint4* fx, unsigned long long* rho_fx, int4* ksamp, int* err);
+                      const uint4* fx, unsigned long long* rho_fx, int4* ksamp, int* kcnt,
+                      float2* kab, int* err);
 void launch_rho_f64(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
                     int tab_smem, const uint64_t* table, const uint64_t* cur_step,
                     const double4* fx64, unsigned long long* rho_fx, int4* ksamp, int* err);
 void launch_fourier_force_mixed(cudaStream_t st, bool one, const Work& w, int nblk, int split,
-                                const uint4* fx, const int4* ksamp,
-                                const unsigned long long* rho_fx, float4* fs);
+                                const uint4* fx, const int4* ksamp, const float2* kab,
+                                float4* fs);
 void launch_fourier_force_f64(cudaStream_t st, bool one, const Work& w, int nblk,
                               const double4* fx64, const int4* ksamp,
                               const unsigned long long* rho_fx, double4* fs64);

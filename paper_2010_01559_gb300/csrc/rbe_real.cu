@@ -141,14 +141,14 @@ __device__ __forceinline__ float lane_sum(float v) {
 // a particle meets itself at distance exactly 0.
 __device__ __forceinline__ float incell(uint32_t s, int ncd, const uint32_t* corner, float Lu) {
     const int c = (int)(((unsigned long long)s * (unsigned long long)ncd) >> 32);
-    return __fmul_rn((float)(s - corner[c]), Lu);
+    return __fmul_rn(u32_to_f32(s - corner[c]), Lu);
 }
 
 // Corner-to-corner distance from cell c to cell wrap(c + d), d in {-1, 0, 1}.
 __device__ __forceinline__ float cell_shift(int c, int d, int ncd, const uint32_t* corner,
                                             float Lu) {
     const int cn = wrapc(c + d, ncd);
-    return __fmul_rn((float)(int32_t)(corner[cn] - corner[c]), Lu);
+    return __fmul_rn(s32_to_f32((int32_t)(corner[cn] - corner[c])), Lu);
 }
 
 // One block per segment: nseg x-adjacent cells of one (y, z) row (the whole row
@@ -252,16 +252,19 @@ k_real_seg(const __grid_constant__ RealArgs a) {
     }
     __syncthreads();
     PairConst kc;
-    kc.rc2 = do_real ? (float)(S.r_c * S.r_c) : 0.f;
-    kc.lj_rc2 = do_lj ? (float)S.lj_rcut2 : 0.f;
-    kc.alpha = (float)S.alpha;
-    kc.sa = (float)S.sqrt_alpha;
-    kc.two_sa_spi = (float)(2.0 * S.sqrt_alpha / 1.7724538509055160);
-    kc.lB = (float)S.lB;
-    kc.lj_s2 = (float)S.lj_sigma2;
-    kc.lj_eps = (float)S.lj_eps;
-    kc.lj_shift = (float)S.lj_shift;
+    kc.rc2 = do_real ? S.f_rc2 : 0.f;
+    kc.lj_rc2 = do_lj ? S.f_lj_rc2 : 0.f;
+    kc.alpha = S.f_alpha;
+    kc.sa = S.f_sqrt_alpha;
+    kc.two_sa_spi = S.f_two_sa_spi;
+    kc.lB = S.f_lB;
+    kc.lj_s2 = S.f_lj_sigma2;
+    kc.lj_eps = S.f_lj_eps;
+    kc.lj_shift = S.f_lj_shift;
     const float cut2 = fmaxf(kc.rc2, kc.lj_rc2);
+    // the segment's (y, z) row is fixed: shifts to the rows below and above
+    const float sy_m = cell_shift(cy, -1, ncd, s_corner, Lu), sy_p = cell_shift(cy, 1, ncd, s_corner, Lu);
+    const float sz_m = cell_shift(cz, -1, ncd, s_corner, Lu), sz_p = cell_shift(cz, 1, ncd, s_corner, Lu);
     const bool want_phi = a.phi_out != nullptr;
     const bool want_e = a.blk_e != nullptr;
     const int g = threadIdx.x % G;
@@ -288,8 +291,9 @@ k_real_seg(const __grid_constant__ RealArgs a) {
                 int cnt = 0;
 #pragma unroll 1
                 for (int r = 0; r < 9; ++r) {
-                    const float py = pyo - cell_shift(cy, r % 3 - 1, ncd, s_corner, Lu);
-                    const float pz = pzo - cell_shift(cz, r / 3 - 1, ncd, s_corner, Lu);
+                    const int ry = r % 3, rz = r / 3;
+                    const float py = pyo - (ry == 0 ? sy_m : (ry == 1 ? 0.f : sy_p));
+                    const float pz = pzo - (rz == 0 ? sz_m : (rz == 1 ? 0.f : sz_p));
                     const int* bb = s_b + r * bstride + u;
                     const int b1 = bb[1], b2 = bb[2], b3 = bb[3];
                     const uint32_t tag = (uint32_t)r << 24;
@@ -314,9 +318,10 @@ k_real_seg(const __grid_constant__ RealArgs a) {
                     const int k = (int)(ent & 0xFFFFFFu), r = (int)((ent >> 24) & 15u);
                     const int code = (int)(ent >> 28);
                     const float4 sj = s_rec[k];
+                    const int ry = r % 3, rz = r / 3;
                     const float px = (code == 0) ? px_m : ((code == 1) ? pxo : px_p);
-                    const float py = pyo - cell_shift(cy, r % 3 - 1, ncd, s_corner, Lu);
-                    const float pz = pzo - cell_shift(cz, r / 3 - 1, ncd, s_corner, Lu);
+                    const float py = pyo - (ry == 0 ? sy_m : (ry == 1 ? 0.f : sy_p));
+                    const float pz = pzo - (rz == 0 ? sz_m : (rz == 1 ? 0.f : sz_p));
                     const float dx = sj.x - px, dy = sj.y - py, dz = sj.z - pz;
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                     pair_terms(dx, dy, dz, r2, sj.w, lbqi, kc, acc);
@@ -327,8 +332,8 @@ k_real_seg(const __grid_constant__ RealArgs a) {
                     const int dzr = r / 3 - 1, dyr = r % 3 - 1;
                     const int zz = wrapc(cz + dzr, ncd), yy = wrapc(cy + dyr, ncd);
                     const int row = S.off_c + (zz * ncd + yy) * ncd;
-                    const float py = pyo - cell_shift(cy, dyr, ncd, s_corner, Lu);
-                    const float pz = pzo - cell_shift(cz, dzr, ncd, s_corner, Lu);
+                    const float py = pyo - (dyr < 0 ? sy_m : (dyr == 0 ? 0.f : sy_p));
+                    const float pz = pzo - (dzr < 0 ? sz_m : (dzr == 0 ? 0.f : sz_p));
                     for (int d = -1; d <= 1; ++d) {
                         const int xn = wrapc(cxi + d, ncd);
                         const float px = (d < 0) ? px_m : ((d == 0) ? pxo : px_p);
@@ -357,8 +362,10 @@ k_real_seg(const __grid_constant__ RealArgs a) {
         }
         if (active && g == 0) {
             float fx = acc.fx, fy = acc.fy, fz = acc.fz, phi = acc.phr;
-            ec_own += (double)acc.ec;
-            elj_own += (double)acc.elj;
+            if (want_e) {
+                ec_own += (double)acc.ec;
+                elj_own += (double)acc.elj;
+            }
             if (a.parts & kPartFourier) {
                 const float4 f = a.fs[o];
                 fx += f.x; fy += f.y; fz += f.z;
@@ -375,23 +382,23 @@ k_real_seg(const __grid_constant__ RealArgs a) {
                 const uint4 w = philox4x32_10(make_uint4((uint32_t)(o - S.off_p), 0u,
                                                          (uint32_t)step, (S.stream << 8) | 0x02u),
                                               key);
-                const float u1 = (float)((w.x >> 8) + 1u) * 5.9604644775390625e-08f;   // (0, 1]
-                const float u2 = (float)(w.y >> 8) * 5.9604644775390625e-08f;          // [0, 1)
-                const float u3 = (float)((w.z >> 8) + 1u) * 5.9604644775390625e-08f;
-                const float u4 = (float)(w.w >> 8) * 5.9604644775390625e-08f;
+                const float u1 = u32_to_f32((w.x >> 8) + 1u) * 5.9604644775390625e-08f;   // (0, 1]
+                const float u2 = u32_to_f32(w.y >> 8) * 5.9604644775390625e-08f;          // [0, 1)
+                const float u3 = u32_to_f32((w.z >> 8) + 1u) * 5.9604644775390625e-08f;
+                const float u4 = u32_to_f32(w.w >> 8) * 5.9604644775390625e-08f;
                 const float r1 = sqrtf(-2.f * logf(u1)), r3 = sqrtf(-2.f * logf(u3));
                 float s2, c2v, s4, c4;
                 sincospif(2.f * u2, &s2, &c2v);
                 sincospif(2.f * u4, &s4, &c4);
                 const float xi0 = r1 * c2v, xi1 = r1 * s2, xi2 = r3 * c4;
-                const float c1 = (float)S.c1, c2 = (float)S.c2, dtm = (float)S.dt_over_m;
-                const float dt = (float)S.dt;
+                const float c1 = S.f_c1, c2 = S.f_c2, dtm = S.f_dt_over_m;
+                const float dt = S.f_dt;
                 float4 v = a.md_vel[o];
                 float4 rp = a.md_pos[o];
                 v.x = fmaf(c1, fmaf(dtm, fx, v.x), c2 * xi0);
                 v.y = fmaf(c1, fmaf(dtm, fy, v.y), c2 * xi1);
                 v.z = fmaf(c1, fmaf(dtm, fz, v.z), c2 * xi2);
-                const float L = S.Lf, invL = (float)S.invL;
+                const float L = S.Lf, invL = S.f_invL;
                 rp.x = fmaf(dt, v.x, rp.x); rp.x -= L * floorf(rp.x * invL);
                 rp.y = fmaf(dt, v.y, rp.y); rp.y -= L * floorf(rp.y * invL);
                 rp.z = fmaf(dt, v.z, rp.z); rp.z -= L * floorf(rp.z * invL);
