@@ -198,7 +198,9 @@ rbe_status rbe_sync(rbe_handle h);
 typedef struct {
     int32_t rho_chunk;     /* particles per structure-factor chunk: power of two in [32, 8192] */
     int32_t force_split;   /* threads per particle in the Fourier-force pass: 1, 2, 4 or 8     */
-    int32_t real_split;    /* threads per particle in the real-space pass: 1..32, power of two  */
+    int32_t real_split;    /* threads per particle in the mixed real-space pass: 1, 3 or 9,
+                              each scanning 9 / real_split of the 9 neighbour rows (the FP64
+                              pass uses the largest power of two not above it)             */
     int32_t real_seg;      /* cells along x per real-space block: 1 .. cells per edge           */
 } rbe_tuning;
 

@@ -278,6 +278,9 @@ void fill_sysdev(const SysHost& s, SysDev& d) {
     d.f_dt = (float)d.dt;
     d.f_dt_over_m = (float)d.dt_over_m;
     d.f_invL = (float)d.invL;
+    d.f_inv_Lu = (float)(4294967296.0 / L);
+    d.corner_q = (uint32_t)(4294967296ull / (unsigned long long)std::max(1, s.ncd));
+    d.corner_r = (uint32_t)(4294967296ull - (unsigned long long)d.corner_q * std::max(1, s.ncd));
 }
 
 int auto_chunk(const rbe_ctx* h, long long ntot) {
@@ -296,17 +299,15 @@ int auto_split(long long ntot) {
     return s;
 }
 
-// Threads per particle of the real-space pass: the mixed path runs one block
-// of 64 threads per cell, so give each particle of an average cell
-// 64 / (next power of two of the mean occupancy) threads.
-int auto_real_split(long long ntot, long long ncell) {
-    // at least a few candidates per lane; more lanes when there are few particles
-    const long long target_threads = 152LL * 2048;
-    int s = 1;
-    while (s < 8 && ntot * s * 2 <= target_threads) s <<= 1;
-    (void)ncell;
-    return s;
+// Threads per particle of the mixed real-space pass (each takes 9/R of the 9
+// neighbour rows): 9 while that still leaves few threads per SM, else 3.
+int auto_real_split(long long ntot) {
+    return ntot * 9 <= 152LL * 4096 ? 9 : 3;
 }
+
+// Threads per particle of the FP64 real-space pass: the largest power of two
+// not above the mixed path's.
+int real_split64(int r) { return r >= 8 ? 8 : (r >= 2 ? 2 : 1); }
 
 // Cells along x per real-space block: enough blocks to fill the GPU, and a
 // staged neighbourhood (9 rows of seg + 2 cells) of about 2500 records.
@@ -324,7 +325,7 @@ rbe_status prepare(rbe_ctx* h, int n) {
     const long long ntot = h->batch ? h->ntot : n;
     const int chunk = h->rho_chunk > 0 ? h->rho_chunk : auto_chunk(h, ntot);
     const int split = h->force_split > 0 ? h->force_split : auto_split(ntot);
-    const int rsplit = h->real_split > 0 ? h->real_split : auto_real_split(ntot, h->ncell);
+    const int rsplit = h->real_split > 0 ? h->real_split : auto_real_split(ntot);
     int ncd_max = 3;
     for (auto& sh : h->sys) ncd_max = std::max(ncd_max, sh.ncd);
     const int rseg = h->real_seg > 0 ? std::min(h->real_seg, ncd_max)
@@ -337,7 +338,7 @@ rbe_status prepare(rbe_ctx* h, int n) {
     double stage_need = 0.0;
     std::vector<Tile> pblk, fblk, rblk, chunks;
     const int ftile = kBlockP / split;
-    const int rtile = kBlockP / rsplit;
+    const int rtile = kBlockP / real_split64(rsplit);
     int off_part = 0;
     for (int s = 0; s < h->nsys; ++s) {
         SysHost& sh = h->sys[s];
@@ -419,11 +420,14 @@ rbe_status prepare(rbe_ctx* h, int n) {
     // standard deviations, within a 96 KB budget (larger ones read global memory)
     h->stage_cap = (int)std::min(6144.0, std::ceil(stage_need));
     {
-        // about one group of rsplit threads per particle of a segment
+        // warps of 32 / rsplit particles, enough for a segment two standard
+        // deviations above the mean in one pass (a fuller segment makes a
+        // second pass and stretches the kernel's tail)
         const double per_seg = (double)std::max<long long>(ntot, 1) * seg_max /
                                std::max(1, h->ncell);
-        const double want = per_seg * rsplit;
-        h->seg_threads = want > 160 ? 256 : (want > 80 ? 128 : 64);
+        const double want = 32.0 * std::ceil((per_seg + 2.0 * std::sqrt(per_seg)) /
+                                             (32 / rsplit));
+        h->seg_threads = want > 192 ? 256 : (want > 128 ? 192 : (want > 64 ? 128 : 64));
     }
     h->cur_seg = rseg;
     h->cur_n = n;
@@ -481,7 +485,7 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_ALLOC(h->d_kcnt, h->ktot);
     RBE_ALLOC(h->d_kab, h->ktot);
     RBE_ALLOC(h->d_qsum_fx, h->nsys);
-    RBE_ALLOC(h->d_blk_e, std::max<long long>(rb, h->ncell + 1));
+    RBE_ALLOC(h->d_blk_e, std::max<long long>(rb, (long long)kSegChunks * (h->ncell + 1)));
     RBE_ALLOC(h->d_blk_q, pb);
     RBE_ALLOC(h->d_cur_step, 1);
     RBE_ALLOC(h->d_stage_step, 1);
@@ -637,9 +641,10 @@ Work make_work(const rbe_ctx* h, const Tile* tiles, int tile, int aux_stride) {
 
 RealArgs make_real_args(const rbe_ctx* h, int parts) {
     RealArgs r{};
-    r.w = make_work(h, h->d_rblk, kBlockP / h->rsplit, 0);
+    r.w = make_work(h, h->d_rblk, kBlockP / real_split64(h->rsplit), 0);
     r.nrblk = h->nrblk;
     r.split = h->rsplit;
+    r.split64 = real_split64(h->rsplit);
     r.ncell = h->ncell;
     r.nsys = h->nsys;
     r.cstart = h->d_cstart;
@@ -1056,8 +1061,8 @@ rbe_status rbe_set_tuning(rbe_handle h, const rbe_tuning* t) {
         return fail(h, RBE_ERR_ARG, "rho_chunk must be 0 or a power of two in [32, 8192]");
     if (f != 0 && f != 1 && f != 2 && f != 4 && f != 8)
         return fail(h, RBE_ERR_ARG, "force_split must be 0, 1, 2, 4 or 8");
-    if (r != 0 && (r < 1 || r > 32 || (r & (r - 1))))
-        return fail(h, RBE_ERR_ARG, "real_split must be 0 or a power of two in [1, 32]");
+    if (r != 0 && r != 1 && r != 3 && r != 9)
+        return fail(h, RBE_ERR_ARG, "real_split must be 0, 1, 3 or 9");
     if (sg < 0 || sg > 256) return fail(h, RBE_ERR_ARG, "real_seg must be in [0, 256]");
     h->rho_chunk = c;
     h->force_split = f;
@@ -1077,7 +1082,7 @@ rbe_status rbe_get_tuning(rbe_handle h, rbe_tuning* t) {
                                       : (h->force_split > 0 ? h->force_split : auto_split(ntot));
     t->real_split = h->cur_rsplit > 0 ? h->cur_rsplit
                                       : (h->real_split > 0 ? h->real_split
-                                                           : auto_real_split(ntot, h->ncell));
+                                                           : auto_real_split(ntot));
     int ncd_max = 3;
     for (auto& sh : h->sys) ncd_max = std::max(ncd_max, sh.ncd);
     t->real_seg = h->cur_seg > 0 ? h->cur_seg
@@ -1133,7 +1138,7 @@ rbe_status rbe_autotune(rbe_handle h, int32_t n, const float* pos_q, rbe_tuning*
     for (int sg = 1; sg <= ncd_max; sg = sg < 4 ? sg + 1 : sg * 2) segs_try.push_back(sg);
     if (segs_try.back() != ncd_max) segs_try.push_back(ncd_max);
     for (int sg : segs_try) {
-        for (int sp = 1; sp <= 8 && s == RBE_OK; sp <<= 1) {
+        for (int sp = 1; sp <= 9 && s == RBE_OK; sp *= 3) {
             h->real_split = sp;
             h->real_seg = sg;
             if ((s = prepare(h, n)) != RBE_OK) break;

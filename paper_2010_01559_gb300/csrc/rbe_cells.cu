@@ -227,8 +227,10 @@ __global__ void k_scatter(int n, const int* __restrict__ cid, const int* __restr
 }
 
 // Canonical order inside each cell: the particle at atomic slot s goes to
-// cell_start + (number of members of its cell with a smaller caller index).
-// One thread per particle; cells hold a handful of particles.
+// cell_start + (number of members of its cell that precede it).  The mixed
+// path orders by fixed-point x (ties by caller index), which the real-space
+// kernel's x windows rely on; the FP64 path by caller index.  One thread per
+// particle; cells hold a handful of particles.
 __global__ void k_order(int n, const int* __restrict__ cid, const int* __restrict__ cell_start,
                         const int* __restrict__ perm_tmp, const uint4* __restrict__ fx,
                         uint4* __restrict__ spos, const double4* __restrict__ fx64,
@@ -239,7 +241,17 @@ __global__ void k_order(int n, const int* __restrict__ cid, const int* __restric
     const int c = cid[i];
     const int b = cell_start[c], e = cell_start[c + 1];
     int r = 0;
-    for (int k = b; k < e; ++k) r += (__ldg(perm_tmp + k) < i) ? 1 : 0;
+    if (fx) {
+        // mixed path: ascending fixed-point x, ties by index
+        const uint32_t xi = fx[i].x;
+        for (int k = b; k < e; ++k) {
+            const int j = __ldg(perm_tmp + k);
+            const uint32_t xj = __ldg(&fx[j].x);
+            r += (xj < xi || (xj == xi && j < i)) ? 1 : 0;
+        }
+    } else {
+        for (int k = b; k < e; ++k) r += (__ldg(perm_tmp + k) < i) ? 1 : 0;
+    }
     const int dst = b + r;
     perm[dst] = i;
     if (fx) spos[dst] = fx[i];

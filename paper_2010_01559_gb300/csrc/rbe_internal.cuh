@@ -64,22 +64,9 @@ struct SysDev {
     float f_rc2, f_lj_rc2, f_alpha, f_sqrt_alpha, f_two_sa_spi, f_lB;
     float f_lj_sigma2, f_lj_eps, f_lj_shift;
     float f_c1, f_c2, f_dt, f_dt_over_m, f_invL;
+    float f_inv_Lu;         // 2^32 / L: length to fixed-point units
+    uint32_t corner_q, corner_r;   // 2^32 = corner_q * ncd + corner_r (cell corners)
 };
-
-// Unsigned 32-bit integer to the nearest float, as (float)x rounds it, on the
-// FP32/integer pipes: each 16-bit half is exact as 2^23 + half - 2^23, and the
-// FMA forms hi * 2^16 + lo exactly before its single rounding.
-__device__ __forceinline__ float u32_to_f32(uint32_t x) {
-    const float hi = __uint_as_float(0x4B000000u | (x >> 16)) - 8388608.0f;
-    const float lo = __uint_as_float(0x4B000000u | (x & 0xFFFFu)) - 8388608.0f;
-    return fmaf(hi, 65536.0f, lo);
-}
-
-// Signed counterpart (|x| < 2^31): round-to-nearest is symmetric in the sign.
-__device__ __forceinline__ float s32_to_f32(int32_t x) {
-    const float a = u32_to_f32(x < 0 ? 0u - (uint32_t)x : (uint32_t)x);
-    return x < 0 ? -a : a;
-}
 
 // A tile of particles of one system: (system, first particle, count, aux).
 // aux = first partial index (chunks) or unused (particle blocks).
@@ -199,10 +186,17 @@ void launch_fourier_force_f64(cudaStream_t st, bool one, const Work& w, int nblk
                               const unsigned long long* rho_fx, double4* fs64);
 
 // real space, LJ, Langevin, energies (rbe_real.cu)
+// Blocks per real-space segment (mixed path): the first takes the particles
+// one pass of the block holds, the second the rest (most segments have none,
+// and that block returns at once), so a crowded segment does not stretch the
+// kernel's tail with a second pass.
+constexpr int kSegChunks = 2;
+
 struct RealArgs {
     Work w;                  // real-space tiles of kBlockP / split particles (FP64 path)
     int nrblk;
-    int split;               // threads per particle
+    int split;               // threads per particle, mixed path (1, 3 or 9)
+    int split64;             // threads per particle, FP64 path (power of two)
     int ncell;               // cells over all systems
     int nsys;
     const int* cstart;       // first cell of each system (nsys + 1), batch only
@@ -210,7 +204,7 @@ struct RealArgs {
     int nseg;
     int seg_max;             // most cells in one segment
     int stage_cap;           // staged records per segment block
-    int seg_threads;         // threads per segment block (64, 128 or 256)
+    int seg_threads;         // threads per segment block (64, 128, 192 or 256)
     int parts;               // RBE_PART_* mask
     const int* cell_start;
     const int* perm;

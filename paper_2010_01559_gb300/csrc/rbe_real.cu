@@ -6,8 +6,9 @@
 // Cells have side >= r_c and there are at least 3 per edge, so every pair
 // within r_c is met exactly once, as the minimum image, among the 27 cells
 // around a particle's own.  Mixed path: one block per segment of x-adjacent
-// cells with the neighbourhood staged in shared memory and G threads per
-// particle (tuning choices).  FP64 path: G threads per particle reading the
+// cells with the neighbourhood staged in shared memory and R = 1, 3 or 9
+// threads per particle, each scanning 9/R neighbour rows (tuning choices).
+// FP64 path: G threads per particle reading the
 // neighbours from global memory.
 //
 // Real-space pair terms for r < r_c (r_ij = r_j - r_i):
@@ -77,6 +78,7 @@ __device__ __forceinline__ void row_ranges(const int* __restrict__ cs, int base,
 // densely.  A cell whose neighbourhood exceeds the staging capacity reads the
 // records from global memory instead.
 constexpr int kNbCap = 24;          // entries of each lane's neighbour list
+constexpr int kBatch = 4;           // candidates a thread tests per step of its scan
 
 struct PairAcc {
     float fx, fy, fz, phr, ec, elj;
@@ -129,50 +131,85 @@ __device__ __forceinline__ void pair_terms(float dx, float dy, float dz, float r
     }
 }
 
-template <int G>
-__device__ __forceinline__ float lane_sum(float v) {
+// Sum of a particle's R lanes (lanes l = 0 .. R-1 of its group), in lane
+// order; the result is valid in lane 0 of the group.
+template <int R>
+__device__ __forceinline__ float lane_combine(float v) {
+    float s = v;
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, G);
-    return v;
+    for (int d = 1; d < R; ++d) s += __shfl_down_sync(0xffffffffu, v, d);
+    return s;
 }
 
-// Offset of a fixed-point coordinate within its cell, in length units.  The
-// product is rounded explicitly, so a record always maps to the same float and
-// a particle meets itself at distance exactly 0.
-__device__ __forceinline__ float incell(uint32_t s, int ncd, const uint32_t* corner, float Lu) {
-    const int c = (int)(((unsigned long long)s * (unsigned long long)ncd) >> 32);
-    return __fmul_rn(u32_to_f32(s - corner[c]), Lu);
+// The neighbour rows (r = 3 (dz + 1) + dy + 1) that lane l of a particle's R
+// lanes scans, j = 0 .. 9/R - 1.  Along x the centre row reaches r_c on both
+// sides, an edge row about 0.79 r_c and a corner row about 0.52 r_c on
+// average, so with three lanes the sets {centre, 2 corners}, {2 edges,
+// corner}, {2 edges, corner} carry about equal work.
+template <int R>
+__device__ __forceinline__ int row_of(int l, int j) {
+    if constexpr (R == 1) {
+        return j;
+    } else if constexpr (R == 9) {
+        return l;
+    } else {
+        constexpr unsigned long long tab = 4ull | (0ull << 4) | (8ull << 8) | (1ull << 12) |
+                                           (7ull << 16) | (2ull << 20) | (3ull << 24) |
+                                           (5ull << 28) | (6ull << 32);
+        return (int)((tab >> (4 * (3 * l + j))) & 15ull);
+    }
 }
 
-// Corner-to-corner distance from cell c to cell wrap(c + d), d in {-1, 0, 1}.
-__device__ __forceinline__ float cell_shift(int c, int d, int ncd, const uint32_t* corner,
-                                            float Lu) {
-    const int cn = wrapc(c + d, ncd);
-    return __fmul_rn(s32_to_f32((int32_t)(corner[cn] - corner[c])), Lu);
+// Corner of cell c along an axis, floor(c 2^32 / ncd), from the system's
+// quotient and remainder of 2^32 / ncd (c = ncd wraps to 0).  Every fixed-point
+// coordinate of cell c lies in [corner(c), corner(c + 1)), so integer
+// differences to corners bound the distance to any record of a neighbour cell
+// from below, exactly.
+__device__ __forceinline__ uint32_t corner_of(int c, const SysDev& S) {
+    return (uint32_t)c * S.corner_q + ((uint32_t)c * S.corner_r) / (uint32_t)S.ncd;
 }
 
-// One block per segment: nseg x-adjacent cells of one (y, z) row (the whole row
-// for large systems).  The block stages, for each of the 9 neighbour rows, the
-// segment's cells plus one halo cell on each side, as in-cell offsets with the
-// charge; per-cell boundaries of the staged rows go to a small table.  A
-// particle in cell x then finds its 27 neighbour cells as 9 contiguous windows
-// of three cells, and the displacement to a staged record is its in-cell
-// offset minus the particle's plus the exact corner-to-corner shift of the two
-// cells, so FP32 precision does not depend on where the segment sits in the
-// box.  G threads per particle first run the distance test over their share of
-// the candidates and list the ones within the cutoff, then evaluate erfc / exp
-// / LJ densely for the listed ones.  A segment whose neighbourhood exceeds the
-// staging buffer reads its candidates from global memory instead.
-template <int G, bool ONE, int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT)
+// Pair terms from two fixed-point records: the displacement is the 32-bit
+// difference of the coordinates, which is the minimum image (|r_ij| < L / 2),
+// rounded once to FP32 and scaled to length units.
+__device__ __forceinline__ void pair_fixed(const uint4& si, const uint4& sj, float Lu,
+                                           float lbqi, const PairConst& kc, PairAcc& acc) {
+    const float dx = (float)(int32_t)(sj.x - si.x) * Lu;
+    const float dy = (float)(int32_t)(sj.y - si.y) * Lu;
+    const float dz = (float)(int32_t)(sj.z - si.z) * Lu;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (r2 > 0.f) pair_terms(dx, dy, dz, r2, __uint_as_float(sj.w), lbqi, kc, acc);
+}
+
+// One block per segment: nsc x-adjacent cells of one (y, z) row.  The block
+// copies, for each of the 9 neighbour rows, the segment's cells plus one halo
+// cell on each side into shared memory (fixed-point records, each cell's
+// records in ascending x); per-cell boundaries of the staged rows go to a small
+// table.  A particle in cell x finds its 27 neighbour cells as 9 contiguous
+// windows of three cells, ascending in x.  The y and z distances from the
+// particle to a row's cells bound what is left of the cutoff along x, so the
+// window shrinks to the records within that reach: whole rows and halo cells
+// drop out, and the scan stops at the first record past the reach (cells of
+// at least 5 per edge keep the 3-cell window below half the box, where the
+// 32-bit differences are monotone).  Each of a particle's R threads (adjacent
+// lanes of one warp) scans its own rows, lists the records within the cutoff
+// and then evaluates erfc / exp / LJ densely for the listed ones; the R
+// partial sums are added in lane order.  A segment whose neighbourhood exceeds
+// the staging buffer reads its candidates from global memory instead.
+template <int R, bool ONE, int NT>
+__global__ void __launch_bounds__(NT, (NT == 192 ? 5 : 1024 / NT))
 k_real_seg(const __grid_constant__ RealArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    float4* s_rec = (float4*)smem;                                    // [stage_cap]
-    uint32_t* s_nb = (uint32_t*)(s_rec + a.stage_cap);                // [kNbCap][NT]
+    uint4* s_rec = (uint4*)smem;                                      // [stage_cap]
+    uint16_t* s_nb = (uint16_t*)(s_rec + a.stage_cap);                // [kNbCap][NT]
     int* s_b = (int*)(s_nb + kNbCap * NT);                            // [9][seg_max + 3]
-    __shared__ uint32_t s_corner[256];
+    uint32_t* s_cx = (uint32_t*)(s_b + 9 * (a.seg_max + 3));          // [seg_max + 1]
     __shared__ int s_src[27], s_len[27], s_off[28];
-    const Tile sg = a.segs[blockIdx.x];
+    constexpr int PPW = 32 / R;                  // particles per warp (R = 3: two lanes idle)
+    constexpr int NW = NT / 32;
+    constexpr int RPL = 9 / R;                   // neighbour rows per lane
+    const int chunk = blockIdx.x % kSegChunks;
+    const Tile sg = a.segs[blockIdx.x / kSegChunks];
     const int sys = sg.sys;
     const SysDev& S = sys_of<ONE>(a.w, sys);
     const int ncd = S.ncd;
@@ -180,14 +217,20 @@ k_real_seg(const __grid_constant__ RealArgs a) {
     const int x0 = sg.aux & 1023, cy = (sg.aux >> 10) & 1023, cz = (sg.aux >> 20) & 1023;
     const int x1 = x0 + nsc - 1;
     const int bstride = a.seg_max + 3;
-    const int own_s = __ldg(a.cell_start + sg.first), own_e = __ldg(a.cell_start + sg.first + nsc);
-    const int nown = own_e - own_s;
+    const int seg_s = __ldg(a.cell_start + sg.first), seg_e = __ldg(a.cell_start + sg.first + nsc);
+    // this block's share of the segment's particles: one pass, or the rest
+    const int own_s = seg_s + (chunk == 0 ? 0 : NW * PPW);
+    const int own_e = chunk == 0 ? min(seg_e, seg_s + NW * PPW) : seg_e;
+    const int nown = max(0, own_e - own_s);
+    if (chunk > 0 && nown == 0) {                 // nothing beyond the first pass
+        if (a.blk_e && threadIdx.x == 0) a.blk_e[blockIdx.x] = make_double2(0.0, 0.0);
+        return;
+    }
     const bool do_real = (a.parts & kPartReal) != 0;
     const bool do_lj = (a.parts & kPartLJ) != 0 && S.lj_eps != 0.0;
     const bool pairs = nown > 0 && (do_real || do_lj);
     const float Lu = S.L_over_2_32;
-    for (int c = threadIdx.x; c < ncd; c += blockDim.x)
-        s_corner[c] = (uint32_t)(((unsigned long long)c << 32) / (unsigned long long)ncd);
+    for (int j = threadIdx.x; j <= nsc; j += blockDim.x) s_cx[j] = corner_of(x0 + j, S);
     if (pairs && threadIdx.x < 27) {
         const int r = threadIdx.x / 3, part = threadIdx.x % 3;
         const int zz = wrapc(cz + r / 3 - 1, ncd), yy = wrapc(cy + r % 3 - 1, ncd);
@@ -244,10 +287,7 @@ k_real_seg(const __grid_constant__ RealArgs a) {
                     const int mid = (lo + hi + 1) >> 1;
                     if (s_off[mid] <= k) lo = mid; else hi = mid - 1;
                 }
-                const uint4 rec = __ldg(a.spos + s_src[lo] + (k - s_off[lo]));
-                s_rec[k] = make_float4(incell(rec.x, ncd, s_corner, Lu),
-                                       incell(rec.y, ncd, s_corner, Lu),
-                                       incell(rec.z, ncd, s_corner, Lu), __uint_as_float(rec.w));
+                s_rec[k] = __ldg(a.spos + s_src[lo] + (k - s_off[lo]));
             }
     }
     __syncthreads();
@@ -262,105 +302,112 @@ k_real_seg(const __grid_constant__ RealArgs a) {
     kc.lj_eps = S.f_lj_eps;
     kc.lj_shift = S.f_lj_shift;
     const float cut2 = fmaxf(kc.rc2, kc.lj_rc2);
-    // the segment's (y, z) row is fixed: shifts to the rows below and above
-    const float sy_m = cell_shift(cy, -1, ncd, s_corner, Lu), sy_p = cell_shift(cy, 1, ncd, s_corner, Lu);
-    const float sz_m = cell_shift(cz, -1, ncd, s_corner, Lu), sz_p = cell_shift(cz, 1, ncd, s_corner, Lu);
+    const float invLu = S.f_inv_Lu;
+    // distance test in fixed-point units; the margins keep the test and the
+    // reach conservative against FP32 rounding (pair_terms applies the cutoffs)
+    const float cut2u = cut2 * invLu * invLu * 1.00001f;
+    const float reach_slack = cut2 * 1e-5f;
+    const bool prune = ncd >= 5;
+    const uint32_t ylo = corner_of(cy, S), yhi = corner_of(cy + 1, S);
+    const uint32_t zlo = corner_of(cz, S), zhi = corner_of(cz + 1, S);
     const bool want_phi = a.phi_out != nullptr;
     const bool want_e = a.blk_e != nullptr;
-    const int g = threadIdx.x % G;
-    const int t = threadIdx.x / G;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pl = lane / R, l = lane - pl * R;  // particle of the warp, lane within it
     double ec_own = 0.0, elj_own = 0.0;
-    for (int base = 0; base < nown; base += NT / G) {
-        const bool active = base + t < nown;
-        const int i = own_s + min(base + t, nown - 1);
+    for (int base = warp * PPW; base < nown; base += NW * PPW) {
+        const bool active = pl < PPW && base + pl < nown;
+        const int i = own_s + min(base + pl, nown - 1);
         const int o = a.perm[i];                          // issued early: the tail needs it
-        const uint4 rec = a.spos[i];
-        const int cxi = (int)(((unsigned long long)rec.x * (unsigned long long)ncd) >> 32);
-        const float pxo = incell(rec.x, ncd, s_corner, Lu);
-        const float pyo = incell(rec.y, ncd, s_corner, Lu);
-        const float pzo = incell(rec.z, ncd, s_corner, Lu);
-        const float qi = __uint_as_float(rec.w);
+        const uint4 si = a.spos[i];
+        const int cxi = (int)(((unsigned long long)si.x * (unsigned long long)ncd) >> 32);
+        const float qi = __uint_as_float(si.w);
         const float lbqi = kc.lB * qi;
-        // the particle's position relative to the corners of its x-neighbour cells
-        const float px_m = pxo + cell_shift(cxi, -1, ncd, s_corner, Lu) * -1.0f;
-        const float px_p = pxo - cell_shift(cxi, 1, ncd, s_corner, Lu);
         PairAcc acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (active && pairs) {
             const int u = cxi - x0;                       // 0 .. nsc-1
             if (staged) {
+                // distances to the faces of the particle's cell: squared in
+                // length units for y and z, fixed-point for x
+                const float fyl = (float)(si.y - ylo) * Lu, fyh = (float)(yhi - si.y) * Lu;
+                const float fzl = (float)(si.z - zlo) * Lu, fzh = (float)(zhi - si.z) * Lu;
+                const float fyl2 = fyl * fyl, fyh2 = fyh * fyh, fzl2 = fzl * fzl, fzh2 = fzh * fzh;
+                const uint32_t oxl = si.x - s_cx[u], oxh = s_cx[u + 1] - si.x;
                 int cnt = 0;
 #pragma unroll 1
-                for (int r = 0; r < 9; ++r) {
+                for (int jr = 0; jr < RPL; ++jr) {
+                    const int r = row_of<R>(l, jr);
                     const int ry = r % 3, rz = r / 3;
-                    const float py = pyo - (ry == 0 ? sy_m : (ry == 1 ? 0.f : sy_p));
-                    const float pz = pzo - (rz == 0 ? sz_m : (rz == 1 ? 0.f : sz_p));
+                    const float reach2 = cut2 + reach_slack -
+                                         (ry == 0 ? fyl2 : (ry == 2 ? fyh2 : 0.f)) -
+                                         (rz == 0 ? fzl2 : (rz == 2 ? fzh2 : 0.f));
+                    if (reach2 <= 0.f) continue;          // the whole row is beyond the cutoff
                     const int* bb = s_b + r * bstride + u;
-                    const int b1 = bb[1], b2 = bb[2], b3 = bb[3];
-                    const uint32_t tag = (uint32_t)r << 24;
-#pragma unroll 2
-                    for (int k = bb[0] + g; k < b3; k += G) {   // cells x-1, x, x+1 of the row
-                        const float4 sj = s_rec[k];
-                        const float px = (k < b1) ? px_m : ((k < b2) ? pxo : px_p);
-                        const float dx = sj.x - px, dy = sj.y - py, dz = sj.z - pz;
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        if (r2 < cut2 && r2 > 0.f) {
-                            if (cnt < kNbCap) {
-                                const uint32_t m = (k < b1) ? 0u : ((k < b2) ? 1u : 2u);
-                                s_nb[cnt++ * NT + threadIdx.x] = (uint32_t)k | tag | (m << 28);
-                            } else {
-                                pair_terms(dx, dy, dz, r2, sj.w, lbqi, kc, acc);
+                    int kb = bb[0], ke = bb[3];
+                    int w = 0x7FFFFFFF;                   // no x limit below 5 cells per edge
+                    if (prune) {
+                        w = (int)(sqrtf(reach2) * invLu) + 8;
+                        if (oxl > (uint32_t)w) kb = bb[1];    // cell x-1 out of reach
+                        if (oxh > (uint32_t)w) ke = bb[2];    // cell x+1 out of reach
+                    }
+                    const uint32_t wu = (uint32_t)w;
+                    // batches of kBatch consecutive records: the shared-memory
+                    // loads of a batch are independent and overlap
+                    for (int k0 = kb; k0 < ke; k0 += kBatch) {
+                        uint4 sj[kBatch];
+#pragma unroll
+                        for (int q = 0; q < kBatch; ++q) sj[q] = s_rec[min(k0 + q, ke - 1)];
+                        bool past = false;
+#pragma unroll
+                        for (int q = 0; q < kBatch; ++q) {
+                            const int k = k0 + q;
+                            const int dxi = (int)(sj[q].x - si.x);
+                            past |= dxi > w;
+                            if (k < ke && (uint32_t)dxi + wu <= 2u * wu) {   // |dxi| <= w
+                                const float dx = (float)dxi;
+                                const float dy = (float)(int32_t)(sj[q].y - si.y);
+                                const float dz = (float)(int32_t)(sj[q].z - si.z);
+                                const float r2u = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                                if (r2u < cut2u && r2u > 0.f) {
+                                    if (cnt < kNbCap) s_nb[cnt++ * NT + threadIdx.x] = (uint16_t)k;
+                                    else pair_fixed(si, sj[q], Lu, lbqi, kc, acc);
+                                }
                             }
                         }
+                        if (past) break;                   // ascending x: the rest is beyond
                     }
                 }
                 for (int e = 0; e < cnt; ++e) {
-                    const uint32_t ent = s_nb[e * NT + threadIdx.x];
-                    const int k = (int)(ent & 0xFFFFFFu), r = (int)((ent >> 24) & 15u);
-                    const int code = (int)(ent >> 28);
-                    const float4 sj = s_rec[k];
-                    const int ry = r % 3, rz = r / 3;
-                    const float px = (code == 0) ? px_m : ((code == 1) ? pxo : px_p);
-                    const float py = pyo - (ry == 0 ? sy_m : (ry == 1 ? 0.f : sy_p));
-                    const float pz = pzo - (rz == 0 ? sz_m : (rz == 1 ? 0.f : sz_p));
-                    const float dx = sj.x - px, dy = sj.y - py, dz = sj.z - pz;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    pair_terms(dx, dy, dz, r2, sj.w, lbqi, kc, acc);
+                    const uint4 sj = s_rec[s_nb[e * NT + threadIdx.x]];
+                    pair_fixed(si, sj, Lu, lbqi, kc, acc);
                 }
             } else {
                 // candidates straight from the cell-sorted records
-                for (int r = 0; r < 9; ++r) {
-                    const int dzr = r / 3 - 1, dyr = r % 3 - 1;
-                    const int zz = wrapc(cz + dzr, ncd), yy = wrapc(cy + dyr, ncd);
+                for (int jr = 0; jr < RPL; ++jr) {
+                    const int r = row_of<R>(l, jr);
+                    const int zz = wrapc(cz + r / 3 - 1, ncd), yy = wrapc(cy + r % 3 - 1, ncd);
                     const int row = S.off_c + (zz * ncd + yy) * ncd;
-                    const float py = pyo - (dyr < 0 ? sy_m : (dyr == 0 ? 0.f : sy_p));
-                    const float pz = pzo - (dzr < 0 ? sz_m : (dzr == 0 ? 0.f : sz_p));
                     for (int d = -1; d <= 1; ++d) {
                         const int xn = wrapc(cxi + d, ncd);
-                        const float px = (d < 0) ? px_m : ((d == 0) ? pxo : px_p);
                         const int cb = __ldg(a.cell_start + row + xn);
                         const int ce = __ldg(a.cell_start + row + xn + 1);
-                        for (int j = cb + g; j < ce; j += G) {
+                        for (int j = cb; j < ce; ++j) {
                             if (j == i) continue;
-                            const uint4 rj = __ldg(a.spos + j);
-                            const float dx = incell(rj.x, ncd, s_corner, Lu) - px;
-                            const float dy = incell(rj.y, ncd, s_corner, Lu) - py;
-                            const float dz = incell(rj.z, ncd, s_corner, Lu) - pz;
-                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            pair_terms(dx, dy, dz, r2, __uint_as_float(rj.w), lbqi, kc, acc);
+                            pair_fixed(si, __ldg(a.spos + j), Lu, lbqi, kc, acc);
                         }
                     }
                 }
             }
         }
-        acc.fx = lane_sum<G>(acc.fx);
-        acc.fy = lane_sum<G>(acc.fy);
-        acc.fz = lane_sum<G>(acc.fz);
-        if (want_phi) acc.phr = lane_sum<G>(acc.phr);
+        acc.fx = lane_combine<R>(acc.fx);
+        acc.fy = lane_combine<R>(acc.fy);
+        acc.fz = lane_combine<R>(acc.fz);
+        if (want_phi) acc.phr = lane_combine<R>(acc.phr);
         if (want_e) {
-            acc.ec = lane_sum<G>(acc.ec);
-            acc.elj = lane_sum<G>(acc.elj);
+            acc.ec = lane_combine<R>(acc.ec);
+            acc.elj = lane_combine<R>(acc.elj);
         }
-        if (active && g == 0) {
+        if (active && l == 0) {
             float fx = acc.fx, fy = acc.fy, fz = acc.fz, phi = acc.phr;
             if (want_e) {
                 ec_own += (double)acc.ec;
@@ -382,10 +429,10 @@ k_real_seg(const __grid_constant__ RealArgs a) {
                 const uint4 w = philox4x32_10(make_uint4((uint32_t)(o - S.off_p), 0u,
                                                          (uint32_t)step, (S.stream << 8) | 0x02u),
                                               key);
-                const float u1 = u32_to_f32((w.x >> 8) + 1u) * 5.9604644775390625e-08f;   // (0, 1]
-                const float u2 = u32_to_f32(w.y >> 8) * 5.9604644775390625e-08f;          // [0, 1)
-                const float u3 = u32_to_f32((w.z >> 8) + 1u) * 5.9604644775390625e-08f;
-                const float u4 = u32_to_f32(w.w >> 8) * 5.9604644775390625e-08f;
+                const float u1 = (float)((w.x >> 8) + 1u) * 5.9604644775390625e-08f;   // (0, 1]
+                const float u2 = (float)(w.y >> 8) * 5.9604644775390625e-08f;          // [0, 1)
+                const float u3 = (float)((w.z >> 8) + 1u) * 5.9604644775390625e-08f;
+                const float u4 = (float)(w.w >> 8) * 5.9604644775390625e-08f;
                 const float r1 = sqrtf(-2.f * logf(u1)), r3 = sqrtf(-2.f * logf(u3));
                 float s2, c2v, s4, c4;
                 sincospif(2.f * u2, &s2, &c2v);
@@ -569,8 +616,8 @@ __global__ void k_energy(const __grid_constant__ Work w, const int4* __restrict_
             q2 += v.y;
         }
     }
-    const int off = per_cell ? S.off_sg : S.off_rb;
-    const int nb = per_cell ? S.nsg : S.nrb;
+    const int off = per_cell ? S.off_sg * kSegChunks : S.off_rb;
+    const int nb = per_cell ? S.nsg * kSegChunks : S.nrb;
     if (blk_e)
         for (int b = threadIdx.x; b < nb; b += blockDim.x) {
             const double2 v = blk_e[off + b];
@@ -606,30 +653,31 @@ __global__ void k_energy(const __grid_constant__ Work w, const int4* __restrict_
 
 // Dynamic shared memory of the segment kernel for a staging capacity.
 size_t real_seg_smem(int stage_cap, int seg_max, int nt) {
-    return sizeof(float4) * (size_t)stage_cap + sizeof(uint32_t) * kNbCap * (size_t)nt +
-           sizeof(int) * 9 * (size_t)(seg_max + 3);
+    return sizeof(uint4) * (size_t)stage_cap + sizeof(uint16_t) * kNbCap * (size_t)nt +
+           sizeof(int) * 9 * (size_t)(seg_max + 3) + sizeof(uint32_t) * (size_t)(seg_max + 1);
 }
 
-template <int G, int NT>
-static void real_mixed_gn(cudaStream_t st, bool one, const RealArgs& a) {
+template <int R, int NT>
+static void real_mixed_rn(cudaStream_t st, bool one, const RealArgs& a) {
     const size_t smem = real_seg_smem(a.stage_cap, a.seg_max, NT);
     if (one) {
-        cudaFuncSetAttribute(k_real_seg<G, true, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_real_seg<R, true, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-        k_real_seg<G, true, NT><<<a.nseg, NT, smem, st>>>(a);
+        k_real_seg<R, true, NT><<<a.nseg * kSegChunks, NT, smem, st>>>(a);
     } else {
-        cudaFuncSetAttribute(k_real_seg<G, false, NT>,
+        cudaFuncSetAttribute(k_real_seg<R, false, NT>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_real_seg<G, false, NT><<<a.nseg, NT, smem, st>>>(a);
+        k_real_seg<R, false, NT><<<a.nseg * kSegChunks, NT, smem, st>>>(a);
     }
 }
 
-// Block size: about one thread group per particle of a segment, 64 .. 256.
-template <int G>
-static void real_mixed_g(cudaStream_t st, bool one, const RealArgs& a) {
-    if (a.seg_threads >= 256) real_mixed_gn<G, 256>(st, one, a);
-    else if (a.seg_threads >= 128) real_mixed_gn<G, 128>(st, one, a);
-    else real_mixed_gn<G, 64>(st, one, a);
+// Block size: enough warps for the particles of a typical segment, 64 .. 256.
+template <int R>
+static void real_mixed_r(cudaStream_t st, bool one, const RealArgs& a) {
+    if (a.seg_threads >= 256) real_mixed_rn<R, 256>(st, one, a);
+    else if (a.seg_threads >= 192) real_mixed_rn<R, 192>(st, one, a);
+    else if (a.seg_threads >= 128) real_mixed_rn<R, 128>(st, one, a);
+    else real_mixed_rn<R, 64>(st, one, a);
 }
 
 template <int G>
@@ -641,18 +689,15 @@ static void real_f64_g(cudaStream_t st, bool one, const RealArgs& a) {
 void launch_real_mixed(cudaStream_t st, bool one, const RealArgs& a) {
     if (a.nseg <= 0) return;
     switch (a.split) {
-        case 2: real_mixed_g<2>(st, one, a); break;
-        case 4: real_mixed_g<4>(st, one, a); break;
-        case 8: real_mixed_g<8>(st, one, a); break;
-        case 16: real_mixed_g<16>(st, one, a); break;
-        case 32: real_mixed_g<32>(st, one, a); break;
-        default: real_mixed_g<1>(st, one, a); break;
+        case 3: real_mixed_r<3>(st, one, a); break;
+        case 9: real_mixed_r<9>(st, one, a); break;
+        default: real_mixed_r<1>(st, one, a); break;
     }
 }
 
 void launch_real_f64(cudaStream_t st, bool one, const RealArgs& a) {
     if (a.nrblk <= 0) return;
-    switch (a.split) {
+    switch (a.split64) {
         case 2: real_f64_g<2>(st, one, a); break;
         case 4: real_f64_g<4>(st, one, a); break;
         case 8: real_f64_g<8>(st, one, a); break;

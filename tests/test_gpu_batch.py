@@ -80,12 +80,12 @@ def test_replica_in_batch_equals_single_handle(rbe, replicas):
     import torch
     few = replicas[:6]
     h = rbe.RBEBatch([rbe.params_from(w.params) for w in few], [w.n for w in few])
-    h.set_tuning(512, 2, 4)
+    h.set_tuning(512, 2, 3)
     Fb, Eb, _ = h.forces(_concat(few), 4)
     off = 0
     for r, w in enumerate(few):
         s = rbe.RBE(rbe.params_from(w.params, n_max=w.n))
-        s.set_tuning(512, 2, 4)
+        s.set_tuning(512, 2, 3)
         Fs, Es, _ = s.forces(torch.from_numpy(w.pos_q()).cuda(), 4)
         assert torch.equal(Fb[off:off + w.n], Fs), r
         assert torch.equal(Eb[r], Es[0]), r
