@@ -247,10 +247,34 @@ def pair_counts(wl):
     return candidates, pairs
 
 
-def fourier_rooflines(prof, wl):
+def unit_peaks(rbe, clk_mhz):
+    """SFU and FP32 peaks in T ops/s: per-SM-per-clock rates measured by the
+    library's probe kernels (rbe_probe_peaks) times the SM clock seen during the
+    timed region (the probe's own clock if none was sampled); the nominal unit
+    counts if the probe fails."""
+    try:
+        pk = rbe.probe_peaks()
+    except Exception as e:            # reported, never silent
+        pk = {"error": str(e)}
+    measured = "sfu_per_clk_sm" in pk
+    mhz = clk_mhz or (pk.get("sm_clock_mhz") if measured else None) or SM_MAX_MHZ
+    sfu = pk["sfu_per_clk_sm"] if measured else SFU_PER_SM_PER_CLK
+    ffma = pk["ffma_per_clk_sm"] if measured else FP32_LANES_PER_SM
+    sms = pk.get("sms", SM_COUNT) if measured else SM_COUNT
+    basis = (f"{sms} SMs x {sfu:.2f} sin/cos per SM-clock (measured by rbe_probe_peaks) x "
+             f"{mhz:.0f} MHz (SM clock under load)") if measured else \
+        f"{SM_COUNT} SMs x {SFU_PER_SM_PER_CLK} sin/cos per SM-clock (nominal) x {mhz:.0f} MHz"
+    basis_alu = (f"{sms} SMs x {ffma:.1f} FFMA per SM-clock (measured by rbe_probe_peaks) x "
+                 f"{mhz:.0f} MHz") if measured else \
+        f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes (nominal) x {mhz:.0f} MHz"
+    return {"sfu": sms * sfu * mhz * 1e6 / 1e12, "alu": sms * ffma * mhz * 1e6 / 1e12,
+            "sfu_basis": basis, "alu_basis": basis_alu, "probe": pk}
+
+
+def fourier_rooflines(prof, wl, units):
     """SFU roofline of both Fourier kernels (one sine and one cosine per pair)."""
     out = {}
-    peak = SM_COUNT * SFU_PER_SM_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    peak = units["sfu"]
     for name in ("rho", "fourier_force"):
         ms, cnt = prof.get(name, (0.0, 0))
         if not cnt:
@@ -263,7 +287,7 @@ def fourier_rooflines(prof, wl):
     return out
 
 
-def roofline(prof, wl, peaks, clocks, counts=None):
+def roofline(prof, wl, peaks, units, counts=None):
     """Dominant kernel of the profiled pass against its bound."""
     name, (ms, cnt) = max(prof.items(), key=lambda kv: kv[1][0])
     avg_s = ms / max(cnt, 1) / 1e3
@@ -271,20 +295,18 @@ def roofline(prof, wl, peaks, clocks, counts=None):
     if name in ("rho", "fourier_force"):
         # each (particle, wave vector) pair takes one sine and one cosine
         work = 2.0 * N * P
-        peak = SM_COUNT * SFU_PER_SM_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
+        peak = units["sfu"]
         achieved = work / avg_s / 1e12
         out = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
-               "unit": "Tsfu/s", "frac": achieved / peak,
-               "peak_basis": "152 SMs x 16 sin/cos per clock x 2070 MHz (max SM clock)",
+               "unit": "Tsfu/s", "frac": achieved / peak, "peak_basis": units["sfu_basis"],
                "algorithmic": f"2 SFU ops per (particle, k) pair x {N} x {P}"}
     elif name == "real" and counts is not None:
         cand, pairs = counts
         work = REAL_OPS_PER_CANDIDATE * cand + REAL_OPS_PER_PAIR * pairs
-        peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+        peak = units["alu"]
         achieved = work / avg_s / 1e12
         out = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
-               "unit": "Tops/s", "frac": achieved / peak,
-               "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz (max SM clock)",
+               "unit": "Tops/s", "frac": achieved / peak, "peak_basis": units["alu_basis"],
                "algorithmic": f"{REAL_OPS_PER_CANDIDATE} ops x {cand} candidates + "
                               f"{REAL_OPS_PER_PAIR} ops x {pairs} pairs within r_c"}
     else:
@@ -367,6 +389,7 @@ def run_ours(args):
     torch.cuda.profiler.stop()
     barrier(world)
     clk = clocks.stop()
+    units = unit_peaks(rbe, clk.get("sm_mhz"))
     launches = h.launch_count() - launches0
     h.sync()
     t_max = reduce_max(total_ms / 1e3, world, dev)
@@ -419,11 +442,14 @@ def run_ours(args):
     large = None
     if args.large and rank == 0:
         from paper_2010_01559_gb300 import workloads as wls
-        large = measure_system(rbe, torch, wls.config_large(), dev, stream, 50, 3, flush, peaks)
+        large = measure_system(rbe, torch, wls.config_large(), dev, stream, 50, 3, flush, peaks,
+                               units)
+        large["scaling"] = scaling_sweep(rbe, torch, wls, dev, stream, flush) + [
+            {"N": large["N"], "ms_per_step": large["ms_per_step"], "value": large["value"]}]
 
     result = None
     if rank == 0:
-        rl = roofline(prof, wl, peaks, clk, counts=pair_counts(wl))
+        rl = roofline(prof, wl, peaks, units, counts=pair_counts(wl))
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -439,7 +465,8 @@ def run_ours(args):
             "force_evals_per_s": value / wl.n,
             "clocks": clk,
             "roofline": rl,
-            "fourier_rooflines": fourier_rooflines(prof, wl),
+            "fourier_rooflines": fourier_rooflines(prof, wl, units),
+            "unit_peaks": {k: units[k] for k in ("sfu", "alu", "probe")},
             "kernels_avg_us": kernels_us,
             "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_io,
@@ -462,7 +489,41 @@ def run_ours(args):
     return result
 
 
-def measure_system(rbe, torch, wl, dev, stream, K, W, flush, peaks):
+def scaling_sweep(rbe, torch, wls, dev, stream, flush, sizes=(1 << 14, 1 << 16, 1 << 18)):
+    """Mixed MD steps of the 1:1 electrolyte at density 0.064 for growing N (box
+    grows with N), autotuned launch shapes, L2 flushed between timed steps: the
+    O(N) cost per step."""
+    out = []
+    for n in sizes:
+        wl = wls.config_large(n)
+        h = rbe.RBE(rbe.params_from(wl.params, n_max=wl.n))
+        pos = torch.from_numpy(wl.pos_q()).to(dev)
+        vel = torch.zeros((wl.n, 4), dtype=torch.float32, device=dev)
+        vel[:, :3] = torch.from_numpy(wl.vel).to(dev)
+        with torch.cuda.stream(stream):
+            h.autotune(pos)
+            step = torch.zeros(1, dtype=torch.int64, device=dev)
+            h.set_graph(True)
+            h.step(pos, vel, 3, step)
+        stream.synchronize()
+        evs = []
+        with torch.cuda.stream(stream):
+            for k in range(30):
+                flush.fill_(k & 0xFF)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h.step(pos, vel, 1, step)
+                e1.record(stream)
+                evs.append((e0, e1))
+        stream.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+        out.append({"N": wl.n, "ms_per_step": ms, "value": wl.n / (ms / 1e3)})
+        h.close()
+    return out
+
+
+def measure_system(rbe, torch, wl, dev, stream, K, W, flush, peaks, units):
     """Timed MD steps (mixed, graph replay, L2 flushed between steps), a
     profiled pass, the FP64 path and the mixed-vs-FP64 force agreement."""
     h = rbe.RBE(rbe.params_from(wl.params, n_max=wl.n))
@@ -519,8 +580,8 @@ def measure_system(rbe, torch, wl, dev, stream, K, W, flush, peaks):
            "tuning": {"rho_chunk": tuning[0], "force_split": tuning[1], "real_split": tuning[2],
                       "real_seg": tuning[3]},
            "kernels_avg_us": {k: (t / c * 1e3 if c else 0.0) for k, (t, c) in prof.items()},
-           "roofline": roofline(prof, wl, peaks, None, counts=pair_counts(wl)),
-           "fourier_rooflines": fourier_rooflines(prof, wl),
+           "roofline": roofline(prof, wl, peaks, units, counts=pair_counts(wl)),
+           "fourier_rooflines": fourier_rooflines(prof, wl, units),
            "fp64_path": {"value": value64, "unit": UNIT, "steps": K64, "ms_per_step": ms64 / K64},
            "speedup_vs_fp64": value / value64,
            "accuracy": {"force_rel_rms_mixed_vs_fp64_gpu": acc, "target": 1e-5}}

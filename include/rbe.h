@@ -247,6 +247,21 @@ rbe_status rbe_profile_read(rbe_handle h, double *ms, int64_t *launches);
  * kernels of the replayed step). */
 rbe_status rbe_launch_count(rbe_handle h, int64_t *count);
 
+/* Measured throughput of the two units the hot path leans on, for rooflines:
+ * the special-function unit (sin/cos results, as the Fourier passes use them)
+ * and the FP32 FMA pipe, per SM per clock, from short saturating probe kernels
+ * on the current device (about 10 ms; allocates and frees 1 MB).  sm_clock_mhz
+ * is the clock over the probe (SM cycles counted in the probe / its duration).
+ * Not an RBE operation: it turns counters into fractions of what this GPU can
+ * do.  Errors: RBE_ERR_ARG for a NULL out, RBE_ERR_CUDA. */
+typedef struct {
+    double sfu_per_clk_sm;    /* __sincosf results (sin and cos each count 1) per SM per clock */
+    double ffma_per_clk_sm;   /* FP32 FMA instructions per SM per clock                      */
+    double sm_clock_mhz;      /* SM clock measured during the probe                         */
+    int32_t sms;              /* streaming multiprocessors                                  */
+} rbe_peaks;
+rbe_status rbe_probe_peaks(rbe_peaks *out);
+
 /* Fourier part of one RBE evaluation without any device allocation, for
  * callers that cannot call cudaMalloc: an MD engine whose memory pool owns all
  * device memory and forbids plugins to allocate, an application that records

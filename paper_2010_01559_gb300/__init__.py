@@ -222,6 +222,17 @@ class RBEBatch(_HandleBase):
         self.n_list = [int(n) for n in n_list]
 
 
+def probe_peaks() -> dict:
+    """Measured special-function (sin/cos) and FP32-FMA throughput per SM per
+    clock on the current device, the SM clock during the probe and the SM
+    count (``rbe_probe_peaks``)."""
+    lib = capi.load()
+    out = capi.rbe_peaks()
+    capi.check(lib.rbe_probe_peaks(ctypes.byref(out)))
+    return {"sfu_per_clk_sm": out.sfu_per_clk_sm, "ffma_per_clk_sm": out.ffma_per_clk_sm,
+            "sm_clock_mhz": out.sm_clock_mhz, "sms": out.sms}
+
+
 class RBEEnergy:
     """autograd.Function: E(positions, charges) for a frozen k-batch (step).
 

@@ -38,6 +38,11 @@ class rbe_tuning(ctypes.Structure):
                 ("real_split", ctypes.c_int32), ("real_seg", ctypes.c_int32)]
 
 
+class rbe_peaks(ctypes.Structure):
+    _fields_ = [("sfu_per_clk_sm", ctypes.c_double), ("ffma_per_clk_sm", ctypes.c_double),
+                ("sm_clock_mhz", ctypes.c_double), ("sms", ctypes.c_int32)]
+
+
 class rbe_info(ctypes.Structure):
     _fields_ = [("H", ctypes.c_double), ("S", ctypes.c_double), ("M", ctypes.c_int32),
                 ("n_cells_dim", ctypes.c_int32), ("n", ctypes.c_int32), ("P", ctypes.c_int32),
@@ -78,6 +83,7 @@ _SIGS = {
     "rbe_launch_count": ([_H, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "rbe_fourier_forces_noalloc": ([ctypes.POINTER(rbe_params), ctypes.c_int32, _P,
                                     ctypes.c_uint64, _P, _P, _P], ctypes.c_int),
+    "rbe_probe_peaks": ([ctypes.POINTER(rbe_peaks)], ctypes.c_int),
 }
 
 #: kernel names in RBE_K_* order

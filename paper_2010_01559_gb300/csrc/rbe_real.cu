@@ -160,6 +160,43 @@ __device__ __forceinline__ int row_of(int l, int j) {
     }
 }
 
+// Langevin step of Sec. 3.3 for particle o (caller index) with total force F:
+// kick, exact Ornstein-Uhlenbeck with Philox/Box-Muller normals, drift, wrap.
+__device__ __forceinline__ void langevin_update(const RealArgs& a, const SysDev& S, int o,
+                                                float fx, float fy, float fz) {
+    const uint64_t step = *a.cur_step;
+    const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)(o - S.off_p), 0u,
+                                             (uint32_t)step, (S.stream << 8) | 0x02u),
+                                  key);
+    const float u1 = (float)((w.x >> 8) + 1u) * 5.9604644775390625e-08f;   // (0, 1]
+    const float u2 = (float)(w.y >> 8) * 5.9604644775390625e-08f;          // [0, 1)
+    const float u3 = (float)((w.z >> 8) + 1u) * 5.9604644775390625e-08f;
+    const float u4 = (float)(w.w >> 8) * 5.9604644775390625e-08f;
+    const float r1 = sqrtf(-2.f * logf(u1)), r3 = sqrtf(-2.f * logf(u3));
+    float s2, c2v, s4, c4;
+    sincospif(2.f * u2, &s2, &c2v);
+    sincospif(2.f * u4, &s4, &c4);
+    const float xi0 = r1 * c2v, xi1 = r1 * s2, xi2 = r3 * c4;
+    const float c1 = S.f_c1, c2 = S.f_c2, dtm = S.f_dt_over_m;
+    const float dt = S.f_dt;
+    float4 v = a.md_vel[o];
+    float4 rp = a.md_pos[o];
+    v.x = fmaf(c1, fmaf(dtm, fx, v.x), c2 * xi0);
+    v.y = fmaf(c1, fmaf(dtm, fy, v.y), c2 * xi1);
+    v.z = fmaf(c1, fmaf(dtm, fz, v.z), c2 * xi2);
+    const float L = S.Lf, invL = S.f_invL;
+    rp.x = fmaf(dt, v.x, rp.x); rp.x -= L * floorf(rp.x * invL);
+    rp.y = fmaf(dt, v.y, rp.y); rp.y -= L * floorf(rp.y * invL);
+    rp.z = fmaf(dt, v.z, rp.z); rp.z -= L * floorf(rp.z * invL);
+    // a coordinate just below 0 can round up to exactly L: that is 0
+    if (rp.x >= L) rp.x = 0.f;
+    if (rp.y >= L) rp.y = 0.f;
+    if (rp.z >= L) rp.z = 0.f;
+    a.md_vel[o] = v;
+    a.md_pos[o] = rp;
+}
+
 // Corner of cell c along an axis, floor(c 2^32 / ncd), from the system's
 // quotient and remainder of 2^32 / ncd (c = ncd wraps to 0).  Every fixed-point
 // coordinate of cell c lies in [corner(c), corner(c + 1)), so integer
@@ -315,14 +352,15 @@ k_real_seg(const __grid_constant__ RealArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int pl = lane / R, l = lane - pl * R;  // particle of the warp, lane within it
     double ec_own = 0.0, elj_own = 0.0;
-    for (int base = warp * PPW; base < nown; base += NW * PPW) {
+    constexpr int kPass = NW * PPW;              // particles per pass of the block
+    __shared__ float4 s_f[kPass];                // a pass's real-space force and phi
+    for (int pass = 0; pass < nown; pass += kPass) {
+        const int base = pass + warp * PPW;
         const bool active = pl < PPW && base + pl < nown;
         const int i = own_s + min(base + pl, nown - 1);
-        const int o = a.perm[i];                          // issued early: the tail needs it
         const uint4 si = a.spos[i];
         const int cxi = (int)(((unsigned long long)si.x * (unsigned long long)ncd) >> 32);
-        const float qi = __uint_as_float(si.w);
-        const float lbqi = kc.lB * qi;
+        const float lbqi = kc.lB * __uint_as_float(si.w);
         PairAcc acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (active && pairs) {
             const int u = cxi - x0;                       // 0 .. nsc-1
@@ -408,55 +446,34 @@ k_real_seg(const __grid_constant__ RealArgs a) {
             acc.elj = lane_combine<R>(acc.elj);
         }
         if (active && l == 0) {
-            float fx = acc.fx, fy = acc.fy, fz = acc.fz, phi = acc.phr;
+            s_f[warp * PPW + pl] = make_float4(acc.fx, acc.fy, acc.fz, acc.phr);
             if (want_e) {
                 ec_own += (double)acc.ec;
                 elj_own += (double)acc.elj;
             }
+        }
+        __syncthreads();
+        // the rest runs one thread per particle: total force, outputs, Langevin
+        const int np = min(kPass, nown - pass);
+        if ((int)threadIdx.x < np) {
+            const int i = own_s + pass + threadIdx.x;
+            const int o = a.perm[i];
+            const float4 fr = s_f[threadIdx.x];
+            float fx = fr.x, fy = fr.y, fz = fr.z, phi = fr.w;
             if (a.parts & kPartFourier) {
                 const float4 f = a.fs[o];
                 fx += f.x; fy += f.y; fz += f.z;
                 if (want_phi) {
+                    const double qi = (double)__uint_as_float(a.spos[i].w);
                     const double qs = (double)(long long)__ldcg(a.qsum_fx + sys) / kQScale;
-                    phi += f.w - (float)(2.0 * S.self_coef * (double)qi + S.bg_coef * qs);
+                    phi += f.w - (float)(2.0 * S.self_coef * qi + S.bg_coef * qs);
                 }
             }
             if (a.F_out) a.F_out[o] = make_float4(fx, fy, fz, 0.f);
             if (want_phi) a.phi_out[o] = phi;
-            if (a.md_pos) {
-                const uint64_t step = *a.cur_step;
-                const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
-                const uint4 w = philox4x32_10(make_uint4((uint32_t)(o - S.off_p), 0u,
-                                                         (uint32_t)step, (S.stream << 8) | 0x02u),
-                                              key);
-                const float u1 = (float)((w.x >> 8) + 1u) * 5.9604644775390625e-08f;   // (0, 1]
-                const float u2 = (float)(w.y >> 8) * 5.9604644775390625e-08f;          // [0, 1)
-                const float u3 = (float)((w.z >> 8) + 1u) * 5.9604644775390625e-08f;
-                const float u4 = (float)(w.w >> 8) * 5.9604644775390625e-08f;
-                const float r1 = sqrtf(-2.f * logf(u1)), r3 = sqrtf(-2.f * logf(u3));
-                float s2, c2v, s4, c4;
-                sincospif(2.f * u2, &s2, &c2v);
-                sincospif(2.f * u4, &s4, &c4);
-                const float xi0 = r1 * c2v, xi1 = r1 * s2, xi2 = r3 * c4;
-                const float c1 = S.f_c1, c2 = S.f_c2, dtm = S.f_dt_over_m;
-                const float dt = S.f_dt;
-                float4 v = a.md_vel[o];
-                float4 rp = a.md_pos[o];
-                v.x = fmaf(c1, fmaf(dtm, fx, v.x), c2 * xi0);
-                v.y = fmaf(c1, fmaf(dtm, fy, v.y), c2 * xi1);
-                v.z = fmaf(c1, fmaf(dtm, fz, v.z), c2 * xi2);
-                const float L = S.Lf, invL = S.f_invL;
-                rp.x = fmaf(dt, v.x, rp.x); rp.x -= L * floorf(rp.x * invL);
-                rp.y = fmaf(dt, v.y, rp.y); rp.y -= L * floorf(rp.y * invL);
-                rp.z = fmaf(dt, v.z, rp.z); rp.z -= L * floorf(rp.z * invL);
-                // a coordinate just below 0 can round up to exactly L: that is 0
-                if (rp.x >= L) rp.x = 0.f;
-                if (rp.y >= L) rp.y = 0.f;
-                if (rp.z >= L) rp.z = 0.f;
-                a.md_vel[o] = v;
-                a.md_pos[o] = rp;
-            }
+            if (a.md_pos) langevin_update(a, S, o, fx, fy, fz);
         }
+        __syncthreads();
     }
     if (want_e) {
         const double2 r = block_sum2_real(ec_own, elj_own);
