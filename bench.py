@@ -157,14 +157,28 @@ def cpu_baseline(wl, budget_s):
 
 
 # --------------------------------------------------------------------- distributed
-def dist_setup():
+def dist_setup(backend="nccl"):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group(backend)
     return world, rank, local
+
+
+def replica_stream(base_stream, rank):
+    """Each rank runs its own replica: the same workload on Philox stream
+    base + rank (independent k-batches and Langevin noise, no communication)."""
+    return base_stream + rank
+
+
+def combine_ranks(world, local_seconds, local_particles, steps, device):
+    """Whole-job throughput: particles of all ranks x steps / the slowest rank's
+    time (weak scaling: every rank steps its own replica)."""
+    t_max = reduce_max(local_seconds, world, device)
+    n_all = reduce_sum(float(local_particles), world, device)
+    return {"seconds": t_max, "particles": n_all, "value": n_all * steps / t_max}
 
 
 def barrier(world):
@@ -199,8 +213,9 @@ def source_hash(kernel_file):
 
 
 def traffic_for(kernel, workload_name):
-    """dram bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source; else None."""
+    """dram bytes (read + write) per launch of ``kernel`` on ``workload_name`` from
+    the committed ncu summary (profiles/ncu_traffic.json), if the counters were
+    taken on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
@@ -208,8 +223,8 @@ def traffic_for(kernel, workload_name):
         db = json.load(open(path))
     except ValueError:
         return None
-    e = db.get(kernel)
-    if not e or e.get("workload") != workload_name:
+    e = db.get(kernel, {}).get(workload_name)
+    if not e:
         return None
     src = os.path.join(ROOT, "paper_2010_01559_gb300", "csrc", e["source"])
     if not os.path.exists(src) or source_hash(src) != e.get("source_sha256_16"):
@@ -338,7 +353,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     wl = workload()
     if world > 1:
-        wl.params.stream = rank                      # independent replica per rank
+        wl.params.stream = replica_stream(wl.params.stream, rank)
     K, W = args.steps, args.warmup
     peaks = {}
     pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -392,9 +407,8 @@ def run_ours(args):
     units = unit_peaks(rbe, clk.get("sm_mhz"))
     launches = h.launch_count() - launches0
     h.sync()
-    t_max = reduce_max(total_ms / 1e3, world, dev)
-    n_all = reduce_sum(float(wl.n), world, dev)
-    value = n_all * K / t_max
+    agg = combine_ranks(world, total_ms / 1e3, wl.n, K, dev)
+    t_max, n_all, value = agg["seconds"], agg["particles"], agg["value"]
     ms_per_step = t_max * 1e3 / K
 
     # per-kernel profile of the same steps (events around each kernel)
