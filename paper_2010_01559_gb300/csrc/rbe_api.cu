@@ -117,7 +117,6 @@ struct rbe_ctx {
     int npblk = 0, nfblk = 0, nrblk = 0, nchunks = 0, split = 1, rsplit = 1;
     int nseg = 0, seg_max = 1, stage_cap = 0, seg_threads = 64;
     int max_pblk = 0, max_fblk = 0, max_rblk = 0, max_chunks = 0, max_seg = 0;
-    int tab_smem = 0;                        // table entries staged in shared memory
     size_t max_part = 0;
     bool use_graph = false;
     std::vector<GraphEntry> graphs;
@@ -155,6 +154,7 @@ struct rbe_ctx {
     unsigned long long* d_rho_fx = nullptr;   // rho(k) accumulators (fixed point)
     int* d_kcnt = nullptr;                    // per k tile: chunks done (rho kernel)
     float2* d_kab = nullptr;                  // FP32 force coefficients per k
+    double* d_kcoef = nullptr;                // coef_scale / k^2 per k
     unsigned long long* d_qsum_fx = nullptr;  // sum q per system (fixed point)
     double2* d_blk_e = nullptr;
     double2* d_blk_q = nullptr;
@@ -483,6 +483,7 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_ALLOC(h->d_ksamp, h->ktot);
     RBE_ALLOC(h->d_rho_fx, 2 * (size_t)h->ktot);
     RBE_ALLOC(h->d_kcnt, h->ktot);
+    RBE_ALLOC(h->d_kcoef, h->ktot);
     RBE_ALLOC(h->d_kab, h->ktot);
     RBE_ALLOC(h->d_qsum_fx, h->nsys);
     RBE_ALLOC(h->d_blk_e, std::max<long long>(rb, (long long)kSegChunks * (h->ncell + 1)));
@@ -532,7 +533,7 @@ void release(rbe_ctx* h) {
                     h->d_table, h->d_fx, h->d_spos, h->d_fx64, h->d_spos64, h->d_cid, h->d_rank,
                     h->d_perm, h->d_perm_tmp, h->d_fs, h->d_fs64, h->d_cell_cnt,
                     h->d_cell_start, h->d_ksamp, h->d_rho_fx, h->d_kcnt, h->d_kab,
-                    h->d_qsum_fx, h->d_blk_e, h->d_blk_q, h->d_cur_step, h->d_stage_step,
+                    h->d_kcoef, h->d_qsum_fx, h->d_blk_e, h->d_blk_q, h->d_cur_step, h->d_stage_step,
                     h->d_err, h->d_stage_pos, h->d_stage_vel, h->d_stage_F, h->d_stage_E};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -587,11 +588,6 @@ rbe_status create_common(const rbe_params* ps, const int32_t* ns, int nsys, bool
     }
     h->ntot = off_p;
     h->ncell = off_c;
-    {
-        int tmax = 0;
-        for (auto& sh : h->sys) tmax = std::max(tmax, 2 * sh.M);
-        h->tab_smem = tmax <= 8192 ? tmax : 0;
-    }
     h->ktot = off_k;
     h->ttot = off_t;
     rbe_status st = allocate(h);
@@ -671,11 +667,10 @@ void launch_rho(const rbe_ctx* h, cudaStream_t st, bool mixed) {
     const int ltiles = (h->pmax + kLTile - 1) / kLTile;
     const Work w = make_work(h, h->d_chunks, h->cur_chunk, 1);
     if (mixed)
-        launch_rho_mixed(st, one, w, h->nchunks, ltiles, h->tab_smem, h->d_table, h->d_cur_step,
-                         h->d_fx, h->d_rho_fx, h->d_ksamp, h->d_kcnt, h->d_kab, h->d_err);
+        launch_rho_mixed(st, one, w, h->nchunks, ltiles, h->d_ksamp, h->d_kcoef, h->d_fx,
+                         h->d_rho_fx, h->d_kcnt, h->d_kab);
     else
-        launch_rho_f64(st, one, w, h->nchunks, ltiles, h->tab_smem, h->d_table, h->d_cur_step,
-                       h->d_fx64, h->d_rho_fx, h->d_ksamp, h->d_err);
+        launch_rho_f64(st, one, w, h->nchunks, ltiles, h->d_ksamp, h->d_fx64, h->d_rho_fx);
 }
 
 void launch_force(const rbe_ctx* h, cudaStream_t st, bool mixed) {
@@ -726,6 +721,15 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     pa.step_dev = a.step_dev;
     pa.step_arg = a.step;
     pa.cur_step = h->d_cur_step;
+    pa.npblk = h->npblk;
+    pa.ktot = fourier ? h->ktot : 0;
+    pa.nsys = h->nsys;
+    pa.kstart = h->d_kstart;
+    pa.table = h->d_table;
+    pa.tab_words = h->ttot <= 8192 ? h->ttot : 0;    // 32 KB of shared memory at most
+    pa.ksamp = h->d_ksamp;
+    pa.kcoef = h->d_kcoef;
+    pa.err = h->d_err;
     if (want_q)
         cudaMemsetAsync(h->d_qsum_fx, 0, sizeof(unsigned long long) * h->nsys, st);
     run(RBE_K_PREP, st, [&] {
@@ -743,7 +747,9 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
         run(RBE_K_FOURIER_FORCE, st2, [&] { launch_force(h, st2, mixed); });
         cudaEventRecord(h->ev_join, st2);
     }
-    run(RBE_K_SCAN, st, [&] { launch_scan(st, h->d_cell_cnt, h->d_cell_start, h->ncell); });
+    run(RBE_K_SCAN, st, [&] {
+        launch_scan(st, h->d_cell_cnt, h->d_cell_start, h->ncell, a.step_dev, h->d_cur_step);
+    });
     run(RBE_K_SCATTER, st, [&] {
         launch_scatter(st, n, h->d_cid, h->d_rank, h->d_cell_start, h->d_perm_tmp);
     });

@@ -54,23 +54,43 @@ __device__ __forceinline__ double2 block_sum2(double a, double b) {
 }
 
 // Thread 0 of block 0 latches the step index of this evaluation: the
-// caller's device counter (incremented here, once per step) or the host value.
-__device__ __forceinline__ void latch_step(uint64_t* step_dev, uint64_t step_arg,
+// caller's device counter or the host value.  The counter is advanced by the
+// cell-count scan, a later kernel, so every block of this one reads the same
+// value.
+__device__ __forceinline__ void latch_step(const uint64_t* step_dev, uint64_t step_arg,
                                           uint64_t* cur_step) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (step_dev) {
-            const uint64_t s = *step_dev;
-            *cur_step = s;
-            *step_dev = s + 1;
-        } else {
-            *cur_step = step_arg;
-        }
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *cur_step = step_dev ? *step_dev : step_arg;
 }
 
-// Zero the rho(k) accumulators for this evaluation (grid-stride).
-__device__ __forceinline__ void clear_rho(unsigned long long* rho_fx, int nrho) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 2 * nrho; k += gridDim.x * blockDim.x)
+// The k-batch of this step (Eq. probexpression): the blocks after the particle
+// blocks draw one sample per thread and its coefficient coef_scale / k^2 of
+// Eq. rbmapprox, for the structure-factor and force passes that follow.
+template <bool ONE>
+__device__ __forceinline__ void draw_samples(const Work& w, const PrepArgs& pa) {
+    extern __shared__ uint32_t s_tab[];
+    if (pa.tab_words > 0) {
+        for (int j = threadIdx.x; j < pa.tab_words; j += blockDim.x)
+            s_tab[j] = (uint32_t)__ldg(pa.table + j);
+        __syncthreads();
+    }
+    const int g = ((int)blockIdx.x - pa.npblk) * blockDim.x + threadIdx.x;
+    if (g >= pa.ktot) return;
+    const int s = ONE ? 0 : find_sys(pa.kstart, pa.nsys, g);
+    const SysDev& S = sys_of<ONE>(w, s);
+    const uint64_t step = pa.step_dev ? *pa.step_dev : pa.step_arg;
+    const int4 m = pa.tab_words > 0
+                       ? sample_one_smem(S, s_tab + S.off_t, g - S.off_k, step, pa.err)
+                       : sample_one(S, pa.table + S.off_t, g - S.off_k, step, pa.err);
+    pa.ksamp[g] = m;
+    const double tp = 2.0 * M_PI * S.invL;
+    const double k2 = tp * tp * ((double)m.x * m.x + (double)m.y * m.y + (double)m.z * m.z);
+    pa.kcoef[g] = S.coef_scale / k2;
+}
+
+// Zero the rho(k) accumulators for this evaluation (stride over the nblk
+// particle blocks; the sampling blocks after them do not take part).
+__device__ __forceinline__ void clear_rho(unsigned long long* rho_fx, int nrho, int nblk) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 2 * nrho; k += nblk * blockDim.x)
         rho_fx[k] = 0ull;
 }
 
@@ -79,8 +99,12 @@ __global__ void __launch_bounds__(kBlockP)
 k_prep_mixed(const __grid_constant__ Work w, const float4* __restrict__ pos_q,
              uint4* __restrict__ fx, int* __restrict__ cid, int* __restrict__ rank,
              int* __restrict__ cell_cnt, const __grid_constant__ PrepArgs pa) {
+    if ((int)blockIdx.x >= pa.npblk) {             // a k-sampling block
+        draw_samples<ONE>(w, pa);
+        return;
+    }
     latch_step(pa.step_dev, pa.step_arg, pa.cur_step);
-    clear_rho(pa.rho_fx, pa.nrho);
+    clear_rho(pa.rho_fx, pa.nrho, pa.npblk);
     const Tile tl = tile_of<ONE>(w);
     const SysDev& S = sys_of<ONE>(w, tl.sys);
     const int t = threadIdx.x;
@@ -127,8 +151,12 @@ __global__ void __launch_bounds__(kBlockP)
 k_prep_f64(const __grid_constant__ Work w, const double4* __restrict__ pos_q,
            double4* __restrict__ fx64, int* __restrict__ cid, int* __restrict__ rank,
            int* __restrict__ cell_cnt, const __grid_constant__ PrepArgs pa) {
+    if ((int)blockIdx.x >= pa.npblk) {             // a k-sampling block
+        draw_samples<ONE>(w, pa);
+        return;
+    }
     latch_step(pa.step_dev, pa.step_arg, pa.cur_step);
-    clear_rho(pa.rho_fx, pa.nrho);
+    clear_rho(pa.rho_fx, pa.nrho, pa.npblk);
     const Tile tl = tile_of<ONE>(w);
     const SysDev& S = sys_of<ONE>(w, tl.sys);
     const int t = threadIdx.x;
@@ -164,7 +192,9 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanPer = 4;
 
 __global__ void __launch_bounds__(kScanThreads)
-k_scan(int* __restrict__ cell_cnt, int* __restrict__ cell_start, int ncell) {
+k_scan(int* __restrict__ cell_cnt, int* __restrict__ cell_start, int ncell,
+       uint64_t* __restrict__ step_dev, const uint64_t* __restrict__ cur_step) {
+    if (step_dev && threadIdx.x == 0) *step_dev = *cur_step + 1;   // one increment per step
     __shared__ int warp_tot[kScanThreads / 32];
     __shared__ int carry_s;
     if (threadIdx.x == 0) carry_s = 0;
@@ -261,24 +291,29 @@ __global__ void k_order(int n, const int* __restrict__ cid, const int* __restric
 // ------------------------------------------------------------- launchers
 void launch_prep_mixed(cudaStream_t st, bool one, const Work& w, int nblk, const float4* pos_q,
                        uint4* fx, int* cid, int* rank, int* cell_cnt, const PrepArgs& pa) {
+    nblk += (pa.ktot + kBlockP - 1) / kBlockP;       // particle blocks, then sampling blocks
     if (nblk <= 0) return;
+    const size_t smem = sizeof(uint32_t) * (size_t)pa.tab_words;
     if (one)
-        k_prep_mixed<true><<<nblk, kBlockP, 0, st>>>(w, pos_q, fx, cid, rank, cell_cnt, pa);
+        k_prep_mixed<true><<<nblk, kBlockP, smem, st>>>(w, pos_q, fx, cid, rank, cell_cnt, pa);
     else
-        k_prep_mixed<false><<<nblk, kBlockP, 0, st>>>(w, pos_q, fx, cid, rank, cell_cnt, pa);
+        k_prep_mixed<false><<<nblk, kBlockP, smem, st>>>(w, pos_q, fx, cid, rank, cell_cnt, pa);
 }
 
 void launch_prep_f64(cudaStream_t st, bool one, const Work& w, int nblk, const double4* pos_q,
                      double4* fx64, int* cid, int* rank, int* cell_cnt, const PrepArgs& pa) {
+    nblk += (pa.ktot + kBlockP - 1) / kBlockP;       // particle blocks, then sampling blocks
     if (nblk <= 0) return;
+    const size_t smem = sizeof(uint32_t) * (size_t)pa.tab_words;
     if (one)
-        k_prep_f64<true><<<nblk, kBlockP, 0, st>>>(w, pos_q, fx64, cid, rank, cell_cnt, pa);
+        k_prep_f64<true><<<nblk, kBlockP, smem, st>>>(w, pos_q, fx64, cid, rank, cell_cnt, pa);
     else
-        k_prep_f64<false><<<nblk, kBlockP, 0, st>>>(w, pos_q, fx64, cid, rank, cell_cnt, pa);
+        k_prep_f64<false><<<nblk, kBlockP, smem, st>>>(w, pos_q, fx64, cid, rank, cell_cnt, pa);
 }
 
-void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell) {
-    k_scan<<<1, kScanThreads, 0, st>>>(cell_cnt, cell_start, ncell);
+void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell, uint64_t* step_dev,
+                 const uint64_t* cur_step) {
+    k_scan<<<1, kScanThreads, 0, st>>>(cell_cnt, cell_start, ncell, step_dev, cur_step);
 }
 
 void launch_scatter(cudaStream_t st, int n, const int* cid, const int* rank,

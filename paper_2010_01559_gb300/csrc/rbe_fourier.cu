@@ -30,64 +30,6 @@ namespace rbe {
 constexpr float kTwoPiOver2p32 = 1.4629180792671596e-09f;   // 2 pi / 2^32
 constexpr int kStage = 512;                                 // particles staged per pass
 
-// Smallest j in [0, n) with w < T[j] (T[n-1] = 2^32 > any w).
-__device__ __forceinline__ int axis_lookup(const uint64_t* __restrict__ T, int n, uint32_t w) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if ((uint64_t)w < __ldg(T + mid)) hi = mid; else lo = mid + 1;
-    }
-    return lo;
-}
-
-// Sample l of system S at `step`: (m_x, m_y, m_z, attempts).
-__device__ __forceinline__ int4 sample_one(const SysDev& S, const uint64_t* __restrict__ T, int l,
-                                           uint64_t step, int* err) {
-    const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
-    const int n = 2 * S.M + 1;
-    for (int a = 0; a < kMaxAttempts; ++a) {
-        const uint4 w = philox4x32_10(
-            make_uint4((uint32_t)l, (uint32_t)a, (uint32_t)step, (S.stream << 8) | 0x01u), key);
-        const int mx = axis_lookup(T, n, w.x) - S.M;
-        const int my = axis_lookup(T, n, w.y) - S.M;
-        const int mz = axis_lookup(T, n, w.z) - S.M;
-        if (mx != 0 || my != 0 || mz != 0) return make_int4(mx, my, mz, a + 1);
-    }
-    atomicOr(err, kErrSampler);
-    return make_int4(1, 0, 0, kMaxAttempts + 1);   // keeps later arithmetic finite
-}
-
-// As sample_one, with the table's first 2M entries staged in shared memory as
-// 32-bit words (entry 2M = 2^32 is implicit).
-__device__ __forceinline__ int4 sample_one_smem(const SysDev& S, const uint32_t* __restrict__ T,
-                                                int l, uint64_t step, int* err) {
-    const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
-    const int last = 2 * S.M;
-    auto lookup = [&](uint32_t w) {
-        int lo = 0, hi = last;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (w < T[mid]) hi = mid; else lo = mid + 1;
-        }
-        return lo - S.M;
-    };
-    for (int a = 0; a < kMaxAttempts; ++a) {
-        const uint4 w = philox4x32_10(
-            make_uint4((uint32_t)l, (uint32_t)a, (uint32_t)step, (S.stream << 8) | 0x01u), key);
-        const int mx = lookup(w.x), my = lookup(w.y), mz = lookup(w.z);
-        if (mx != 0 || my != 0 || mz != 0) return make_int4(mx, my, mz, a + 1);
-    }
-    atomicOr(err, kErrSampler);
-    return make_int4(1, 0, 0, kMaxAttempts + 1);
-}
-
-// Stage the first 2M table entries of system S into shared memory.
-__device__ __forceinline__ void stage_table(const SysDev& S, const uint64_t* __restrict__ table,
-                                            uint32_t* s_tab) {
-    const uint64_t* T = table + S.off_t;
-    for (int j = threadIdx.x; j < 2 * S.M; j += blockDim.x) s_tab[j] = (uint32_t)__ldg(T + j);
-}
-
 __global__ void k_sample(const SysDev* __restrict__ sysv, int nsys, int ktot,
                          const int* __restrict__ kstart, const uint64_t* __restrict__ table,
                          const uint64_t* __restrict__ cur_step, int4* __restrict__ ksamp,
@@ -113,27 +55,18 @@ __device__ __forceinline__ double2 kcoef(const SysDev& S, int4 m,
 // ----------------------------------------------------------------- rho (mixed)
 template <bool ONE>
 __global__ void __launch_bounds__(kLTile)
-k_rho_mixed(const __grid_constant__ Work w, int tab_smem, const uint64_t* __restrict__ table,
-            const uint64_t* __restrict__ cur_step, const uint4* __restrict__ fx,
-            unsigned long long* __restrict__ rho_fx, int4* __restrict__ ksamp,
-            int* __restrict__ kcnt, float2* __restrict__ kab, int* __restrict__ err) {
+k_rho_mixed(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
+            const double* __restrict__ kcoef, const uint4* __restrict__ fx,
+            unsigned long long* __restrict__ rho_fx, int* __restrict__ kcnt,
+            float2* __restrict__ kab) {
     __shared__ uint4 sp[kStage];
-    extern __shared__ uint32_t s_tab[];
     const Tile ch = tile_of<ONE>(w);
     const SysDev& S = sys_of<ONE>(w, ch.sys);
     const int l = blockIdx.y * kLTile + threadIdx.x;
     if (blockIdx.y * kLTile >= S.P) return;          // whole block beyond this system's P
     const bool active = l < S.P;
-    if (tab_smem) {
-        stage_table(S, table, s_tab);
-        __syncthreads();
-    }
     int4 m = make_int4(0, 0, 0, 0);
-    if (active) {
-        m = tab_smem ? sample_one_smem(S, s_tab, l, *cur_step, err)
-                     : sample_one(S, table + S.off_t, l, *cur_step, err);
-        if (ch.aux == 0) ksamp[S.off_k + l] = m;
-    }
+    if (active) m = ksamp[S.off_k + l];              // drawn by the prep kernel
     const uint32_t mx = (uint32_t)m.x, my = (uint32_t)m.y, mz = (uint32_t)m.z;
     float re = 0.f, im = 0.f;
     for (int base = 0; base < ch.count; base += kStage) {
@@ -170,8 +103,9 @@ k_rho_mixed(const __grid_constant__ Work w, int tab_smem, const uint64_t* __rest
     if (s_last) {
         __threadfence();
         if (active) {
-            const double2 ab = kcoef(S, m, rho_fx + 2 * (S.off_k + l));
-            kab[S.off_k + l] = make_float2((float)ab.x, (float)ab.y);
+            const double2 r = rho_read(rho_fx + 2 * (S.off_k + l), S.rho_inv_scale);
+            const double c = kcoef[S.off_k + l];
+            kab[S.off_k + l] = make_float2((float)(c * r.y), (float)(c * r.x));
         }
         if (threadIdx.x == 0) kcnt[slot] = 0;        // ready for the next evaluation
     }
@@ -180,27 +114,16 @@ k_rho_mixed(const __grid_constant__ Work w, int tab_smem, const uint64_t* __rest
 // ----------------------------------------------------------------- rho (FP64)
 template <bool ONE>
 __global__ void __launch_bounds__(kLTile)
-k_rho_f64(const __grid_constant__ Work w, int tab_smem, const uint64_t* __restrict__ table,
-          const uint64_t* __restrict__ cur_step, const double4* __restrict__ fx64,
-          unsigned long long* __restrict__ rho_fx, int4* __restrict__ ksamp,
-          int* __restrict__ err) {
+k_rho_f64(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
+          const double4* __restrict__ fx64, unsigned long long* __restrict__ rho_fx) {
     __shared__ double4 sp[kStage / 2];
-    extern __shared__ uint32_t s_tab[];
     const Tile ch = tile_of<ONE>(w);
     const SysDev& S = sys_of<ONE>(w, ch.sys);
     const int l = blockIdx.y * kLTile + threadIdx.x;
     if (blockIdx.y * kLTile >= S.P) return;
     const bool active = l < S.P;
-    if (tab_smem) {
-        stage_table(S, table, s_tab);
-        __syncthreads();
-    }
     int4 m = make_int4(0, 0, 0, 0);
-    if (active) {
-        m = tab_smem ? sample_one_smem(S, s_tab, l, *cur_step, err)
-                     : sample_one(S, table + S.off_t, l, *cur_step, err);
-        if (ch.aux == 0) ksamp[S.off_k + l] = m;
-    }
+    if (active) m = ksamp[S.off_k + l];
     const double tp = 2.0 * M_PI * S.invL;
     const double kx = tp * m.x, ky = tp * m.y, kz = tp * m.z;
     double re = 0.0, im = 0.0;
@@ -341,35 +264,26 @@ void launch_sample(cudaStream_t st, const SysDev* sys, int nsys, int ktot, const
                                                  err);
 }
 
-// tab_smem: number of 32-bit table entries to stage per block (max 2M over the
-// systems), 0 to search the table in global memory.
+// The k-batch (ksamp) and coef_scale / k^2 (kcoef) come from the prep kernel.
 void launch_rho_mixed(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
-                      int tab_smem, const uint64_t* table, const uint64_t* cur_step,
-                      const uint4* fx, unsigned long long* rho_fx, int4* ksamp, int* kcnt,
-                      float2* kab, int* err) {
+                      const int4* ksamp, const double* kcoef, const uint4* fx,
+                      unsigned long long* rho_fx, int* kcnt, float2* kab) {
     if (nchunks <= 0 || ltiles <= 0) return;
     dim3 grid(nchunks, ltiles);
-    const size_t smem = sizeof(uint32_t) * tab_smem;
     if (one)
-        k_rho_mixed<true><<<grid, kLTile, smem, st>>>(w, tab_smem > 0, table, cur_step, fx,
-                                                      rho_fx, ksamp, kcnt, kab, err);
+        k_rho_mixed<true><<<grid, kLTile, 0, st>>>(w, ksamp, kcoef, fx, rho_fx, kcnt, kab);
     else
-        k_rho_mixed<false><<<grid, kLTile, smem, st>>>(w, tab_smem > 0, table, cur_step, fx,
-                                                       rho_fx, ksamp, kcnt, kab, err);
+        k_rho_mixed<false><<<grid, kLTile, 0, st>>>(w, ksamp, kcoef, fx, rho_fx, kcnt, kab);
 }
 
 void launch_rho_f64(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
-                    int tab_smem, const uint64_t* table, const uint64_t* cur_step,
-                    const double4* fx64, unsigned long long* rho_fx, int4* ksamp, int* err) {
+                    const int4* ksamp, const double4* fx64, unsigned long long* rho_fx) {
     if (nchunks <= 0 || ltiles <= 0) return;
     dim3 grid(nchunks, ltiles);
-    const size_t smem = sizeof(uint32_t) * tab_smem;
     if (one)
-        k_rho_f64<true><<<grid, kLTile, smem, st>>>(w, tab_smem > 0, table, cur_step, fx64,
-                                                    rho_fx, ksamp, err);
+        k_rho_f64<true><<<grid, kLTile, 0, st>>>(w, ksamp, fx64, rho_fx);
     else
-        k_rho_f64<false><<<grid, kLTile, smem, st>>>(w, tab_smem > 0, table, cur_step, fx64,
-                                                     rho_fx, ksamp, err);
+        k_rho_f64<false><<<grid, kLTile, 0, st>>>(w, ksamp, fx64, rho_fx);
 }
 
 template <int SPLIT>

@@ -129,6 +129,59 @@ __device__ __forceinline__ int find_sys(const int* __restrict__ start, int nsys,
     return lo;
 }
 
+// Smallest j in [0, n) with w < T[j] (T[n-1] = 2^32 > any w).
+__device__ __forceinline__ int axis_lookup(const uint64_t* __restrict__ T, int n, uint32_t w) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((uint64_t)w < __ldg(T + mid)) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// Sample l of system S at `step` (Eq. probexpression, exact inverse CDF per
+// axis, (0,0,0) redrawn): (m_x, m_y, m_z, attempts).
+__device__ __forceinline__ int4 sample_one(const SysDev& S, const uint64_t* __restrict__ T, int l,
+                                           uint64_t step, int* err) {
+    const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
+    const int n = 2 * S.M + 1;
+    for (int a = 0; a < kMaxAttempts; ++a) {
+        const uint4 w = philox4x32_10(
+            make_uint4((uint32_t)l, (uint32_t)a, (uint32_t)step, (S.stream << 8) | 0x01u), key);
+        const int mx = axis_lookup(T, n, w.x) - S.M;
+        const int my = axis_lookup(T, n, w.y) - S.M;
+        const int mz = axis_lookup(T, n, w.z) - S.M;
+        if (mx != 0 || my != 0 || mz != 0) return make_int4(mx, my, mz, a + 1);
+    }
+    atomicOr(err, kErrSampler);
+    return make_int4(1, 0, 0, kMaxAttempts + 1);   // keeps later arithmetic finite
+}
+
+// As sample_one, with the tables staged in shared memory as 32-bit words (the
+// last entry of each system's table, 2^32, is never read: the search ends at
+// index 2M by construction).
+__device__ __forceinline__ int4 sample_one_smem(const SysDev& S, const uint32_t* __restrict__ T,
+                                                int l, uint64_t step, int* err) {
+    const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
+    const int last = 2 * S.M;
+    auto lookup = [&](uint32_t w) {
+        int lo = 0, hi = last;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (w < T[mid]) hi = mid; else lo = mid + 1;
+        }
+        return lo - S.M;
+    };
+    for (int a = 0; a < kMaxAttempts; ++a) {
+        const uint4 w = philox4x32_10(
+            make_uint4((uint32_t)l, (uint32_t)a, (uint32_t)step, (S.stream << 8) | 0x01u), key);
+        const int mx = lookup(w.x), my = lookup(w.y), mz = lookup(w.z);
+        if (mx != 0 || my != 0 || mz != 0) return make_int4(mx, my, mz, a + 1);
+    }
+    atomicOr(err, kErrSampler);
+    return make_int4(1, 0, 0, kMaxAttempts + 1);
+}
+
 // ------------------------------------------------------------- launchers
 // `one` selects the single-system kernels (Work.one / Work.tile), else tables.
 // cells / sorting (rbe_cells.cu)
@@ -143,12 +196,22 @@ struct PrepArgs {
     uint64_t* step_dev;
     uint64_t step_arg;
     uint64_t* cur_step;
+    // k-batch drawn by the blocks after the particle blocks (one sample per thread)
+    int npblk;               // particle blocks; blocks npblk .. draw samples
+    int ktot, nsys;
+    const int* kstart;       // first sample of each system (nsys + 1)
+    const uint64_t* table;
+    int tab_words;           // > 0: all tables (this many entries) staged in shared memory
+    int4* ksamp;
+    double* kcoef;           // coef_scale / k^2 per sample (Eq. rbmapprox)
+    int* err;
 };
 void launch_prep_mixed(cudaStream_t st, bool one, const Work& w, int nblk, const float4* pos_q,
                        uint4* fx, int* cid, int* rank, int* cell_cnt, const PrepArgs& pa);
 void launch_prep_f64(cudaStream_t st, bool one, const Work& w, int nblk, const double4* pos_q,
                      double4* fx64, int* cid, int* rank, int* cell_cnt, const PrepArgs& pa);
-void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell);
+void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell, uint64_t* step_dev,
+                 const uint64_t* cur_step);
 void launch_scatter(cudaStream_t st, int n, const int* cid, const int* rank,
                     const int* cell_start, int* perm_tmp);
 void launch_order(cudaStream_t st, int n, const int* cid, const int* cell_start,
@@ -172,12 +235,10 @@ __device__ __forceinline__ double2 rho_read(const unsigned long long* src, doubl
 }
 
 void launch_rho_mixed(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
-                      int tab_smem, const uint64_t* table, const uint64_t* cur_step,
-                      const uint4* fx, unsigned long long* rho_fx, int4* ksamp, int* kcnt,
-                      float2* kab, int* err);
+                      const int4* ksamp, const double* kcoef, const uint4* fx,
+                      unsigned long long* rho_fx, int* kcnt, float2* kab);
 void launch_rho_f64(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
-                    int tab_smem, const uint64_t* table, const uint64_t* cur_step,
-                    const double4* fx64, unsigned long long* rho_fx, int4* ksamp, int* err);
+                    const int4* ksamp, const double4* fx64, unsigned long long* rho_fx);
 void launch_fourier_force_mixed(cudaStream_t st, bool one, const Work& w, int nblk, int split,
                                 const uint4* fx, const int4* ksamp, const float2* kab,
                                 float4* fs);
