@@ -100,6 +100,16 @@ def _load():
                                           ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
                                           ctypes.c_uint64]
         lib.orc_langevin_step.restype = None
+        lib.orc_mh_tables.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, _U64, _D]
+        lib.orc_mh_tables.restype = None
+        lib.orc_mh_sample_k.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                        ctypes.c_uint32, ctypes.c_int, _I32, _U64, _I32]
+        lib.orc_mh_sample_k.restype = ctypes.c_int
+        lib.orc_andersen_step.argtypes = [ctypes.c_int, _D, _D, _D, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
+                                          ctypes.c_uint64, _INT]
+        lib.orc_andersen_step.restype = None
         _lib = lib
         return lib
 
@@ -162,6 +172,37 @@ def sample_k(alpha, L, seed, stream, step, P):
     bad = lib.orc_sample_k(alpha, L, seed, stream, step, P, m.ctypes.data_as(_I32),
                            att.ctypes.data_as(_I32))
     return m, att, int(bad)
+
+
+class MHChain:
+    """The paper's Metropolis-Hastings k-sampler (Sec. 3.1): three per-axis
+    independence chains with the rounded-Gaussian proposal, consumed in order
+    (the set K of Algorithm 1).  ``draw(P)`` returns the next P nonzero triples
+    and advances the chains."""
+
+    def __init__(self, alpha, L, seed, stream, state=(0, 0, 0), pos=0):
+        self.alpha, self.L, self.seed, self.stream = alpha, L, seed, stream
+        self.state = np.array(state, dtype=np.int32)
+        self.pos = np.array([pos], dtype=np.uint64)
+
+    def draw(self, P):
+        m = np.zeros((P, 3), dtype=np.int32)
+        bad = _load().orc_mh_sample_k(self.alpha, self.L, self.seed, self.stream, P,
+                                      self.state.ctypes.data_as(_I32),
+                                      self.pos.ctypes.data_as(_U64), m.ctypes.data_as(_I32))
+        if bad:
+            raise RuntimeError("MH chain emitted fewer than P nonzero triples")
+        return m
+
+
+def mh_tables(alpha, L):
+    """(Tq uint64[2M+1], rho float64[2M+1], M): proposal thresholds and P/qbar."""
+    lib = _load()
+    M = lib.orc_axis_M(alpha, L)
+    Tq = np.zeros(2 * M + 1, dtype=np.uint64)
+    rho = np.zeros(2 * M + 1)
+    lib.orc_mh_tables(alpha, L, M, Tq.ctypes.data_as(_U64), _dp(rho))
+    return Tq, rho, M
 
 
 # ---------------------------------------------------------------- Fourier part
@@ -259,15 +300,29 @@ def langevin_step(pos, vel, F, L, gamma, kT, dt, mass, seed, stream, step):
     return pos, vel
 
 
+def andersen_step(pos, vel, F, L, nu, kT, dt, mass, seed, stream, step):
+    """One leapfrog step with Andersen collisions; returns (pos, vel, collided)."""
+    pos = _f64(pos, (-1, 3)).copy(); vel = _f64(vel, (-1, 3)).copy(); F = _f64(F, (-1, 3))
+    hit = np.zeros(len(pos), dtype=np.int32)
+    _load().orc_andersen_step(len(pos), _dp(pos), _dp(vel), _dp(F), L, nu, kT, dt, mass,
+                              seed, stream, step, hit.ctypes.data_as(_INT))
+    return pos, vel, hit.astype(bool)
+
+
 # ---------------------------------------------------------------- composites
 def rbe_forces(pos, q, L, alpha, r_c, P, seed, stream, step, lB=1.0, lj_eps=0.0,
-               lj_sigma=1.0, lj_rcut=0.0, sub=None, want_phi=False):
+               lj_sigma=1.0, lj_rcut=0.0, sub=None, want_phi=False, m=None):
     """One RBE force evaluation (sample, Fourier estimator, real space, LJ).
 
     Returns a dict with m, E parts (total, fourier, real, lj), forces per part
     and their sum, and optionally phi = dE/dq.  Forces for ``sub`` only if given.
+    ``m`` (P x 3) replaces the i.i.d. sample of this step (e.g. the MH chain's).
     """
-    m, att, bad = sample_k(alpha, L, seed, stream, step, P)
+    if m is None:
+        m, att, bad = sample_k(alpha, L, seed, stream, step, P)
+    else:
+        m = np.ascontiguousarray(m, dtype=np.int32)
+        att, bad = np.ones(len(m), dtype=np.int32), 0
     S = S_of(alpha, L)
     Ef, Ff, phif, rho = rbe_fourier(pos, q, L, alpha, m, S=S, lB=lB, sub=sub, want_phi=want_phi)
     Ec, Elj, Fc, Flj, phir = real_space(pos, q, L, alpha, r_c, lB=lB, lj_eps=lj_eps,

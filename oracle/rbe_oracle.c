@@ -482,3 +482,144 @@ void orc_langevin_step(int N, double *pos, double *vel, const double *F, double 
     }
     free(xi);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Metropolis-Hastings sampling of the per-axis marginal P(m) as the paper    */
+/* prints it (Sec. 3.1): the proposal m* = round(x*), x* ~ N(0, alpha L^2 /   */
+/* (2 pi^2)), has the pmf                                                     */
+/*   qbar(0) = erf(1/(2s)),                                                   */
+/*   qbar(m) = (erf((|m|+1/2)/s) - erf((|m|-1/2)/s)) / 2,  s = sqrt(alpha) L/pi,*/
+/* written here with erfc (same value, no cancellation in the tails).  The    */
+/* chain is an independence sampler: from state m it accepts m* with          */
+/* probability min(1, [P(m*)/qbar(m*)] / [P(m)/qbar(m)]) (the garbled         */
+/* "accepted with probability q(m*|m)" read as the standard MH rule).  Three  */
+/* independent chains give m_x, m_y, m_z; triples (0,0,0) are discarded; the  */
+/* chain is consumed in order, P nonzero triples per step (the set K of       */
+/* Algorithm 1).                                                              */
+/*                                                                            */
+/* Tables over |m| <= M (index j = m + M):                                    */
+/*   Tq[j] = floor(2^32 * (sum_{i<=j} qbar_i) / (sum_all qbar)), Tq[2M] = 2^32 */
+/*   rho[j] = exp(-pi^2 m^2 / (alpha L^2)) / qbar(m)   (ratios are what count) */
+/* Iteration t of the chains: for axis c, w = Philox(key = seed,              */
+/* ctr = (t_lo, t_hi, c, (stream << 8) | 6)); m* = inverse-CDF lookup of w0 in */
+/* Tq; u = ((w2 << 32 | w3) >> 11) 2^-53; accept iff u * rho(m) < rho(m*).    */
+/* ------------------------------------------------------------------------- */
+void orc_mh_tables(double alpha, double L, int M, uint64_t *Tq, double *rho)
+{
+    const int n = 2 * M + 1;
+    const double s = sqrt(alpha) * L / M_PI;
+    const double a = (M_PI * M_PI) / (alpha * L * L);
+    double *qb = (double *)malloc(sizeof(double) * (size_t)n);
+    double Q = 0.0;
+    for (int j = 0; j < n; ++j) {
+        int m = j - M;
+        int am = m < 0 ? -m : m;
+        if (am == 0)
+            qb[j] = erf(0.5 / s);
+        else
+            qb[j] = 0.5 * (erfc(((double)am - 0.5) / s) - erfc(((double)am + 0.5) / s));
+        Q += qb[j];
+    }
+    double cum = 0.0;
+    for (int j = 0; j < n; ++j) {
+        cum += qb[j];
+        if (j == n - 1) {
+            Tq[j] = 4294967296ull;
+        } else {
+            double f = floor((cum / Q) * 4294967296.0);
+            if (f > 4294967295.0) f = 4294967295.0;
+            Tq[j] = (uint64_t)f;
+        }
+        long mm = (long)(j - M) * (long)(j - M);
+        rho[j] = exp(-(a * (double)mm)) / qb[j];
+    }
+    free(qb);
+}
+
+/* Advance the three chains from state[3] / *pos (iterations done) until P
+ * nonzero triples are emitted into m_out (P x 3).  Returns 0, or 1 if more
+ * than 64 P + 1024 iterations were needed (then the rest is zero). */
+int orc_mh_sample_k(double alpha, double L, uint64_t seed, uint32_t stream, int P,
+                    int32_t *state, uint64_t *pos, int32_t *m_out)
+{
+    int M = orc_axis_M(alpha, L);
+    int n = 2 * M + 1;
+    uint64_t *Tq = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    double *rho = (double *)malloc(sizeof(double) * (size_t)n);
+    orc_mh_tables(alpha, L, M, Tq, rho);
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint64_t t = *pos;
+    const uint64_t tmax = t + 64ull * (uint64_t)P + 1024ull;
+    int emitted = 0, bad = 0;
+    while (emitted < P) {
+        if (t >= tmax) { bad = 1; break; }
+        for (int c = 0; c < 3; ++c) {
+            uint32_t ctr[4] = {(uint32_t)t, (uint32_t)(t >> 32), (uint32_t)c, (stream << 8) | 0x06u};
+            uint32_t w[4];
+            orc_philox4x32_10(ctr, key, w);
+            int ms = orc_axis_lookup(Tq, M, w[0]);
+            double u = (double)(((uint64_t)w[2] << 32 | (uint64_t)w[3]) >> 11) * 0x1.0p-53;
+            volatile double lhs = u * rho[state[c] + M];     /* rounded product, no fma */
+            if (lhs < rho[ms + M]) state[c] = ms;
+        }
+        ++t;
+        if (state[0] != 0 || state[1] != 0 || state[2] != 0) {
+            m_out[3 * emitted + 0] = state[0];
+            m_out[3 * emitted + 1] = state[1];
+            m_out[3 * emitted + 2] = state[2];
+            ++emitted;
+        }
+    }
+    for (int l = emitted; l < P; ++l) m_out[3 * l] = m_out[3 * l + 1] = m_out[3 * l + 2] = 0;
+    *pos = t;
+    free(Tq);
+    free(rho);
+    return bad;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Leapfrog with the Andersen thermostat, the loop step of Algorithm 1 as    */
+/* printed (Sec. 3.1, steps (2) and (3)):                                    */
+/*   v^{n+1/2} = v^{n-1/2} + (dt/m) F^n;  r^{n+1} = wrap(r^n + dt v^{n+1/2}); */
+/*   then, with probability nu dt, v^{n+1/2} <- N(0, kT/m) per component.    */
+/* (The first call, from v^0, is the Euler start the paper mentions.)        */
+/* Particle i at step n: collision iff w0 < floor(nu dt 2^32) with           */
+/* w = Philox(key = seed, ctr = (i, 0, step_lo, (stream << 8) | 7)); the new  */
+/* velocity's normals come from ctr = (i, 1, step_lo, (stream << 8) | 7) by   */
+/* Box-Muller as in orc_langevin_normals.                                    */
+/* ------------------------------------------------------------------------- */
+void orc_andersen_step(int N, double *pos, double *vel, const double *F, double L,
+                       double nu, double kT, double dt, double mass,
+                       uint64_t seed, uint32_t stream, uint64_t step, int *collided)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    double pc = nu * dt;
+    double thr = floor(pc * 4294967296.0);
+    if (thr > 4294967296.0) thr = 4294967296.0;
+    double sd = sqrt(kT / mass);
+    for (int i = 0; i < N; ++i) {
+        for (int a = 0; a < 3; ++a) {
+            double v = vel[3 * i + a] + (dt / mass) * F[3 * i + a];
+            double r = pos[3 * i + a] + dt * v;
+            r -= L * floor(r / L);
+            vel[3 * i + a] = v;
+            pos[3 * i + a] = r;
+        }
+        uint32_t c0[4] = {(uint32_t)i, 0u, (uint32_t)step, (stream << 8) | 0x07u};
+        uint32_t w[4];
+        orc_philox4x32_10(c0, key, w);
+        int hit = (double)w[0] < thr;
+        if (collided) collided[i] = hit;
+        if (!hit) continue;
+        uint32_t c1[4] = {(uint32_t)i, 1u, (uint32_t)step, (stream << 8) | 0x07u};
+        orc_philox4x32_10(c1, key, w);
+        double u1 = ((double)w[0] + 1.0) / 4294967296.0;
+        double u2 = (double)w[1] / 4294967296.0;
+        double u3 = ((double)w[2] + 1.0) / 4294967296.0;
+        double u4 = (double)w[3] / 4294967296.0;
+        double r1 = sqrt(-2.0 * log(u1)), r2 = sqrt(-2.0 * log(u3));
+        vel[3 * i + 0] = sd * r1 * cos(2.0 * M_PI * u2);
+        vel[3 * i + 1] = sd * r1 * sin(2.0 * M_PI * u2);
+        vel[3 * i + 2] = sd * r2 * cos(2.0 * M_PI * u4);
+    }
+}
