@@ -66,10 +66,26 @@ typedef enum {
 
 enum { RBE_FP64 = 0, RBE_MIXED = 1 };
 
+/* k-samplers (rbe_params.sampler).  RBE_SAMPLER_EXACT: P i.i.d. samples per
+ * step by an integer inverse-CDF table per axis, a pure function of (seed,
+ * stream, step, l).  RBE_SAMPLER_MH: the paper's Metropolis-Hastings sampler
+ * (Sec. 3.1): three per-axis independence chains with the rounded-Gaussian
+ * proposal, (0,0,0) triples discarded, consumed in order across evaluations
+ * (the set K of Algorithm 1); the chain state lives in the handle and starts
+ * at m = 0, iteration 0. */
+enum { RBE_SAMPLER_EXACT = 0, RBE_SAMPLER_MH = 1 };
+
+/* Thermostats of rbe_step (rbe_params.thermostat).  RBE_THERMO_LANGEVIN:
+ * kick, exact Ornstein-Uhlenbeck with friction gamma, drift (Sec. 3.3).
+ * RBE_THERMO_ANDERSEN: the loop step of Algorithm 1 as printed -- leapfrog
+ * (kick, drift) and then, with probability andersen_nu * dt per particle, a
+ * new velocity drawn from N(0, kT/m). */
+enum { RBE_THERMO_LANGEVIN = 0, RBE_THERMO_ANDERSEN = 1 };
+
 /* Parts selectable in rbe_forces_ex. */
 enum { RBE_PART_FOURIER = 1, RBE_PART_REAL = 2, RBE_PART_LJ = 4, RBE_PART_ALL = 7 };
 
-/* Parameters of one periodic system (cubic box, reduced units).  112 bytes. */
+/* Parameters of one periodic system (cubic box, reduced units).  128 bytes. */
 typedef struct {
     double box;               /* L > 0: edge of the cubic periodic box (Sec. 2)          */
     double alpha;             /* Ewald splitting parameter, erfc(sqrt(alpha) r) (Sec. 2) */
@@ -87,6 +103,9 @@ typedef struct {
     int32_t P;                /* batch size p >= 1 (Eq. rbmapprox)                        */
     int32_t n_max;            /* capacity in particles (single-system handles)           */
     int32_t precision;        /* RBE_MIXED (default path of rbe_step) or RBE_FP64         */
+    double andersen_nu;       /* Andersen collision frequency nu, 0 <= nu dt <= 1          */
+    int32_t sampler;          /* RBE_SAMPLER_EXACT (0) or RBE_SAMPLER_MH; one per handle  */
+    int32_t thermostat;       /* RBE_THERMO_LANGEVIN (0) or RBE_THERMO_ANDERSEN          */
 } rbe_params;
 
 /* Derived constants of system `sys` of a handle (for inspection and tests). */
@@ -139,7 +158,9 @@ rbe_status rbe_get_table(rbe_handle h, int32_t sys, uint64_t *table_out);
  * sample.  Sample l of a system uses Philox4x32-10 with key (seed_lo, seed_hi)
  * and counter (l, attempt, step_lo, (stream << 8) | 1); each 32-bit word maps
  * to one axis by the integer table; (0,0,0) is discarded and redrawn
- * (Sec. 3.1), at most 32 attempts. */
+ * (Sec. 3.1), at most 32 attempts.  With RBE_SAMPLER_MH the batch depends on
+ * the chains' history, not on `step`: m_out receives the batch of the last
+ * evaluation (attempts field 1), and the chains do not advance. */
 rbe_status rbe_sample_k(rbe_handle h, uint64_t step, int32_t *m_out);
 
 /* One RBE force evaluation, mixed precision (FP32 phases / sincos / forces

@@ -18,7 +18,8 @@ import ctypes
 
 from . import capi
 from .capi import (RBE_FP64, RBE_MIXED, RBE_PART_ALL, RBE_PART_FOURIER, RBE_PART_LJ,
-                   RBE_PART_REAL, RBEError)
+                   RBE_PART_REAL, RBE_SAMPLER_EXACT, RBE_SAMPLER_MH, RBE_THERMO_ANDERSEN,
+                   RBE_THERMO_LANGEVIN, RBEError)
 
 __all__ = ["capi", "RBE", "RBEBatch", "RBEEnergy", "params_from", "RBEError",
            "RBE_FP64", "RBE_MIXED", "RBE_PART_ALL", "RBE_PART_FOURIER", "RBE_PART_LJ",
@@ -36,7 +37,9 @@ def params_from(sp, n_max=0, precision=RBE_MIXED) -> capi.rbe_params:
                             stream=sp.stream, coulomb_prefactor=sp.coulomb_prefactor,
                             lj_eps=sp.lj_eps, lj_sigma=sp.lj_sigma, lj_rcut=sp.lj_rcut,
                             gamma=sp.gamma, kT=sp.kT, dt=sp.dt, mass=sp.mass, n_max=n_max,
-                            precision=precision)
+                            precision=precision, sampler=getattr(sp, "sampler", 0),
+                            thermostat=getattr(sp, "thermostat", 0),
+                            andersen_nu=getattr(sp, "andersen_nu", 0.0))
 
 
 def _ptr(t):

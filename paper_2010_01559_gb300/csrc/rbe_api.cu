@@ -37,6 +37,8 @@ struct SysHost {
     double H = 0.0, S = 0.0;
     int ncd = 0;
     std::vector<uint64_t> table;
+    std::vector<uint64_t> mh_tq;       // MH proposal thresholds (2M+1)
+    std::vector<double> mh_rho;        // MH target / proposal ratios (2M+1)
     int off_p = 0, off_c = 0, off_k = 0, off_t = 0;
 };
 
@@ -77,6 +79,43 @@ double build_table(double alpha, double L, int M, std::vector<uint64_t>& T) {
         }
     }
     return Z;
+}
+
+// Tables of the paper's Metropolis-Hastings sampler (Sec. 3.1) over |m| <= M,
+// index j = m + M.  The proposal m* = round(x*), x* ~ N(0, alpha L^2 / (2 pi^2)),
+// has the pmf qbar(0) = erf(1/(2s)), qbar(m) = (erf((|m|+1/2)/s) - erf((|m|-1/2)/s))/2
+// with s = sqrt(alpha) L / pi, evaluated through erfc so the tails keep their
+// precision.  tq[j] = floor(2^32 CDF_qbar(j)) (tq[2M] = 2^32) draws m* from a
+// 32-bit word; rho[j] = exp(-pi^2 m^2 / (alpha L^2)) / qbar(m) gives the
+// acceptance test u * rho(m) < rho(m*) of the independence sampler.
+void build_mh_tables(double alpha, double L, int M, std::vector<uint64_t>& tq,
+                     std::vector<double>& rho) {
+    const int n = 2 * M + 1;
+    const double s = std::sqrt(alpha) * L / M_PI;
+    const double a = (M_PI * M_PI) / (alpha * L * L);
+    std::vector<double> qb(n);
+    double Q = 0.0;
+    for (int j = 0; j < n; ++j) {
+        const int m = std::abs(j - M);
+        qb[j] = m == 0 ? std::erf(0.5 / s)
+                       : 0.5 * (std::erfc(((double)m - 0.5) / s) - std::erfc(((double)m + 0.5) / s));
+        Q += qb[j];
+    }
+    tq.assign(n, 0);
+    rho.assign(n, 0.0);
+    double cum = 0.0;
+    for (int j = 0; j < n; ++j) {
+        cum += qb[j];
+        if (j == n - 1) {
+            tq[j] = 4294967296ull;
+        } else {
+            double f = std::floor((cum / Q) * 4294967296.0);
+            if (f > 4294967295.0) f = 4294967295.0;
+            tq[j] = (uint64_t)f;
+        }
+        const long long d = (long long)(j - M);
+        rho[j] = std::exp(-(a * (double)(d * d))) / qb[j];
+    }
 }
 
 int pow2_ceil(long long v) {
@@ -155,6 +194,12 @@ struct rbe_ctx {
     int* d_kcnt = nullptr;                    // per k tile: chunks done (rho kernel)
     float2* d_kab = nullptr;                  // FP32 force coefficients per k
     double* d_kcoef = nullptr;                // coef_scale / k^2 per k
+    bool mh = false;                          // paper's MH sampler (chains in the handle)
+    int mh_words = 0;                         // largest 2M+1 (MH tables staged per block)
+    uint64_t* d_mh_tq = nullptr;              // MH proposal thresholds, all systems
+    double* d_mh_rho = nullptr;               // MH acceptance ratios, all systems
+    int4* d_mh_state = nullptr;               // per system: current (m_x, m_y, m_z)
+    uint64_t* d_mh_pos = nullptr;             // per system: chain iterations done
     unsigned long long* d_qsum_fx = nullptr;  // sum q per system (fixed point)
     double2* d_blk_e = nullptr;
     double2* d_blk_q = nullptr;
@@ -198,6 +243,9 @@ rbe_status validate_params(const rbe_params& p, std::string& why) {
         if (p.lj_rcut > p.r_c) { why = "lj_rcut must be <= r_c"; return RBE_ERR_ARG; }
     }
     if (!(p.mass > 0.0)) { why = "mass must be > 0"; return RBE_ERR_ARG; }
+    if (p.sampler != RBE_SAMPLER_EXACT && p.sampler != RBE_SAMPLER_MH) { why = "sampler must be RBE_SAMPLER_EXACT or RBE_SAMPLER_MH"; return RBE_ERR_ARG; }
+    if (p.thermostat != RBE_THERMO_LANGEVIN && p.thermostat != RBE_THERMO_ANDERSEN) { why = "thermostat must be RBE_THERMO_LANGEVIN or RBE_THERMO_ANDERSEN"; return RBE_ERR_ARG; }
+    if (!(p.andersen_nu >= 0.0) || !(p.andersen_nu * p.dt <= 1.0)) { why = "andersen_nu must satisfy 0 <= nu dt <= 1"; return RBE_ERR_ARG; }
     if (p.gamma < 0.0 || p.kT < 0.0) { why = "gamma and kT must be >= 0"; return RBE_ERR_ARG; }
     const int M = axis_M(p.alpha, p.box);
     if (M > 200000) { why = "alpha L^2 too large for the sampling table"; return RBE_ERR_ARG; }
@@ -278,6 +326,13 @@ void fill_sysdev(const SysHost& s, SysDev& d) {
     d.f_dt = (float)d.dt;
     d.f_dt_over_m = (float)d.dt_over_m;
     d.f_invL = (float)d.invL;
+    d.thermostat = p.thermostat;
+    {
+        double thr = std::floor(p.andersen_nu * p.dt * 4294967296.0);
+        d.andersen_thr = (uint64_t)std::min(thr, 4294967296.0);
+    }
+    d.vsd = std::sqrt(p.kT / p.mass);
+    d.f_vsd = (float)d.vsd;
     d.f_inv_Lu = (float)(4294967296.0 / L);
     d.corner_q = (uint32_t)(4294967296ull / (unsigned long long)std::max(1, s.ncd));
     d.corner_r = (uint32_t)(4294967296ull - (unsigned long long)d.corner_q * std::max(1, s.ncd));
@@ -484,6 +539,10 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_ALLOC(h->d_rho_fx, 2 * (size_t)h->ktot);
     RBE_ALLOC(h->d_kcnt, h->ktot);
     RBE_ALLOC(h->d_kcoef, h->ktot);
+    RBE_ALLOC(h->d_mh_tq, h->ttot);
+    RBE_ALLOC(h->d_mh_rho, h->ttot);
+    RBE_ALLOC(h->d_mh_state, h->nsys);
+    RBE_ALLOC(h->d_mh_pos, h->nsys);
     RBE_ALLOC(h->d_kab, h->ktot);
     RBE_ALLOC(h->d_qsum_fx, h->nsys);
     RBE_ALLOC(h->d_blk_e, std::max<long long>(rb, (long long)kSegChunks * (h->ncell + 1)));
@@ -501,10 +560,13 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_CUDA(h, cudaMemset(h->d_qsum_fx, 0, sizeof(unsigned long long) * h->nsys));
     RBE_CUDA(h, cudaMemset(h->d_rho_fx, 0, sizeof(unsigned long long) * 2 * h->ktot));
     RBE_CUDA(h, cudaMemset(h->d_kcnt, 0, sizeof(int) * h->ktot));
-    std::vector<uint64_t> tab;
+    std::vector<uint64_t> tab, mtq;
+    std::vector<double> mrho;
     std::vector<int> kstart, cstart;
     for (auto& s : h->sys) {
         tab.insert(tab.end(), s.table.begin(), s.table.end());
+        mtq.insert(mtq.end(), s.mh_tq.begin(), s.mh_tq.end());
+        mrho.insert(mrho.end(), s.mh_rho.begin(), s.mh_rho.end());
         kstart.push_back(s.off_k);
         cstart.push_back(s.off_c);
     }
@@ -516,6 +578,12 @@ rbe_status allocate(rbe_ctx* h) {
                            cudaMemcpyHostToDevice));
     RBE_CUDA(h, cudaMemcpy(h->d_kstart, kstart.data(), sizeof(int) * kstart.size(),
                            cudaMemcpyHostToDevice));
+    RBE_CUDA(h, cudaMemcpy(h->d_mh_tq, mtq.data(), sizeof(uint64_t) * mtq.size(),
+                           cudaMemcpyHostToDevice));
+    RBE_CUDA(h, cudaMemcpy(h->d_mh_rho, mrho.data(), sizeof(double) * mrho.size(),
+                           cudaMemcpyHostToDevice));
+    RBE_CUDA(h, cudaMemset(h->d_mh_state, 0, sizeof(int4) * h->nsys));   // chains start at m = 0
+    RBE_CUDA(h, cudaMemset(h->d_mh_pos, 0, sizeof(uint64_t) * h->nsys));
     RBE_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     RBE_CUDA(h, cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking));
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
@@ -533,7 +601,8 @@ void release(rbe_ctx* h) {
                     h->d_table, h->d_fx, h->d_spos, h->d_fx64, h->d_spos64, h->d_cid, h->d_rank,
                     h->d_perm, h->d_perm_tmp, h->d_fs, h->d_fs64, h->d_cell_cnt,
                     h->d_cell_start, h->d_ksamp, h->d_rho_fx, h->d_kcnt, h->d_kab,
-                    h->d_kcoef, h->d_qsum_fx, h->d_blk_e, h->d_blk_q, h->d_cur_step, h->d_stage_step,
+                    h->d_kcoef, h->d_mh_tq, h->d_mh_rho, h->d_mh_state, h->d_mh_pos,
+                    h->d_qsum_fx, h->d_blk_e, h->d_blk_q, h->d_cur_step, h->d_stage_step,
                     h->d_err, h->d_stage_pos, h->d_stage_vel, h->d_stage_F, h->d_stage_E};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -574,6 +643,11 @@ rbe_status create_common(const rbe_params* ps, const int32_t* ns, int nsys, bool
         }
         sh.M = axis_M(sh.p.alpha, sh.p.box);
         sh.H = build_table(sh.p.alpha, sh.p.box, sh.M, sh.table);
+        build_mh_tables(sh.p.alpha, sh.p.box, sh.M, sh.mh_tq, sh.mh_rho);
+        if (sh.p.sampler != ps[0].sampler) {
+            delete h;
+            return fail(nullptr, RBE_ERR_ARG, "all systems of a handle must use the same sampler");
+        }
         sh.S = sh.H * sh.H * sh.H - 1.0;
         sh.ncd = std::min(256, (int)std::floor(sh.p.box / sh.p.r_c));
         sh.off_p = off_p;
@@ -590,6 +664,8 @@ rbe_status create_common(const rbe_params* ps, const int32_t* ns, int nsys, bool
     h->ncell = off_c;
     h->ktot = off_k;
     h->ttot = off_t;
+    h->mh = ps[0].sampler == RBE_SAMPLER_MH;
+    for (auto& sh : h->sys) h->mh_words = std::max(h->mh_words, 2 * sh.M + 1);
     rbe_status st = allocate(h);
     if (st != RBE_OK) {
         std::string m = h->err;
@@ -727,6 +803,12 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     pa.kstart = h->d_kstart;
     pa.table = h->d_table;
     pa.tab_words = h->ttot <= 8192 ? h->ttot : 0;    // 32 KB of shared memory at most
+    pa.mh = h->mh ? 1 : 0;
+    pa.mh_words = h->mh_words;
+    pa.mh_tq = h->d_mh_tq;
+    pa.mh_rho = h->d_mh_rho;
+    pa.mh_state = h->d_mh_state;
+    pa.mh_pos = h->d_mh_pos;
     pa.ksamp = h->d_ksamp;
     pa.kcoef = h->d_kcoef;
     pa.err = h->d_err;
@@ -966,10 +1048,16 @@ rbe_status rbe_sample_k(rbe_handle h, uint64_t step, int32_t* m_out) {
     const int n = h->batch ? h->ntot : std::max(h->cur_n, 0);
     rbe_status s = prepare(h, n);
     if (s != RBE_OK) return s;
-    RBE_CUDA(h, cudaMemcpyAsync(h->d_stage_step, &step, sizeof(uint64_t), cudaMemcpyHostToDevice,
-                                h->stream));
-    launch_sample(h->stream, h->d_sys, h->nsys, h->ktot, h->d_kstart, h->d_table,
-                  h->d_stage_step, (int4*)m_out, h->d_err);
+    if (h->mh) {
+        // the chains are consumed in order: report the batch of the last evaluation
+        RBE_CUDA(h, cudaMemcpyAsync(m_out, h->d_ksamp, sizeof(int4) * h->ktot,
+                                    cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+        RBE_CUDA(h, cudaMemcpyAsync(h->d_stage_step, &step, sizeof(uint64_t),
+                                    cudaMemcpyHostToDevice, h->stream));
+        launch_sample(h->stream, h->d_sys, h->nsys, h->ktot, h->d_kstart, h->d_table,
+                      h->d_stage_step, (int4*)m_out, h->d_err);
+    }
     RBE_CUDA(h, cudaStreamSynchronize(h->stream));
     return finish(h, "rbe_sample_k");
 }

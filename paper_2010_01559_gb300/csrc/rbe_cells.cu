@@ -65,6 +65,98 @@ __device__ __forceinline__ void latch_step(const uint64_t* step_dev, uint64_t st
 // The k-batch of this step (Eq. probexpression): the blocks after the particle
 // blocks draw one sample per thread and its coefficient coef_scale / k^2 of
 // Eq. rbmapprox, for the structure-factor and force passes that follow.
+// The paper's Metropolis-Hastings sampler (Sec. 3.1), one block per system:
+// three per-axis independence chains with the rounded-Gaussian proposal, run
+// in windows of kMhWin iterations.  Proposals and uniforms of a window come
+// from Philox in parallel (iteration t, axis c: ctr = (t_lo, t_hi, c,
+// (stream << 8) | 6)); threads 0..2 then walk their chain through the window
+// (accept m* iff u * rho(m) < rho(m*)); thread 0 keeps the nonzero triples in
+// order until P are out.  The chains' state and position persist in the handle
+// (the set K of Algorithm 1, consumed in order).
+constexpr int kMhWin = 64;
+
+template <bool ONE>
+__device__ void draw_samples_mh(const Work& w, const PrepArgs& pa) {
+    extern __shared__ __align__(16) unsigned char mh_smem[];
+    double* s_rho = (double*)mh_smem;                          // [mh_words]
+    uint32_t* s_tq = (uint32_t*)(s_rho + pa.mh_words);         // [mh_words]
+    __shared__ int s_prop[3][kMhWin];
+    __shared__ double s_u[3][kMhWin];
+    __shared__ int s_st[3][kMhWin];
+    __shared__ int s_state[3], s_emitted, s_used, s_bad;
+    const int sys = (int)blockIdx.x - pa.npblk;
+    if (sys >= pa.nsys) return;
+    const SysDev& S = sys_of<ONE>(w, sys);
+    const int n = 2 * S.M + 1;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        s_rho[j] = __ldg(pa.mh_rho + S.off_t + j);
+        s_tq[j] = (uint32_t)__ldg(pa.mh_tq + S.off_t + j);   // entry 2M (= 2^32) is never read
+    }
+    if (threadIdx.x < 3) s_state[threadIdx.x] = (&pa.mh_state[sys].x)[threadIdx.x];
+    if (threadIdx.x == 0) { s_emitted = 0; s_bad = 0; }
+    __syncthreads();
+    const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
+    uint64_t t0 = pa.mh_pos[sys];
+    const uint64_t tmax = t0 + 64ull * (uint64_t)S.P + 1024ull;
+    while (s_emitted < S.P && !s_bad) {
+        for (int idx = threadIdx.x; idx < 3 * kMhWin; idx += blockDim.x) {
+            const int c = idx / kMhWin, it = idx - c * kMhWin;
+            const uint64_t t = t0 + (uint64_t)it;
+            const uint4 r = philox4x32_10(
+                make_uint4((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)c, (S.stream << 8) | 0x06u), key);
+            int lo = 0, hi = n - 1;                 // smallest j with r.x < T[j] (T[n-1] = 2^32)
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (r.x < s_tq[mid]) hi = mid; else lo = mid + 1;
+            }
+            s_prop[c][it] = lo - S.M;
+            s_u[c][it] = (double)((((unsigned long long)r.z << 32) | r.w) >> 11) * 0x1.0p-53;
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            const int c = threadIdx.x;
+            int st = s_state[c];
+            for (int it = 0; it < kMhWin; ++it) {
+                const int ms = s_prop[c][it];
+                if (__dmul_rn(s_u[c][it], s_rho[st + S.M]) < s_rho[ms + S.M]) st = ms;
+                s_st[c][it] = st;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int e = s_emitted, used = kMhWin;
+            for (int it = 0; it < kMhWin; ++it) {
+                const int mx = s_st[0][it], my = s_st[1][it], mz = s_st[2][it];
+                if (mx != 0 || my != 0 || mz != 0) {
+                    pa.ksamp[S.off_k + e] = make_int4(mx, my, mz, 1);
+                    if (++e == S.P) { used = it + 1; break; }
+                }
+            }
+            for (int c = 0; c < 3; ++c) s_state[c] = s_st[c][used - 1];
+            s_emitted = e;
+            s_used = used;
+            if (t0 + (uint64_t)used >= tmax && e < S.P) s_bad = 1;
+        }
+        __syncthreads();
+        t0 += (uint64_t)s_used;
+    }
+    if (threadIdx.x == 0) {
+        pa.mh_state[sys] = make_int4(s_state[0], s_state[1], s_state[2], 0);
+        pa.mh_pos[sys] = t0;
+        if (s_bad) {
+            atomicOr(pa.err, kErrSampler);
+            for (int l = s_emitted; l < S.P; ++l) pa.ksamp[S.off_k + l] = make_int4(1, 0, 0, 0);
+        }
+    }
+    __syncthreads();
+    const double tp = 2.0 * M_PI * S.invL;
+    for (int l = threadIdx.x; l < S.P; l += blockDim.x) {
+        const int4 m = pa.ksamp[S.off_k + l];
+        const double k2 = tp * tp * ((double)m.x * m.x + (double)m.y * m.y + (double)m.z * m.z);
+        pa.kcoef[S.off_k + l] = S.coef_scale / k2;
+    }
+}
+
 template <bool ONE>
 __device__ __forceinline__ void draw_samples(const Work& w, const PrepArgs& pa) {
     extern __shared__ uint32_t s_tab[];
@@ -100,7 +192,8 @@ k_prep_mixed(const __grid_constant__ Work w, const float4* __restrict__ pos_q,
              uint4* __restrict__ fx, int* __restrict__ cid, int* __restrict__ rank,
              int* __restrict__ cell_cnt, const __grid_constant__ PrepArgs pa) {
     if ((int)blockIdx.x >= pa.npblk) {             // a k-sampling block
-        draw_samples<ONE>(w, pa);
+        if (pa.mh) draw_samples_mh<ONE>(w, pa);
+        else draw_samples<ONE>(w, pa);
         return;
     }
     latch_step(pa.step_dev, pa.step_arg, pa.cur_step);
@@ -152,7 +245,8 @@ k_prep_f64(const __grid_constant__ Work w, const double4* __restrict__ pos_q,
            double4* __restrict__ fx64, int* __restrict__ cid, int* __restrict__ rank,
            int* __restrict__ cell_cnt, const __grid_constant__ PrepArgs pa) {
     if ((int)blockIdx.x >= pa.npblk) {             // a k-sampling block
-        draw_samples<ONE>(w, pa);
+        if (pa.mh) draw_samples_mh<ONE>(w, pa);
+        else draw_samples<ONE>(w, pa);
         return;
     }
     latch_step(pa.step_dev, pa.step_arg, pa.cur_step);
@@ -291,9 +385,11 @@ __global__ void k_order(int n, const int* __restrict__ cid, const int* __restric
 // ------------------------------------------------------------- launchers
 void launch_prep_mixed(cudaStream_t st, bool one, const Work& w, int nblk, const float4* pos_q,
                        uint4* fx, int* cid, int* rank, int* cell_cnt, const PrepArgs& pa) {
-    nblk += (pa.ktot + kBlockP - 1) / kBlockP;       // particle blocks, then sampling blocks
+    // particle blocks, then sampling blocks: one per system (MH chains) or one per kBlockP samples
+    if (pa.ktot > 0) nblk += pa.mh ? pa.nsys : (pa.ktot + kBlockP - 1) / kBlockP;
     if (nblk <= 0) return;
-    const size_t smem = sizeof(uint32_t) * (size_t)pa.tab_words;
+    const size_t smem = pa.mh ? (sizeof(double) + sizeof(uint32_t)) * (size_t)pa.mh_words
+                              : sizeof(uint32_t) * (size_t)pa.tab_words;
     if (one)
         k_prep_mixed<true><<<nblk, kBlockP, smem, st>>>(w, pos_q, fx, cid, rank, cell_cnt, pa);
     else
@@ -302,9 +398,11 @@ void launch_prep_mixed(cudaStream_t st, bool one, const Work& w, int nblk, const
 
 void launch_prep_f64(cudaStream_t st, bool one, const Work& w, int nblk, const double4* pos_q,
                      double4* fx64, int* cid, int* rank, int* cell_cnt, const PrepArgs& pa) {
-    nblk += (pa.ktot + kBlockP - 1) / kBlockP;       // particle blocks, then sampling blocks
+    // particle blocks, then sampling blocks: one per system (MH chains) or one per kBlockP samples
+    if (pa.ktot > 0) nblk += pa.mh ? pa.nsys : (pa.ktot + kBlockP - 1) / kBlockP;
     if (nblk <= 0) return;
-    const size_t smem = sizeof(uint32_t) * (size_t)pa.tab_words;
+    const size_t smem = pa.mh ? (sizeof(double) + sizeof(uint32_t)) * (size_t)pa.mh_words
+                              : sizeof(uint32_t) * (size_t)pa.tab_words;
     if (one)
         k_prep_f64<true><<<nblk, kBlockP, smem, st>>>(w, pos_q, fx64, cid, rank, cell_cnt, pa);
     else

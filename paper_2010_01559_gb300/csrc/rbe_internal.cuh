@@ -27,6 +27,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "rbe.h"
+
 namespace rbe {
 
 constexpr int kBlockP = 128;      // particles per block of the per-particle kernels
@@ -65,6 +67,10 @@ struct SysDev {
     float f_lj_sigma2, f_lj_eps, f_lj_shift;
     float f_c1, f_c2, f_dt, f_dt_over_m, f_invL;
     float f_inv_Lu;         // 2^32 / L: length to fixed-point units
+    int thermostat;         // RBE_THERMO_LANGEVIN or RBE_THERMO_ANDERSEN
+    uint64_t andersen_thr;  // collision iff 32-bit Philox word < nu dt 2^32
+    double vsd;             // sqrt(kT / m): Andersen velocity standard deviation
+    float f_vsd;
     uint32_t corner_q, corner_r;   // 2^32 = corner_q * ncd + corner_r (cell corners)
 };
 
@@ -202,6 +208,12 @@ struct PrepArgs {
     const int* kstart;       // first sample of each system (nsys + 1)
     const uint64_t* table;
     int tab_words;           // > 0: all tables (this many entries) staged in shared memory
+    // the paper's MH sampler: one block per system runs its three chains
+    int mh, mh_words;        // mh_words: largest 2M+1 (tables staged per block)
+    const uint64_t* mh_tq;
+    const double* mh_rho;
+    int4* mh_state;
+    uint64_t* mh_pos;
     int4* ksamp;
     double* kcoef;           // coef_scale / k^2 per sample (Eq. rbmapprox)
     int* err;

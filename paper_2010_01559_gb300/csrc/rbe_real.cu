@@ -22,6 +22,9 @@
 // sqrt(2 gamma kT) dW): v += (dt/m) F; v = c1 v + c2 xi; r = wrap(r + dt v),
 // c1 = exp(-gamma dt / m), c2 = sqrt((1 - c1^2) kT / m), xi from Philox with
 // counter (i, 0, step_lo, (stream << 8) | 2) by Box-Muller.
+// Andersen (the loop of Algorithm 1): v += (dt/m) F; r = wrap(r + dt v); then
+// if word 0 of Philox(i, 0, step_lo, (stream << 8) | 7) is below nu dt 2^32,
+// v = sqrt(kT/m) xi with xi from Philox(i, 1, step_lo, (stream << 8) | 7).
 #include <cmath>
 
 #include "rbe_internal.cuh"
@@ -78,7 +81,7 @@ __device__ __forceinline__ void row_ranges(const int* __restrict__ cs, int base,
 // densely.  A cell whose neighbourhood exceeds the staging capacity reads the
 // records from global memory instead.
 constexpr int kNbCap = 24;          // entries of each lane's neighbour list
-constexpr int kBatch = 4;           // candidates a thread tests per step of its scan
+constexpr int kBatch = 2;           // candidates a thread tests per step of its scan
 
 struct PairAcc {
     float fx, fy, fz, phr, ec, elj;
@@ -166,25 +169,39 @@ __device__ __forceinline__ void langevin_update(const RealArgs& a, const SysDev&
                                                 float fx, float fy, float fz) {
     const uint64_t step = *a.cur_step;
     const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)(o - S.off_p), 0u,
-                                             (uint32_t)step, (S.stream << 8) | 0x02u),
-                                  key);
-    const float u1 = (float)((w.x >> 8) + 1u) * 5.9604644775390625e-08f;   // (0, 1]
-    const float u2 = (float)(w.y >> 8) * 5.9604644775390625e-08f;          // [0, 1)
-    const float u3 = (float)((w.z >> 8) + 1u) * 5.9604644775390625e-08f;
-    const float u4 = (float)(w.w >> 8) * 5.9604644775390625e-08f;
-    const float r1 = sqrtf(-2.f * logf(u1)), r3 = sqrtf(-2.f * logf(u3));
-    float s2, c2v, s4, c4;
-    sincospif(2.f * u2, &s2, &c2v);
-    sincospif(2.f * u4, &s4, &c4);
-    const float xi0 = r1 * c2v, xi1 = r1 * s2, xi2 = r3 * c4;
-    const float c1 = S.f_c1, c2 = S.f_c2, dtm = S.f_dt_over_m;
-    const float dt = S.f_dt;
+    const uint32_t pid = (uint32_t)(o - S.off_p);
+    const bool andersen = S.thermostat == RBE_THERMO_ANDERSEN;
+    // Langevin: normals of the OU step; Andersen: collision word, then normals
+    const uint4 c = philox4x32_10(make_uint4(pid, 0u, (uint32_t)step,
+                                             (S.stream << 8) | (andersen ? 0x07u : 0x02u)), key);
+    const bool hit = andersen && (uint64_t)c.x < S.andersen_thr;
     float4 v = a.md_vel[o];
     float4 rp = a.md_pos[o];
-    v.x = fmaf(c1, fmaf(dtm, fx, v.x), c2 * xi0);
-    v.y = fmaf(c1, fmaf(dtm, fy, v.y), c2 * xi1);
-    v.z = fmaf(c1, fmaf(dtm, fz, v.z), c2 * xi2);
+    const float dtm = S.f_dt_over_m, dt = S.f_dt;
+    v.x = fmaf(dtm, fx, v.x);
+    v.y = fmaf(dtm, fy, v.y);
+    v.z = fmaf(dtm, fz, v.z);
+    float xi0 = 0.f, xi1 = 0.f, xi2 = 0.f;
+    if (!andersen || hit) {
+        const uint4 w = andersen ? philox4x32_10(make_uint4(pid, 1u, (uint32_t)step,
+                                                            (S.stream << 8) | 0x07u), key)
+                                 : c;
+        const float u1 = (float)((w.x >> 8) + 1u) * 5.9604644775390625e-08f;   // (0, 1]
+        const float u2 = (float)(w.y >> 8) * 5.9604644775390625e-08f;          // [0, 1)
+        const float u3 = (float)((w.z >> 8) + 1u) * 5.9604644775390625e-08f;
+        const float u4 = (float)(w.w >> 8) * 5.9604644775390625e-08f;
+        const float r1 = sqrtf(-2.f * logf(u1)), r3 = sqrtf(-2.f * logf(u3));
+        float s2, c2v, s4, c4;
+        sincospif(2.f * u2, &s2, &c2v);
+        sincospif(2.f * u4, &s4, &c4);
+        xi0 = r1 * c2v; xi1 = r1 * s2; xi2 = r3 * c4;
+    }
+    if (!andersen) {                                   // exact Ornstein-Uhlenbeck step
+        const float c1 = S.f_c1, c2 = S.f_c2;
+        v.x = fmaf(c1, v.x, c2 * xi0);
+        v.y = fmaf(c1, v.y, c2 * xi1);
+        v.z = fmaf(c1, v.z, c2 * xi2);
+    }
     const float L = S.Lf, invL = S.f_invL;
     rp.x = fmaf(dt, v.x, rp.x); rp.x -= L * floorf(rp.x * invL);
     rp.y = fmaf(dt, v.y, rp.y); rp.y -= L * floorf(rp.y * invL);
@@ -193,6 +210,10 @@ __device__ __forceinline__ void langevin_update(const RealArgs& a, const SysDev&
     if (rp.x >= L) rp.x = 0.f;
     if (rp.y >= L) rp.y = 0.f;
     if (rp.z >= L) rp.z = 0.f;
+    if (hit) {                                         // Andersen collision after the drift
+        const float sd = S.f_vsd;
+        v.x = sd * xi0; v.y = sd * xi1; v.z = sd * xi2;
+    }
     a.md_vel[o] = v;
     a.md_pos[o] = rp;
 }
@@ -571,9 +592,16 @@ k_real_f64(const __grid_constant__ RealArgs a) {
         if (a.md_pos64) {
             const uint64_t step = *a.cur_step;
             const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
-            const uint4 w = philox4x32_10(
-                make_uint4((uint32_t)(o - S.off_p), 0u, (uint32_t)step, (S.stream << 8) | 0x02u),
-                key);
+            const uint32_t pid = (uint32_t)(o - S.off_p);
+            const bool andersen = S.thermostat == RBE_THERMO_ANDERSEN;
+            // Langevin: normals of the OU step; Andersen: collision word, then normals
+            const uint4 c = philox4x32_10(make_uint4(pid, 0u, (uint32_t)step,
+                                                     (S.stream << 8) | (andersen ? 0x07u : 0x02u)),
+                                          key);
+            const bool hit = andersen && (uint64_t)c.x < S.andersen_thr;
+            const uint4 w = andersen ? philox4x32_10(make_uint4(pid, 1u, (uint32_t)step,
+                                                                (S.stream << 8) | 0x07u), key)
+                                     : c;
             const double u1 = ((double)w.x + 1.0) / 4294967296.0;
             const double u2 = (double)w.y / 4294967296.0;
             const double u3 = ((double)w.z + 1.0) / 4294967296.0;
@@ -589,9 +617,10 @@ k_real_f64(const __grid_constant__ RealArgs a) {
             const double L = S.L;
             for (int d = 0; d < 3; ++d) {
                 double vd = *vv[d] + S.dt_over_m * F3[d];
-                vd = S.c1 * vd + S.c2 * xi[d];
+                if (!andersen) vd = S.c1 * vd + S.c2 * xi[d];
                 double rd = *rr[d] + S.dt * vd;
                 rd -= L * floor(rd / L);
+                if (hit) vd = S.vsd * xi[d];           // Andersen collision after the drift
                 *vv[d] = vd;
                 *rr[d] = rd;
             }

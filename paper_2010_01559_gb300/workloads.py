@@ -45,6 +45,9 @@ class SystemParams:
     kT: float = 1.0
     dt: float = 1e-3
     mass: float = 1.0
+    sampler: int = 0          # 0: exact i.i.d. inverse CDF, 1: the paper's MH chains
+    thermostat: int = 0       # 0: Langevin (kick / OU / drift), 1: leapfrog + Andersen
+    andersen_nu: float = 0.0  # Andersen collision frequency
 
 
 @dataclass

@@ -34,9 +34,12 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_params_layout_matches_header():
-    assert ctypes.sizeof(capi.rbe_params) == 112
+    assert ctypes.sizeof(capi.rbe_params) == 128
     assert capi.rbe_params.seed.offset == 88
     assert capi.rbe_params.precision.offset == 108
+    assert capi.rbe_params.andersen_nu.offset == 112
+    assert capi.rbe_params.sampler.offset == 120
+    assert capi.rbe_params.thermostat.offset == 124
 
 
 def _create(lib, **kw):
@@ -58,6 +61,10 @@ def _create(lib, **kw):
     (dict(lj_rcut=6.0), "lj_rcut"),
     (dict(box=1.0, r_c=0.3, alpha=0.5, lj_eps=0.0), "too small"),
     (dict(mass=0.0), "mass"),
+    (dict(sampler=2), "sampler"),
+    (dict(thermostat=3), "thermostat"),
+    (dict(andersen_nu=-1.0), "andersen_nu"),
+    (dict(andersen_nu=2000.0, dt=1e-3), "andersen_nu"),
 ])
 def test_create_rejects_bad_parameters_on_host(lib, kw, needle):
     st, h = _create(lib, **kw)
