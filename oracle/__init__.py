@@ -110,6 +110,11 @@ def _load():
                                           ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
                                           ctypes.c_uint64, _INT]
         lib.orc_andersen_step.restype = None
+        lib.orc_true_energy_virial.argtypes = [ctypes.c_int, _D, _D, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_int, _D]
+        lib.orc_true_energy_virial.restype = None
         _lib = lib
         return lib
 
@@ -307,6 +312,20 @@ def andersen_step(pos, vel, F, L, nu, kT, dt, mass, seed, stream, step):
     _load().orc_andersen_step(len(pos), _dp(pos), _dp(vel), _dp(F), L, nu, kT, dt, mass,
                               seed, stream, step, hit.ctypes.data_as(_INT))
     return pos, vel, hit.astype(bool)
+
+
+# ---------------------------------------------------------------- observables
+def true_energy_virial(pos, q, L, alpha, r_c, mmax, lB=1.0, lj_eps=0.0, lj_sigma=1.0,
+                       lj_rcut=0.0):
+    """Full-Ewald energy parts and virials (no random batch): dict with E_fourier
+    (incl. self, background), E_real, E_lj, E_bg, W_fourier, W_real, W_lj, W_bg;
+    pressure = (2 E_kin + W) / (3 V), W the sum of the W parts."""
+    pos = _f64(pos, (-1, 3)); q = _f64(q, (-1,))
+    out = np.zeros(8)
+    _load().orc_true_energy_virial(len(q), _dp(pos), _dp(q), L, alpha, r_c, lB, lj_eps,
+                                   lj_sigma, lj_rcut, mmax, _dp(out))
+    keys = ("E_fourier", "E_real", "E_lj", "E_bg", "W_fourier", "W_real", "W_lj", "W_bg")
+    return dict(zip(keys, out.tolist()))
 
 
 # ---------------------------------------------------------------- composites

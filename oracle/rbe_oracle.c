@@ -623,3 +623,83 @@ void orc_andersen_step(int N, double *pos, double *vel, const double *F, double 
         vel[3 * i + 2] = sd * r2 * cos(2.0 * M_PI * u4);
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* True (non-random) energy and virial for the pressure (the paper computes  */
+/* observables "without random batch").  Full Ewald with the cube            */
+/* 0 < |m|_inf <= mmax, real space under r_c, shifted LJ under lj_rcut.      */
+/* Virial W such that P = (2 E_kin + W) / (3 V), W = -dE/dlambda at lambda = */
+/* 1 under r -> lambda r, L -> lambda L (alpha fixed):                       */
+/*   real space  sum_{i<j} lB q_i q_j [erfc(sqrt(a) r)/r + 2 sqrt(a/pi) e^{-a r^2}] */
+/*   Fourier     sum_k A_k |rho_k|^2 (1 - k^2 / (2 alpha)),                   */
+/*               A_k = (2 pi lB / V) e^{-k^2/(4 alpha)} / k^2                 */
+/*   background  3 E_bg,  E_bg = -lB pi (sum q)^2 / (2 V alpha); self: 0      */
+/*   LJ          sum_{i<j} 24 eps (2 (s/r)^12 - (s/r)^6)                      */
+/* out[0..3] = E_fourier (incl. self and background), E_real, E_lj, E_bg;    */
+/* out[4..7] = W_fourier (reciprocal sum only), W_real, W_lj, W_bg.          */
+/* ------------------------------------------------------------------------- */
+void orc_true_energy_virial(int N, const double *pos, const double *q, double L, double alpha,
+                            double r_c, double lB, double lj_eps, double lj_sigma,
+                            double lj_rcut, int mmax, double *out)
+{
+    const double V = L * L * L, tp = 2.0 * M_PI / L;
+    double sq = 0.0, sq2 = 0.0;
+    for (int i = 0; i < N; ++i) { sq += q[i]; sq2 += q[i] * q[i]; }
+    double ef = 0.0, wf = 0.0;
+    #pragma omp parallel for schedule(dynamic) reduction(+ : ef, wf) collapse(2)
+    for (int a = -mmax; a <= mmax; ++a)
+        for (int b = -mmax; b <= mmax; ++b)
+            for (int d = -mmax; d <= mmax; ++d) {
+                if (a == 0 && b == 0 && d == 0) continue;
+                double kx = tp * a, ky = tp * b, kz = tp * d;
+                double k2 = kx * kx + ky * ky + kz * kz;
+                double sr = 0.0, si = 0.0;
+                for (int j = 0; j < N; ++j) {
+                    double th = kx * pos[3 * j] + ky * pos[3 * j + 1] + kz * pos[3 * j + 2];
+                    sr += q[j] * cos(th);
+                    si += q[j] * sin(th);
+                }
+                double A = 2.0 * M_PI * lB / V * exp(-k2 / (4.0 * alpha)) / k2;
+                double e = A * (sr * sr + si * si);
+                ef += e;
+                wf += e * (1.0 - k2 / (2.0 * alpha));
+            }
+    const double ebg = -lB * M_PI * sq * sq / (2.0 * V * alpha);
+    const double eself = -lB * sqrt(alpha / M_PI) * sq2;
+    const double sa = sqrt(alpha), tsa = 2.0 * sqrt(alpha / M_PI);
+    double vshift = 0.0;
+    if (lj_eps != 0.0) {
+        double s6 = pow(lj_sigma / lj_rcut, 6.0);
+        vshift = -4.0 * lj_eps * (s6 * s6 - s6);
+    }
+    double er = 0.0, wr = 0.0, el = 0.0, wl = 0.0;
+    #pragma omp parallel for schedule(dynamic, 16) reduction(+ : er, wr, el, wl)
+    for (int i = 0; i < N; ++i)
+        for (int j = i + 1; j < N; ++j) {
+            double r2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                double x = pos[3 * j + c] - pos[3 * i + c];
+                x -= L * nearbyint(x / L);
+                r2 += x * x;
+            }
+            double r = sqrt(r2);
+            if (r < r_c) {
+                double qq = lB * q[i] * q[j];
+                er += qq * erfc(sa * r) / r;
+                wr += qq * (erfc(sa * r) / r + tsa * exp(-alpha * r2));
+            }
+            if (lj_eps != 0.0 && r < lj_rcut) {
+                double s2 = lj_sigma * lj_sigma / r2, s6 = s2 * s2 * s2;
+                el += 4.0 * lj_eps * (s6 * s6 - s6) + vshift;
+                wl += 24.0 * lj_eps * (2.0 * s6 * s6 - s6);
+            }
+        }
+    out[0] = ef + eself + ebg;
+    out[1] = er;
+    out[2] = el;
+    out[3] = ebg;
+    out[4] = wf;
+    out[5] = wr;
+    out[6] = wl;
+    out[7] = 3.0 * ebg;
+}
