@@ -268,6 +268,26 @@ rbe_status rbe_profile_read(rbe_handle h, double *ms, int64_t *launches);
  * kernels of the replayed step). */
 rbe_status rbe_launch_count(rbe_handle h, int64_t *count);
 
+/* True (non-random) energy and pressure of a configuration, the observables
+ * the paper evaluates "without random batch": the full Ewald sum over the
+ * cube 0 < |m|_inf <= mmax (mmax <= 0: the sampler's M, tail below 2^-64),
+ * the real-space and LJ parts under their cutoffs, the kinetic energy of
+ * `vel`, and the virial W = -dE/dlambda under r -> lambda r, L -> lambda L:
+ *   real space  sum_{i<j} lB q_i q_j [erfc(sqrt(a) r)/r + 2 sqrt(a/pi) e^{-a r^2}]
+ *   Fourier     sum_k A_k |rho_k|^2 (1 - k^2/(2 alpha)),
+ *               A_k = (2 pi lB / V) e^{-k^2/(4 alpha)} / k^2
+ *   background  3 E_bg;   LJ  sum_{i<j} r.F_ij
+ * P = (2 E_kin + W) / (3 V).  Structure factors use the mixed path's phases
+ * (FP32 sin/cos of exact 32-bit phases), sums in FP64.
+ * pos_q: device float4[n] (x, y, z, q); vel: device float4[n] or NULL (E_kin
+ * = 0).  out: HOST double[12 * systems], per system: E_total, E_fourier (incl.
+ * self and background), E_real, E_lj, E_kin, W_fourier, W_real, W_lj,
+ * W_background, pressure, kinetic temperature 2 E_kin / (3 n), 0.  Synchronous.
+ * Errors: RBE_ERR_ARG (NULL, n, mmax above 2^24 wave vectors), RBE_ERR_OOM,
+ * RBE_ERR_CUDA. */
+rbe_status rbe_observables(rbe_handle h, int32_t n, const float *pos_q, const float *vel,
+                           int32_t mmax, double *out);
+
 /* Measured throughput of the two units the hot path leans on, for rooflines:
  * the special-function unit (sin/cos results, as the Fourier passes use them)
  * and the FP32 FMA pipe, per SM per clock, from short saturating probe kernels

@@ -127,6 +127,25 @@ class _HandleBase:
     def profile(self, on=True):
         capi.check(self.lib.rbe_profile(self._h, 1 if on else 0), self._h)
 
+    def observables(self, pos_q, vel=None, mmax=0):
+        """True (non-random) energy and pressure (rbe_observables): a list of
+        dicts, one per system, with E_total, E_fourier, E_real, E_lj, E_kin,
+        W_fourier, W_real, W_lj, W_bg, pressure and T_kin."""
+        import numpy as np
+        torch = _torch()
+        n = pos_q.shape[0]
+        _need(pos_q, torch.float32, 4, n, "pos_q")
+        if vel is not None:
+            _need(vel, torch.float32, 4, n, "vel")
+        nsys = self._nsys()
+        out = np.zeros(12 * nsys)
+        capi.check(self.lib.rbe_observables(self._h, n, _ptr(pos_q),
+                                            _ptr(vel) if vel is not None else None, mmax,
+                                            out.ctypes.data_as(ctypes.c_void_p)), self._h)
+        keys = ("E_total", "E_fourier", "E_real", "E_lj", "E_kin", "W_fourier", "W_real",
+                "W_lj", "W_bg", "pressure", "T_kin")
+        return [dict(zip(keys, out[12 * s:12 * s + 11].tolist())) for s in range(nsys)]
+
     def profile_read(self):
         """{kernel name: (device ms, launches)} accumulated since the last read."""
         import numpy as np

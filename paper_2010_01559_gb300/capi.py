@@ -88,6 +88,7 @@ _SIGS = {
     "rbe_fourier_forces_noalloc": ([ctypes.POINTER(rbe_params), ctypes.c_int32, _P,
                                     ctypes.c_uint64, _P, _P, _P], ctypes.c_int),
     "rbe_probe_peaks": ([ctypes.POINTER(rbe_peaks)], ctypes.c_int),
+    "rbe_observables": ([_H, ctypes.c_int32, _P, _P, ctypes.c_int32, _P], ctypes.c_int),
 }
 
 #: kernel names in RBE_K_* order

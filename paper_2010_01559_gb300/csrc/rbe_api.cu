@@ -202,6 +202,15 @@ struct rbe_ctx {
     uint64_t* d_mh_pos = nullptr;             // per system: chain iterations done
     unsigned long long* d_qsum_fx = nullptr;  // sum q per system (fixed point)
     double2* d_blk_e = nullptr;
+    double2* d_blk_w = nullptr;               // per real-space block (W_coul, W_lj)
+    // observables (allocated on first use): half-space wave vectors per system,
+    // their fixed-point structure factors, the real-space virials and the results
+    int obs_mmax = -1;
+    std::vector<int> obs_off, obs_K;
+    int4* d_obs_m = nullptr;
+    unsigned long long* d_obs_rho = nullptr;
+    double* d_obs_w = nullptr;
+    double* d_obs_out = nullptr;
     double2* d_blk_q = nullptr;
     uint64_t* d_cur_step = nullptr;
     uint64_t* d_stage_step = nullptr;
@@ -546,6 +555,7 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_ALLOC(h->d_kab, h->ktot);
     RBE_ALLOC(h->d_qsum_fx, h->nsys);
     RBE_ALLOC(h->d_blk_e, std::max<long long>(rb, (long long)kSegChunks * (h->ncell + 1)));
+    RBE_ALLOC(h->d_blk_w, std::max<long long>(rb, (long long)kSegChunks * (h->ncell + 1)));
     RBE_ALLOC(h->d_blk_q, pb);
     RBE_ALLOC(h->d_cur_step, 1);
     RBE_ALLOC(h->d_stage_step, 1);
@@ -602,7 +612,8 @@ void release(rbe_ctx* h) {
                     h->d_perm, h->d_perm_tmp, h->d_fs, h->d_fs64, h->d_cell_cnt,
                     h->d_cell_start, h->d_ksamp, h->d_rho_fx, h->d_kcnt, h->d_kab,
                     h->d_kcoef, h->d_mh_tq, h->d_mh_rho, h->d_mh_state, h->d_mh_pos,
-                    h->d_qsum_fx, h->d_blk_e, h->d_blk_q, h->d_cur_step, h->d_stage_step,
+                    h->d_qsum_fx, h->d_blk_e, h->d_blk_w, h->d_obs_m, h->d_obs_rho, h->d_obs_w,
+                    h->d_obs_out, h->d_blk_q, h->d_cur_step, h->d_stage_step,
                     h->d_err, h->d_stage_pos, h->d_stage_vel, h->d_stage_F, h->d_stage_E};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -688,6 +699,7 @@ struct EvalArgs {
     float4* F;
     double4* F64;
     double* E;
+    double* W;                // nullable: real-space Coulomb and LJ virials (2 per system)
     float* phi;
     double* phi64;
     float4* md_pos;
@@ -850,13 +862,15 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     r.md_pos64 = a.md_pos64;
     r.md_vel64 = a.md_vel64;
     r.blk_e = a.E ? h->d_blk_e : nullptr;
+    r.blk_w = (a.E && a.W) ? h->d_blk_w : nullptr;
     run(RBE_K_REAL, st, [&] {
         if (mixed) launch_real_mixed(st, one, r); else launch_real_f64(st, one, r);
     });
     if (a.E)
         run(RBE_K_ENERGY, st, [&] {
             launch_energy(st, one, make_work(h, nullptr, 0, 0), h->nsys, h->d_ksamp, h->d_rho_fx,
-                          h->d_blk_e, h->d_blk_q, a.parts, mixed ? 1 : 0, a.E);
+                          h->d_blk_e, h->d_blk_q, r.blk_w, a.parts, mixed ? 1 : 0, a.E,
+                          r.blk_w ? a.W : nullptr);
         });
     if (prof) {
         cudaEventSynchronize(h->ev_end[a.E ? RBE_K_ENERGY : RBE_K_REAL]);
@@ -913,6 +927,74 @@ rbe_status forces_impl(rbe_ctx* h, int n, int prec, const void* pos, uint64_t st
     }
     enqueue_eval(h, h->stream, a);
     return finish(h, "rbe_forces");
+}
+
+// Wave vectors of the half space {m_x > 0} u {m_x = 0, m_y > 0} u {m = (0,0,m_z>0)}
+// of the cube |m|_inf <= mmax: each pair (m, -m) once.
+static void half_space_cube(int mmax, std::vector<int4>& out) {
+    for (int a = 0; a <= mmax; ++a)
+        for (int b = -mmax; b <= mmax; ++b)
+            for (int c = -mmax; c <= mmax; ++c) {
+                if (a == 0 && (b < 0 || (b == 0 && c <= 0))) continue;
+                out.push_back(make_int4(a, b, c, 0));
+            }
+}
+
+rbe_status observables_impl(rbe_ctx* h, int n, const float* pos_q, const float* vel, int mmax,
+                            double* out) {
+    if (!h || !out) return fail(h, RBE_ERR_ARG, "null argument");
+    rbe_status s = check_n(h, n);
+    if (s != RBE_OK) return s;
+    if (n > 0 && !pos_q) return fail(h, RBE_ERR_ARG, "pos_q must be non-null");
+    int mm = mmax;
+    if (mm <= 0)
+        for (auto& sh : h->sys) mm = std::max(mm, sh.M);
+    const long long side = 2LL * mm + 1;
+    if ((side * side * side - 1) / 2 > (1LL << 24))
+        return fail(h, RBE_ERR_ARG, "mmax too large (more than 2^24 wave vectors)");
+    if ((s = prepare(h, n)) != RBE_OK) return s;
+    if (h->obs_mmax != mm) {                         // wave-vector lists, once per mmax
+        std::vector<int4> all, one;
+        half_space_cube(mm, one);
+        h->obs_off.assign(h->nsys, 0);
+        h->obs_K.assign(h->nsys, (int)one.size());
+        for (int sy = 0; sy < h->nsys; ++sy) {
+            h->obs_off[sy] = (int)all.size();
+            all.insert(all.end(), one.begin(), one.end());
+        }
+        if (h->d_obs_m) cudaFree(h->d_obs_m);
+        if (h->d_obs_rho) cudaFree(h->d_obs_rho);
+        h->d_obs_m = nullptr;
+        h->d_obs_rho = nullptr;
+        if (dalloc(&h->d_obs_m, all.size()) != RBE_OK ||
+            dalloc(&h->d_obs_rho, 2 * all.size()) != RBE_OK ||
+            (!h->d_obs_w && dalloc(&h->d_obs_w, 2 * (size_t)h->nsys) != RBE_OK) ||
+            (!h->d_obs_out && dalloc(&h->d_obs_out, 12 * (size_t)h->nsys) != RBE_OK))
+            return fail(h, RBE_ERR_OOM, "cudaMalloc failed: observables workspace");
+        RBE_CUDA(h, cudaMemcpy(h->d_obs_m, all.data(), sizeof(int4) * all.size(),
+                               cudaMemcpyHostToDevice));
+        h->obs_mmax = mm;
+    }
+    // real-space Coulomb and LJ energies and virials (mixed path), fixed-point positions
+    EvalArgs a{};
+    a.prec = RBE_MIXED;
+    a.parts = RBE_PART_REAL | RBE_PART_LJ;
+    a.pos = (const float4*)pos_q;
+    a.E = h->d_stage_E;
+    a.W = h->d_obs_w;
+    enqueue_eval(h, h->stream, a);
+    for (int sy = 0; sy < h->nsys; ++sy) {
+        const SysHost& sh = h->sys[sy];
+        launch_observables(h->stream, h->sysdev[sy], h->d_fx, sh.off_p, sh.n,
+                           h->d_obs_m + h->obs_off[sy], h->obs_K[sy],
+                           h->d_obs_rho + 2 * (size_t)h->obs_off[sy], (const float4*)pos_q,
+                           (const float4*)vel, h->d_stage_E + 4 * sy, h->d_obs_w + 2 * sy,
+                           sh.p.mass, h->d_obs_out + 12 * sy);
+    }
+    RBE_CUDA(h, cudaMemcpyAsync(out, h->d_obs_out, sizeof(double) * 12 * h->nsys,
+                                cudaMemcpyDeviceToHost, h->stream));
+    RBE_CUDA(h, cudaStreamSynchronize(h->stream));
+    return finish(h, "rbe_observables");
 }
 
 rbe_status step_impl(rbe_ctx* h, int n, int prec, void* pos, void* vel, int nsteps,
@@ -1060,6 +1142,11 @@ rbe_status rbe_sample_k(rbe_handle h, uint64_t step, int32_t* m_out) {
     }
     RBE_CUDA(h, cudaStreamSynchronize(h->stream));
     return finish(h, "rbe_sample_k");
+}
+
+rbe_status rbe_observables(rbe_handle h, int32_t n, const float* pos_q, const float* vel,
+                           int32_t mmax, double* out) {
+    return observables_impl(h, n, pos_q, vel, mmax, out);
 }
 
 rbe_status rbe_forces(rbe_handle h, int32_t n, const float* pos_q, uint64_t step, float* F_out,

@@ -21,6 +21,7 @@
 // so the only phase error is the conversion of a 32-bit integer to FP32
 // (2^-25 turns).  sin/cos then run on the special-function unit for arguments
 // in [-pi, pi).  No FP32 work grows with |m| or L.
+#include <algorithm>
 #include <cmath>
 
 #include "rbe_internal.cuh"
@@ -315,6 +316,131 @@ void launch_fourier_force_f64(cudaStream_t st, bool one, const Work& w, int nblk
         k_force_f64<true><<<nblk, kBlockP, 0, st>>>(w, fx64, ksamp, rho_fx, fs64);
     else
         k_force_f64<false><<<nblk, kBlockP, 0, st>>>(w, fx64, ksamp, rho_fx, fs64);
+}
+
+}  // namespace rbe
+
+namespace rbe {
+
+// ----------------------------------------------------------------- observables
+// Full (non-random) Ewald structure factors of one system over a half space of
+// wave vectors (m and -m give conjugate rho(k)): the phases as in the
+// structure-factor pass (exact 32-bit phase, FP32 sin/cos), the sums in the
+// 64-bit fixed-point accumulators.  Grid: (particle chunks, k tiles).
+__global__ void __launch_bounds__(kLTile)
+k_struct_full(const uint4* __restrict__ fx, int first, int n, int chunk,
+              const int4* __restrict__ mlist, int K, double scale,
+              unsigned long long* __restrict__ rho_fx) {
+    __shared__ uint4 sp[kStage];
+    const int l = blockIdx.y * kLTile + threadIdx.x;
+    const bool active = l < K;
+    const int4 m = active ? mlist[l] : make_int4(0, 0, 0, 0);
+    const uint32_t mx = (uint32_t)m.x, my = (uint32_t)m.y, mz = (uint32_t)m.z;
+    const int b0 = blockIdx.x * chunk;
+    const int cnt_all = min(chunk, n - b0);
+    float re = 0.f, im = 0.f;
+    for (int base = 0; base < cnt_all; base += kStage) {
+        const int cnt = min(kStage, cnt_all - base);
+        __syncthreads();
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) sp[t] = fx[first + b0 + base + t];
+        __syncthreads();
+        if (active) {
+#pragma unroll 4
+            for (int j = 0; j < cnt; ++j) {
+                const uint4 p = sp[j];
+                const uint32_t ph = mx * p.x + my * p.y + mz * p.z;
+                float sn, cs;
+                __sincosf((float)(int32_t)ph * kTwoPiOver2p32, &sn, &cs);
+                const float q = __uint_as_float(p.w);
+                re = fmaf(q, cs, re);
+                im = fmaf(q, sn, im);
+            }
+        }
+    }
+    if (active && cnt_all > 0) rho_accumulate(rho_fx + 2 * l, (double)re, (double)im, scale);
+}
+
+// One block: the true energy and the virial of one system from the full
+// structure factors, the real-space Coulomb / LJ energies and virials of the
+// preceding evaluation, the charges and the velocities, all summed in FP64 in
+// a fixed order.  out[12]: E_total, E_fourier (incl. self and background),
+// E_real, E_lj, E_kin, W_fourier, W_real, W_lj, W_background, pressure,
+// kinetic temperature, 0.  P = (2 E_kin + W) / (3 V); W_bg = 3 E_bg.
+__global__ void __launch_bounds__(256)
+k_observables(const __grid_constant__ SysDev S, const int4* __restrict__ mlist, int K,
+              const unsigned long long* __restrict__ rho_fx, const float4* __restrict__ pos_q,
+              const float4* __restrict__ vel, int n, const double* __restrict__ E_in,
+              const double* __restrict__ W_in, double mass, double* __restrict__ out) {
+    __shared__ double sa[256], sb[256], sc[256], sd[256], se[256];
+    const double tp = 2.0 * M_PI * S.invL;
+    const double pref = 2.0 * 2.0 * M_PI * S.lB / S.V;          // half space: each k twice
+    double ef = 0.0, wf = 0.0, q1 = 0.0, q2 = 0.0, ke = 0.0;
+    for (int l = threadIdx.x; l < K; l += blockDim.x) {
+        const int4 m = mlist[l];
+        const double k2 = tp * tp * ((double)m.x * m.x + (double)m.y * m.y + (double)m.z * m.z);
+        const double2 r = rho_read(rho_fx + 2 * l, S.rho_inv_scale);
+        const double e = pref * exp(-k2 / (4.0 * S.alpha)) / k2 * (r.x * r.x + r.y * r.y);
+        ef += e;
+        wf += e * (1.0 - k2 / (2.0 * S.alpha));
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double q = (double)pos_q[i].w;
+        q1 += q;
+        q2 += q * q;
+        if (vel) {
+            const float4 v = vel[i];
+            ke += 0.5 * mass * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
+        }
+    }
+    sa[threadIdx.x] = ef; sb[threadIdx.x] = wf; sc[threadIdx.x] = q1; sd[threadIdx.x] = q2;
+    se[threadIdx.x] = ke;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sa[threadIdx.x] += sa[threadIdx.x + o];
+            sb[threadIdx.x] += sb[threadIdx.x + o];
+            sc[threadIdx.x] += sc[threadIdx.x + o];
+            sd[threadIdx.x] += sd[threadIdx.x + o];
+            se[threadIdx.x] += se[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double ebg = -S.lB * M_PI * sc[0] * sc[0] / (2.0 * S.V * S.alpha);
+        const double eself = -S.self_coef * sd[0];
+        const double Ef = sa[0] + eself + ebg;
+        const double Er = E_in[2], El = E_in[3];
+        const double W = sb[0] + W_in[0] + W_in[1] + 3.0 * ebg;
+        out[0] = Ef + Er + El;
+        out[1] = Ef;
+        out[2] = Er;
+        out[3] = El;
+        out[4] = se[0];
+        out[5] = sb[0];
+        out[6] = W_in[0];
+        out[7] = W_in[1];
+        out[8] = 3.0 * ebg;
+        out[9] = (2.0 * se[0] + W) / (3.0 * S.V);
+        out[10] = n > 0 ? 2.0 * se[0] / (3.0 * (double)n) : 0.0;
+        out[11] = 0.0;
+    }
+}
+
+void launch_observables(cudaStream_t st, const SysDev& S, const uint4* fx, int first, int n,
+                        const int4* mlist, int K, unsigned long long* rho_fx,
+                        const float4* pos_q, const float4* vel, const double* E_in,
+                        const double* W_in, double mass, double* out) {
+    if (K > 0) {
+        const int chunk = 1024;
+        const int nch = std::max(1, (n + chunk - 1) / chunk);
+        dim3 grid(nch, (K + kLTile - 1) / kLTile);
+        cudaMemsetAsync(rho_fx, 0, sizeof(unsigned long long) * 2 * (size_t)K, st);
+        if (n > 0)
+            k_struct_full<<<grid, kLTile, 0, st>>>(fx, first, n, chunk, mlist, K, S.rho_scale,
+                                                   rho_fx);
+    }
+    k_observables<<<1, 256, 0, st>>>(S, mlist, K, rho_fx, pos_q + first, vel ? vel + first : nullptr,
+                                     n, E_in, W_in, mass, out);
 }
 
 }  // namespace rbe

@@ -298,11 +298,17 @@ struct RealArgs {
     double4* md_pos64;
     double4* md_vel64;
     double2* blk_e;          // per block (E_coul, E_lj), nullable
+    double2* blk_w;          // per block (W_coul, W_lj): pair virials r.F, nullable
 };
 void launch_real_mixed(cudaStream_t st, bool one, const RealArgs& a);
 void launch_real_f64(cudaStream_t st, bool one, const RealArgs& a);
+void launch_observables(cudaStream_t st, const SysDev& S, const uint4* fx, int first, int n,
+                        const int4* mlist, int K, unsigned long long* rho_fx,
+                        const float4* pos_q, const float4* vel, const double* E_in,
+                        const double* W_in, double mass, double* out);
 void launch_energy(cudaStream_t st, bool one, const Work& w, int nsys, const int4* ksamp,
                    const unsigned long long* rho_fx, const double2* blk_e,
-                   const double2* blk_q, int parts, int per_cell, double* E_out);
+                   const double2* blk_q, const double2* blk_w, int parts, int per_cell,
+                   double* E_out, double* W_out);
 
 }  // namespace rbe

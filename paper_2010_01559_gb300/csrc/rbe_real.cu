@@ -84,7 +84,7 @@ constexpr int kNbCap = 24;          // entries of each lane's neighbour list
 constexpr int kBatch = 2;           // candidates a thread tests per step of its scan
 
 struct PairAcc {
-    float fx, fy, fz, phr, ec, elj;
+    float fx, fy, fz, phr, ec, elj, wc, wlj;     // wc, wlj: half the pair virials r.F
 };
 
 // erfc(x) for x >= 0 given e = exp(-x^2): the rational approximation of
@@ -104,6 +104,7 @@ __device__ __forceinline__ float erfc_as(float e, float x) {
 // Per-system constants of the pair terms, in registers.
 struct PairConst {
     float rc2, lj_rc2, alpha, sa, two_sa_spi, lB, lj_s2, lj_eps, lj_shift;
+    bool vir;                                   // accumulate the virials
 };
 
 // Pair terms for displacement r_ij = (dx, dy, dz), |r_ij|^2 = r2 > 0.
@@ -121,6 +122,8 @@ __device__ __forceinline__ void pair_terms(float dx, float dy, float dz, float r
         acc.fz = fmaf(s_, dz, acc.fz);
         acc.phr = fmaf(k.lB * qj, pot, acc.phr);
         acc.ec = fmaf(0.5f * lbqi * qj, pot, acc.ec);
+        // r.F of the pair: lB q_i q_j (erfc(sqrt(a) r)/r + 2 sqrt(a/pi) e^{-a r^2})
+        if (k.vir) acc.wc = fmaf(0.5f * lbqi * qj, fmaf(k.two_sa_spi, ex, pot), acc.wc);
     }
     if (r2 < k.lj_rc2) {
         const float inv_r2 = inv_r * inv_r;
@@ -131,6 +134,7 @@ __device__ __forceinline__ void pair_terms(float dx, float dy, float dz, float r
         acc.fy = fmaf(-mag, dy, acc.fy);
         acc.fz = fmaf(-mag, dz, acc.fz);
         acc.elj += 0.5f * (4.f * k.lj_eps * (sr6 * sr6 - sr6) + k.lj_shift);
+        if (k.vir) acc.wlj = fmaf(0.5f * mag, r2, acc.wlj);   // r.F = 24 eps (2 (s/r)^12 - (s/r)^6)
     }
 }
 
@@ -282,6 +286,7 @@ k_real_seg(const __grid_constant__ RealArgs a) {
     const int nown = max(0, own_e - own_s);
     if (chunk > 0 && nown == 0) {                 // nothing beyond the first pass
         if (a.blk_e && threadIdx.x == 0) a.blk_e[blockIdx.x] = make_double2(0.0, 0.0);
+        if (a.blk_w && threadIdx.x == 0) a.blk_w[blockIdx.x] = make_double2(0.0, 0.0);
         return;
     }
     const bool do_real = (a.parts & kPartReal) != 0;
@@ -359,6 +364,7 @@ k_real_seg(const __grid_constant__ RealArgs a) {
     kc.lj_s2 = S.f_lj_sigma2;
     kc.lj_eps = S.f_lj_eps;
     kc.lj_shift = S.f_lj_shift;
+    kc.vir = a.blk_w != nullptr;
     const float cut2 = fmaxf(kc.rc2, kc.lj_rc2);
     const float invLu = S.f_inv_Lu;
     // distance test in fixed-point units; the margins keep the test and the
@@ -372,7 +378,7 @@ k_real_seg(const __grid_constant__ RealArgs a) {
     const bool want_e = a.blk_e != nullptr;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int pl = lane / R, l = lane - pl * R;  // particle of the warp, lane within it
-    double ec_own = 0.0, elj_own = 0.0;
+    double ec_own = 0.0, elj_own = 0.0, wc_own = 0.0, wlj_own = 0.0;
     constexpr int kPass = NW * PPW;              // particles per pass of the block
     __shared__ float4 s_f[kPass];                // a pass's real-space force and phi
     for (int pass = 0; pass < nown; pass += kPass) {
@@ -382,7 +388,7 @@ k_real_seg(const __grid_constant__ RealArgs a) {
         const uint4 si = a.spos[i];
         const int cxi = (int)(((unsigned long long)si.x * (unsigned long long)ncd) >> 32);
         const float lbqi = kc.lB * __uint_as_float(si.w);
-        PairAcc acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        PairAcc acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (active && pairs) {
             const int u = cxi - x0;                       // 0 .. nsc-1
             if (staged) {
@@ -466,11 +472,19 @@ k_real_seg(const __grid_constant__ RealArgs a) {
             acc.ec = lane_combine<R>(acc.ec);
             acc.elj = lane_combine<R>(acc.elj);
         }
+        if (kc.vir) {
+            acc.wc = lane_combine<R>(acc.wc);
+            acc.wlj = lane_combine<R>(acc.wlj);
+        }
         if (active && l == 0) {
             s_f[warp * PPW + pl] = make_float4(acc.fx, acc.fy, acc.fz, acc.phr);
             if (want_e) {
                 ec_own += (double)acc.ec;
                 elj_own += (double)acc.elj;
+            }
+            if (kc.vir) {
+                wc_own += (double)acc.wc;
+                wlj_own += (double)acc.wlj;
             }
         }
         __syncthreads();
@@ -500,6 +514,11 @@ k_real_seg(const __grid_constant__ RealArgs a) {
         const double2 r = block_sum2_real(ec_own, elj_own);
         if (threadIdx.x == 0) a.blk_e[blockIdx.x] = r;
     }
+    if (kc.vir) {
+        __syncthreads();                                // the partial buffers are reused
+        const double2 r = block_sum2_real(wc_own, wlj_own);
+        if (threadIdx.x == 0) a.blk_w[blockIdx.x] = r;
+    }
 }
 
 // ----------------------------------------------------------------- FP64
@@ -517,7 +536,8 @@ k_real_f64(const __grid_constant__ RealArgs a) {
     const double qi = pi.w;
     const bool do_real = (a.parts & kPartReal) != 0;
     const bool do_lj = (a.parts & kPartLJ) != 0 && S.lj_eps != 0.0;
-    double fx = 0, fy = 0, fz = 0, phr = 0, ec = 0, elj = 0;
+    double fx = 0, fy = 0, fz = 0, phr = 0, ec = 0, elj = 0, wc = 0, wlj = 0;
+    const bool vir = a.blk_w != nullptr;
     if (active && (do_real || do_lj)) {
         const int ncd = S.ncd;
         auto cell = [&](double w) {
@@ -553,6 +573,9 @@ k_real_f64(const __grid_constant__ RealArgs a) {
                             fx += s_ * ddx; fy += s_ * ddy; fz += s_ * ddz;
                             phr += S.lB * pj.w * erfc_v / r;
                             ec += 0.5 * S.lB * qi * pj.w * erfc_v / r;
+                            if (vir)
+                                wc += 0.5 * S.lB * qi * pj.w *
+                                      (erfc_v / r + two_sa_spi * exp(-S.alpha * r2));
                         }
                         if (r2 < lj_rc2) {
                             const double sr2 = S.lj_sigma2 / r2;
@@ -560,6 +583,7 @@ k_real_f64(const __grid_constant__ RealArgs a) {
                             const double mag = 24.0 * S.lj_eps * (2.0 * sr6 * sr6 - sr6) / r2;
                             fx -= mag * ddx; fy -= mag * ddy; fz -= mag * ddz;
                             elj += 0.5 * (4.0 * S.lj_eps * (sr6 * sr6 - sr6) + S.lj_shift);
+                            if (vir) wlj += 0.5 * mag * r2;
                         }
                     }
                 }
@@ -574,6 +598,8 @@ k_real_f64(const __grid_constant__ RealArgs a) {
         phr += __shfl_down_sync(0xffffffffu, phr, o, G);
         ec += __shfl_down_sync(0xffffffffu, ec, o, G);
         elj += __shfl_down_sync(0xffffffffu, elj, o, G);
+        wc += __shfl_down_sync(0xffffffffu, wc, o, G);
+        wlj += __shfl_down_sync(0xffffffffu, wlj, o, G);
     }
     const bool owner = active && g == 0;
     if (owner) {
@@ -632,6 +658,11 @@ k_real_f64(const __grid_constant__ RealArgs a) {
         const double2 r = block_sum2_real(owner ? ec : 0.0, owner ? elj : 0.0);
         if (threadIdx.x == 0) a.blk_e[blockIdx.x] = r;
     }
+    if (vir) {
+        __syncthreads();                                // the partial buffers are reused
+        const double2 r = block_sum2_real(owner ? wc : 0.0, owner ? wlj : 0.0);
+        if (threadIdx.x == 0) a.blk_w[blockIdx.x] = r;
+    }
 }
 
 // ----------------------------------------------------------------- energy
@@ -645,7 +676,8 @@ template <bool ONE>
 __global__ void k_energy(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
                          const unsigned long long* __restrict__ rho_fx,
                          const double2* __restrict__ blk_e, const double2* __restrict__ blk_q,
-                         int parts, int per_cell, double* __restrict__ E_out) {
+                         const double2* __restrict__ blk_w, int parts, int per_cell,
+                         double* __restrict__ E_out, double* __restrict__ W_out) {
     const SysDev& S = sys_of<ONE>(w, blockIdx.x);
     double ef = 0.0, ec = 0.0, elj = 0.0, q1 = 0.0, q2 = 0.0;
     if (parts & kPartFourier) {
@@ -664,15 +696,23 @@ __global__ void k_energy(const __grid_constant__ Work w, const int4* __restrict_
     }
     const int off = per_cell ? S.off_sg * kSegChunks : S.off_rb;
     const int nb = per_cell ? S.nsg * kSegChunks : S.nrb;
+    double wc = 0.0, wlj = 0.0;
     if (blk_e)
         for (int b = threadIdx.x; b < nb; b += blockDim.x) {
             const double2 v = blk_e[off + b];
             ec += v.x;
             elj += v.y;
         }
-    __shared__ double sf[256], sc[256], sl[256], s1[256], s2[256];
+    if (blk_w)
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            const double2 v = blk_w[off + b];
+            wc += v.x;
+            wlj += v.y;
+        }
+    __shared__ double sf[256], sc[256], sl[256], s1[256], s2[256], sw[256], sv[256];
     sf[threadIdx.x] = ef; sc[threadIdx.x] = ec; sl[threadIdx.x] = elj;
     s1[threadIdx.x] = q1; s2[threadIdx.x] = q2;
+    sw[threadIdx.x] = wc; sv[threadIdx.x] = wlj;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) {
@@ -681,6 +721,8 @@ __global__ void k_energy(const __grid_constant__ Work w, const int4* __restrict_
             sl[threadIdx.x] += sl[threadIdx.x + o];
             s1[threadIdx.x] += s1[threadIdx.x + o];
             s2[threadIdx.x] += s2[threadIdx.x + o];
+            sw[threadIdx.x] += sw[threadIdx.x + o];
+            sv[threadIdx.x] += sv[threadIdx.x + o];
         }
         __syncthreads();
     }
@@ -694,6 +736,10 @@ __global__ void k_energy(const __grid_constant__ Work w, const int4* __restrict_
         E_out[4 * blockIdx.x + 1] = Ef;
         E_out[4 * blockIdx.x + 2] = Ec;
         E_out[4 * blockIdx.x + 3] = El;
+        if (W_out) {                                    // real-space Coulomb and LJ virials
+            W_out[2 * blockIdx.x + 0] = (parts & kPartReal) ? sw[0] : 0.0;
+            W_out[2 * blockIdx.x + 1] = (parts & kPartLJ) ? sv[0] : 0.0;
+        }
     }
 }
 
@@ -755,14 +801,15 @@ void launch_real_f64(cudaStream_t st, bool one, const RealArgs& a) {
 
 void launch_energy(cudaStream_t st, bool one, const Work& w, int nsys, const int4* ksamp,
                    const unsigned long long* rho_fx, const double2* blk_e,
-                   const double2* blk_q, int parts, int per_cell, double* E_out) {
+                   const double2* blk_q, const double2* blk_w, int parts, int per_cell,
+                   double* E_out, double* W_out) {
     if (nsys <= 0) return;
     if (one)
-        k_energy<true><<<nsys, 256, 0, st>>>(w, ksamp, rho_fx, blk_e, blk_q, parts, per_cell,
-                                             E_out);
+        k_energy<true><<<nsys, 256, 0, st>>>(w, ksamp, rho_fx, blk_e, blk_q, blk_w, parts,
+                                             per_cell, E_out, W_out);
     else
-        k_energy<false><<<nsys, 256, 0, st>>>(w, ksamp, rho_fx, blk_e, blk_q, parts, per_cell,
-                                              E_out);
+        k_energy<false><<<nsys, 256, 0, st>>>(w, ksamp, rho_fx, blk_e, blk_q, blk_w, parts,
+                                              per_cell, E_out, W_out);
 }
 
 }  // namespace rbe
