@@ -209,6 +209,7 @@ struct rbe_ctx {
     std::vector<int> obs_off, obs_K;
     int4* d_obs_m = nullptr;
     unsigned long long* d_obs_rho = nullptr;
+    double2* d_obs_part = nullptr;            // per-block wave-vector partials
     double* d_obs_w = nullptr;
     double* d_obs_out = nullptr;
     double2* d_blk_q = nullptr;
@@ -613,7 +614,7 @@ void release(rbe_ctx* h) {
                     h->d_cell_start, h->d_ksamp, h->d_rho_fx, h->d_kcnt, h->d_kab,
                     h->d_kcoef, h->d_mh_tq, h->d_mh_rho, h->d_mh_state, h->d_mh_pos,
                     h->d_qsum_fx, h->d_blk_e, h->d_blk_w, h->d_obs_m, h->d_obs_rho, h->d_obs_w,
-                    h->d_obs_out, h->d_blk_q, h->d_cur_step, h->d_stage_step,
+                    h->d_obs_out, h->d_obs_part, h->d_blk_q, h->d_cur_step, h->d_stage_step,
                     h->d_err, h->d_stage_pos, h->d_stage_vel, h->d_stage_F, h->d_stage_E};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -964,10 +965,13 @@ rbe_status observables_impl(rbe_ctx* h, int n, const float* pos_q, const float* 
         }
         if (h->d_obs_m) cudaFree(h->d_obs_m);
         if (h->d_obs_rho) cudaFree(h->d_obs_rho);
+        if (h->d_obs_part) cudaFree(h->d_obs_part);
         h->d_obs_m = nullptr;
         h->d_obs_rho = nullptr;
+        h->d_obs_part = nullptr;
         if (dalloc(&h->d_obs_m, all.size()) != RBE_OK ||
             dalloc(&h->d_obs_rho, 2 * all.size()) != RBE_OK ||
+            dalloc(&h->d_obs_part, (one.size() + 255) / 256 + 1) != RBE_OK ||
             (!h->d_obs_w && dalloc(&h->d_obs_w, 2 * (size_t)h->nsys) != RBE_OK) ||
             (!h->d_obs_out && dalloc(&h->d_obs_out, 12 * (size_t)h->nsys) != RBE_OK))
             return fail(h, RBE_ERR_OOM, "cudaMalloc failed: observables workspace");
@@ -987,7 +991,8 @@ rbe_status observables_impl(rbe_ctx* h, int n, const float* pos_q, const float* 
         const SysHost& sh = h->sys[sy];
         launch_observables(h->stream, h->sysdev[sy], h->d_fx, sh.off_p, sh.n,
                            h->d_obs_m + h->obs_off[sy], h->obs_K[sy],
-                           h->d_obs_rho + 2 * (size_t)h->obs_off[sy], (const float4*)pos_q,
+                           h->d_obs_rho + 2 * (size_t)h->obs_off[sy], h->d_obs_part,
+                           (const float4*)pos_q,
                            (const float4*)vel, h->d_stage_E + 4 * sy, h->d_obs_w + 2 * sy,
                            sh.p.mass, h->d_obs_out + 12 * sy);
     }

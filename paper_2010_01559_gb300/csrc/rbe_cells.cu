@@ -67,13 +67,13 @@ __device__ __forceinline__ void latch_step(const uint64_t* step_dev, uint64_t st
 // Eq. rbmapprox, for the structure-factor and force passes that follow.
 // The paper's Metropolis-Hastings sampler (Sec. 3.1), one block per system:
 // three per-axis independence chains with the rounded-Gaussian proposal, run
-// in windows of kMhWin iterations.  Proposals and uniforms of a window come
+// in windows of kMhWin iterations (one window covers P up to about 250).  Proposals and uniforms of a window come
 // from Philox in parallel (iteration t, axis c: ctr = (t_lo, t_hi, c,
 // (stream << 8) | 6)); threads 0..2 then walk their chain through the window
 // (accept m* iff u * rho(m) < rho(m*)); thread 0 keeps the nonzero triples in
 // order until P are out.  The chains' state and position persist in the handle
 // (the set K of Algorithm 1, consumed in order).
-constexpr int kMhWin = 64;
+constexpr int kMhWin = 256;
 
 template <bool ONE>
 __device__ void draw_samples_mh(const Work& w, const PrepArgs& pa) {
@@ -82,6 +82,7 @@ __device__ void draw_samples_mh(const Work& w, const PrepArgs& pa) {
     uint32_t* s_tq = (uint32_t*)(s_rho + pa.mh_words);         // [mh_words]
     __shared__ int s_prop[3][kMhWin];
     __shared__ double s_u[3][kMhWin];
+    __shared__ unsigned char s_dec[3][kMhWin];   // decision if the state is the previous proposal
     __shared__ int s_st[3][kMhWin];
     __shared__ int s_state[3], s_emitted, s_used, s_bad;
     const int sys = (int)blockIdx.x - pa.npblk;
@@ -113,12 +114,25 @@ __device__ void draw_samples_mh(const Work& w, const PrepArgs& pa) {
             s_u[c][it] = (double)((((unsigned long long)r.z << 32) | r.w) >> 11) * 0x1.0p-53;
         }
         __syncthreads();
+        // The acceptance test depends on the state only through its value, and the
+        // state is nearly always the previous proposal: decide every iteration for
+        // that state in parallel; the walk below recomputes only when it differs.
+        for (int idx = threadIdx.x; idx < 3 * kMhWin; idx += blockDim.x) {
+            const int c = idx / kMhWin, it = idx - c * kMhWin;
+            if (it > 0)
+                s_dec[c][it] = __dmul_rn(s_u[c][it], s_rho[s_prop[c][it - 1] + S.M]) <
+                               s_rho[s_prop[c][it] + S.M];
+        }
+        __syncthreads();
         if (threadIdx.x < 3) {
             const int c = threadIdx.x;
             int st = s_state[c];
             for (int it = 0; it < kMhWin; ++it) {
                 const int ms = s_prop[c][it];
-                if (__dmul_rn(s_u[c][it], s_rho[st + S.M]) < s_rho[ms + S.M]) st = ms;
+                const bool acc = (it > 0 && st == s_prop[c][it - 1])
+                                     ? s_dec[c][it] != 0
+                                     : __dmul_rn(s_u[c][it], s_rho[st + S.M]) < s_rho[ms + S.M];
+                if (acc) st = ms;
                 s_st[c][it] = st;
             }
         }

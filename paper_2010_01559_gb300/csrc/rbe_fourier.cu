@@ -360,28 +360,55 @@ k_struct_full(const uint4* __restrict__ fx, int first, int n, int chunk,
     if (active && cnt_all > 0) rho_accumulate(rho_fx + 2 * l, (double)re, (double)im, scale);
 }
 
-// One block: the true energy and the virial of one system from the full
-// structure factors, the real-space Coulomb / LJ energies and virials of the
+// Energy and virial terms of the full structure factors, one thread per wave
+// vector, FP64, summed per block in a fixed order: part[b] = (sum e_k, sum w_k)
+// with e_k = 2 A_k |rho_k|^2 (half space: each k stands for +-k),
+// A_k = (2 pi lB / V) e^{-k^2/(4 alpha)} / k^2, w_k = e_k (1 - k^2 / (2 alpha)).
+__global__ void __launch_bounds__(256)
+k_obs_terms(const __grid_constant__ SysDev S, const int4* __restrict__ mlist, int K,
+            const unsigned long long* __restrict__ rho_fx, double2* __restrict__ part) {
+    __shared__ double sa[256], sb[256];
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    double e = 0.0, wv = 0.0;
+    if (l < K) {
+        const double tp = 2.0 * M_PI * S.invL;
+        const int4 m = mlist[l];
+        const double k2 = tp * tp * ((double)m.x * m.x + (double)m.y * m.y + (double)m.z * m.z);
+        const double2 r = rho_read(rho_fx + 2 * l, S.rho_inv_scale);
+        e = 2.0 * (2.0 * M_PI * S.lB / S.V) * exp(-k2 / (4.0 * S.alpha)) / k2 *
+            (r.x * r.x + r.y * r.y);
+        wv = e * (1.0 - k2 / (2.0 * S.alpha));
+    }
+    sa[threadIdx.x] = e;
+    sb[threadIdx.x] = wv;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sa[threadIdx.x] += sa[threadIdx.x + o];
+            sb[threadIdx.x] += sb[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = make_double2(sa[0], sb[0]);
+}
+
+// One block: the true energy and the virial of one system from the per-block
+// wave-vector partials, the real-space Coulomb / LJ energies and virials of the
 // preceding evaluation, the charges and the velocities, all summed in FP64 in
 // a fixed order.  out[12]: E_total, E_fourier (incl. self and background),
 // E_real, E_lj, E_kin, W_fourier, W_real, W_lj, W_background, pressure,
 // kinetic temperature, 0.  P = (2 E_kin + W) / (3 V); W_bg = 3 E_bg.
 __global__ void __launch_bounds__(256)
-k_observables(const __grid_constant__ SysDev S, const int4* __restrict__ mlist, int K,
-              const unsigned long long* __restrict__ rho_fx, const float4* __restrict__ pos_q,
-              const float4* __restrict__ vel, int n, const double* __restrict__ E_in,
-              const double* __restrict__ W_in, double mass, double* __restrict__ out) {
+k_observables(const __grid_constant__ SysDev S, const double2* __restrict__ part, int nparts,
+              const float4* __restrict__ pos_q, const float4* __restrict__ vel, int n,
+              const double* __restrict__ E_in, const double* __restrict__ W_in, double mass,
+              double* __restrict__ out) {
     __shared__ double sa[256], sb[256], sc[256], sd[256], se[256];
-    const double tp = 2.0 * M_PI * S.invL;
-    const double pref = 2.0 * 2.0 * M_PI * S.lB / S.V;          // half space: each k twice
     double ef = 0.0, wf = 0.0, q1 = 0.0, q2 = 0.0, ke = 0.0;
-    for (int l = threadIdx.x; l < K; l += blockDim.x) {
-        const int4 m = mlist[l];
-        const double k2 = tp * tp * ((double)m.x * m.x + (double)m.y * m.y + (double)m.z * m.z);
-        const double2 r = rho_read(rho_fx + 2 * l, S.rho_inv_scale);
-        const double e = pref * exp(-k2 / (4.0 * S.alpha)) / k2 * (r.x * r.x + r.y * r.y);
-        ef += e;
-        wf += e * (1.0 - k2 / (2.0 * S.alpha));
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+        const double2 v = part[b];
+        ef += v.x;
+        wf += v.y;
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const double q = (double)pos_q[i].w;
@@ -427,9 +454,10 @@ k_observables(const __grid_constant__ SysDev S, const int4* __restrict__ mlist, 
 }
 
 void launch_observables(cudaStream_t st, const SysDev& S, const uint4* fx, int first, int n,
-                        const int4* mlist, int K, unsigned long long* rho_fx,
+                        const int4* mlist, int K, unsigned long long* rho_fx, double2* part,
                         const float4* pos_q, const float4* vel, const double* E_in,
                         const double* W_in, double mass, double* out) {
+    const int nparts = (K + 255) / 256;
     if (K > 0) {
         const int chunk = 1024;
         const int nch = std::max(1, (n + chunk - 1) / chunk);
@@ -438,9 +466,10 @@ void launch_observables(cudaStream_t st, const SysDev& S, const uint4* fx, int f
         if (n > 0)
             k_struct_full<<<grid, kLTile, 0, st>>>(fx, first, n, chunk, mlist, K, S.rho_scale,
                                                    rho_fx);
+        k_obs_terms<<<nparts, 256, 0, st>>>(S, mlist, K, rho_fx, part);
     }
-    k_observables<<<1, 256, 0, st>>>(S, mlist, K, rho_fx, pos_q + first, vel ? vel + first : nullptr,
-                                     n, E_in, W_in, mass, out);
+    k_observables<<<1, 256, 0, st>>>(S, part, nparts, pos_q + first,
+                                     vel ? vel + first : nullptr, n, E_in, W_in, mass, out);
 }
 
 }  // namespace rbe

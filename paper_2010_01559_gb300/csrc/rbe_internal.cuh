@@ -303,7 +303,7 @@ struct RealArgs {
 void launch_real_mixed(cudaStream_t st, bool one, const RealArgs& a);
 void launch_real_f64(cudaStream_t st, bool one, const RealArgs& a);
 void launch_observables(cudaStream_t st, const SysDev& S, const uint4* fx, int first, int n,
-                        const int4* mlist, int K, unsigned long long* rho_fx,
+                        const int4* mlist, int K, unsigned long long* rho_fx, double2* part,
                         const float4* pos_q, const float4* vel, const double* E_in,
                         const double* W_in, double mass, double* out);
 void launch_energy(cudaStream_t st, bool one, const Work& w, int nsys, const int4* ksamp,
