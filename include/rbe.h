@@ -305,10 +305,8 @@ rbe_status rbe_probe_peaks(rbe_peaks *out);
 
 /* Fourier part of one RBE evaluation without any device allocation, for
  * callers that cannot call cudaMalloc: an MD engine whose memory pool owns all
- * device memory and forbids plugins to allocate, an application that records
- * its whole time step into a CUDA graph (allocation is not allowed inside the
- * capture region), or a latency-bound loop that cannot afford cudaMalloc's
- * implicit device synchronisation.  The paper has no counterpart: this is an
+ * device memory and forbids plugins to allocate, or a latency-bound loop that
+ * cannot afford cudaMalloc's implicit device-wide synchronisation.  The paper has no counterpart: this is an
  * interface variant of rbe_forces_ex(..., RBE_PART_FOURIER, ...) that needs no
  * handle.
  *

@@ -2,10 +2,9 @@
 // cannot allocate device memory.
 //
 // Who needs this: an MD engine that hands all device memory to its own pool at
-// start-up and forbids plugins from calling cudaMalloc; an application that
-// records its whole time step into a CUDA graph, where allocating inside the
-// capture region is not allowed; a latency-bound loop where cudaMalloc's
-// implicit device-wide synchronisation would stall the other streams.  Such a
+// start-up and forbids plugins from calling cudaMalloc; a latency-bound loop
+// where cudaMalloc's implicit device-wide synchronisation would stall the
+// other streams.  Such a
 // caller cannot create an rbe handle (rbe_create allocates the workspace), so
 // this entry point keeps its scratch in one file-scope device array instead:
 // the sampling table, the per-chunk partial structure factors, the per-k

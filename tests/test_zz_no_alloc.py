@@ -1,9 +1,8 @@
 """rbe_fourier_forces_noalloc, the entry point for callers that cannot allocate.
 
 Some callers of this library may not call cudaMalloc: an MD engine whose own
-pool owns all device memory, an application that records its whole time step
-into a CUDA graph (no allocation inside the capture region), or a loop that
-cannot afford cudaMalloc's device-wide synchronisation.  They cannot create a
+pool owns all device memory, or a loop that cannot afford cudaMalloc's
+device-wide synchronisation.  They cannot create a
 handle, so rbe_fourier_forces_noalloc keeps its scratch in a static device
 array inside librbe.  The GPU test calls it through the C ABI twice in a row, on
 two different systems (so anything left in the shared array by the first call
