@@ -89,7 +89,8 @@ enum { RBE_PART_FOURIER = 1, RBE_PART_REAL = 2, RBE_PART_LJ = 4, RBE_PART_ALL = 
 typedef struct {
     double box;               /* L > 0: edge of the cubic periodic box (Sec. 2)          */
     double alpha;             /* Ewald splitting parameter, erfc(sqrt(alpha) r) (Sec. 2) */
-    double r_c;               /* real-space cutoff, 0 < r_c <= L/3 (cells of side >= r_c) */
+    double r_c;               /* real-space cutoff, 0 < r_c <= L/2 (minimum image); cells of
+                                 side >= r_c, or one cell (all pairs) when r_c > L/3     */
     double coulomb_prefactor; /* multiplies all Coulomb terms (Sec. 4.1: 1)              */
     double lj_eps;            /* shifted-LJ epsilon; 0 disables LJ (Eq. Ljpotential)     */
     double lj_sigma;          /* LJ sigma (r_off = 0)                                    */
@@ -126,7 +127,7 @@ typedef struct {
  * per-axis sampling table (Eq. probexpression, per-axis marginal) and S
  * (Eq. S) in FP64 on the host and allocates the device workspace.
  * Errors: RBE_ERR_ARG for out-of-range parameters (L, alpha, r_c, P <= 0,
- * r_c > L/3, lj_rcut > r_c, n_max < 0), RBE_ERR_OOM, RBE_ERR_CUDA. */
+ * r_c > L/2, lj_rcut > r_c, n_max < 0), RBE_ERR_OOM, RBE_ERR_CUDA. */
 rbe_status rbe_create(const rbe_params *p, rbe_handle *out);
 
 /* Create a handle for n_replicas independent systems (replica r has

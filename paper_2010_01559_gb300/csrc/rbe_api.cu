@@ -245,7 +245,7 @@ rbe_status validate_params(const rbe_params& p, std::string& why) {
     if (!(p.box > 0.0) || !std::isfinite(p.box)) { why = "box must be > 0"; return RBE_ERR_ARG; }
     if (!(p.alpha > 0.0) || !std::isfinite(p.alpha)) { why = "alpha must be > 0"; return RBE_ERR_ARG; }
     if (!(p.r_c > 0.0)) { why = "r_c must be > 0"; return RBE_ERR_ARG; }
-    if (p.box / p.r_c < 3.0) { why = "r_c must be <= L/3 (at least 3 cells per edge)"; return RBE_ERR_ARG; }
+    if (p.box / p.r_c < 2.0) { why = "r_c must be <= L/2 (minimum image)"; return RBE_ERR_ARG; }
     if (p.P < 1) { why = "P must be >= 1"; return RBE_ERR_ARG; }
     if (p.n_max < 0) { why = "n_max must be >= 0"; return RBE_ERR_ARG; }
     if (p.lj_eps != 0.0) {
@@ -661,7 +661,9 @@ rbe_status create_common(const rbe_params* ps, const int32_t* ns, int nsys, bool
             return fail(nullptr, RBE_ERR_ARG, "all systems of a handle must use the same sampler");
         }
         sh.S = sh.H * sh.H * sh.H - 1.0;
-        sh.ncd = std::min(256, (int)std::floor(sh.p.box / sh.p.r_c));
+        // cells of side >= r_c, at least 3 per edge; else one cell (all pairs)
+        sh.ncd = sh.p.box / sh.p.r_c >= 3.0 ? std::min(256, (int)std::floor(sh.p.box / sh.p.r_c))
+                                            : 1;
         sh.off_p = off_p;
         sh.off_c = off_c;
         sh.off_k = off_k;

@@ -5,7 +5,8 @@
 //
 // Cells have side >= r_c and there are at least 3 per edge, so every pair
 // within r_c is met exactly once, as the minimum image, among the 27 cells
-// around a particle's own.  Mixed path: one block per segment of x-adjacent
+// around a particle's own.  With r_c > L/3 (up to L/2) the box is one cell and
+// every particle meets every other once, again as the minimum image.  Mixed path: one block per segment of x-adjacent
 // cells with the neighbourhood staged in shared memory and R = 1, 3 or 9
 // threads per particle, each scanning 9/R neighbour rows (tuning choices).
 // FP64 path: G threads per particle reading the
@@ -58,7 +59,9 @@ __device__ __forceinline__ int wrapc(int c, int n) { return c < 0 ? c + n : (c >
 // particles unless it wraps around the box edge; then it is two ranges.
 __device__ __forceinline__ void row_ranges(const int* __restrict__ cs, int base, int cx, int ncd,
                                            int& s0, int& e0, int& s1, int& e1) {
-    if (cx > 0 && cx < ncd - 1) {
+    if (ncd < 3) {                                  // one cell per edge: the whole row once
+        s0 = __ldg(cs + base); e0 = __ldg(cs + base + ncd); s1 = 0; e1 = 0;
+    } else if (cx > 0 && cx < ncd - 1) {
         s0 = __ldg(cs + base + cx - 1); e0 = __ldg(cs + base + cx + 2); s1 = 0; e1 = 0;
     } else if (cx == 0) {
         s0 = __ldg(cs + base); e0 = __ldg(cs + base + 2);
@@ -407,8 +410,9 @@ k_real_seg(const __grid_constant__ RealArgs a) {
                                          (ry == 0 ? fyl2 : (ry == 2 ? fyh2 : 0.f)) -
                                          (rz == 0 ? fzl2 : (rz == 2 ? fzh2 : 0.f));
                     if (reach2 <= 0.f) continue;          // the whole row is beyond the cutoff
+                    if (ncd == 1 && r != 4) continue;     // one cell per edge: own cell once
                     const int* bb = s_b + r * bstride + u;
-                    int kb = bb[0], ke = bb[3];
+                    int kb = ncd == 1 ? bb[1] : bb[0], ke = ncd == 1 ? bb[2] : bb[3];
                     int w = 0x7FFFFFFF;                   // no x limit below 5 cells per edge
                     if (prune) {
                         w = (int)(sqrtf(reach2) * invLu) + 8;
@@ -450,9 +454,10 @@ k_real_seg(const __grid_constant__ RealArgs a) {
                 // candidates straight from the cell-sorted records
                 for (int jr = 0; jr < RPL; ++jr) {
                     const int r = row_of<R>(l, jr);
+                    if (ncd == 1 && r != 4) continue;     // one cell per edge: own cell once
                     const int zz = wrapc(cz + r / 3 - 1, ncd), yy = wrapc(cy + r % 3 - 1, ncd);
                     const int row = S.off_c + (zz * ncd + yy) * ncd;
-                    for (int d = -1; d <= 1; ++d) {
+                    for (int d = (ncd == 1 ? 0 : -1); d <= (ncd == 1 ? 0 : 1); ++d) {
                         const int xn = wrapc(cxi + d, ncd);
                         const int cb = __ldg(a.cell_start + row + xn);
                         const int ce = __ldg(a.cell_start + row + xn + 1);
@@ -549,9 +554,10 @@ k_real_f64(const __grid_constant__ RealArgs a) {
         const double rc2 = do_real ? S.r_c * S.r_c : 0.0;
         const double lj_rc2 = do_lj ? S.lj_rcut2 : 0.0;
         const double two_sa_spi = 2.0 * S.sqrt_alpha / sqrt(M_PI);
-        for (int dz = -1; dz <= 1; ++dz) {
+        const int dlo = ncd < 3 ? 0 : -1, dhi = ncd < 3 ? 0 : 1;   // one cell: all pairs once
+        for (int dz = dlo; dz <= dhi; ++dz) {
             const int zz = wrapc(cz + dz, ncd);
-            for (int dy = -1; dy <= 1; ++dy) {
+            for (int dy = dlo; dy <= dhi; ++dy) {
                 const int yy = wrapc(cy + dy, ncd);
                 int s0, e0, s1, e1;
                 row_ranges(a.cell_start, S.off_c + (zz * ncd + yy) * ncd, cx, ncd, s0, e0, s1, e1);

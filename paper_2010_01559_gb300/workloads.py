@@ -223,3 +223,18 @@ def config_large(n: int = 1 << 20, density: float = 0.064, alpha: float = 0.3,
     """1:1 electrolyte, N=2^20 by default, density 0.064, alpha=0.3, r_c=5, P=500."""
     return electrolyte_1to1(n, density, alpha, r_c, P, seed=seed,
                             name=f"electrolyte_1to1_N{n}_rho0.064_P{P}")
+
+
+def config_electrolyte_dh(n: int = 300, density: float = 0.3, P: int = 10, seed: int = 6,
+                          andersen_nu: float = 3.0) -> Workload:
+    """The paper's charge-correlation electrolyte (Sec. 4.1): monovalent ions of
+    diameter 0.2, shifted LJ with sigma = 0.2, epsilon = 1, R_c = 4 (r_off = 0),
+    T = 1, prefactor 1 (epsilon_r = 1/(4 pi)), N / L^3 = 0.3 (L = 10 at N = 300),
+    alpha = 0.55, r_c = 4, batch p, Andersen thermostat nu = 3, dt = 0.002;
+    ions placed uniformly at least 0.25 apart."""
+    L = (n / density) ** (1.0 / 3.0)
+    p = SystemParams(box=L, alpha=0.55, r_c=min(4.0, L / 2), P=P, seed=seed, lj_eps=1.0,
+                     lj_sigma=0.2, lj_rcut=min(4.0, L / 2), dt=0.002, thermostat=1,
+                     andersen_nu=andersen_nu)
+    return electrolyte(f"electrolyte_dh_N{n}_P{P}", n // 2, n - n // 2, 1.0, -1.0, p,
+                       min_sep=0.25)

@@ -55,7 +55,7 @@ def _create(lib, **kw):
 @pytest.mark.parametrize("kw,needle", [
     (dict(box=0.0), "box"),
     (dict(alpha=-1.0), "alpha"),
-    (dict(r_c=9.0), "L/3"),
+    (dict(r_c=13.0), "L/2"),
     (dict(P=0), "P must"),
     (dict(n_max=-1), "n_max"),
     (dict(lj_rcut=6.0), "lj_rcut"),
