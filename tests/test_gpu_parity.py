@@ -113,6 +113,26 @@ def test_fp64_path_matches_oracle_per_part(rbe, c1):
     assert rel_rms(phi.cpu().numpy(), ref["phi"]) <= TOL_F64
 
 
+def test_one_cell_box_all_pairs_match_oracle(rbe):
+    """r_c > L/3 (the paper's electrolyte: r_c = 4, L = 10): the box is one cell
+    and every pair is met once as the minimum image, on both paths."""
+    wl = workloads.config_electrolyte_dh()
+    assert wl.params.box / wl.params.r_c < 3
+    h = _handle(rbe, wl)
+    step = 2
+    ref = oracle_eval(wl, step, want_phi=True)
+    F64, E64, phi64 = h.forces_f64(_dev(wl, "float64"), step, phi=True)
+    assert rel_rms(F64[:, :3].cpu().numpy(), ref["F"]) <= TOL_F64
+    assert energy_rel(E64.cpu().numpy()[0], ref["E"]) <= TOL_F64
+    assert rel_rms(phi64.cpu().numpy(), ref["phi"]) <= TOL_F64
+    for R in (1, 3, 9):
+        h.set_tuning(0, 0, R, 0)
+        F, E, phi = h.forces(_dev(wl), step, phi=True)
+        assert rel_rms(F[:, :3].cpu().numpy(), ref["F"]) <= TOL_MIXED, R
+        assert energy_rel(E.cpu().numpy()[0], ref["E"]) <= TOL_E_MIXED, R
+        assert rel_rms(phi.cpu().numpy(), ref["phi"]) <= TOL_MIXED, R
+
+
 # ------------------------------------------------------------------ mixed path
 @pytest.mark.parametrize("cfg", ["c1", "c2"])
 def test_mixed_path_matches_oracle_per_part(rbe, cfg, request):
