@@ -115,6 +115,10 @@ def _load():
                                                ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_int, _D]
         lib.orc_true_energy_virial.restype = None
+        lib.orc_nose_hoover_step.argtypes = [ctypes.c_int, _D, _D, _D, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, _D]
+        lib.orc_nose_hoover_step.restype = None
         _lib = lib
         return lib
 
@@ -312,6 +316,25 @@ def andersen_step(pos, vel, F, L, nu, kT, dt, mass, seed, stream, step):
     _load().orc_andersen_step(len(pos), _dp(pos), _dp(vel), _dp(F), L, nu, kT, dt, mass,
                               seed, stream, step, hit.ctypes.data_as(_INT))
     return pos, vel, hit.astype(bool)
+
+
+class NoseHoover:
+    """Nose-Hoover thermostat state (xi, previous kinetic sum, first-step flag)
+    and its leapfrog step (see orc_nose_hoover_step); tau = sqrt(Q / (3 N kT))."""
+
+    def __init__(self, tau):
+        self.tau = tau
+        self.state = np.array([0.0, 0.0, 1.0])
+
+    def step(self, pos, vel, F, L, kT, dt, mass):
+        pos = _f64(pos, (-1, 3)).copy(); vel = _f64(vel, (-1, 3)).copy(); F = _f64(F, (-1, 3))
+        _load().orc_nose_hoover_step(len(pos), _dp(pos), _dp(vel), _dp(F), L, self.tau, kT, dt,
+                                     mass, _dp(self.state))
+        return pos, vel
+
+    @property
+    def xi(self):
+        return float(self.state[0])
 
 
 # ---------------------------------------------------------------- observables

@@ -703,3 +703,37 @@ void orc_true_energy_virial(int N, const double *pos, const double *q, double L,
     out[6] = wl;
     out[7] = 3.0 * ebg;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Nose-Hoover thermostat (Sec. 3.3: dr/dt = p/m, dp/dt = F - xi p,           */
+/* dxi/dt = (sum |p|^2/m - 3 N kT) / Q), discretised as a leapfrog in which  */
+/* xi advances from the kinetic sum of the previous step's half-step         */
+/* velocities and the friction enters symmetrically:                         */
+/*   xi <- xi + (dt/Q) (K2 - 3 N kT)          (skipped on the first step)    */
+/*   v  <- [v (1 - xi dt/2) + (dt/m) F] / (1 + xi dt/2);  r <- wrap(r + dt v) */
+/*   K2 <- sum_i m |v_i|^2                                                    */
+/* with Q = 3 N kT tau^2.  state[0] = xi, state[1] = K2, state[2] = 1 until  */
+/* the first step has run (then 0).                                          */
+/* ------------------------------------------------------------------------- */
+void orc_nose_hoover_step(int N, double *pos, double *vel, const double *F, double L,
+                          double tau, double kT, double dt, double mass, double *state)
+{
+    const double Q = 3.0 * (double)N * kT * tau * tau;
+    if (state[2] == 0.0)
+        state[0] += dt / Q * (state[1] - 3.0 * (double)N * kT);
+    state[2] = 0.0;
+    const double xi = state[0];
+    const double a = 1.0 - 0.5 * xi * dt, b = 1.0 / (1.0 + 0.5 * xi * dt);
+    double k2 = 0.0;
+    for (int i = 0; i < N; ++i) {
+        for (int c = 0; c < 3; ++c) {
+            double v = (vel[3 * i + c] * a + (dt / mass) * F[3 * i + c]) * b;
+            double r = pos[3 * i + c] + dt * v;
+            r -= L * floor(r / L);
+            vel[3 * i + c] = v;
+            pos[3 * i + c] = r;
+            k2 += mass * v * v;
+        }
+    }
+    state[1] = k2;
+}

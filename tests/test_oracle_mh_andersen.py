@@ -144,3 +144,50 @@ def test_andersen_collision_rate_and_velocity_law():
     vv = v[hit].ravel()
     assert abs(vv.mean()) < 5 * math.sqrt(kT / len(vv))
     assert abs(vv.var() / kT - 1) < 5 * math.sqrt(2.0 / len(vv))
+
+
+# ------------------------------------------------------------------ Nose-Hoover
+def _nh_run(nsteps, dt, tau, kT=1.0, N=200, w=1.0, seed=0):
+    """Independent 3-D harmonic oscillators (F = -w^2 (r - r0)) under the
+    oracle's Nose-Hoover step.  Returns the kinetic temperatures of the
+    half-step velocities and the extended energy H' = K + U + Q xi^2/2 +
+    3 N kT eta (eta = integral of xi) at integer times: U at the positions the
+    step starts from, K from the mean of the two half-step velocities around
+    them, eta by the trapezoid rule."""
+    rng = np.random.default_rng(seed)
+    L = 1e4
+    r0 = rng.uniform(100, L - 100, (N, 3))
+    pos = r0 + rng.normal(scale=0.5, size=(N, 3))
+    vel = rng.normal(scale=0.3, size=(N, 3))          # starts far colder than kT
+    nh = oracle.NoseHoover(tau)
+    Q = 3 * N * kT * tau ** 2
+    T, H = [], []
+    eta, xi_prev = 0.0, 0.0
+    for n in range(nsteps):
+        F = -w ** 2 * (pos - r0)
+        U = 0.5 * w ** 2 * float(((pos - r0) ** 2).sum())
+        pos, vnew = nh.step(pos, vel, F, L, kT, dt, 1.0)
+        eta += 0.5 * dt * (xi_prev + nh.xi) if n else 0.0
+        xi_prev = nh.xi
+        K = 0.5 * float((((vel + vnew) / 2) ** 2).sum())
+        vel = vnew
+        T.append(float((vel ** 2).sum()) / (3 * N))
+        if n:
+            H.append(K + U + 0.5 * Q * nh.xi ** 2 + 3 * N * kT * eta)
+    return np.array(T), np.array(H)
+
+
+def test_nose_hoover_drives_temperature_to_kT():
+    T, _ = _nh_run(40000, 0.01, tau=0.5)
+    assert T[0] < 0.2
+    assert abs(T[20000:].mean() - 1.0) < 0.03
+
+
+def test_nose_hoover_extended_energy_conserved():
+    # the Nose-Hoover flow conserves H'; the leapfrog keeps it to O(dt^2) with
+    # no drift, which a wrong sign of the friction or of the xi equation breaks
+    _, H1 = _nh_run(10000, 0.02, tau=0.5)
+    _, H2 = _nh_run(20000, 0.01, tau=0.5)
+    d1 = np.abs(H1 - H1[0]).max() / abs(H1[0])
+    d2 = np.abs(H2 - H2[0]).max() / abs(H2[0])
+    assert d1 < 0.01 and d2 < d1 / 3             # second order: halving dt quarters it
