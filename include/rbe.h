@@ -79,13 +79,21 @@ enum { RBE_SAMPLER_EXACT = 0, RBE_SAMPLER_MH = 1 };
  * kick, exact Ornstein-Uhlenbeck with friction gamma, drift (Sec. 3.3).
  * RBE_THERMO_ANDERSEN: the loop step of Algorithm 1 as printed -- leapfrog
  * (kick, drift) and then, with probability andersen_nu * dt per particle, a
- * new velocity drawn from N(0, kT/m). */
-enum { RBE_THERMO_LANGEVIN = 0, RBE_THERMO_ANDERSEN = 1 };
+ * new velocity drawn from N(0, kT/m).
+ * RBE_THERMO_NOSE_HOOVER: the deterministic thermostat whose equations of
+ * motion Sec. 3.3 states (dr/dt = v, m dv/dt = F - xi m v, dxi/dt =
+ * (sum m |v|^2 - 3 N kT) / Q) and leaves for later work; Q = 3 N kT nh_tau^2.
+ * Discretised as a leapfrog: xi advances from the previous step's sum m|v|^2
+ * (not on the first step after creation or rbe_nose_hoover_xi(..., set=1)),
+ * then v <- [v (1 - xi dt/2) + (dt/m) F] / (1 + xi dt/2) and the drift.  The
+ * kinetic sum is accumulated in 64-bit fixed point (m|v|^2 / kT in units of
+ * 2^-32), so runs are deterministic. */
+enum { RBE_THERMO_LANGEVIN = 0, RBE_THERMO_ANDERSEN = 1, RBE_THERMO_NOSE_HOOVER = 2 };
 
 /* Parts selectable in rbe_forces_ex. */
 enum { RBE_PART_FOURIER = 1, RBE_PART_REAL = 2, RBE_PART_LJ = 4, RBE_PART_ALL = 7 };
 
-/* Parameters of one periodic system (cubic box, reduced units).  128 bytes. */
+/* Parameters of one periodic system (cubic box, reduced units).  136 bytes. */
 typedef struct {
     double box;               /* L > 0: edge of the cubic periodic box (Sec. 2)          */
     double alpha;             /* Ewald splitting parameter, erfc(sqrt(alpha) r) (Sec. 2) */
@@ -106,7 +114,8 @@ typedef struct {
     int32_t precision;        /* RBE_MIXED (default path of rbe_step) or RBE_FP64         */
     double andersen_nu;       /* Andersen collision frequency nu, 0 <= nu dt <= 1          */
     int32_t sampler;          /* RBE_SAMPLER_EXACT (0) or RBE_SAMPLER_MH; one per handle  */
-    int32_t thermostat;       /* RBE_THERMO_LANGEVIN (0) or RBE_THERMO_ANDERSEN          */
+    int32_t thermostat;       /* RBE_THERMO_LANGEVIN (0), _ANDERSEN or _NOSE_HOOVER       */
+    double nh_tau;            /* Nose-Hoover time constant, Q = 3 N kT nh_tau^2 (> 0 there) */
 } rbe_params;
 
 /* Derived constants of system `sys` of a handle (for inspection and tests). */
@@ -197,6 +206,14 @@ rbe_status rbe_step(rbe_handle h, int32_t n, float *pos_q, float *vel, int32_t n
 /* FP64 MD steps: pos_q, vel double4[n]. */
 rbe_status rbe_step_f64(rbe_handle h, int32_t n, double *pos_q, double *vel, int32_t nsteps,
                         uint64_t *step_dev);
+
+/* Nose-Hoover friction xi of every system (double[n_systems], host).
+ * set = 0: read the current values into xi (synchronises h's stream).
+ * set = 1: replace them with xi (e.g. to resume a run); the next step then
+ * uses them as given and advances them from its own kinetic sum afterwards.
+ * Systems with another thermostat carry a xi that no step uses.  Errors:
+ * RBE_ERR_ARG (null handle or xi), RBE_ERR_CUDA. */
+rbe_status rbe_nose_hoover_xi(rbe_handle h, double *xi, int32_t set);
 
 /* Enable (1) or disable (0) CUDA-graph replay of rbe_step.  The first
  * rbe_step call after enabling captures one step per distinct argument set. */

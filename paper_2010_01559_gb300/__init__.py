@@ -19,7 +19,7 @@ import ctypes
 from . import capi
 from .capi import (RBE_FP64, RBE_MIXED, RBE_PART_ALL, RBE_PART_FOURIER, RBE_PART_LJ,
                    RBE_PART_REAL, RBE_SAMPLER_EXACT, RBE_SAMPLER_MH, RBE_THERMO_ANDERSEN,
-                   RBE_THERMO_LANGEVIN, RBEError)
+                   RBE_THERMO_LANGEVIN, RBE_THERMO_NOSE_HOOVER, RBEError)
 
 __all__ = ["capi", "RBE", "RBEBatch", "RBEEnergy", "params_from", "RBEError",
            "RBE_FP64", "RBE_MIXED", "RBE_PART_ALL", "RBE_PART_FOURIER", "RBE_PART_LJ",
@@ -39,7 +39,8 @@ def params_from(sp, n_max=0, precision=RBE_MIXED) -> capi.rbe_params:
                             gamma=sp.gamma, kT=sp.kT, dt=sp.dt, mass=sp.mass, n_max=n_max,
                             precision=precision, sampler=getattr(sp, "sampler", 0),
                             thermostat=getattr(sp, "thermostat", 0),
-                            andersen_nu=getattr(sp, "andersen_nu", 0.0))
+                            andersen_nu=getattr(sp, "andersen_nu", 0.0),
+                            nh_tau=getattr(sp, "nh_tau", 0.0))
 
 
 def _ptr(t):
@@ -159,6 +160,14 @@ class _HandleBase:
         c = ctypes.c_int64()
         capi.check(self.lib.rbe_launch_count(self._h, ctypes.byref(c)), self._h)
         return c.value
+
+    def nose_hoover_xi(self, xi=None):
+        """The Nose-Hoover friction of every system (``rbe_nose_hoover_xi``):
+        returns them as a list, or with ``xi`` given sets them (a resume)."""
+        n = self._nsys()
+        buf = (ctypes.c_double * n)(*([0.0] * n if xi is None else [float(v) for v in xi]))
+        capi.check(self.lib.rbe_nose_hoover_xi(self._h, buf, 0 if xi is None else 1), self._h)
+        return list(buf)
 
     def set_graph(self, on=True):
         capi.check(self.lib.rbe_set_graph(self._h, 1 if on else 0), self._h)

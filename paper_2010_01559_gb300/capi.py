@@ -19,7 +19,7 @@ RBE_ERR_SAMPLER, RBE_ERR_TIMEOUT, RBE_ERR_NONFINITE, RBE_ERR_STATE = 4, 5, 6, 7
 RBE_FP64, RBE_MIXED = 0, 1
 RBE_PART_FOURIER, RBE_PART_REAL, RBE_PART_LJ, RBE_PART_ALL = 1, 2, 4, 7
 RBE_SAMPLER_EXACT, RBE_SAMPLER_MH = 0, 1
-RBE_THERMO_LANGEVIN, RBE_THERMO_ANDERSEN = 0, 1
+RBE_THERMO_LANGEVIN, RBE_THERMO_ANDERSEN, RBE_THERMO_NOSE_HOOVER = 0, 1, 2
 
 STATUS_NAMES = {0: "RBE_OK", 1: "RBE_ERR_ARG", 2: "RBE_ERR_CUDA", 3: "RBE_ERR_OOM",
                 4: "RBE_ERR_SAMPLER", 5: "RBE_ERR_TIMEOUT", 6: "RBE_ERR_NONFINITE",
@@ -34,7 +34,7 @@ class rbe_params(ctypes.Structure):
                 ("mass", ctypes.c_double), ("seed", ctypes.c_uint64), ("stream", ctypes.c_uint32),
                 ("P", ctypes.c_int32), ("n_max", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("andersen_nu", ctypes.c_double), ("sampler", ctypes.c_int32),
-                ("thermostat", ctypes.c_int32)]
+                ("thermostat", ctypes.c_int32), ("nh_tau", ctypes.c_double)]
 
 
 class rbe_tuning(ctypes.Structure):
@@ -54,7 +54,7 @@ class rbe_info(ctypes.Structure):
                 ("first_k", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
-assert ctypes.sizeof(rbe_params) == 128
+assert ctypes.sizeof(rbe_params) == 136
 
 _H = ctypes.c_void_p
 _P = ctypes.c_void_p
@@ -88,6 +88,7 @@ _SIGS = {
     "rbe_fourier_forces_noalloc": ([ctypes.POINTER(rbe_params), ctypes.c_int32, _P,
                                     ctypes.c_uint64, _P, _P, _P], ctypes.c_int),
     "rbe_probe_peaks": ([ctypes.POINTER(rbe_peaks)], ctypes.c_int),
+    "rbe_nose_hoover_xi": ([_H, _P, ctypes.c_int32], ctypes.c_int),
     "rbe_observables": ([_H, ctypes.c_int32, _P, _P, ctypes.c_int32, _P], ctypes.c_int),
 }
 
@@ -137,12 +138,12 @@ def check(status: int, handle=None) -> None:
 def make_params(box, alpha, r_c, P, seed=0, stream=0, coulomb_prefactor=1.0, lj_eps=0.0,
                 lj_sigma=1.0, lj_rcut=0.0, gamma=1.0, kT=1.0, dt=1e-3, mass=1.0, n_max=0,
                 precision=RBE_MIXED, sampler=RBE_SAMPLER_EXACT, thermostat=RBE_THERMO_LANGEVIN,
-                andersen_nu=0.0) -> rbe_params:
+                andersen_nu=0.0, nh_tau=0.0) -> rbe_params:
     return rbe_params(box=box, alpha=alpha, r_c=r_c, coulomb_prefactor=coulomb_prefactor,
                       lj_eps=lj_eps, lj_sigma=lj_sigma, lj_rcut=lj_rcut, gamma=gamma, kT=kT,
                       dt=dt, mass=mass, seed=seed, stream=stream, P=P, n_max=n_max,
                       precision=precision, andersen_nu=andersen_nu, sampler=sampler,
-                      thermostat=thermostat)
+                      thermostat=thermostat, nh_tau=nh_tau)
 
 
 def __getattr__(name):

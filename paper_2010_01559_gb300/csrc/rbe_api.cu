@@ -200,6 +200,7 @@ struct rbe_ctx {
     double* d_mh_rho = nullptr;               // MH acceptance ratios, all systems
     int4* d_mh_state = nullptr;               // per system: current (m_x, m_y, m_z)
     uint64_t* d_mh_pos = nullptr;             // per system: chain iterations done
+    NhState* d_nh = nullptr;                  // per system: Nose-Hoover state
     unsigned long long* d_qsum_fx = nullptr;  // sum q per system (fixed point)
     double2* d_blk_e = nullptr;
     double2* d_blk_w = nullptr;               // per real-space block (W_coul, W_lj)
@@ -254,7 +255,9 @@ rbe_status validate_params(const rbe_params& p, std::string& why) {
     }
     if (!(p.mass > 0.0)) { why = "mass must be > 0"; return RBE_ERR_ARG; }
     if (p.sampler != RBE_SAMPLER_EXACT && p.sampler != RBE_SAMPLER_MH) { why = "sampler must be RBE_SAMPLER_EXACT or RBE_SAMPLER_MH"; return RBE_ERR_ARG; }
-    if (p.thermostat != RBE_THERMO_LANGEVIN && p.thermostat != RBE_THERMO_ANDERSEN) { why = "thermostat must be RBE_THERMO_LANGEVIN or RBE_THERMO_ANDERSEN"; return RBE_ERR_ARG; }
+    if (p.thermostat != RBE_THERMO_LANGEVIN && p.thermostat != RBE_THERMO_ANDERSEN &&
+        p.thermostat != RBE_THERMO_NOSE_HOOVER) { why = "thermostat must be RBE_THERMO_LANGEVIN, RBE_THERMO_ANDERSEN or RBE_THERMO_NOSE_HOOVER"; return RBE_ERR_ARG; }
+    if (p.thermostat == RBE_THERMO_NOSE_HOOVER && (!(p.nh_tau > 0.0) || !std::isfinite(p.nh_tau) || !(p.kT > 0.0))) { why = "Nose-Hoover needs nh_tau > 0 and kT > 0"; return RBE_ERR_ARG; }
     if (!(p.andersen_nu >= 0.0) || !(p.andersen_nu * p.dt <= 1.0)) { why = "andersen_nu must satisfy 0 <= nu dt <= 1"; return RBE_ERR_ARG; }
     if (p.gamma < 0.0 || p.kT < 0.0) { why = "gamma and kT must be >= 0"; return RBE_ERR_ARG; }
     const int M = axis_M(p.alpha, p.box);
@@ -344,6 +347,9 @@ void fill_sysdev(const SysHost& s, SysDev& d) {
     d.vsd = std::sqrt(p.kT / p.mass);
     d.f_vsd = (float)d.vsd;
     d.f_inv_Lu = (float)(4294967296.0 / L);
+    d.nh_rate = p.thermostat == RBE_THERMO_NOSE_HOOVER
+                    ? p.dt / (3.0 * std::max(1, s.n) * p.nh_tau * p.nh_tau) : 0.0;
+    d.nh_k2scale = p.kT > 0.0 ? p.mass / p.kT * 4294967296.0 : 0.0;
     d.corner_q = (uint32_t)(4294967296ull / (unsigned long long)std::max(1, s.ncd));
     d.corner_r = (uint32_t)(4294967296ull - (unsigned long long)d.corner_q * std::max(1, s.ncd));
 }
@@ -553,6 +559,7 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_ALLOC(h->d_mh_rho, h->ttot);
     RBE_ALLOC(h->d_mh_state, h->nsys);
     RBE_ALLOC(h->d_mh_pos, h->nsys);
+    RBE_ALLOC(h->d_nh, h->nsys);
     RBE_ALLOC(h->d_kab, h->ktot);
     RBE_ALLOC(h->d_qsum_fx, h->nsys);
     RBE_ALLOC(h->d_blk_e, std::max<long long>(rb, (long long)kSegChunks * (h->ncell + 1)));
@@ -595,6 +602,15 @@ rbe_status allocate(rbe_ctx* h) {
                            cudaMemcpyHostToDevice));
     RBE_CUDA(h, cudaMemset(h->d_mh_state, 0, sizeof(int4) * h->nsys));   // chains start at m = 0
     RBE_CUDA(h, cudaMemset(h->d_mh_pos, 0, sizeof(uint64_t) * h->nsys));
+    {
+        std::vector<NhState> nh(h->nsys);             // xi = 0, kept on the first step
+        for (auto& v : nh) {
+            v = NhState{};
+            v.first = 1;
+        }
+        RBE_CUDA(h, cudaMemcpy(h->d_nh, nh.data(), sizeof(NhState) * h->nsys,
+                               cudaMemcpyHostToDevice));
+    }
     RBE_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     RBE_CUDA(h, cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking));
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
@@ -612,7 +628,7 @@ void release(rbe_ctx* h) {
                     h->d_table, h->d_fx, h->d_spos, h->d_fx64, h->d_spos64, h->d_cid, h->d_rank,
                     h->d_perm, h->d_perm_tmp, h->d_fs, h->d_fs64, h->d_cell_cnt,
                     h->d_cell_start, h->d_ksamp, h->d_rho_fx, h->d_kcnt, h->d_kab,
-                    h->d_kcoef, h->d_mh_tq, h->d_mh_rho, h->d_mh_state, h->d_mh_pos,
+                    h->d_kcoef, h->d_mh_tq, h->d_mh_rho, h->d_mh_state, h->d_mh_pos, h->d_nh,
                     h->d_qsum_fx, h->d_blk_e, h->d_blk_w, h->d_obs_m, h->d_obs_rho, h->d_obs_w,
                     h->d_obs_out, h->d_obs_part, h->d_blk_q, h->d_cur_step, h->d_stage_step,
                     h->d_err, h->d_stage_pos, h->d_stage_vel, h->d_stage_F, h->d_stage_E};
@@ -827,6 +843,7 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     pa.ksamp = h->d_ksamp;
     pa.kcoef = h->d_kcoef;
     pa.err = h->d_err;
+    pa.nh = (a.md_pos || a.md_pos64) ? h->d_nh : nullptr;
     if (want_q)
         cudaMemsetAsync(h->d_qsum_fx, 0, sizeof(unsigned long long) * h->nsys, st);
     run(RBE_K_PREP, st, [&] {
@@ -864,6 +881,7 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     r.phi_out64 = a.phi64;
     r.md_pos64 = a.md_pos64;
     r.md_vel64 = a.md_vel64;
+    r.nh = pa.nh;
     r.blk_e = a.E ? h->d_blk_e : nullptr;
     r.blk_w = (a.E && a.W) ? h->d_blk_w : nullptr;
     run(RBE_K_REAL, st, [&] {
@@ -1179,6 +1197,28 @@ rbe_status rbe_step(rbe_handle h, int32_t n, float* pos_q, float* vel, int32_t n
 rbe_status rbe_step_f64(rbe_handle h, int32_t n, double* pos_q, double* vel, int32_t nsteps,
                         uint64_t* step_dev) {
     return step_impl(h, n, RBE_FP64, pos_q, vel, nsteps, step_dev);
+}
+
+rbe_status rbe_nose_hoover_xi(rbe_handle h, double* xi, int32_t set) {
+    if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
+    if (!xi) return fail(h, RBE_ERR_ARG, "xi is NULL");
+    std::vector<NhState> nh(h->nsys);
+    if (set) {
+        for (int sy = 0; sy < h->nsys; ++sy) {
+            nh[sy] = NhState{};
+            nh[sy].xi = xi[sy];
+            nh[sy].first = 1;
+        }
+        RBE_CUDA(h, cudaMemcpyAsync(h->d_nh, nh.data(), sizeof(NhState) * h->nsys,
+                                    cudaMemcpyHostToDevice, h->stream));
+        RBE_CUDA(h, cudaStreamSynchronize(h->stream));
+    } else {
+        RBE_CUDA(h, cudaMemcpyAsync(nh.data(), h->d_nh, sizeof(NhState) * h->nsys,
+                                    cudaMemcpyDeviceToHost, h->stream));
+        RBE_CUDA(h, cudaStreamSynchronize(h->stream));
+        for (int sy = 0; sy < h->nsys; ++sy) xi[sy] = nh[sy].xi;
+    }
+    return finish(h, "rbe_nose_hoover_xi");
 }
 
 rbe_status rbe_set_graph(rbe_handle h, int32_t use_graph) {

@@ -62,6 +62,31 @@ __device__ __forceinline__ void latch_step(const uint64_t* step_dev, uint64_t st
     if (blockIdx.x == 0 && threadIdx.x == 0) *cur_step = step_dev ? *step_dev : step_arg;
 }
 
+// Nose-Hoover (the equations of motion of Sec. 3.3): thread s of block 0
+// advances the friction of system s from the kinetic sum of the previous step,
+// xi += dt / Q (sum m|v|^2 - 3 n kT) with Q = 3 n kT tau^2 (not on the first
+// step after a reset), and sets this step's velocity coefficients.  The
+// real-space kernel of this step, launched after this one, reads them and
+// accumulates the next sum.
+template <bool ONE>
+__device__ __forceinline__ void nh_advance(const Work& w, const PrepArgs& pa) {
+    if (!pa.nh || blockIdx.x != 0) return;
+    for (int s = threadIdx.x; s < pa.nsys; s += blockDim.x) {
+        const SysDev& S = sys_of<ONE>(w, s);
+        if (S.thermostat != RBE_THERMO_NOSE_HOOVER) continue;
+        NhState st = pa.nh[s];
+        if (!st.first) st.xi += S.nh_rate * ((double)st.k2 * 0x1p-32 - 3.0 * (double)S.n);
+        st.first = 0;
+        st.k2 = 0ull;
+        const double hx = 0.5 * st.xi * S.dt;
+        st.a = 1.0 - hx;
+        st.b = 1.0 / (1.0 + hx);
+        st.f_va = (float)(st.a * st.b);
+        st.f_vf = (float)(S.dt_over_m * st.b);
+        pa.nh[s] = st;
+    }
+}
+
 // The k-batch of this step (Eq. probexpression): the blocks after the particle
 // blocks draw one sample per thread and its coefficient coef_scale / k^2 of
 // Eq. rbmapprox, for the structure-factor and force passes that follow.
@@ -211,6 +236,7 @@ k_prep_mixed(const __grid_constant__ Work w, const float4* __restrict__ pos_q,
         return;
     }
     latch_step(pa.step_dev, pa.step_arg, pa.cur_step);
+    nh_advance<ONE>(w, pa);
     clear_rho(pa.rho_fx, pa.nrho, pa.npblk);
     const Tile tl = tile_of<ONE>(w);
     const SysDev& S = sys_of<ONE>(w, tl.sys);
@@ -264,6 +290,7 @@ k_prep_f64(const __grid_constant__ Work w, const double4* __restrict__ pos_q,
         return;
     }
     latch_step(pa.step_dev, pa.step_arg, pa.cur_step);
+    nh_advance<ONE>(w, pa);
     clear_rho(pa.rho_fx, pa.nrho, pa.npblk);
     const Tile tl = tile_of<ONE>(w);
     const SysDev& S = sys_of<ONE>(w, tl.sys);

@@ -67,11 +67,25 @@ struct SysDev {
     float f_lj_sigma2, f_lj_eps, f_lj_shift;
     float f_c1, f_c2, f_dt, f_dt_over_m, f_invL;
     float f_inv_Lu;         // 2^32 / L: length to fixed-point units
-    int thermostat;         // RBE_THERMO_LANGEVIN or RBE_THERMO_ANDERSEN
+    int thermostat;         // RBE_THERMO_LANGEVIN, _ANDERSEN or _NOSE_HOOVER
     uint64_t andersen_thr;  // collision iff 32-bit Philox word < nu dt 2^32
     double vsd;             // sqrt(kT / m): Andersen velocity standard deviation
     float f_vsd;
     uint32_t corner_q, corner_r;   // 2^32 = corner_q * ncd + corner_r (cell corners)
+    double nh_rate;         // Nose-Hoover: dt / (3 n tau^2), xi += nh_rate (K2 / kT - 3 n)
+    double nh_k2scale;      // m / kT * 2^32: fixed-point units of the kinetic sum
+};
+
+// Nose-Hoover state of one system: the friction xi, the velocity update of
+// this step, v <- (v a + (dt/m) F) b with a = 1 - xi dt/2, b = 1 / (1 + xi dt/2)
+// (FP32: v <- va v + vf F), and the kinetic sum sum m|v|^2 / kT of the step in
+// 64-bit fixed point (2^-32), advanced by the prep kernel of the next step.
+struct NhState {
+    double xi, a, b;
+    float f_va, f_vf;
+    unsigned long long k2;
+    int first;              // 1: the next step keeps xi as it is
+    int pad;
 };
 
 // A tile of particles of one system: (system, first particle, count, aux).
@@ -217,6 +231,7 @@ struct PrepArgs {
     int4* ksamp;
     double* kcoef;           // coef_scale / k^2 per sample (Eq. rbmapprox)
     int* err;
+    NhState* nh;             // MD steps: Nose-Hoover state per system (null otherwise)
 };
 void launch_prep_mixed(cudaStream_t st, bool one, const Work& w, int nblk, const float4* pos_q,
                        uint4* fx, int* cid, int* rank, int* cell_cnt, const PrepArgs& pa);
@@ -297,6 +312,7 @@ struct RealArgs {
     double* phi_out64;
     double4* md_pos64;
     double4* md_vel64;
+    NhState* nh;             // MD steps: Nose-Hoover state per system
     double2* blk_e;          // per block (E_coul, E_lj), nullable
     double2* blk_w;          // per block (W_coul, W_lj): pair virials r.F, nullable
 };

@@ -170,6 +170,43 @@ __device__ __forceinline__ int row_of(int l, int j) {
     }
 }
 
+// Drift r += dt v and wrap into [0, L).
+__device__ __forceinline__ void drift_wrap(const SysDev& S, const float4& v, float4& rp) {
+    const float L = S.Lf, invL = S.f_invL, dt = S.f_dt;
+    rp.x = fmaf(dt, v.x, rp.x); rp.x -= L * floorf(rp.x * invL);
+    rp.y = fmaf(dt, v.y, rp.y); rp.y -= L * floorf(rp.y * invL);
+    rp.z = fmaf(dt, v.z, rp.z); rp.z -= L * floorf(rp.z * invL);
+    // a coordinate just below 0 can round up to exactly L: that is 0
+    if (rp.x >= L) rp.x = 0.f;
+    if (rp.y >= L) rp.y = 0.f;
+    if (rp.z >= L) rp.z = 0.f;
+}
+
+// Nose-Hoover leapfrog step for particle o: v <- va v + vf F (the friction
+// taken half before and half after the kick), drift, wrap.  Returns m|v|^2/kT
+// in 64-bit fixed point (2^-32) for the kinetic sum of the step.
+__device__ __forceinline__ unsigned long long nose_hoover_update(const RealArgs& a,
+                                                                 const SysDev& S, float va,
+                                                                 float vf, int o, float fx,
+                                                                 float fy, float fz) {
+    float4 v = a.md_vel[o];
+    float4 rp = a.md_pos[o];
+    v.x = fmaf(va, v.x, vf * fx);
+    v.y = fmaf(va, v.y, vf * fy);
+    v.z = fmaf(va, v.z, vf * fz);
+    drift_wrap(S, v, rp);
+    a.md_vel[o] = v;
+    a.md_pos[o] = rp;
+    const float v2 = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z));
+    return __double2ull_rn((double)v2 * S.nh_k2scale);
+}
+
+// Sum of a 64-bit value over the warp, added by lane 0 to *dst.
+__device__ __forceinline__ void warp_add_u64(unsigned long long v, unsigned long long* dst) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
+
 // Langevin step of Sec. 3.3 for particle o (caller index) with total force F:
 // kick, exact Ornstein-Uhlenbeck with Philox/Box-Muller normals, drift, wrap.
 __device__ __forceinline__ void langevin_update(const RealArgs& a, const SysDev& S, int o,
@@ -184,7 +221,7 @@ __device__ __forceinline__ void langevin_update(const RealArgs& a, const SysDev&
     const bool hit = andersen && (uint64_t)c.x < S.andersen_thr;
     float4 v = a.md_vel[o];
     float4 rp = a.md_pos[o];
-    const float dtm = S.f_dt_over_m, dt = S.f_dt;
+    const float dtm = S.f_dt_over_m;
     v.x = fmaf(dtm, fx, v.x);
     v.y = fmaf(dtm, fy, v.y);
     v.z = fmaf(dtm, fz, v.z);
@@ -209,14 +246,7 @@ __device__ __forceinline__ void langevin_update(const RealArgs& a, const SysDev&
         v.y = fmaf(c1, v.y, c2 * xi1);
         v.z = fmaf(c1, v.z, c2 * xi2);
     }
-    const float L = S.Lf, invL = S.f_invL;
-    rp.x = fmaf(dt, v.x, rp.x); rp.x -= L * floorf(rp.x * invL);
-    rp.y = fmaf(dt, v.y, rp.y); rp.y -= L * floorf(rp.y * invL);
-    rp.z = fmaf(dt, v.z, rp.z); rp.z -= L * floorf(rp.z * invL);
-    // a coordinate just below 0 can round up to exactly L: that is 0
-    if (rp.x >= L) rp.x = 0.f;
-    if (rp.y >= L) rp.y = 0.f;
-    if (rp.z >= L) rp.z = 0.f;
+    drift_wrap(S, v, rp);
     if (hit) {                                         // Andersen collision after the drift
         const float sd = S.f_vsd;
         v.x = sd * xi0; v.y = sd * xi1; v.z = sd * xi2;
@@ -295,6 +325,12 @@ k_real_seg(const __grid_constant__ RealArgs a) {
     const bool do_real = (a.parts & kPartReal) != 0;
     const bool do_lj = (a.parts & kPartLJ) != 0 && S.lj_eps != 0.0;
     const bool pairs = nown > 0 && (do_real || do_lj);
+    const bool nhm = a.md_pos && a.nh && S.thermostat == RBE_THERMO_NOSE_HOOVER;
+    float nh_va = 0.f, nh_vf = 0.f;
+    if (nhm) {
+        nh_va = a.nh[sys].f_va;
+        nh_vf = a.nh[sys].f_vf;
+    }
     const float Lu = S.L_over_2_32;
     for (int j = threadIdx.x; j <= nsc; j += blockDim.x) s_cx[j] = corner_of(x0 + j, S);
     if (pairs && threadIdx.x < 27) {
@@ -495,6 +531,7 @@ k_real_seg(const __grid_constant__ RealArgs a) {
         __syncthreads();
         // the rest runs one thread per particle: total force, outputs, Langevin
         const int np = min(kPass, nown - pass);
+        unsigned long long k2 = 0ull;
         if ((int)threadIdx.x < np) {
             const int i = own_s + pass + threadIdx.x;
             const int o = a.perm[i];
@@ -511,8 +548,10 @@ k_real_seg(const __grid_constant__ RealArgs a) {
             }
             if (a.F_out) a.F_out[o] = make_float4(fx, fy, fz, 0.f);
             if (want_phi) a.phi_out[o] = phi;
-            if (a.md_pos) langevin_update(a, S, o, fx, fy, fz);
+            if (nhm) k2 = nose_hoover_update(a, S, nh_va, nh_vf, o, fx, fy, fz);
+            else if (a.md_pos) langevin_update(a, S, o, fx, fy, fz);
         }
+        if (nhm) warp_add_u64(k2, &a.nh[sys].k2);
         __syncthreads();
     }
     if (want_e) {
@@ -621,7 +660,27 @@ k_real_f64(const __grid_constant__ RealArgs a) {
         }
         if (a.F_out64) a.F_out64[o] = make_double4(fx, fy, fz, 0.0);
         if (a.phi_out64) a.phi_out64[o] = phi;
-        if (a.md_pos64) {
+        if (a.md_pos64 && a.nh && S.thermostat == RBE_THERMO_NOSE_HOOVER) {
+            // Nose-Hoover leapfrog: v <- (v a + (dt/m) F) b, drift, wrap
+            const double na = a.nh[tl.sys].a, nb = a.nh[tl.sys].b;
+            const double F3[3] = {fx, fy, fz};
+            double4 v = a.md_vel64[o];
+            double4 rp = a.md_pos64[o];
+            double* vv[3] = {&v.x, &v.y, &v.z};
+            double* rr[3] = {&rp.x, &rp.y, &rp.z};
+            double v2 = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                const double vd = (*vv[d] * na + S.dt_over_m * F3[d]) * nb;
+                double rd = *rr[d] + S.dt * vd;
+                rd -= S.L * floor(rd / S.L);
+                *vv[d] = vd;
+                *rr[d] = rd;
+                v2 += vd * vd;
+            }
+            a.md_vel64[o] = v;
+            a.md_pos64[o] = rp;
+            atomicAdd(&a.nh[tl.sys].k2, __double2ull_rn(v2 * S.nh_k2scale));
+        } else if (a.md_pos64) {
             const uint64_t step = *a.cur_step;
             const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
             const uint32_t pid = (uint32_t)(o - S.off_p);

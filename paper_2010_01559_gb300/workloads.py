@@ -46,8 +46,10 @@ class SystemParams:
     dt: float = 1e-3
     mass: float = 1.0
     sampler: int = 0          # 0: exact i.i.d. inverse CDF, 1: the paper's MH chains
-    thermostat: int = 0       # 0: Langevin (kick / OU / drift), 1: leapfrog + Andersen
+    thermostat: int = 0       # 0: Langevin (kick / OU / drift), 1: leapfrog + Andersen,
+                              # 2: Nose-Hoover leapfrog
     andersen_nu: float = 0.0  # Andersen collision frequency
+    nh_tau: float = 0.0       # Nose-Hoover time constant (Q = 3 N kT tau^2)
 
 
 @dataclass
