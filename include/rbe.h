@@ -61,7 +61,11 @@ typedef enum {
     RBE_ERR_SAMPLER = 4,    /* a k-sample hit (0,0,0) on 32 attempts in a row           */
     RBE_ERR_TIMEOUT = 5,    /* reserved: a bounded device wait gave up                  */
     RBE_ERR_NONFINITE = 6,  /* reserved: non-finite input detected                      */
-    RBE_ERR_STATE = 7       /* call not valid for this handle (e.g. wrong n for a batch) */
+    RBE_ERR_STATE = 7,      /* call not valid for this handle (e.g. wrong n for a batch) */
+    RBE_ERR_LIST = 8        /* a particle had more neighbours within r_c + skin than the
+                               list holds (a much denser region than the mean density):
+                               the steps since the last rbe_sync missed pairs; run with
+                               skin < 0 (no list) or a smaller skin */
 } rbe_status;
 
 enum { RBE_FP64 = 0, RBE_MIXED = 1 };
@@ -93,7 +97,7 @@ enum { RBE_THERMO_LANGEVIN = 0, RBE_THERMO_ANDERSEN = 1, RBE_THERMO_NOSE_HOOVER 
 /* Parts selectable in rbe_forces_ex. */
 enum { RBE_PART_FOURIER = 1, RBE_PART_REAL = 2, RBE_PART_LJ = 4, RBE_PART_ALL = 7 };
 
-/* Parameters of one periodic system (cubic box, reduced units).  136 bytes. */
+/* Parameters of one periodic system (cubic box, reduced units).  144 bytes. */
 typedef struct {
     double box;               /* L > 0: edge of the cubic periodic box (Sec. 2)          */
     double alpha;             /* Ewald splitting parameter, erfc(sqrt(alpha) r) (Sec. 2) */
@@ -116,6 +120,11 @@ typedef struct {
     int32_t sampler;          /* RBE_SAMPLER_EXACT (0) or RBE_SAMPLER_MH; one per handle  */
     int32_t thermostat;       /* RBE_THERMO_LANGEVIN (0), _ANDERSEN or _NOSE_HOOVER       */
     double nh_tau;            /* Nose-Hoover time constant, Q = 3 N kT nh_tau^2 (> 0 there) */
+    double skin;              /* Verlet skin of rbe_step's neighbour list: 0 = automatic
+                                 (0.1 r_c), < 0 = no list (every step scans the cells);
+                                 at most L/3 - r_c (L/2 - r_c in the one-cell mode).  The
+                                 cells of every path of the handle then have side
+                                 >= r_c + skin                                          */
 } rbe_params;
 
 /* Derived constants of system `sys` of a handle (for inspection and tests). */
@@ -203,6 +212,29 @@ rbe_status rbe_forces_f64(rbe_handle h, int32_t n, const double *pos_q, uint64_t
 rbe_status rbe_step(rbe_handle h, int32_t n, float *pos_q, float *vel, int32_t nsteps,
                     uint64_t *step_dev);
 
+/* rbe_step that also writes each step's total force (float4[n], caller order,
+ * w = 0) to F_out (nullable); after the call F_out holds the last step's
+ * force, evaluated at the positions that step started from.
+ *
+ * Neighbour list (mixed steps, skin >= 0): the real-space pairs of a step come
+ * from a list of the pairs within r_c + skin built on the device whenever some
+ * particle has moved more than skin/2 (minimum image) since the last build --
+ * then every pair within r_c is still in the list, so the step's forces equal
+ * those of a full cell scan up to FP32 summation order.  Each step's first
+ * kernel tests the displacements of the positions it is given, so positions
+ * changed by the caller between calls are also caught; any other evaluation
+ * on the handle (forces, FP64 steps, observables, autotune) forces a rebuild
+ * at the next step.  A list overflow is latched and reported by rbe_sync as
+ * RBE_ERR_LIST. */
+rbe_status rbe_step_ex(rbe_handle h, int32_t n, float *pos_q, float *vel, int32_t nsteps,
+                       uint64_t *step_dev, float *F_out);
+
+/* Neighbour-list statistics since the handle was created (synchronises h's
+ * stream): builds, the number of list builds; max_count, the largest number of
+ * neighbours within r_c + skin any particle had at a build; capacity, the
+ * entries each particle's list holds (0 when the handle has no list). */
+rbe_status rbe_list_stats(rbe_handle h, int64_t *builds, int32_t *max_count, int32_t *capacity);
+
 /* FP64 MD steps: pos_q, vel double4[n]. */
 rbe_status rbe_step_f64(rbe_handle h, int32_t n, double *pos_q, double *vel, int32_t nsteps,
                         uint64_t *step_dev);
@@ -241,6 +273,8 @@ typedef struct {
                               each scanning 9 / real_split of the 9 neighbour rows (the FP64
                               pass uses the largest power of two not above it)             */
     int32_t real_seg;      /* cells along x per real-space block: 1 .. cells per edge           */
+    int32_t list_split;    /* threads per particle in the neighbour-list pass of rbe_step:
+                              1, 2, 4 or 8                                                   */
 } rbe_tuning;
 
 /* Set the launch shapes (results change only by floating-point summation
@@ -269,7 +303,9 @@ enum {
     RBE_K_FOURIER_FORCE = 6, /* RBE Fourier force and dE/dq (Eq. rbmapprox)         */
     RBE_K_REAL = 7,          /* real space + LJ + assembly (+ Langevin)             */
     RBE_K_ENERGY = 8,        /* FP64 energy reduction                               */
-    RBE_K_COUNT = 9
+    RBE_K_LIST_BUILD = 9,    /* neighbour-list build (list MD steps; returns at once
+                                when no particle moved beyond skin/2)             */
+    RBE_K_COUNT = 10
 };
 
 /* Enable (1) or disable (0) per-kernel timing.  While enabled, rbe_forces*,

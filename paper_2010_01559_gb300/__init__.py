@@ -40,7 +40,8 @@ def params_from(sp, n_max=0, precision=RBE_MIXED) -> capi.rbe_params:
                             precision=precision, sampler=getattr(sp, "sampler", 0),
                             thermostat=getattr(sp, "thermostat", 0),
                             andersen_nu=getattr(sp, "andersen_nu", 0.0),
-                            nh_tau=getattr(sp, "nh_tau", 0.0))
+                            nh_tau=getattr(sp, "nh_tau", 0.0),
+                            skin=getattr(sp, "skin", 0.0))
 
 
 def _ptr(t):
@@ -107,15 +108,15 @@ class _HandleBase:
     def sync(self):
         capi.check(self.lib.rbe_sync(self._h), self._h)
 
-    def set_tuning(self, rho_chunk=0, force_split=0, real_split=0, real_seg=0):
-        t = capi.rbe_tuning(rho_chunk, force_split, real_split, real_seg)
+    def set_tuning(self, rho_chunk=0, force_split=0, real_split=0, real_seg=0, list_split=0):
+        t = capi.rbe_tuning(rho_chunk, force_split, real_split, real_seg, list_split)
         capi.check(self.lib.rbe_set_tuning(self._h, ctypes.byref(t)), self._h)
 
     def get_tuning(self):
-        """(rho_chunk, force_split, real_split, real_seg) in effect."""
+        """(rho_chunk, force_split, real_split, real_seg, list_split) in effect."""
         t = capi.rbe_tuning()
         capi.check(self.lib.rbe_get_tuning(self._h, ctypes.byref(t)), self._h)
-        return t.rho_chunk, t.force_split, t.real_split, t.real_seg
+        return t.rho_chunk, t.force_split, t.real_split, t.real_seg, t.list_split
 
     def autotune(self, pos_q):
         """Pick the fastest launch shapes on this input; returns them."""
@@ -123,7 +124,7 @@ class _HandleBase:
         self._stream()
         capi.check(self.lib.rbe_autotune(self._h, pos_q.shape[0], _ptr(pos_q), ctypes.byref(t)),
                    self._h)
-        return t.rho_chunk, t.force_split, t.real_split, t.real_seg
+        return t.rho_chunk, t.force_split, t.real_split, t.real_seg, t.list_split
 
     def profile(self, on=True):
         capi.check(self.lib.rbe_profile(self._h, 1 if on else 0), self._h)
@@ -160,6 +161,14 @@ class _HandleBase:
         c = ctypes.c_int64()
         capi.check(self.lib.rbe_launch_count(self._h, ctypes.byref(c)), self._h)
         return c.value
+
+    def list_stats(self):
+        """Neighbour-list builds so far, the largest neighbour count seen at a
+        build and the per-particle capacity (``rbe_list_stats``)."""
+        b = ctypes.c_int64(0); m = ctypes.c_int32(0); c = ctypes.c_int32(0)
+        capi.check(self.lib.rbe_list_stats(self._h, ctypes.byref(b), ctypes.byref(m),
+                                           ctypes.byref(c)), self._h)
+        return {"builds": b.value, "max_count": m.value, "capacity": c.value}
 
     def nose_hoover_xi(self, xi=None):
         """The Nose-Hoover friction of every system (``rbe_nose_hoover_xi``):
@@ -203,9 +212,11 @@ class _HandleBase:
                                            _ptr(ph)), self._h)
         return F, E, ph
 
-    def step(self, pos_q, vel, nsteps, step_dev):
+    def step(self, pos_q, vel, nsteps, step_dev, F_out=None):
         """nsteps MD steps in place (mixed: float32, FP64: float64 tensors [n,4]);
-        step_dev: int64 CUDA tensor of one element holding the next step index."""
+        step_dev: int64 CUDA tensor of one element holding the next step index.
+        F_out (mixed only, float32 [n,4]): receives each step's total force
+        (``rbe_step_ex``); after the call, the last step's."""
         torch = _torch()
         n = pos_q.shape[0]
         if step_dev.dtype != torch.int64 or not step_dev.is_cuda or step_dev.numel() != 1:
@@ -213,6 +224,11 @@ class _HandleBase:
         self._stream()
         if pos_q.dtype == torch.float32:
             _need(pos_q, torch.float32, 4, n, "pos_q"); _need(vel, torch.float32, 4, n, "vel")
+            if F_out is not None:
+                _need(F_out, torch.float32, 4, n, "F_out")
+                capi.check(self.lib.rbe_step_ex(self._h, n, _ptr(pos_q), _ptr(vel), nsteps,
+                                                _ptr(step_dev), _ptr(F_out)), self._h)
+                return
             capi.check(self.lib.rbe_step(self._h, n, _ptr(pos_q), _ptr(vel), nsteps,
                                          _ptr(step_dev)), self._h)
         else:

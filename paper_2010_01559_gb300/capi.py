@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "librbe.so")
 
 RBE_OK, RBE_ERR_ARG, RBE_ERR_CUDA, RBE_ERR_OOM = 0, 1, 2, 3
-RBE_ERR_SAMPLER, RBE_ERR_TIMEOUT, RBE_ERR_NONFINITE, RBE_ERR_STATE = 4, 5, 6, 7
+RBE_ERR_SAMPLER, RBE_ERR_TIMEOUT, RBE_ERR_NONFINITE, RBE_ERR_STATE, RBE_ERR_LIST = 4, 5, 6, 7, 8
 RBE_FP64, RBE_MIXED = 0, 1
 RBE_PART_FOURIER, RBE_PART_REAL, RBE_PART_LJ, RBE_PART_ALL = 1, 2, 4, 7
 RBE_SAMPLER_EXACT, RBE_SAMPLER_MH = 0, 1
@@ -23,7 +23,7 @@ RBE_THERMO_LANGEVIN, RBE_THERMO_ANDERSEN, RBE_THERMO_NOSE_HOOVER = 0, 1, 2
 
 STATUS_NAMES = {0: "RBE_OK", 1: "RBE_ERR_ARG", 2: "RBE_ERR_CUDA", 3: "RBE_ERR_OOM",
                 4: "RBE_ERR_SAMPLER", 5: "RBE_ERR_TIMEOUT", 6: "RBE_ERR_NONFINITE",
-                7: "RBE_ERR_STATE"}
+                7: "RBE_ERR_STATE", 8: "RBE_ERR_LIST"}
 
 
 class rbe_params(ctypes.Structure):
@@ -34,12 +34,14 @@ class rbe_params(ctypes.Structure):
                 ("mass", ctypes.c_double), ("seed", ctypes.c_uint64), ("stream", ctypes.c_uint32),
                 ("P", ctypes.c_int32), ("n_max", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("andersen_nu", ctypes.c_double), ("sampler", ctypes.c_int32),
-                ("thermostat", ctypes.c_int32), ("nh_tau", ctypes.c_double)]
+                ("thermostat", ctypes.c_int32), ("nh_tau", ctypes.c_double),
+                ("skin", ctypes.c_double)]
 
 
 class rbe_tuning(ctypes.Structure):
     _fields_ = [("rho_chunk", ctypes.c_int32), ("force_split", ctypes.c_int32),
-                ("real_split", ctypes.c_int32), ("real_seg", ctypes.c_int32)]
+                ("real_split", ctypes.c_int32), ("real_seg", ctypes.c_int32),
+                ("list_split", ctypes.c_int32)]
 
 
 class rbe_peaks(ctypes.Structure):
@@ -54,7 +56,7 @@ class rbe_info(ctypes.Structure):
                 ("first_k", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
-assert ctypes.sizeof(rbe_params) == 136
+assert ctypes.sizeof(rbe_params) == 144
 
 _H = ctypes.c_void_p
 _P = ctypes.c_void_p
@@ -89,12 +91,14 @@ _SIGS = {
                                     ctypes.c_uint64, _P, _P, _P], ctypes.c_int),
     "rbe_probe_peaks": ([ctypes.POINTER(rbe_peaks)], ctypes.c_int),
     "rbe_nose_hoover_xi": ([_H, _P, ctypes.c_int32], ctypes.c_int),
+    "rbe_step_ex": ([_H, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P], ctypes.c_int),
+    "rbe_list_stats": ([_H, _P, _P, _P], ctypes.c_int),
     "rbe_observables": ([_H, ctypes.c_int32, _P, _P, ctypes.c_int32, _P], ctypes.c_int),
 }
 
 #: kernel names in RBE_K_* order
 KERNELS = ("prep", "scan", "scatter", "cell_order", "rho", "finalize", "fourier_force",
-           "real", "energy")
+           "real", "energy", "list_build")
 
 #: every symbol include/rbe.h declares
 EXPORTED = tuple(_SIGS)
@@ -138,12 +142,12 @@ def check(status: int, handle=None) -> None:
 def make_params(box, alpha, r_c, P, seed=0, stream=0, coulomb_prefactor=1.0, lj_eps=0.0,
                 lj_sigma=1.0, lj_rcut=0.0, gamma=1.0, kT=1.0, dt=1e-3, mass=1.0, n_max=0,
                 precision=RBE_MIXED, sampler=RBE_SAMPLER_EXACT, thermostat=RBE_THERMO_LANGEVIN,
-                andersen_nu=0.0, nh_tau=0.0) -> rbe_params:
+                andersen_nu=0.0, nh_tau=0.0, skin=0.0) -> rbe_params:
     return rbe_params(box=box, alpha=alpha, r_c=r_c, coulomb_prefactor=coulomb_prefactor,
                       lj_eps=lj_eps, lj_sigma=lj_sigma, lj_rcut=lj_rcut, gamma=gamma, kT=kT,
                       dt=dt, mass=mass, seed=seed, stream=stream, P=P, n_max=n_max,
                       precision=precision, andersen_nu=andersen_nu, sampler=sampler,
-                      thermostat=thermostat, nh_tau=nh_tau)
+                      thermostat=thermostat, nh_tau=nh_tau, skin=skin)
 
 
 def __getattr__(name):

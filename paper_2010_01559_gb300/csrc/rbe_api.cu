@@ -36,6 +36,7 @@ struct SysHost {
     int M = 0;
     double H = 0.0, S = 0.0;
     int ncd = 0;
+    double skin = 0.0;                 // neighbour-list skin in effect (0 without a list)
     std::vector<uint64_t> table;
     std::vector<uint64_t> mh_tq;       // MH proposal thresholds (2M+1)
     std::vector<double> mh_rho;        // MH target / proposal ratios (2M+1)
@@ -47,6 +48,7 @@ struct GraphEntry {
     const void* pos;
     const void* vel;
     const void* step;
+    const void* F;
     int prec;
     cudaGraphExec_t exec;
     int kernels;           // kernels in one replay
@@ -201,6 +203,19 @@ struct rbe_ctx {
     int4* d_mh_state = nullptr;               // per system: current (m_x, m_y, m_z)
     uint64_t* d_mh_pos = nullptr;             // per system: chain iterations done
     NhState* d_nh = nullptr;                  // per system: Nose-Hoover state
+    // neighbour list of the mixed MD step (pairs within r_c + skin)
+    bool list = false;                        // the handle keeps a list (skin >= 0)
+    bool list_valid = false;                  // sorted arrays still those of the last build
+    int list_split = 0, cur_lsplit = -1;      // lanes per particle of the list pass (0 = auto)
+    int lsplit = 1, nlblk = 0, max_lblk = 0;
+    int list_cap = 0;                         // entries per particle
+    Tile* d_lblk = nullptr;
+    int* d_nbr = nullptr;                     // [slot * ntot + sorted index]
+    int* d_ncnt = nullptr;
+    uint4* d_sref = nullptr;
+    int* d_iperm = nullptr;
+    int* d_list_flag = nullptr;
+    unsigned long long* d_list_stats = nullptr;   // builds, largest count
     unsigned long long* d_qsum_fx = nullptr;  // sum q per system (fixed point)
     double2* d_blk_e = nullptr;
     double2* d_blk_w = nullptr;               // per real-space block (W_coul, W_lj)
@@ -242,6 +257,20 @@ rbe_status cuda_fail(rbe_ctx* h, cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
     } while (0)
 
+// Largest skin that keeps the cell grid (side >= r_c + skin, at least 3 per
+// edge) when r_c <= L/3, or the minimum image (r_c + skin <= L/2) in the
+// one-cell mode.
+double max_skin(const rbe_params& p) {
+    return p.box >= 3.0 * p.r_c ? p.box / 3.0 - p.r_c : p.box / 2.0 - p.r_c;
+}
+
+// The skin in effect: 0.1 r_c by default, capped as above; 0 for skin < 0.
+double skin_of(const rbe_params& p) {
+    if (p.skin < 0.0) return 0.0;
+    const double s = p.skin > 0.0 ? p.skin : 0.1 * p.r_c;
+    return std::max(0.0, std::min(s, max_skin(p)));
+}
+
 rbe_status validate_params(const rbe_params& p, std::string& why) {
     if (!(p.box > 0.0) || !std::isfinite(p.box)) { why = "box must be > 0"; return RBE_ERR_ARG; }
     if (!(p.alpha > 0.0) || !std::isfinite(p.alpha)) { why = "alpha must be > 0"; return RBE_ERR_ARG; }
@@ -260,6 +289,8 @@ rbe_status validate_params(const rbe_params& p, std::string& why) {
     if (p.thermostat == RBE_THERMO_NOSE_HOOVER && (!(p.nh_tau > 0.0) || !std::isfinite(p.nh_tau) || !(p.kT > 0.0))) { why = "Nose-Hoover needs nh_tau > 0 and kT > 0"; return RBE_ERR_ARG; }
     if (!(p.andersen_nu >= 0.0) || !(p.andersen_nu * p.dt <= 1.0)) { why = "andersen_nu must satisfy 0 <= nu dt <= 1"; return RBE_ERR_ARG; }
     if (p.gamma < 0.0 || p.kT < 0.0) { why = "gamma and kT must be >= 0"; return RBE_ERR_ARG; }
+    if (!std::isfinite(p.skin)) { why = "skin must be finite"; return RBE_ERR_ARG; }
+    if (p.skin > 0.0 && p.skin > max_skin(p) * (1.0 + 1e-12)) { why = "skin must be <= L/3 - r_c (L/2 - r_c when r_c > L/3)"; return RBE_ERR_ARG; }
     const int M = axis_M(p.alpha, p.box);
     if (M > 200000) { why = "alpha L^2 too large for the sampling table"; return RBE_ERR_ARG; }
     // (0,0,0) is drawn with probability 1/H^3; keep the 32-attempt loop safe.
@@ -350,6 +381,8 @@ void fill_sysdev(const SysHost& s, SysDev& d) {
     d.nh_rate = p.thermostat == RBE_THERMO_NOSE_HOOVER
                     ? p.dt / (3.0 * std::max(1, s.n) * p.nh_tau * p.nh_tau) : 0.0;
     d.nh_k2scale = p.kT > 0.0 ? p.mass / p.kT * 4294967296.0 : 0.0;
+    d.f_list_cut2 = (float)((p.r_c + s.skin) * (p.r_c + s.skin) * (1.0 + 1e-5));
+    d.f_half_skin2 = (float)(0.25 * s.skin * s.skin * (1.0 - 1e-5));
     d.corner_q = (uint32_t)(4294967296ull / (unsigned long long)std::max(1, s.ncd));
     d.corner_r = (uint32_t)(4294967296ull - (unsigned long long)d.corner_q * std::max(1, s.ncd));
 }
@@ -376,6 +409,14 @@ int auto_real_split(long long ntot) {
     return ntot * 9 <= 152LL * 4096 ? 9 : 3;
 }
 
+// Threads per particle of the neighbour-list pass: enough for about 1024
+// threads per SM.
+int auto_list_split(long long ntot) {
+    int r = 1;
+    while (r < 8 && ntot * r < 152LL * 1024) r <<= 1;
+    return r;
+}
+
 // Threads per particle of the FP64 real-space pass: the largest power of two
 // not above the mixed path's.
 int real_split64(int r) { return r >= 8 ? 8 : (r >= 2 ? 2 : 1); }
@@ -397,17 +438,20 @@ rbe_status prepare(rbe_ctx* h, int n) {
     const int chunk = h->rho_chunk > 0 ? h->rho_chunk : auto_chunk(h, ntot);
     const int split = h->force_split > 0 ? h->force_split : auto_split(ntot);
     const int rsplit = h->real_split > 0 ? h->real_split : auto_real_split(ntot);
+    const int lsplit = h->list_split > 0 ? h->list_split : auto_list_split(ntot);
     int ncd_max = 3;
     for (auto& sh : h->sys) ncd_max = std::max(ncd_max, sh.ncd);
     const int rseg = h->real_seg > 0 ? std::min(h->real_seg, ncd_max)
                                      : auto_real_seg(ntot, h->ncell, ncd_max);
     if (h->cur_n == n && h->cur_chunk == chunk && h->cur_split == split &&
-        h->cur_rsplit == rsplit && h->cur_seg == rseg)
+        h->cur_rsplit == rsplit && h->cur_seg == rseg && h->cur_lsplit == lsplit)
         return RBE_OK;
+    h->list_valid = false;                 // the sorted arrays are rebuilt from scratch
     std::vector<Tile> segs;
     int seg_max = 1;
     double stage_need = 0.0;
-    std::vector<Tile> pblk, fblk, rblk, chunks;
+    std::vector<Tile> pblk, fblk, rblk, chunks, lblk;
+    const int ltile = kBlockP / lsplit;
     const int ftile = kBlockP / split;
     const int rtile = kBlockP / real_split64(rsplit);
     int off_part = 0;
@@ -435,6 +479,11 @@ rbe_status prepare(rbe_ctx* h, int n) {
             if (sh.n == 0) break;
         }
         d.nrb = nrb;
+        if (h->list)
+            for (int f = 0; f < sh.n || f == 0; f += ltile) {
+                lblk.push_back(Tile{s, sh.off_p + f, std::max(0, std::min(ltile, sh.n - f)), 0});
+                if (sh.n == 0) break;
+            }
         d.off_sg = (int)segs.size();
         {
             const int ncd = sh.ncd, seg = std::min(rseg, ncd);
@@ -463,7 +512,7 @@ rbe_status prepare(rbe_ctx* h, int n) {
     }
     if ((int)pblk.size() > h->max_pblk || (int)fblk.size() > h->max_fblk ||
         (int)rblk.size() > h->max_rblk || (int)chunks.size() > h->max_chunks ||
-        (int)segs.size() > h->max_seg ||
+        (int)segs.size() > h->max_seg || (int)lblk.size() > h->max_lblk ||
         (size_t)off_part > h->max_part)
         return fail(h, RBE_ERR_ARG, "work tables exceed the workspace (n > capacity?)");
     RBE_CUDA(h, cudaMemcpyAsync(h->d_sys, h->sysdev.data(), sizeof(SysDev) * h->nsys,
@@ -478,6 +527,11 @@ rbe_status prepare(rbe_ctx* h, int n) {
                                 cudaMemcpyHostToDevice, h->stream));
     RBE_CUDA(h, cudaMemcpyAsync(h->d_chunks, chunks.data(), sizeof(Tile) * chunks.size(),
                                 cudaMemcpyHostToDevice, h->stream));
+    if (!lblk.empty())
+        RBE_CUDA(h, cudaMemcpyAsync(h->d_lblk, lblk.data(), sizeof(Tile) * lblk.size(),
+                                    cudaMemcpyHostToDevice, h->stream));
+    h->nlblk = (int)lblk.size();
+    h->lsplit = lsplit;
     RBE_CUDA(h, cudaStreamSynchronize(h->stream));
     h->npblk = (int)pblk.size();
     h->nfblk = (int)fblk.size();
@@ -505,6 +559,7 @@ rbe_status prepare(rbe_ctx* h, int n) {
     h->cur_chunk = chunk;
     h->cur_split = split;
     h->cur_rsplit = rsplit;
+    h->cur_lsplit = lsplit;
     return RBE_OK;
 }
 
@@ -521,6 +576,7 @@ rbe_status allocate(rbe_ctx* h) {
         part += c * s.p.P;
     }
     h->max_pblk = (int)pb;
+    h->max_lblk = (int)(pb * 8);             // list tiles as small as kBlockP / 8
     h->max_fblk = (int)fb;
     h->max_rblk = (int)rb;
     h->max_seg = std::max(1, h->ncell);
@@ -560,6 +616,15 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_ALLOC(h->d_mh_state, h->nsys);
     RBE_ALLOC(h->d_mh_pos, h->nsys);
     RBE_ALLOC(h->d_nh, h->nsys);
+    if (h->list) {
+        RBE_ALLOC(h->d_lblk, h->max_lblk);
+        RBE_ALLOC(h->d_nbr, (size_t)h->list_cap * N);
+        RBE_ALLOC(h->d_ncnt, N);
+        RBE_ALLOC(h->d_sref, N);
+        RBE_ALLOC(h->d_iperm, N);
+        RBE_ALLOC(h->d_list_flag, 1);
+        RBE_ALLOC(h->d_list_stats, 2);
+    }
     RBE_ALLOC(h->d_kab, h->ktot);
     RBE_ALLOC(h->d_qsum_fx, h->nsys);
     RBE_ALLOC(h->d_blk_e, std::max<long long>(rb, (long long)kSegChunks * (h->ncell + 1)));
@@ -575,6 +640,15 @@ rbe_status allocate(rbe_ctx* h) {
 #undef RBE_ALLOC
     RBE_CUDA(h, cudaMemset(h->d_cell_cnt, 0, sizeof(int) * (h->ncell + 1)));
     RBE_CUDA(h, cudaMemset(h->d_err, 0, sizeof(int)));
+    if (h->list) {
+        // sorted slots 0 until the first build (which the set flag forces)
+        RBE_CUDA(h, cudaMemset(h->d_iperm, 0, sizeof(int) * N));
+        RBE_CUDA(h, cudaMemset(h->d_ncnt, 0, sizeof(int) * N));
+        RBE_CUDA(h, cudaMemset(h->d_sref, 0, sizeof(uint4) * N));
+        RBE_CUDA(h, cudaMemset(h->d_list_stats, 0, sizeof(unsigned long long) * 2));
+        const int one = 1;
+        RBE_CUDA(h, cudaMemcpy(h->d_list_flag, &one, sizeof(int), cudaMemcpyHostToDevice));
+    }
     RBE_CUDA(h, cudaMemset(h->d_qsum_fx, 0, sizeof(unsigned long long) * h->nsys));
     RBE_CUDA(h, cudaMemset(h->d_rho_fx, 0, sizeof(unsigned long long) * 2 * h->ktot));
     RBE_CUDA(h, cudaMemset(h->d_kcnt, 0, sizeof(int) * h->ktot));
@@ -629,6 +703,8 @@ void release(rbe_ctx* h) {
                     h->d_perm, h->d_perm_tmp, h->d_fs, h->d_fs64, h->d_cell_cnt,
                     h->d_cell_start, h->d_ksamp, h->d_rho_fx, h->d_kcnt, h->d_kab,
                     h->d_kcoef, h->d_mh_tq, h->d_mh_rho, h->d_mh_state, h->d_mh_pos, h->d_nh,
+                    h->d_lblk, h->d_nbr, h->d_ncnt, h->d_sref, h->d_iperm, h->d_list_flag,
+                    h->d_list_stats,
                     h->d_qsum_fx, h->d_blk_e, h->d_blk_w, h->d_obs_m, h->d_obs_rho, h->d_obs_w,
                     h->d_obs_out, h->d_obs_part, h->d_blk_q, h->d_cur_step, h->d_stage_step,
                     h->d_err, h->d_stage_pos, h->d_stage_vel, h->d_stage_F, h->d_stage_E};
@@ -677,9 +753,14 @@ rbe_status create_common(const rbe_params* ps, const int32_t* ns, int nsys, bool
             return fail(nullptr, RBE_ERR_ARG, "all systems of a handle must use the same sampler");
         }
         sh.S = sh.H * sh.H * sh.H - 1.0;
-        // cells of side >= r_c, at least 3 per edge; else one cell (all pairs)
-        sh.ncd = sh.p.box / sh.p.r_c >= 3.0 ? std::min(256, (int)std::floor(sh.p.box / sh.p.r_c))
-                                            : 1;
+        // cells of side >= r_c + skin, at least 3 per edge; else one cell (all pairs)
+        sh.skin = skin_of(sh.p);
+        const double side = sh.p.r_c + sh.skin;
+        sh.ncd = sh.p.box / side >= 3.0 ? std::min(256, (int)std::floor(sh.p.box / side)) : 1;
+        if ((sh.p.skin < 0.0) != (ps[0].skin < 0.0)) {
+            delete h;
+            return fail(nullptr, RBE_ERR_ARG, "all systems of a handle must agree on skin < 0");
+        }
         sh.off_p = off_p;
         sh.off_c = off_c;
         sh.off_k = off_k;
@@ -695,6 +776,19 @@ rbe_status create_common(const rbe_params* ps, const int32_t* ns, int nsys, bool
     h->ktot = off_k;
     h->ttot = off_t;
     h->mh = ps[0].sampler == RBE_SAMPLER_MH;
+    h->list = ps[0].skin >= 0.0;
+    if (h->list) {
+        // entries per particle: the mean count within r_c + skin at the
+        // system's density, plus 50 % and eight standard deviations
+        double most = 0.0;
+        for (auto& sh : h->sys) {
+            const double rr = sh.p.r_c + sh.skin;
+            const double nn = batch ? sh.n : sh.p.n_max;
+            most = std::max(most, 4.0 / 3.0 * M_PI * rr * rr * rr * nn /
+                                      (sh.p.box * sh.p.box * sh.p.box));
+        }
+        h->list_cap = (int)std::min(4096.0, 8.0 * std::ceil((1.5 * most + 8.0 * std::sqrt(most) + 16.0) / 8.0));
+    }
     for (auto& sh : h->sys) h->mh_words = std::max(h->mh_words, 2 * sh.M + 1);
     rbe_status st = allocate(h);
     if (st != RBE_OK) {
@@ -725,6 +819,7 @@ struct EvalArgs {
     float4* md_vel;
     double4* md_pos64;
     double4* md_vel64;
+    bool list;                // mixed MD step over the neighbour list
 };
 
 // Kernel work descriptor: tables for a batch, by-value constants and a tile
@@ -844,6 +939,15 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     pa.kcoef = h->d_kcoef;
     pa.err = h->d_err;
     pa.nh = (a.md_pos || a.md_pos64) ? h->d_nh : nullptr;
+    if (a.list) {
+        pa.sref = h->d_sref;
+        pa.iperm = h->d_iperm;
+        pa.spos = h->d_spos;
+        pa.list_flag = h->d_list_flag;
+    } else {
+        h->list_valid = false;              // the sorted arrays are about to change
+    }
+    const int* lflag = a.list ? h->d_list_flag : nullptr;
     if (want_q)
         cudaMemsetAsync(h->d_qsum_fx, 0, sizeof(unsigned long long) * h->nsys, st);
     run(RBE_K_PREP, st, [&] {
@@ -862,15 +966,34 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
         cudaEventRecord(h->ev_join, st2);
     }
     run(RBE_K_SCAN, st, [&] {
-        launch_scan(st, h->d_cell_cnt, h->d_cell_start, h->ncell, a.step_dev, h->d_cur_step);
+        launch_scan(st, h->d_cell_cnt, h->d_cell_start, h->ncell, a.step_dev, h->d_cur_step,
+                    lflag);
     });
     run(RBE_K_SCATTER, st, [&] {
-        launch_scatter(st, n, h->d_cid, h->d_rank, h->d_cell_start, h->d_perm_tmp);
+        launch_scatter(st, n, h->d_cid, h->d_rank, h->d_cell_start, h->d_perm_tmp, lflag);
     });
     run(RBE_K_CELL_ORDER, st, [&] {
         launch_order(st, n, h->d_cid, h->d_cell_start, h->d_perm_tmp, mixed ? h->d_fx : nullptr,
-                     h->d_spos, mixed ? nullptr : h->d_fx64, h->d_spos64, h->d_perm);
+                     h->d_spos, mixed ? nullptr : h->d_fx64, h->d_spos64, h->d_perm, lflag,
+                     a.list ? h->d_iperm : nullptr);
     });
+    if (a.list)
+        run(RBE_K_LIST_BUILD, st, [&] {
+            ListArgs la{};
+            la.w = make_work(h, h->d_pblk, kBlockP, 0);
+            la.nblk = h->npblk;
+            la.list_flag = h->d_list_flag;
+            la.spos = h->d_spos;
+            la.cell_start = h->d_cell_start;
+            la.nbr = h->d_nbr;
+            la.ncnt = h->d_ncnt;
+            la.stride = std::max(h->ntot, 1);
+            la.cap = h->list_cap;
+            la.sref = h->d_sref;
+            la.stats = h->d_list_stats;
+            la.err = h->d_err;
+            launch_list_build(st, one, la);
+        });
     if (fourier) cudaStreamWaitEvent(st, h->ev_join, 0);
     RealArgs r = make_real_args(h, a.parts);
     r.F_out = a.F;
@@ -884,8 +1007,19 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     r.nh = pa.nh;
     r.blk_e = a.E ? h->d_blk_e : nullptr;
     r.blk_w = (a.E && a.W) ? h->d_blk_w : nullptr;
+    if (a.list) {
+        r.lw = make_work(h, h->d_lblk, kBlockP / h->lsplit, 0);
+        r.nlblk = h->nlblk;
+        r.lsplit = h->lsplit;
+        r.nbr = h->d_nbr;
+        r.ncnt = h->d_ncnt;
+        r.nbr_stride = std::max(h->ntot, 1);
+        r.list_flag = h->d_list_flag;
+    }
     run(RBE_K_REAL, st, [&] {
-        if (mixed) launch_real_mixed(st, one, r); else launch_real_f64(st, one, r);
+        if (a.list) launch_real_list(st, one, r);
+        else if (mixed) launch_real_mixed(st, one, r);
+        else launch_real_f64(st, one, r);
     });
     if (a.E)
         run(RBE_K_ENERGY, st, [&] {
@@ -1023,7 +1157,7 @@ rbe_status observables_impl(rbe_ctx* h, int n, const float* pos_q, const float* 
 }
 
 rbe_status step_impl(rbe_ctx* h, int n, int prec, void* pos, void* vel, int nsteps,
-                     uint64_t* step_dev) {
+                     uint64_t* step_dev, float* F_out = nullptr) {
     if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
     rbe_status s = check_n(h, n);
     if (s != RBE_OK) return s;
@@ -1039,10 +1173,20 @@ rbe_status step_impl(rbe_ctx* h, int n, int prec, void* pos, void* vel, int nste
         a.pos = (const float4*)pos;
         a.md_pos = (float4*)pos;
         a.md_vel = (float4*)vel;
+        a.F = (float4*)F_out;
+        a.list = h->list;
     } else {
         a.pos64 = (const double4*)pos;
         a.md_pos64 = (double4*)pos;
         a.md_vel64 = (double4*)vel;
+    }
+    if (a.list) {
+        // the first step after anything else touched the sorted arrays builds a list
+        if (!h->list_valid && nsteps > 0)
+            RBE_CUDA(h, cudaMemsetAsync(h->d_list_flag, 0xFF, sizeof(int), h->stream));
+        if (nsteps > 0) h->list_valid = true;
+    } else if (nsteps > 0) {
+        h->list_valid = false;
     }
     if (!h->use_graph || h->prof_on) {
         for (int k = 0; k < nsteps; ++k) enqueue_eval(h, h->stream, a);
@@ -1051,7 +1195,8 @@ rbe_status step_impl(rbe_ctx* h, int n, int prec, void* pos, void* vel, int nste
     cudaGraphExec_t exec = nullptr;
     int kernels = 0;
     for (auto& g : h->graphs)
-        if (g.n == n && g.pos == pos && g.vel == vel && g.step == step_dev && g.prec == prec) {
+        if (g.n == n && g.pos == pos && g.vel == vel && g.step == step_dev && g.prec == prec &&
+            g.F == (const void*)F_out) {
             exec = g.exec;
             kernels = g.kernels;
         }
@@ -1066,7 +1211,7 @@ rbe_status step_impl(rbe_ctx* h, int n, int prec, void* pos, void* vel, int nste
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
-        h->graphs.push_back(GraphEntry{n, pos, vel, step_dev, prec, exec, kernels});
+        h->graphs.push_back(GraphEntry{n, pos, vel, step_dev, F_out, prec, exec, kernels});
     }
     for (int k = 0; k < nsteps; ++k) RBE_CUDA(h, cudaGraphLaunch(exec, h->stream));
     h->kernel_count += (int64_t)kernels * nsteps;
@@ -1199,6 +1344,24 @@ rbe_status rbe_step_f64(rbe_handle h, int32_t n, double* pos_q, double* vel, int
     return step_impl(h, n, RBE_FP64, pos_q, vel, nsteps, step_dev);
 }
 
+rbe_status rbe_step_ex(rbe_handle h, int32_t n, float* pos_q, float* vel, int32_t nsteps,
+                       uint64_t* step_dev, float* F_out) {
+    return step_impl(h, n, RBE_MIXED, pos_q, vel, nsteps, step_dev, F_out);
+}
+
+rbe_status rbe_list_stats(rbe_handle h, int64_t* builds, int32_t* max_count, int32_t* capacity) {
+    if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
+    unsigned long long st[2] = {0ull, 0ull};
+    if (h->list) {
+        RBE_CUDA(h, cudaStreamSynchronize(h->stream));
+        RBE_CUDA(h, cudaMemcpy(st, h->d_list_stats, sizeof(st), cudaMemcpyDeviceToHost));
+    }
+    if (builds) *builds = (int64_t)st[0];
+    if (max_count) *max_count = (int32_t)st[1];
+    if (capacity) *capacity = h->list ? h->list_cap : 0;
+    return finish(h, "rbe_list_stats");
+}
+
 rbe_status rbe_nose_hoover_xi(rbe_handle h, double* xi, int32_t set) {
     if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
     if (!xi) return fail(h, RBE_ERR_ARG, "xi is NULL");
@@ -1278,6 +1441,9 @@ rbe_status rbe_sync(rbe_handle h) {
         RBE_CUDA(h, cudaMemset(h->d_err, 0, sizeof(int)));
         if (err & kErrSampler)
             return fail(h, RBE_ERR_SAMPLER, "a k-sample drew (0,0,0) on 32 attempts in a row");
+        if (err & kErrList)
+            return fail(h, RBE_ERR_LIST, "a particle had more neighbours within r_c + skin than "
+                                         "the list holds (" + std::to_string(h->list_cap) + ")");
     }
     return finish(h, "rbe_sync");
 }
@@ -1292,6 +1458,10 @@ rbe_status rbe_set_tuning(rbe_handle h, const rbe_tuning* t) {
     if (r != 0 && r != 1 && r != 3 && r != 9)
         return fail(h, RBE_ERR_ARG, "real_split must be 0, 1, 3 or 9");
     if (sg < 0 || sg > 256) return fail(h, RBE_ERR_ARG, "real_seg must be in [0, 256]");
+    const int ls = t->list_split;
+    if (ls != 0 && ls != 1 && ls != 2 && ls != 4 && ls != 8)
+        return fail(h, RBE_ERR_ARG, "list_split must be 0, 1, 2, 4 or 8");
+    h->list_split = ls;
     h->rho_chunk = c;
     h->force_split = f;
     h->real_split = r;
@@ -1316,6 +1486,8 @@ rbe_status rbe_get_tuning(rbe_handle h, rbe_tuning* t) {
     t->real_seg = h->cur_seg > 0 ? h->cur_seg
                                  : (h->real_seg > 0 ? std::min(h->real_seg, ncd_max)
                                                     : auto_real_seg(ntot, h->ncell, ncd_max));
+    t->list_split = h->cur_lsplit > 0 ? h->cur_lsplit
+                                      : (h->list_split > 0 ? h->list_split : auto_list_split(ntot));
     return RBE_OK;
 }
 
@@ -1380,6 +1552,32 @@ rbe_status rbe_autotune(rbe_handle h, int32_t n, const float* pos_q, rbe_tuning*
     }
     h->real_split = best_rsplit;
     h->real_seg = best_seg;
+    // neighbour-list pass: lanes per particle, timed on a list built for this input
+    int best_lsplit = 0;
+    if (h->list) {
+        best = 1e30f;
+        for (int ls = 1; ls <= 8 && s == RBE_OK; ls <<= 1) {
+            h->list_split = ls;
+            if ((s = prepare(h, n)) != RBE_OK) break;
+            EvalArgs b = a;
+            b.list = true;
+            RBE_CUDA(h, cudaMemsetAsync(h->d_list_flag, 0xFF, sizeof(int), h->stream));
+            enqueue_eval(h, h->stream, b);
+            RealArgs r = make_real_args(h, RBE_PART_ALL);
+            r.F_out = h->d_stage_F;
+            r.lw = make_work(h, h->d_lblk, kBlockP / h->lsplit, 0);
+            r.nlblk = h->nlblk;
+            r.lsplit = h->lsplit;
+            r.nbr = h->d_nbr;
+            r.ncnt = h->d_ncnt;
+            r.nbr_stride = std::max(h->ntot, 1);
+            r.list_flag = h->d_list_flag;
+            const float t = time_kernel(h, e0, e1, [&] { launch_real_list(h->stream, !h->batch, r); });
+            if (t < best) { best = t; best_lsplit = ls; }
+        }
+        h->list_split = best_lsplit;
+        h->list_valid = false;
+    }
     h->prof_on = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1392,6 +1590,7 @@ rbe_status rbe_autotune(rbe_handle h, int32_t n, const float* pos_q, rbe_tuning*
         out->force_split = best_split;
         out->real_split = best_rsplit;
         out->real_seg = best_seg;
+        out->list_split = best_lsplit;
     }
     return finish(h, "rbe_autotune");
 }

@@ -242,6 +242,7 @@ k_prep_mixed(const __grid_constant__ Work w, const float4* __restrict__ pos_q,
     const SysDev& S = sys_of<ONE>(w, tl.sys);
     const int t = threadIdx.x;
     double qs = 0.0, q2s = 0.0;
+    int moved = 0;
     if (t < tl.count) {
         const int i = tl.first + t;
         const float4 p = pos_q[i];
@@ -253,9 +254,26 @@ k_prep_mixed(const __grid_constant__ Work w, const float4* __restrict__ pos_q,
                       cell_of_fixed(sx, ncd);
         cid[i] = c;
         rank[i] = atomicAdd(cell_cnt + c, 1);
-        fx[i] = make_uint4(sx, sy, sz, __float_as_uint(p.w));
+        const uint4 rec = make_uint4(sx, sy, sz, __float_as_uint(p.w));
+        fx[i] = rec;
         qs = (double)p.w;
         q2s = (double)p.w * (double)p.w;
+        if (pa.list_flag) {
+            // neighbour-list step: the record goes to its sorted slot of the
+            // last build, and a displacement beyond skin/2 since that build
+            // (minimum image, from the fixed-point difference) asks for a new list
+            const int si = pa.iperm[i];
+            const uint4 r0 = pa.sref[si];
+            const float Lu = S.L_over_2_32;
+            const float dx = (float)(int32_t)(sx - r0.x) * Lu;
+            const float dy = (float)(int32_t)(sy - r0.y) * Lu;
+            const float dz = (float)(int32_t)(sz - r0.z) * Lu;
+            moved = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > S.f_half_skin2;
+            pa.spos[si] = rec;
+        }
+    }
+    if (pa.list_flag) {
+        if (__syncthreads_or(moved) && t == 0) atomicOr(pa.list_flag, 1);
     }
     if (pa.want_q) {
         const double2 r = block_sum2(qs, q2s);
@@ -328,8 +346,13 @@ constexpr int kScanPer = 4;
 
 __global__ void __launch_bounds__(kScanThreads)
 k_scan(int* __restrict__ cell_cnt, int* __restrict__ cell_start, int ncell,
-       uint64_t* __restrict__ step_dev, const uint64_t* __restrict__ cur_step) {
+       uint64_t* __restrict__ step_dev, const uint64_t* __restrict__ cur_step,
+       const int* __restrict__ list_flag) {
     if (step_dev && threadIdx.x == 0) *step_dev = *cur_step + 1;   // one increment per step
+    if (list_flag && !*list_flag) {               // the list stands: only clear the counts
+        for (int i = threadIdx.x; i < ncell; i += blockDim.x) cell_cnt[i] = 0;
+        return;
+    }
     __shared__ int warp_tot[kScanThreads / 32];
     __shared__ int carry_s;
     if (threadIdx.x == 0) carry_s = 0;
@@ -385,9 +408,10 @@ k_scan(int* __restrict__ cell_cnt, int* __restrict__ cell_start, int ncell,
 // Scatter of the caller's indices to their atomic slots (arbitrary order
 // inside each cell).
 __global__ void k_scatter(int n, const int* __restrict__ cid, const int* __restrict__ rank,
-                          const int* __restrict__ cell_start, int* __restrict__ perm_tmp) {
+                          const int* __restrict__ cell_start, int* __restrict__ perm_tmp,
+                          const int* __restrict__ list_flag) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || (list_flag && !*list_flag)) return;
     perm_tmp[cell_start[cid[i]] + rank[i]] = i;
 }
 
@@ -399,9 +423,10 @@ __global__ void k_scatter(int n, const int* __restrict__ cid, const int* __restr
 __global__ void k_order(int n, const int* __restrict__ cid, const int* __restrict__ cell_start,
                         const int* __restrict__ perm_tmp, const uint4* __restrict__ fx,
                         uint4* __restrict__ spos, const double4* __restrict__ fx64,
-                        double4* __restrict__ spos64, int* __restrict__ perm) {
+                        double4* __restrict__ spos64, int* __restrict__ perm,
+                        const int* __restrict__ list_flag, int* __restrict__ iperm) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
+    if (s >= n || (list_flag && !*list_flag)) return;
     const int i = perm_tmp[s];
     const int c = cid[i];
     const int b = cell_start[c], e = cell_start[c + 1];
@@ -419,6 +444,7 @@ __global__ void k_order(int n, const int* __restrict__ cid, const int* __restric
     }
     const int dst = b + r;
     perm[dst] = i;
+    if (iperm) iperm[i] = dst;
     if (fx) spos[dst] = fx[i];
     if (fx64) spos64[dst] = fx64[i];
 }
@@ -451,22 +477,23 @@ void launch_prep_f64(cudaStream_t st, bool one, const Work& w, int nblk, const d
 }
 
 void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell, uint64_t* step_dev,
-                 const uint64_t* cur_step) {
-    k_scan<<<1, kScanThreads, 0, st>>>(cell_cnt, cell_start, ncell, step_dev, cur_step);
+                 const uint64_t* cur_step, const int* list_flag) {
+    k_scan<<<1, kScanThreads, 0, st>>>(cell_cnt, cell_start, ncell, step_dev, cur_step,
+                                       list_flag);
 }
 
 void launch_scatter(cudaStream_t st, int n, const int* cid, const int* rank,
-                    const int* cell_start, int* perm_tmp) {
+                    const int* cell_start, int* perm_tmp, const int* list_flag) {
     if (n <= 0) return;
-    k_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, cid, rank, cell_start, perm_tmp);
+    k_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, cid, rank, cell_start, perm_tmp, list_flag);
 }
 
 void launch_order(cudaStream_t st, int n, const int* cid, const int* cell_start,
                   const int* perm_tmp, const uint4* fx, uint4* spos, const double4* fx64,
-                  double4* spos64, int* perm) {
+                  double4* spos64, int* perm, const int* list_flag, int* iperm) {
     if (n <= 0) return;
     k_order<<<(n + 255) / 256, 256, 0, st>>>(n, cid, cell_start, perm_tmp, fx, spos, fx64, spos64,
-                                             perm);
+                                             perm, list_flag, iperm);
 }
 
 }  // namespace rbe

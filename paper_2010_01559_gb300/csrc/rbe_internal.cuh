@@ -34,7 +34,8 @@ namespace rbe {
 constexpr int kBlockP = 128;      // particles per block of the per-particle kernels
 constexpr int kLTile = 128;       // wave vectors per block of the structure-factor kernel
 constexpr int kMaxAttempts = 32;  // bound on the (0,0,0) rejection loop
-constexpr int kErrSampler = 1;    // bit in the device error word
+constexpr int kErrSampler = 1;    // bits in the device error word
+constexpr int kErrList = 2;       // a neighbour list overflowed
 constexpr double kQScale = 4294967296.0;           // 2^32: fixed point of sum q
 
 // Per-system constants (device copy).  All derived in FP64 on the host.
@@ -74,6 +75,9 @@ struct SysDev {
     uint32_t corner_q, corner_r;   // 2^32 = corner_q * ncd + corner_r (cell corners)
     double nh_rate;         // Nose-Hoover: dt / (3 n tau^2), xi += nh_rate (K2 / kT - 3 n)
     double nh_k2scale;      // m / kT * 2^32: fixed-point units of the kinetic sum
+    // neighbour list of the MD step (pairs within r_c + skin)
+    float f_list_cut2;      // (r_c + skin)^2, widened by 1e-5 (the build keeps more, never less)
+    float f_half_skin2;     // (skin / 2)^2, narrowed by 1e-5 (a rebuild comes early, never late)
 };
 
 // Nose-Hoover state of one system: the friction xi, the velocity update of
@@ -232,18 +236,44 @@ struct PrepArgs {
     double* kcoef;           // coef_scale / k^2 per sample (Eq. rbmapprox)
     int* err;
     NhState* nh;             // MD steps: Nose-Hoover state per system (null otherwise)
+    // neighbour-list MD steps: displacement test against the last build and
+    // the sorted records for the list kernel (null otherwise)
+    const uint4* sref;       // [sorted] records at the last build
+    const int* iperm;        // caller index -> sorted index of the last build
+    uint4* spos;             // [sorted] current records
+    int* list_flag;          // set: rebuild the list in this step
 };
 void launch_prep_mixed(cudaStream_t st, bool one, const Work& w, int nblk, const float4* pos_q,
                        uint4* fx, int* cid, int* rank, int* cell_cnt, const PrepArgs& pa);
 void launch_prep_f64(cudaStream_t st, bool one, const Work& w, int nblk, const double4* pos_q,
                      double4* fx64, int* cid, int* rank, int* cell_cnt, const PrepArgs& pa);
+// list_flag (nullable): the cell list is rebuilt only when *list_flag is set
+// (the scan then only clears the counts the prep kernel left).
 void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell, uint64_t* step_dev,
-                 const uint64_t* cur_step);
+                 const uint64_t* cur_step, const int* list_flag = nullptr);
 void launch_scatter(cudaStream_t st, int n, const int* cid, const int* rank,
-                    const int* cell_start, int* perm_tmp);
+                    const int* cell_start, int* perm_tmp, const int* list_flag = nullptr);
 void launch_order(cudaStream_t st, int n, const int* cid, const int* cell_start,
                   const int* perm_tmp, const uint4* fx, uint4* spos, const double4* fx64,
-                  double4* spos64, int* perm);
+                  double4* spos64, int* perm, const int* list_flag = nullptr,
+                  int* iperm = nullptr);
+
+// Neighbour-list build (rbe_real.cu): for every sorted particle the sorted
+// indices of the particles within r_c + skin among its 27 neighbour cells.
+struct ListArgs {
+    Work w;                  // tiles of kBlockP sorted particles
+    int nblk;
+    const int* list_flag;    // build only when set
+    const uint4* spos;
+    const int* cell_start;
+    int* nbr;                // [slot * stride + i]
+    int* ncnt;               // [i]
+    int stride, cap;
+    uint4* sref;             // copy of spos at the build
+    unsigned long long* stats;   // [0] builds, [1] largest count
+    int* err;
+};
+void launch_list_build(cudaStream_t st, bool one, const ListArgs& la);
 
 // Fourier part (rbe_fourier.cu).  The structure factors and the Fourier force
 // run over the unsorted fixed-point records (caller's order).
@@ -313,11 +343,20 @@ struct RealArgs {
     double4* md_pos64;
     double4* md_vel64;
     NhState* nh;             // MD steps: Nose-Hoover state per system
+    // neighbour-list MD step (k_real_list): tiles of kBlockP / lsplit sorted
+    // particles, lsplit lanes per particle
+    Work lw;
+    int nlblk, lsplit;
+    const int* nbr;
+    const int* ncnt;
+    int nbr_stride;
+    int* list_flag;          // cleared by the list kernel (consumed by this step)
     double2* blk_e;          // per block (E_coul, E_lj), nullable
     double2* blk_w;          // per block (W_coul, W_lj): pair virials r.F, nullable
 };
 void launch_real_mixed(cudaStream_t st, bool one, const RealArgs& a);
 void launch_real_f64(cudaStream_t st, bool one, const RealArgs& a);
+void launch_real_list(cudaStream_t st, bool one, const RealArgs& a);
 void launch_observables(cudaStream_t st, const SysDev& S, const uint4* fx, int first, int n,
                         const int4* mlist, int K, unsigned long long* rho_fx, double2* part,
                         const float4* pos_q, const float4* vel, const double* E_in,

@@ -565,6 +565,148 @@ k_real_seg(const __grid_constant__ RealArgs a) {
     }
 }
 
+// ----------------------------------------------------------- neighbour list
+// Verlet list of the MD step: the pairs within r_c + skin, rebuilt only when
+// some particle has moved more than skin/2 since the last build (the prep
+// kernel tests that), so every pair within r_c stays in the list between
+// builds.  Cells have side >= r_c + skin.
+
+// One thread per sorted particle: the 27 neighbour cells as 9 rows of three
+// x-adjacent cells (one row, once, with one cell per edge), every j != i whose
+// fixed-point minimum-image distance is within r_c + skin, in scan order.  The
+// record of the build is kept as the reference of the displacement test.
+template <bool ONE>
+__global__ void __launch_bounds__(kBlockP) k_list_build(const __grid_constant__ ListArgs la) {
+    if (!*la.list_flag) return;
+    const Tile tl = tile_of<ONE>(la.w);
+    const SysDev& S = sys_of<ONE>(la.w, tl.sys);
+    const int t = threadIdx.x;
+    int cnt = 0;
+    if (t < tl.count) {
+        const int i = tl.first + t;
+        const uint4 si = la.spos[i];
+        const int ncd = S.ncd;
+        const int cx = (int)(((unsigned long long)si.x * (unsigned long long)ncd) >> 32);
+        const int cy = (int)(((unsigned long long)si.y * (unsigned long long)ncd) >> 32);
+        const int cz = (int)(((unsigned long long)si.z * (unsigned long long)ncd) >> 32);
+        const float Lu = S.L_over_2_32, cut2 = S.f_list_cut2;
+        const int dlo = ncd < 3 ? 0 : -1, dhi = ncd < 3 ? 0 : 1;
+        int* out = la.nbr + i;
+        const size_t stride = (size_t)la.stride;
+        for (int dz = dlo; dz <= dhi; ++dz) {
+            for (int dy = dlo; dy <= dhi; ++dy) {
+                const int zz = wrapc(cz + dz, ncd), yy = wrapc(cy + dy, ncd);
+                int r0, e0, r1, e1;
+                row_ranges(la.cell_start, S.off_c + (zz * ncd + yy) * ncd, cx, ncd, r0, e0, r1, e1);
+                for (int part = 0; part < 2; ++part) {
+                    const int b = part ? r1 : r0, e = part ? e1 : e0;
+                    for (int j = b; j < e; ++j) {
+                        const uint4 sj = __ldg(la.spos + j);
+                        const float dx = (float)(int32_t)(sj.x - si.x) * Lu;
+                        const float dyy = (float)(int32_t)(sj.y - si.y) * Lu;
+                        const float dzz = (float)(int32_t)(sj.z - si.z) * Lu;
+                        const float r2 = fmaf(dx, dx, fmaf(dyy, dyy, dzz * dzz));
+                        if (r2 < cut2 && j != i) {
+                            if (cnt < la.cap) out[(size_t)cnt * stride] = j;
+                            ++cnt;
+                        }
+                    }
+                }
+            }
+        }
+        la.ncnt[i] = min(cnt, la.cap);
+        la.sref[i] = si;
+        if (cnt > la.cap) atomicOr(la.err, kErrList);
+    }
+    const unsigned wmax = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
+    if ((t & 31) == 0 && wmax) atomicMax(la.stats + 1, (unsigned long long)wmax);
+    if (blockIdx.x == 0 && t == 0) atomicAdd(la.stats, 1ull);
+}
+
+// The MD step's real-space pass over the list: R lanes per particle (adjacent
+// lanes) take every R-th entry of the particle's list and the pair terms of
+// those within the cutoffs (four gathers in flight per lane); the lanes' sums
+// are added, and one thread per particle applies the Fourier force and the
+// thermostat, as in the cell-scan pass.
+template <int R, bool ONE>
+__global__ void __launch_bounds__(kBlockP) k_real_list(const __grid_constant__ RealArgs a) {
+    constexpr int T = kBlockP / R;               // particles per block
+    const Tile tl = tile_of<ONE>(a.lw);
+    const int sys = tl.sys;
+    const SysDev& S = sys_of<ONE>(a.lw, sys);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.list_flag = 0;   // consumed by this step
+    const int p = threadIdx.x / R, l = threadIdx.x - p * R;
+    const bool do_real = (a.parts & kPartReal) != 0;
+    const bool do_lj = (a.parts & kPartLJ) != 0 && S.lj_eps != 0.0;
+    PairConst kc;
+    kc.rc2 = do_real ? S.f_rc2 : 0.f;
+    kc.lj_rc2 = do_lj ? S.f_lj_rc2 : 0.f;
+    kc.alpha = S.f_alpha;
+    kc.sa = S.f_sqrt_alpha;
+    kc.two_sa_spi = S.f_two_sa_spi;
+    kc.lB = S.f_lB;
+    kc.lj_s2 = S.f_lj_sigma2;
+    kc.lj_eps = S.f_lj_eps;
+    kc.lj_shift = S.f_lj_shift;
+    kc.vir = false;
+    PairAcc acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (p < tl.count && (do_real || do_lj)) {
+        const int i = tl.first + p;
+        const uint4 si = a.spos[i];
+        const float lbqi = kc.lB * __uint_as_float(si.w);
+        const float Lu = S.L_over_2_32;
+        const int cnt = __ldg(a.ncnt + i);
+        const int* nb = a.nbr + i;
+        const size_t st = (size_t)a.nbr_stride;
+        int k = l;
+        for (; k + 3 * R < cnt; k += 4 * R) {
+            const int j0 = __ldg(nb + (size_t)k * st);
+            const int j1 = __ldg(nb + (size_t)(k + R) * st);
+            const int j2 = __ldg(nb + (size_t)(k + 2 * R) * st);
+            const int j3 = __ldg(nb + (size_t)(k + 3 * R) * st);
+            const uint4 s0 = __ldg(a.spos + j0), s1 = __ldg(a.spos + j1);
+            const uint4 s2 = __ldg(a.spos + j2), s3 = __ldg(a.spos + j3);
+            pair_fixed(si, s0, Lu, lbqi, kc, acc);
+            pair_fixed(si, s1, Lu, lbqi, kc, acc);
+            pair_fixed(si, s2, Lu, lbqi, kc, acc);
+            pair_fixed(si, s3, Lu, lbqi, kc, acc);
+        }
+        for (; k < cnt; k += R) pair_fixed(si, __ldg(a.spos + __ldg(nb + (size_t)k * st)), Lu,
+                                           lbqi, kc, acc);
+    }
+    float fx = acc.fx, fy = acc.fy, fz = acc.fz;
+    if constexpr (R > 1) {
+#pragma unroll
+        for (int o = R / 2; o > 0; o >>= 1) {
+            fx += __shfl_down_sync(0xffffffffu, fx, o, R);
+            fy += __shfl_down_sync(0xffffffffu, fy, o, R);
+            fz += __shfl_down_sync(0xffffffffu, fz, o, R);
+        }
+        __shared__ float4 s_f[T];
+        if (p < tl.count && l == 0) s_f[p] = make_float4(fx, fy, fz, 0.f);
+        __syncthreads();
+        if ((int)threadIdx.x < tl.count) {
+            const float4 f = s_f[threadIdx.x];
+            fx = f.x; fy = f.y; fz = f.z;
+        }
+    }
+    // one thread per particle from here (thread t: particle t of the tile)
+    const bool nhm = a.md_pos && a.nh && S.thermostat == RBE_THERMO_NOSE_HOOVER;
+    unsigned long long k2 = 0ull;
+    if ((int)threadIdx.x < tl.count) {
+        const int i = tl.first + threadIdx.x;
+        const int o = a.perm[i];
+        if (a.parts & kPartFourier) {
+            const float4 f = a.fs[o];
+            fx += f.x; fy += f.y; fz += f.z;
+        }
+        if (a.F_out) a.F_out[o] = make_float4(fx, fy, fz, 0.f);
+        if (nhm) k2 = nose_hoover_update(a, S, a.nh[sys].f_va, a.nh[sys].f_vf, o, fx, fy, fz);
+        else if (a.md_pos) langevin_update(a, S, o, fx, fy, fz);
+    }
+    if (nhm) warp_add_u64(k2, &a.nh[sys].k2);
+}
+
 // ----------------------------------------------------------------- FP64
 template <int G, bool ONE>
 __global__ void __launch_bounds__(kBlockP)
@@ -850,6 +992,28 @@ void launch_real_mixed(cudaStream_t st, bool one, const RealArgs& a) {
         case 9: real_mixed_r<9>(st, one, a); break;
         default: real_mixed_r<1>(st, one, a); break;
     }
+}
+
+template <int R>
+static void real_list_r(cudaStream_t st, bool one, const RealArgs& a) {
+    if (one) k_real_list<R, true><<<a.nlblk, kBlockP, 0, st>>>(a);
+    else k_real_list<R, false><<<a.nlblk, kBlockP, 0, st>>>(a);
+}
+
+void launch_real_list(cudaStream_t st, bool one, const RealArgs& a) {
+    if (a.nlblk <= 0) return;
+    switch (a.lsplit) {
+        case 2: real_list_r<2>(st, one, a); break;
+        case 4: real_list_r<4>(st, one, a); break;
+        case 8: real_list_r<8>(st, one, a); break;
+        default: real_list_r<1>(st, one, a); break;
+    }
+}
+
+void launch_list_build(cudaStream_t st, bool one, const ListArgs& la) {
+    if (la.nblk <= 0) return;
+    if (one) k_list_build<true><<<la.nblk, kBlockP, 0, st>>>(la);
+    else k_list_build<false><<<la.nblk, kBlockP, 0, st>>>(la);
 }
 
 void launch_real_f64(cudaStream_t st, bool one, const RealArgs& a) {

@@ -50,6 +50,7 @@ class SystemParams:
                               # 2: Nose-Hoover leapfrog
     andersen_nu: float = 0.0  # Andersen collision frequency
     nh_tau: float = 0.0       # Nose-Hoover time constant (Q = 3 N kT tau^2)
+    skin: float = 0.0         # neighbour-list skin of the MD step (0: automatic, < 0: none)
 
 
 @dataclass

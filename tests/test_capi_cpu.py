@@ -34,13 +34,15 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_params_layout_matches_header():
-    assert ctypes.sizeof(capi.rbe_params) == 136
+    assert ctypes.sizeof(capi.rbe_params) == 144
     assert capi.rbe_params.seed.offset == 88
     assert capi.rbe_params.precision.offset == 108
     assert capi.rbe_params.andersen_nu.offset == 112
     assert capi.rbe_params.sampler.offset == 120
     assert capi.rbe_params.thermostat.offset == 124
     assert capi.rbe_params.nh_tau.offset == 128
+    assert capi.rbe_params.skin.offset == 136
+    assert ctypes.sizeof(capi.rbe_tuning) == 20
 
 
 def _create(lib, **kw):
@@ -66,6 +68,8 @@ def _create(lib, **kw):
     (dict(thermostat=3), "thermostat"),
     (dict(thermostat=2, nh_tau=0.0), "nh_tau"),
     (dict(thermostat=2, nh_tau=0.5, kT=0.0), "kT > 0"),
+    (dict(skin=float("nan")), "skin"),
+    (dict(skin=4.0), "skin must be <="),        # L/3 - r_c = 3.33 at L = 25, r_c = 5
     (dict(andersen_nu=-1.0), "andersen_nu"),
     (dict(andersen_nu=2000.0, dt=1e-3), "andersen_nu"),
 ])
@@ -82,6 +86,8 @@ def test_null_arguments_are_rejected(lib):
     assert lib.rbe_step(None, 0, None, None, 1, None) == capi.RBE_ERR_ARG
     assert lib.rbe_sync(None) == capi.RBE_ERR_ARG
     assert lib.rbe_nose_hoover_xi(None, None, 0) == capi.RBE_ERR_ARG
+    assert lib.rbe_list_stats(None, None, None, None) == capi.RBE_ERR_ARG
+    assert lib.rbe_step_ex(None, 0, None, None, 1, None, None) == capi.RBE_ERR_ARG
     lib.rbe_destroy(None)
     n = ctypes.c_int32(0)
     assert lib.rbe_create_batch(None, ctypes.byref(n), 0, None) == capi.RBE_ERR_ARG
