@@ -216,6 +216,8 @@ struct rbe_ctx {
     int* d_iperm = nullptr;
     int* d_list_flag = nullptr;
     unsigned long long* d_list_stats = nullptr;   // builds, largest count
+    float4* d_freal = nullptr;                // real-space force of a list step
+    cudaEvent_t ev_real = nullptr;            // list step: real-space pass done
     unsigned long long* d_qsum_fx = nullptr;  // sum q per system (fixed point)
     double2* d_blk_e = nullptr;
     double2* d_blk_w = nullptr;               // per real-space block (W_coul, W_lj)
@@ -624,6 +626,7 @@ rbe_status allocate(rbe_ctx* h) {
         RBE_ALLOC(h->d_iperm, N);
         RBE_ALLOC(h->d_list_flag, 1);
         RBE_ALLOC(h->d_list_stats, 2);
+        RBE_ALLOC(h->d_freal, N);
     }
     RBE_ALLOC(h->d_kab, h->ktot);
     RBE_ALLOC(h->d_qsum_fx, h->nsys);
@@ -689,6 +692,7 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_CUDA(h, cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking));
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_real, cudaEventDisableTiming));
     return RBE_OK;
 }
 
@@ -704,7 +708,7 @@ void release(rbe_ctx* h) {
                     h->d_cell_start, h->d_ksamp, h->d_rho_fx, h->d_kcnt, h->d_kab,
                     h->d_kcoef, h->d_mh_tq, h->d_mh_rho, h->d_mh_state, h->d_mh_pos, h->d_nh,
                     h->d_lblk, h->d_nbr, h->d_ncnt, h->d_sref, h->d_iperm, h->d_list_flag,
-                    h->d_list_stats,
+                    h->d_list_stats, h->d_freal,
                     h->d_qsum_fx, h->d_blk_e, h->d_blk_w, h->d_obs_m, h->d_obs_rho, h->d_obs_w,
                     h->d_obs_out, h->d_obs_part, h->d_blk_q, h->d_cur_step, h->d_stage_step,
                     h->d_err, h->d_stage_pos, h->d_stage_vel, h->d_stage_F, h->d_stage_E};
@@ -714,6 +718,7 @@ void release(rbe_ctx* h) {
     if (h->stream2) cudaStreamDestroy(h->stream2);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_real) cudaEventDestroy(h->ev_real);
     for (int k = 0; k < RBE_K_COUNT; ++k) {
         if (h->ev_beg[k]) cudaEventDestroy(h->ev_beg[k]);
         if (h->ev_end[k]) cudaEventDestroy(h->ev_end[k]);
@@ -875,12 +880,12 @@ void launch_rho(const rbe_ctx* h, cudaStream_t st, bool mixed) {
         launch_rho_f64(st, one, w, h->nchunks, ltiles, h->d_ksamp, h->d_fx64, h->d_rho_fx);
 }
 
-void launch_force(const rbe_ctx* h, cudaStream_t st, bool mixed) {
+void launch_force(const rbe_ctx* h, cudaStream_t st, bool mixed, const MdOut& md = MdOut{}) {
     const bool one = !h->batch;
     if (mixed) {
         const Work w = make_work(h, h->split == 1 ? h->d_pblk : h->d_fblk, kBlockP / h->split, 0);
         launch_fourier_force_mixed(st, one, w, h->split == 1 ? h->npblk : h->nfblk, h->split,
-                                   h->d_fx, h->d_ksamp, h->d_kab, h->d_fs);
+                                   h->d_fx, h->d_ksamp, h->d_kab, h->d_fs, md);
     } else {
         const Work w = make_work(h, h->d_pblk, kBlockP, 0);
         launch_fourier_force_f64(st, one, w, h->npblk, h->d_fx64, h->d_ksamp, h->d_rho_fx,
@@ -962,8 +967,10 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
         cudaEventRecord(h->ev_fork, st);
         cudaStreamWaitEvent(st2, h->ev_fork, 0);
         run(RBE_K_RHO, st2, [&] { launch_rho(h, st2, mixed); });
-        run(RBE_K_FOURIER_FORCE, st2, [&] { launch_force(h, st2, mixed); });
-        cudaEventRecord(h->ev_join, st2);
+        if (!a.list) {
+            run(RBE_K_FOURIER_FORCE, st2, [&] { launch_force(h, st2, mixed); });
+            cudaEventRecord(h->ev_join, st2);
+        }
     }
     run(RBE_K_SCAN, st, [&] {
         launch_scan(st, h->d_cell_cnt, h->d_cell_start, h->ncell, a.step_dev, h->d_cur_step,
@@ -994,7 +1001,7 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
             la.err = h->d_err;
             launch_list_build(st, one, la);
         });
-    if (fourier) cudaStreamWaitEvent(st, h->ev_join, 0);
+    if (fourier && !a.list) cudaStreamWaitEvent(st, h->ev_join, 0);
     RealArgs r = make_real_args(h, a.parts);
     r.F_out = a.F;
     r.phi_out = a.phi;
@@ -1015,12 +1022,27 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
         r.ncnt = h->d_ncnt;
         r.nbr_stride = std::max(h->ntot, 1);
         r.list_flag = h->d_list_flag;
+        r.freal = h->d_freal;
+        // the real-space pass (concurrent with the structure factors), then
+        // the Fourier force, which adds it and applies the thermostat
+        run(RBE_K_REAL, st, [&] { launch_real_list(st, one, r); });
+        cudaEventRecord(h->ev_real, st);
+        cudaStreamWaitEvent(st2, h->ev_real, 0);
+        MdOut md;
+        md.freal = h->d_freal;
+        md.F_out = a.F;
+        md.md_pos = a.md_pos;
+        md.md_vel = a.md_vel;
+        md.nh = pa.nh;
+        md.cur_step = h->d_cur_step;
+        run(RBE_K_FOURIER_FORCE, st2, [&] { launch_force(h, st2, true, md); });
+        cudaEventRecord(h->ev_join, st2);
+        cudaStreamWaitEvent(st, h->ev_join, 0);
+    } else {
+        run(RBE_K_REAL, st, [&] {
+            if (mixed) launch_real_mixed(st, one, r); else launch_real_f64(st, one, r);
+        });
     }
-    run(RBE_K_REAL, st, [&] {
-        if (a.list) launch_real_list(st, one, r);
-        else if (mixed) launch_real_mixed(st, one, r);
-        else launch_real_f64(st, one, r);
-    });
     if (a.E)
         run(RBE_K_ENERGY, st, [&] {
             launch_energy(st, one, make_work(h, nullptr, 0, 0), h->nsys, h->d_ksamp, h->d_rho_fx,
@@ -1028,7 +1050,7 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
                           r.blk_w ? a.W : nullptr);
         });
     if (prof) {
-        cudaEventSynchronize(h->ev_end[a.E ? RBE_K_ENERGY : RBE_K_REAL]);
+        cudaStreamSynchronize(st);                      // every branch has joined st
         for (int k = 0; k < RBE_K_COUNT; ++k) {
             if (!used[k]) continue;
             float ms = 0.f;
@@ -1572,6 +1594,7 @@ rbe_status rbe_autotune(rbe_handle h, int32_t n, const float* pos_q, rbe_tuning*
             r.ncnt = h->d_ncnt;
             r.nbr_stride = std::max(h->ntot, 1);
             r.list_flag = h->d_list_flag;
+            r.freal = h->d_freal;
             const float t = time_kernel(h, e0, e1, [&] { launch_real_list(h->stream, !h->batch, r); });
             if (t < best) { best = t; best_lsplit = ls; }
         }

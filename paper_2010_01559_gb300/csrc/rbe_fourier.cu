@@ -157,7 +157,7 @@ template <int SPLIT, bool ONE>
 __global__ void __launch_bounds__(kBlockP)
 k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
               const int4* __restrict__ ksamp, const float2* __restrict__ kab,
-              float4* __restrict__ fs) {
+              float4* __restrict__ fs, const __grid_constant__ MdOut md) {
     constexpr int kKT = 256;                        // wave vectors staged per pass
     __shared__ KPhase kp[kKT];
     __shared__ KForce kf[kKT];
@@ -205,11 +205,38 @@ k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
         fz += __shfl_down_sync(0xffffffffu, fz, o, SPLIT);
         ph += __shfl_down_sync(0xffffffffu, ph, o, SPLIT);
     }
+    if (!md.freal) {
+        if (active && sub == 0) {
+            const float q = __uint_as_float(p.w);
+            const float sc = -q * (float)(2.0 * M_PI) * S.f_invL;
+            fs[i] = make_float4(sc * fx, sc * fy, sc * fz, ph);
+        }
+        return;
+    }
+    // neighbour-list MD step: the total force and the thermostat, one thread
+    // per particle (thread t: particle t of the tile)
+    __shared__ float4 s_t[kBlockP / SPLIT];
     if (active && sub == 0) {
         const float q = __uint_as_float(p.w);
         const float sc = -q * (float)(2.0 * M_PI) * S.f_invL;
-        fs[i] = make_float4(sc * fx, sc * fy, sc * fz, ph);
+        s_t[t] = make_float4(sc * fx, sc * fy, sc * fz, 0.f);
     }
+    __syncthreads();
+    const bool nhm = md.md_pos && md.nh && S.thermostat == RBE_THERMO_NOSE_HOOVER;
+    unsigned long long k2 = 0ull;
+    if ((int)threadIdx.x < tl.count) {
+        const int o = tl.first + threadIdx.x;
+        const float4 fr = md.freal[o];
+        const float4 ff = s_t[threadIdx.x];
+        const float Fx = fr.x + ff.x, Fy = fr.y + ff.y, Fz = fr.z + ff.z;
+        if (md.F_out) md.F_out[o] = make_float4(Fx, Fy, Fz, 0.f);
+        if (nhm)
+            k2 = nose_hoover_update(md.md_pos, md.md_vel, S, md.nh[tl.sys].f_va,
+                                    md.nh[tl.sys].f_vf, o, Fx, Fy, Fz);
+        else if (md.md_pos)
+            langevin_update(md.md_pos, md.md_vel, md.cur_step, S, o, Fx, Fy, Fz);
+    }
+    if (nhm) warp_add_u64(k2, &md.nh[tl.sys].k2);
 }
 
 // ----------------------------------------------------------------- force (FP64)
@@ -289,22 +316,23 @@ void launch_rho_f64(cudaStream_t st, bool one, const Work& w, int nchunks, int l
 
 template <int SPLIT>
 static void force_mixed_split(cudaStream_t st, bool one, const Work& w, int nblk, const uint4* fx,
-                              const int4* ksamp, const float2* kab, float4* fs) {
+                              const int4* ksamp, const float2* kab, float4* fs,
+                              const MdOut& md) {
     if (one)
-        k_force_mixed<SPLIT, true><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, kab, fs);
+        k_force_mixed<SPLIT, true><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, kab, fs, md);
     else
-        k_force_mixed<SPLIT, false><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, kab, fs);
+        k_force_mixed<SPLIT, false><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, kab, fs, md);
 }
 
 void launch_fourier_force_mixed(cudaStream_t st, bool one, const Work& w, int nblk, int split,
                                 const uint4* fx, const int4* ksamp, const float2* kab,
-                                float4* fs) {
+                                float4* fs, const MdOut& md) {
     if (nblk <= 0) return;
     switch (split) {
-        case 2: force_mixed_split<2>(st, one, w, nblk, fx, ksamp, kab, fs); break;
-        case 4: force_mixed_split<4>(st, one, w, nblk, fx, ksamp, kab, fs); break;
-        case 8: force_mixed_split<8>(st, one, w, nblk, fx, ksamp, kab, fs); break;
-        default: force_mixed_split<1>(st, one, w, nblk, fx, ksamp, kab, fs); break;
+        case 2: force_mixed_split<2>(st, one, w, nblk, fx, ksamp, kab, fs, md); break;
+        case 4: force_mixed_split<4>(st, one, w, nblk, fx, ksamp, kab, fs, md); break;
+        case 8: force_mixed_split<8>(st, one, w, nblk, fx, ksamp, kab, fs, md); break;
+        default: force_mixed_split<1>(st, one, w, nblk, fx, ksamp, kab, fs, md); break;
     }
 }
 

@@ -114,6 +114,97 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     return c;
 }
 
+// ------------------------------------------------- MD update (Sec. 3.3)
+// The step's last stage, run by whichever kernel holds a particle's total
+// force: the Langevin, Andersen or Nose-Hoover update of its velocity and
+// position (caller index o).
+//
+// Drift r += dt v and wrap into [0, L).
+__device__ __forceinline__ void drift_wrap(const SysDev& S, const float4& v, float4& rp) {
+    const float L = S.Lf, invL = S.f_invL, dt = S.f_dt;
+    rp.x = fmaf(dt, v.x, rp.x); rp.x -= L * floorf(rp.x * invL);
+    rp.y = fmaf(dt, v.y, rp.y); rp.y -= L * floorf(rp.y * invL);
+    rp.z = fmaf(dt, v.z, rp.z); rp.z -= L * floorf(rp.z * invL);
+    // a coordinate just below 0 can round up to exactly L: that is 0
+    if (rp.x >= L) rp.x = 0.f;
+    if (rp.y >= L) rp.y = 0.f;
+    if (rp.z >= L) rp.z = 0.f;
+}
+
+// Nose-Hoover leapfrog step for particle o: v <- va v + vf F (the friction
+// taken half before and half after the kick), drift, wrap.  Returns m|v|^2/kT
+// in 64-bit fixed point (2^-32) for the kinetic sum of the step.
+__device__ __forceinline__ unsigned long long nose_hoover_update(float4* md_pos, float4* md_vel,
+                                                                 const SysDev& S, float va,
+                                                                 float vf, int o, float fx,
+                                                                 float fy, float fz) {
+    float4 v = md_vel[o];
+    float4 rp = md_pos[o];
+    v.x = fmaf(va, v.x, vf * fx);
+    v.y = fmaf(va, v.y, vf * fy);
+    v.z = fmaf(va, v.z, vf * fz);
+    drift_wrap(S, v, rp);
+    md_vel[o] = v;
+    md_pos[o] = rp;
+    const float v2 = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z));
+    return __double2ull_rn((double)v2 * S.nh_k2scale);
+}
+
+// Sum of a 64-bit value over the warp, added by lane 0 to *dst.
+__device__ __forceinline__ void warp_add_u64(unsigned long long v, unsigned long long* dst) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
+
+// Langevin step of Sec. 3.3 for particle o (caller index) with total force F:
+// kick, exact Ornstein-Uhlenbeck with Philox/Box-Muller normals, drift, wrap.
+__device__ __forceinline__ void langevin_update(float4* md_pos, float4* md_vel,
+                                                const uint64_t* cur_step, const SysDev& S, int o,
+                                                float fx, float fy, float fz) {
+    const uint64_t step = *cur_step;
+    const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
+    const uint32_t pid = (uint32_t)(o - S.off_p);
+    const bool andersen = S.thermostat == RBE_THERMO_ANDERSEN;
+    // Langevin: normals of the OU step; Andersen: collision word, then normals
+    const uint4 c = philox4x32_10(make_uint4(pid, 0u, (uint32_t)step,
+                                             (S.stream << 8) | (andersen ? 0x07u : 0x02u)), key);
+    const bool hit = andersen && (uint64_t)c.x < S.andersen_thr;
+    float4 v = md_vel[o];
+    float4 rp = md_pos[o];
+    const float dtm = S.f_dt_over_m;
+    v.x = fmaf(dtm, fx, v.x);
+    v.y = fmaf(dtm, fy, v.y);
+    v.z = fmaf(dtm, fz, v.z);
+    float xi0 = 0.f, xi1 = 0.f, xi2 = 0.f;
+    if (!andersen || hit) {
+        const uint4 w = andersen ? philox4x32_10(make_uint4(pid, 1u, (uint32_t)step,
+                                                            (S.stream << 8) | 0x07u), key)
+                                 : c;
+        const float u1 = (float)((w.x >> 8) + 1u) * 5.9604644775390625e-08f;   // (0, 1]
+        const float u2 = (float)(w.y >> 8) * 5.9604644775390625e-08f;          // [0, 1)
+        const float u3 = (float)((w.z >> 8) + 1u) * 5.9604644775390625e-08f;
+        const float u4 = (float)(w.w >> 8) * 5.9604644775390625e-08f;
+        const float r1 = sqrtf(-2.f * logf(u1)), r3 = sqrtf(-2.f * logf(u3));
+        float s2, c2v, s4, c4;
+        sincospif(2.f * u2, &s2, &c2v);
+        sincospif(2.f * u4, &s4, &c4);
+        xi0 = r1 * c2v; xi1 = r1 * s2; xi2 = r3 * c4;
+    }
+    if (!andersen) {                                   // exact Ornstein-Uhlenbeck step
+        const float c1 = S.f_c1, c2 = S.f_c2;
+        v.x = fmaf(c1, v.x, c2 * xi0);
+        v.y = fmaf(c1, v.y, c2 * xi1);
+        v.z = fmaf(c1, v.z, c2 * xi2);
+    }
+    drift_wrap(S, v, rp);
+    if (hit) {                                         // Andersen collision after the drift
+        const float sd = S.f_vsd;
+        v.x = sd * xi0; v.y = sd * xi1; v.z = sd * xi2;
+    }
+    md_vel[o] = v;
+    md_pos[o] = rp;
+}
+
 // Where a kernel finds its tile of work and its system.  Batch handles pass
 // tables (tiles[blockIdx.x], then sysv[tile.sys]); single-system handles pass
 // the system's constants by value and the tile size, so a block finds both
@@ -296,9 +387,19 @@ void launch_rho_mixed(cudaStream_t st, bool one, const Work& w, int nchunks, int
                       unsigned long long* rho_fx, int* kcnt, float2* kab);
 void launch_rho_f64(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
                     const int4* ksamp, const double4* fx64, unsigned long long* rho_fx);
+// The last stage of a neighbour-list MD step, run by the Fourier-force
+// kernel: total force = Fourier + freal, then the thermostat.
+struct MdOut {
+    const float4* freal;     // real-space force, caller's order (null: no MD stage)
+    float4* F_out;           // nullable: total force
+    float4* md_pos;          // nullable: positions / velocities updated in place
+    float4* md_vel;
+    NhState* nh;
+    const uint64_t* cur_step;
+};
 void launch_fourier_force_mixed(cudaStream_t st, bool one, const Work& w, int nblk, int split,
                                 const uint4* fx, const int4* ksamp, const float2* kab,
-                                float4* fs);
+                                float4* fs, const MdOut& md = MdOut{});
 void launch_fourier_force_f64(cudaStream_t st, bool one, const Work& w, int nblk,
                               const double4* fx64, const int4* ksamp,
                               const unsigned long long* rho_fx, double4* fs64);
@@ -351,6 +452,7 @@ struct RealArgs {
     const int* ncnt;
     int nbr_stride;
     int* list_flag;          // cleared by the list kernel (consumed by this step)
+    float4* freal;           // list kernel output: real-space force, caller's order
     double2* blk_e;          // per block (E_coul, E_lj), nullable
     double2* blk_w;          // per block (W_coul, W_lj): pair virials r.F, nullable
 };

@@ -170,91 +170,6 @@ __device__ __forceinline__ int row_of(int l, int j) {
     }
 }
 
-// Drift r += dt v and wrap into [0, L).
-__device__ __forceinline__ void drift_wrap(const SysDev& S, const float4& v, float4& rp) {
-    const float L = S.Lf, invL = S.f_invL, dt = S.f_dt;
-    rp.x = fmaf(dt, v.x, rp.x); rp.x -= L * floorf(rp.x * invL);
-    rp.y = fmaf(dt, v.y, rp.y); rp.y -= L * floorf(rp.y * invL);
-    rp.z = fmaf(dt, v.z, rp.z); rp.z -= L * floorf(rp.z * invL);
-    // a coordinate just below 0 can round up to exactly L: that is 0
-    if (rp.x >= L) rp.x = 0.f;
-    if (rp.y >= L) rp.y = 0.f;
-    if (rp.z >= L) rp.z = 0.f;
-}
-
-// Nose-Hoover leapfrog step for particle o: v <- va v + vf F (the friction
-// taken half before and half after the kick), drift, wrap.  Returns m|v|^2/kT
-// in 64-bit fixed point (2^-32) for the kinetic sum of the step.
-__device__ __forceinline__ unsigned long long nose_hoover_update(const RealArgs& a,
-                                                                 const SysDev& S, float va,
-                                                                 float vf, int o, float fx,
-                                                                 float fy, float fz) {
-    float4 v = a.md_vel[o];
-    float4 rp = a.md_pos[o];
-    v.x = fmaf(va, v.x, vf * fx);
-    v.y = fmaf(va, v.y, vf * fy);
-    v.z = fmaf(va, v.z, vf * fz);
-    drift_wrap(S, v, rp);
-    a.md_vel[o] = v;
-    a.md_pos[o] = rp;
-    const float v2 = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z));
-    return __double2ull_rn((double)v2 * S.nh_k2scale);
-}
-
-// Sum of a 64-bit value over the warp, added by lane 0 to *dst.
-__device__ __forceinline__ void warp_add_u64(unsigned long long v, unsigned long long* dst) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
-}
-
-// Langevin step of Sec. 3.3 for particle o (caller index) with total force F:
-// kick, exact Ornstein-Uhlenbeck with Philox/Box-Muller normals, drift, wrap.
-__device__ __forceinline__ void langevin_update(const RealArgs& a, const SysDev& S, int o,
-                                                float fx, float fy, float fz) {
-    const uint64_t step = *a.cur_step;
-    const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
-    const uint32_t pid = (uint32_t)(o - S.off_p);
-    const bool andersen = S.thermostat == RBE_THERMO_ANDERSEN;
-    // Langevin: normals of the OU step; Andersen: collision word, then normals
-    const uint4 c = philox4x32_10(make_uint4(pid, 0u, (uint32_t)step,
-                                             (S.stream << 8) | (andersen ? 0x07u : 0x02u)), key);
-    const bool hit = andersen && (uint64_t)c.x < S.andersen_thr;
-    float4 v = a.md_vel[o];
-    float4 rp = a.md_pos[o];
-    const float dtm = S.f_dt_over_m;
-    v.x = fmaf(dtm, fx, v.x);
-    v.y = fmaf(dtm, fy, v.y);
-    v.z = fmaf(dtm, fz, v.z);
-    float xi0 = 0.f, xi1 = 0.f, xi2 = 0.f;
-    if (!andersen || hit) {
-        const uint4 w = andersen ? philox4x32_10(make_uint4(pid, 1u, (uint32_t)step,
-                                                            (S.stream << 8) | 0x07u), key)
-                                 : c;
-        const float u1 = (float)((w.x >> 8) + 1u) * 5.9604644775390625e-08f;   // (0, 1]
-        const float u2 = (float)(w.y >> 8) * 5.9604644775390625e-08f;          // [0, 1)
-        const float u3 = (float)((w.z >> 8) + 1u) * 5.9604644775390625e-08f;
-        const float u4 = (float)(w.w >> 8) * 5.9604644775390625e-08f;
-        const float r1 = sqrtf(-2.f * logf(u1)), r3 = sqrtf(-2.f * logf(u3));
-        float s2, c2v, s4, c4;
-        sincospif(2.f * u2, &s2, &c2v);
-        sincospif(2.f * u4, &s4, &c4);
-        xi0 = r1 * c2v; xi1 = r1 * s2; xi2 = r3 * c4;
-    }
-    if (!andersen) {                                   // exact Ornstein-Uhlenbeck step
-        const float c1 = S.f_c1, c2 = S.f_c2;
-        v.x = fmaf(c1, v.x, c2 * xi0);
-        v.y = fmaf(c1, v.y, c2 * xi1);
-        v.z = fmaf(c1, v.z, c2 * xi2);
-    }
-    drift_wrap(S, v, rp);
-    if (hit) {                                         // Andersen collision after the drift
-        const float sd = S.f_vsd;
-        v.x = sd * xi0; v.y = sd * xi1; v.z = sd * xi2;
-    }
-    a.md_vel[o] = v;
-    a.md_pos[o] = rp;
-}
-
 // Corner of cell c along an axis, floor(c 2^32 / ncd), from the system's
 // quotient and remainder of 2^32 / ncd (c = ncd wraps to 0).  Every fixed-point
 // coordinate of cell c lies in [corner(c), corner(c + 1)), so integer
@@ -548,8 +463,8 @@ k_real_seg(const __grid_constant__ RealArgs a) {
             }
             if (a.F_out) a.F_out[o] = make_float4(fx, fy, fz, 0.f);
             if (want_phi) a.phi_out[o] = phi;
-            if (nhm) k2 = nose_hoover_update(a, S, nh_va, nh_vf, o, fx, fy, fz);
-            else if (a.md_pos) langevin_update(a, S, o, fx, fy, fz);
+            if (nhm) k2 = nose_hoover_update(a.md_pos, a.md_vel, S, nh_va, nh_vf, o, fx, fy, fz);
+            else if (a.md_pos) langevin_update(a.md_pos, a.md_vel, a.cur_step, S, o, fx, fy, fz);
         }
         if (nhm) warp_add_u64(k2, &a.nh[sys].k2);
         __syncthreads();
@@ -626,14 +541,14 @@ __global__ void __launch_bounds__(kBlockP) k_list_build(const __grid_constant__ 
 // The MD step's real-space pass over the list: R lanes per particle (adjacent
 // lanes) take every R-th entry of the particle's list and the pair terms of
 // those within the cutoffs (four gathers in flight per lane); the lanes' sums
-// are added, and one thread per particle applies the Fourier force and the
-// thermostat, as in the cell-scan pass.
+// are added and stored per particle.  It needs nothing from the Fourier part,
+// so it runs concurrently with the structure factors; the Fourier-force
+// kernel then completes the step.
 template <int R, bool ONE>
 __global__ void __launch_bounds__(kBlockP) k_real_list(const __grid_constant__ RealArgs a) {
     constexpr int T = kBlockP / R;               // particles per block
     const Tile tl = tile_of<ONE>(a.lw);
-    const int sys = tl.sys;
-    const SysDev& S = sys_of<ONE>(a.lw, sys);
+    const SysDev& S = sys_of<ONE>(a.lw, tl.sys);
     if (blockIdx.x == 0 && threadIdx.x == 0) *a.list_flag = 0;   // consumed by this step
     const int p = threadIdx.x / R, l = threadIdx.x - p * R;
     const bool do_real = (a.parts & kPartReal) != 0;
@@ -690,21 +605,10 @@ __global__ void __launch_bounds__(kBlockP) k_real_list(const __grid_constant__ R
             fx = f.x; fy = f.y; fz = f.z;
         }
     }
-    // one thread per particle from here (thread t: particle t of the tile)
-    const bool nhm = a.md_pos && a.nh && S.thermostat == RBE_THERMO_NOSE_HOOVER;
-    unsigned long long k2 = 0ull;
-    if ((int)threadIdx.x < tl.count) {
-        const int i = tl.first + threadIdx.x;
-        const int o = a.perm[i];
-        if (a.parts & kPartFourier) {
-            const float4 f = a.fs[o];
-            fx += f.x; fy += f.y; fz += f.z;
-        }
-        if (a.F_out) a.F_out[o] = make_float4(fx, fy, fz, 0.f);
-        if (nhm) k2 = nose_hoover_update(a, S, a.nh[sys].f_va, a.nh[sys].f_vf, o, fx, fy, fz);
-        else if (a.md_pos) langevin_update(a, S, o, fx, fy, fz);
-    }
-    if (nhm) warp_add_u64(k2, &a.nh[sys].k2);
+    // the real-space force in the caller's order, for the Fourier-force
+    // kernel that adds its part and applies the thermostat
+    if ((int)threadIdx.x < tl.count)
+        a.freal[a.perm[tl.first + threadIdx.x]] = make_float4(fx, fy, fz, 0.f);
 }
 
 // ----------------------------------------------------------------- FP64
