@@ -305,8 +305,7 @@ enum {
     RBE_K_ENERGY = 8,        /* FP64 energy reduction                               */
     RBE_K_LIST_BUILD = 9,    /* neighbour-list build (list MD steps; returns at once
                                 when no particle moved beyond skin/2)             */
-    RBE_K_CELL_COUNT = 10,   /* cell ids and counts of a list rebuild              */
-    RBE_K_COUNT = 11
+    RBE_K_COUNT = 10
 };
 
 /* Enable (1) or disable (0) per-kernel timing.  While enabled, rbe_forces*,
@@ -320,9 +319,7 @@ rbe_status rbe_profile(rbe_handle h, int32_t enable);
 rbe_status rbe_profile_read(rbe_handle h, double *ms, int64_t *launches);
 
 /* Kernels launched through h since it was created (graph replays count the
- * kernels of the replayed step; a neighbour-list rebuild inside a replay runs
- * as a conditional body of five kernels, counted on the device, so this call
- * synchronises h's stream when the handle keeps a list). */
+ * kernels of the replayed step). */
 rbe_status rbe_launch_count(rbe_handle h, int64_t *count);
 
 /* True (non-random) energy and pressure of a configuration, the observables

@@ -98,7 +98,7 @@ _SIGS = {
 
 #: kernel names in RBE_K_* order
 KERNELS = ("prep", "scan", "scatter", "cell_order", "rho", "finalize", "fourier_force",
-           "real", "energy", "list_build", "cell_count")
+           "real", "energy", "list_build")
 
 #: every symbol include/rbe.h declares
 EXPORTED = tuple(_SIGS)

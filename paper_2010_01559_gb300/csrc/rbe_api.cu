@@ -217,8 +217,6 @@ struct rbe_ctx {
     int* d_list_flag = nullptr;
     unsigned long long* d_list_stats = nullptr;   // builds, largest count
     float4* d_freal = nullptr;                // real-space force of a list step
-    int* d_prep_done = nullptr;               // prep blocks done (conditional handoff)
-    cudaStream_t body_stream = nullptr;       // captures conditional graph bodies
     cudaEvent_t ev_real = nullptr;            // list step: real-space pass done
     unsigned long long* d_qsum_fx = nullptr;  // sum q per system (fixed point)
     double2* d_blk_e = nullptr;
@@ -627,9 +625,8 @@ rbe_status allocate(rbe_ctx* h) {
         RBE_ALLOC(h->d_sref, N);
         RBE_ALLOC(h->d_iperm, N);
         RBE_ALLOC(h->d_list_flag, 1);
-        RBE_ALLOC(h->d_list_stats, 3);       // builds, largest count, graph rebuild runs
+        RBE_ALLOC(h->d_list_stats, 2);
         RBE_ALLOC(h->d_freal, N);
-        RBE_ALLOC(h->d_prep_done, 1);
     }
     RBE_ALLOC(h->d_kab, h->ktot);
     RBE_ALLOC(h->d_qsum_fx, h->nsys);
@@ -651,8 +648,7 @@ rbe_status allocate(rbe_ctx* h) {
         RBE_CUDA(h, cudaMemset(h->d_iperm, 0, sizeof(int) * N));
         RBE_CUDA(h, cudaMemset(h->d_ncnt, 0, sizeof(int) * N));
         RBE_CUDA(h, cudaMemset(h->d_sref, 0, sizeof(uint4) * N));
-        RBE_CUDA(h, cudaMemset(h->d_list_stats, 0, sizeof(unsigned long long) * 3));
-        RBE_CUDA(h, cudaMemset(h->d_prep_done, 0, sizeof(int)));
+        RBE_CUDA(h, cudaMemset(h->d_list_stats, 0, sizeof(unsigned long long) * 2));
         const int one = 1;
         RBE_CUDA(h, cudaMemcpy(h->d_list_flag, &one, sizeof(int), cudaMemcpyHostToDevice));
     }
@@ -697,7 +693,6 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_real, cudaEventDisableTiming));
-    RBE_CUDA(h, cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking));
     return RBE_OK;
 }
 
@@ -713,7 +708,7 @@ void release(rbe_ctx* h) {
                     h->d_cell_start, h->d_ksamp, h->d_rho_fx, h->d_kcnt, h->d_kab,
                     h->d_kcoef, h->d_mh_tq, h->d_mh_rho, h->d_mh_state, h->d_mh_pos, h->d_nh,
                     h->d_lblk, h->d_nbr, h->d_ncnt, h->d_sref, h->d_iperm, h->d_list_flag,
-                    h->d_list_stats, h->d_freal, h->d_prep_done,
+                    h->d_list_stats, h->d_freal,
                     h->d_qsum_fx, h->d_blk_e, h->d_blk_w, h->d_obs_m, h->d_obs_rho, h->d_obs_w,
                     h->d_obs_out, h->d_obs_part, h->d_blk_q, h->d_cur_step, h->d_stage_step,
                     h->d_err, h->d_stage_pos, h->d_stage_vel, h->d_stage_F, h->d_stage_E};
@@ -724,7 +719,6 @@ void release(rbe_ctx* h) {
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->ev_real) cudaEventDestroy(h->ev_real);
-    if (h->body_stream) cudaStreamDestroy(h->body_stream);
     for (int k = 0; k < RBE_K_COUNT; ++k) {
         if (h->ev_beg[k]) cudaEventDestroy(h->ev_beg[k]);
         if (h->ev_end[k]) cudaEventDestroy(h->ev_end[k]);
@@ -959,23 +953,6 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
         h->list_valid = false;              // the sorted arrays are about to change
     }
     const int* lflag = a.list ? h->d_list_flag : nullptr;
-    // capturing a list step into a graph: a conditional node will run the rebuild
-    cudaGraph_t cap_graph = nullptr;
-    bool cond = false;
-    if (a.list) {
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        if (cudaStreamGetCaptureInfo(st, &cs, nullptr, &cap_graph, nullptr, nullptr, nullptr) ==
-                cudaSuccess && cs == cudaStreamCaptureStatusActive) {
-            cudaGraphConditionalHandle ch{};
-            if (cudaGraphConditionalHandleCreate(&ch, cap_graph, 0, cudaGraphCondAssignDefault) ==
-                cudaSuccess) {
-                cond = true;
-                pa.use_cond = 1;
-                pa.cond = ch;
-                pa.done = h->d_prep_done;
-            }
-        }
-    }
     if (want_q)
         cudaMemsetAsync(h->d_qsum_fx, 0, sizeof(unsigned long long) * h->nsys, st);
     run(RBE_K_PREP, st, [&] {
@@ -995,73 +972,35 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
             cudaEventRecord(h->ev_join, st2);
         }
     }
-    // the cell list (and, for a list step, the neighbour list): counts, scan,
-    // scatter, canonical order, list build
-    auto rebuild = [&](cudaStream_t s, bool counted, unsigned long long* graph_runs) {
-        auto go = [&](int kid, auto&& launch) {
-            if (counted) run(kid, s, launch); else launch();
-        };
-        if (a.list)
-            go(RBE_K_CELL_COUNT, [&] {
-                launch_cell_count(s, one, wp, h->npblk, h->d_fx, h->d_cid, h->d_rank,
-                                  h->d_cell_cnt, lflag, graph_runs);
-            });
-        go(RBE_K_SCAN, [&] {
-            launch_scan(s, h->d_cell_cnt, h->d_cell_start, h->ncell,
-                        a.list ? nullptr : a.step_dev, h->d_cur_step, lflag);
+    run(RBE_K_SCAN, st, [&] {
+        launch_scan(st, h->d_cell_cnt, h->d_cell_start, h->ncell, a.step_dev, h->d_cur_step,
+                    lflag);
+    });
+    run(RBE_K_SCATTER, st, [&] {
+        launch_scatter(st, n, h->d_cid, h->d_rank, h->d_cell_start, h->d_perm_tmp, lflag);
+    });
+    run(RBE_K_CELL_ORDER, st, [&] {
+        launch_order(st, n, h->d_cid, h->d_cell_start, h->d_perm_tmp, mixed ? h->d_fx : nullptr,
+                     h->d_spos, mixed ? nullptr : h->d_fx64, h->d_spos64, h->d_perm, lflag,
+                     a.list ? h->d_iperm : nullptr);
+    });
+    if (a.list)
+        run(RBE_K_LIST_BUILD, st, [&] {
+            ListArgs la{};
+            la.w = make_work(h, h->d_pblk, kBlockP, 0);
+            la.nblk = h->npblk;
+            la.list_flag = h->d_list_flag;
+            la.spos = h->d_spos;
+            la.cell_start = h->d_cell_start;
+            la.nbr = h->d_nbr;
+            la.ncnt = h->d_ncnt;
+            la.stride = std::max(h->ntot, 1);
+            la.cap = h->list_cap;
+            la.sref = h->d_sref;
+            la.stats = h->d_list_stats;
+            la.err = h->d_err;
+            launch_list_build(st, one, la);
         });
-        go(RBE_K_SCATTER, [&] {
-            launch_scatter(s, n, h->d_cid, h->d_rank, h->d_cell_start, h->d_perm_tmp, lflag);
-        });
-        go(RBE_K_CELL_ORDER, [&] {
-            launch_order(s, n, h->d_cid, h->d_cell_start, h->d_perm_tmp,
-                         mixed ? h->d_fx : nullptr, h->d_spos, mixed ? nullptr : h->d_fx64,
-                         h->d_spos64, h->d_perm, lflag, a.list ? h->d_iperm : nullptr);
-        });
-        if (a.list)
-            go(RBE_K_LIST_BUILD, [&] {
-                ListArgs la{};
-                la.w = make_work(h, h->d_pblk, kBlockP, 0);
-                la.nblk = h->npblk;
-                la.list_flag = h->d_list_flag;
-                la.spos = h->d_spos;
-                la.cell_start = h->d_cell_start;
-                la.nbr = h->d_nbr;
-                la.ncnt = h->d_ncnt;
-                la.stride = std::max(h->ntot, 1);
-                la.cap = h->list_cap;
-                la.sref = h->d_sref;
-                la.stats = h->d_list_stats;
-                la.err = h->d_err;
-                launch_list_build(s, one, la);
-            });
-    };
-    if (cond) {
-        // graph capture: the rebuild is the body of a conditional node after
-        // the prep kernel, which sets the condition; steps without a rebuild
-        // launch none of it
-        cudaStreamCaptureStatus cs2 = cudaStreamCaptureStatusNone;
-        const cudaGraphNode_t* deps = nullptr;
-        size_t nd = 0;
-        cudaStreamGetCaptureInfo(st, &cs2, nullptr, &cap_graph, &deps, nullptr, &nd);
-        cudaGraphNodeParams np{};
-        np.type = cudaGraphNodeTypeConditional;
-        np.conditional.handle = pa.cond;
-        np.conditional.type = cudaGraphCondTypeIf;
-        np.conditional.size = 1;
-        cudaGraphNode_t node = nullptr;
-        cudaGraphAddNode(&node, cap_graph, deps, nullptr, nd, &np);
-        cudaGraph_t body = np.conditional.phGraph_out[0];
-        cudaStreamBeginCaptureToGraph(h->body_stream, body, nullptr, nullptr, 0,
-                                      cudaStreamCaptureModeThreadLocal);
-        rebuild(h->body_stream, false, h->d_list_stats + 2);
-        cudaGraph_t body_out = nullptr;
-        cudaStreamEndCapture(h->body_stream, &body_out);
-        cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1,
-                                            cudaStreamSetCaptureDependencies);
-    } else {
-        rebuild(st, true, nullptr);
-    }
     if (fourier && !a.list) cudaStreamWaitEvent(st, h->ev_join, 0);
     RealArgs r = make_real_args(h, a.parts);
     r.F_out = a.F;
@@ -1096,7 +1035,6 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
         md.md_vel = a.md_vel;
         md.nh = pa.nh;
         md.cur_step = h->d_cur_step;
-        md.step_dev = a.step_dev;
         run(RBE_K_FOURIER_FORCE, st2, [&] { launch_force(h, st2, true, md); });
         cudaEventRecord(h->ev_join, st2);
         cudaStreamWaitEvent(st, h->ev_join, 0);
@@ -1705,16 +1643,7 @@ rbe_status rbe_profile_read(rbe_handle h, double* ms, int64_t* launches) {
 
 rbe_status rbe_launch_count(rbe_handle h, int64_t* count) {
     if (!h || !count) return fail(h, RBE_ERR_ARG, "null argument");
-    int64_t body = 0;
-    if (h->list) {
-        // rebuilds run inside graph replays as conditional bodies of five
-        // kernels; their first kernel counts the runs on the device
-        unsigned long long runs = 0;
-        RBE_CUDA(h, cudaStreamSynchronize(h->stream));
-        RBE_CUDA(h, cudaMemcpy(&runs, h->d_list_stats + 2, sizeof(runs), cudaMemcpyDeviceToHost));
-        body = 5 * (int64_t)runs;
-    }
-    *count = h->kernel_count + body;
+    *count = h->kernel_count;
     return RBE_OK;
 }
 

@@ -252,10 +252,8 @@ k_prep_mixed(const __grid_constant__ Work w, const float4* __restrict__ pos_q,
         const int ncd = S.ncd;
         const int c = S.off_c + (cell_of_fixed(sz, ncd) * ncd + cell_of_fixed(sy, ncd)) * ncd +
                       cell_of_fixed(sx, ncd);
-        if (!pa.list_flag) {                 // list steps count cells only to rebuild
-            cid[i] = c;
-            rank[i] = atomicAdd(cell_cnt + c, 1);
-        }
+        cid[i] = c;
+        rank[i] = atomicAdd(cell_cnt + c, 1);
         const uint4 rec = make_uint4(sx, sy, sz, __float_as_uint(p.w));
         fx[i] = rec;
         qs = (double)p.w;
@@ -276,15 +274,6 @@ k_prep_mixed(const __grid_constant__ Work w, const float4* __restrict__ pos_q,
     }
     if (pa.list_flag) {
         if (__syncthreads_or(moved) && t == 0) atomicOr(pa.list_flag, 1);
-        if (pa.use_cond && t == 0) {
-            // the last particle block to finish sees every block's flag and
-            // sets the graph's rebuild condition (one thread, no waiting)
-            __threadfence();
-            if (atomicAdd(pa.done, 1) == pa.npblk - 1) {
-                *pa.done = 0;
-                cudaGraphSetConditional(pa.cond, atomicOr(pa.list_flag, 0) ? 1u : 0u);
-            }
-        }
     }
     if (pa.want_q) {
         const double2 r = block_sum2(qs, q2s);
@@ -350,28 +339,6 @@ k_prep_f64(const __grid_constant__ Work w, const double4* __restrict__ pos_q,
     }
 }
 
-// Cell ids and in-cell ranks of a neighbour-list rebuild (the prep kernel's
-// counting, moved here so that steps without a rebuild count nothing).
-template <bool ONE>
-__global__ void __launch_bounds__(kBlockP)
-k_cell_count(const __grid_constant__ Work w, const uint4* __restrict__ fx, int* __restrict__ cid,
-             int* __restrict__ rank, int* __restrict__ cell_cnt, const int* __restrict__ list_flag,
-             unsigned long long* __restrict__ graph_runs) {
-    if (!*list_flag) return;
-    if (graph_runs && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(graph_runs, 1ull);
-    const Tile tl = tile_of<ONE>(w);
-    const SysDev& S = sys_of<ONE>(w, tl.sys);
-    if ((int)threadIdx.x < tl.count) {
-        const int i = tl.first + threadIdx.x;
-        const uint4 r = fx[i];
-        const int ncd = S.ncd;
-        const int c = S.off_c + (cell_of_fixed(r.z, ncd) * ncd + cell_of_fixed(r.y, ncd)) * ncd +
-                      cell_of_fixed(r.x, ncd);
-        cid[i] = c;
-        rank[i] = atomicAdd(cell_cnt + c, 1);
-    }
-}
-
 // Exclusive scan of the cell counts (one block), zeroing the counts for the
 // next call.
 constexpr int kScanThreads = 1024;
@@ -382,7 +349,10 @@ k_scan(int* __restrict__ cell_cnt, int* __restrict__ cell_start, int ncell,
        uint64_t* __restrict__ step_dev, const uint64_t* __restrict__ cur_step,
        const int* __restrict__ list_flag) {
     if (step_dev && threadIdx.x == 0) *step_dev = *cur_step + 1;   // one increment per step
-    if (list_flag && !*list_flag) return;         // the list stands (nothing was counted)
+    if (list_flag && !*list_flag) {               // the list stands: only clear the counts
+        for (int i = threadIdx.x; i < ncell; i += blockDim.x) cell_cnt[i] = 0;
+        return;
+    }
     __shared__ int warp_tot[kScanThreads / 32];
     __shared__ int carry_s;
     if (threadIdx.x == 0) carry_s = 0;
@@ -504,18 +474,6 @@ void launch_prep_f64(cudaStream_t st, bool one, const Work& w, int nblk, const d
         k_prep_f64<true><<<nblk, kBlockP, smem, st>>>(w, pos_q, fx64, cid, rank, cell_cnt, pa);
     else
         k_prep_f64<false><<<nblk, kBlockP, smem, st>>>(w, pos_q, fx64, cid, rank, cell_cnt, pa);
-}
-
-void launch_cell_count(cudaStream_t st, bool one, const Work& w, int nblk, const uint4* fx,
-                       int* cid, int* rank, int* cell_cnt, const int* list_flag,
-                       unsigned long long* graph_runs) {
-    if (nblk <= 0) return;
-    if (one)
-        k_cell_count<true><<<nblk, kBlockP, 0, st>>>(w, fx, cid, rank, cell_cnt, list_flag,
-                                                    graph_runs);
-    else
-        k_cell_count<false><<<nblk, kBlockP, 0, st>>>(w, fx, cid, rank, cell_cnt, list_flag,
-                                                     graph_runs);
 }
 
 void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell, uint64_t* step_dev,

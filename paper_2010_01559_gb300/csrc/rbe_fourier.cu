@@ -214,9 +214,7 @@ k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
         return;
     }
     // neighbour-list MD step: the total force and the thermostat, one thread
-    // per particle (thread t: particle t of the tile); this is the step's last
-    // kernel, so it also advances the caller's step counter
-    if (md.step_dev && blockIdx.x == 0 && threadIdx.x == 0) *md.step_dev = *md.cur_step + 1;
+    // per particle (thread t: particle t of the tile)
     __shared__ float4 s_t[kBlockP / SPLIT];
     if (active && sub == 0) {
         const float q = __uint_as_float(p.w);

@@ -333,23 +333,13 @@ struct PrepArgs {
     const int* iperm;        // caller index -> sorted index of the last build
     uint4* spos;             // [sorted] current records
     int* list_flag;          // set: rebuild the list in this step
-    // graph replay: the last particle block sets the conditional node that
-    // runs the rebuild (cell count .. list build) from list_flag
-    int use_cond;
-    cudaGraphConditionalHandle cond;
-    int* done;               // particle blocks finished (reset by the last one)
 };
 void launch_prep_mixed(cudaStream_t st, bool one, const Work& w, int nblk, const float4* pos_q,
                        uint4* fx, int* cid, int* rank, int* cell_cnt, const PrepArgs& pa);
 void launch_prep_f64(cudaStream_t st, bool one, const Work& w, int nblk, const double4* pos_q,
                      double4* fx64, int* cid, int* rank, int* cell_cnt, const PrepArgs& pa);
-// list_flag (nullable): the cell list is rebuilt only when *list_flag is set;
-// the cells are then counted by launch_cell_count (the prep kernel does not).
-// graph_runs (nullable): incremented once per launch, for launch counts of
-// conditional graph bodies.
-void launch_cell_count(cudaStream_t st, bool one, const Work& w, int nblk, const uint4* fx,
-                       int* cid, int* rank, int* cell_cnt, const int* list_flag,
-                       unsigned long long* graph_runs);
+// list_flag (nullable): the cell list is rebuilt only when *list_flag is set
+// (the scan then only clears the counts the prep kernel left).
 void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell, uint64_t* step_dev,
                  const uint64_t* cur_step, const int* list_flag = nullptr);
 void launch_scatter(cudaStream_t st, int n, const int* cid, const int* rank,
@@ -406,7 +396,6 @@ struct MdOut {
     float4* md_vel;
     NhState* nh;
     const uint64_t* cur_step;
-    uint64_t* step_dev;      // nullable: advanced to cur_step + 1 (the step's last kernel)
 };
 void launch_fourier_force_mixed(cudaStream_t st, bool one, const Work& w, int nblk, int split,
                                 const uint4* fx, const int4* ksamp, const float2* kab,
