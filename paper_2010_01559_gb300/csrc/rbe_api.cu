@@ -218,6 +218,8 @@ struct rbe_ctx {
     unsigned long long* d_list_stats = nullptr;   // builds, largest count
     float4* d_freal = nullptr;                // real-space force of a list step
     cudaEvent_t ev_real = nullptr;            // list step: real-space pass done
+    cudaStream_t stream3 = nullptr;           // list step: the rebuild branch
+    cudaEvent_t ev_chain = nullptr;           // list step: rebuild branch done
     unsigned long long* d_qsum_fx = nullptr;  // sum q per system (fixed point)
     double2* d_blk_e = nullptr;
     double2* d_blk_w = nullptr;               // per real-space block (W_coul, W_lj)
@@ -693,6 +695,8 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_real, cudaEventDisableTiming));
+    RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_chain, cudaEventDisableTiming));
+    RBE_CUDA(h, cudaStreamCreateWithFlags(&h->stream3, cudaStreamNonBlocking));
     return RBE_OK;
 }
 
@@ -719,6 +723,8 @@ void release(rbe_ctx* h) {
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->ev_real) cudaEventDestroy(h->ev_real);
+    if (h->ev_chain) cudaEventDestroy(h->ev_chain);
+    if (h->stream3) cudaStreamDestroy(h->stream3);
     for (int k = 0; k < RBE_K_COUNT; ++k) {
         if (h->ev_beg[k]) cudaEventDestroy(h->ev_beg[k]);
         if (h->ev_end[k]) cudaEventDestroy(h->ev_end[k]);
@@ -972,20 +978,28 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
             cudaEventRecord(h->ev_join, st2);
         }
     }
-    run(RBE_K_SCAN, st, [&] {
-        launch_scan(st, h->d_cell_cnt, h->d_cell_start, h->ncell, a.step_dev, h->d_cur_step,
+    // the cell list; on a list step the (usually no-op) rebuild runs on a
+    // third stream, so that the list pass need not wait for it
+    cudaStream_t sc = st;
+    if (a.list) {
+        sc = h->stream3;
+        if (!fourier) cudaEventRecord(h->ev_fork, st);
+        cudaStreamWaitEvent(sc, h->ev_fork, 0);
+    }
+    run(RBE_K_SCAN, sc, [&] {
+        launch_scan(sc, h->d_cell_cnt, h->d_cell_start, h->ncell, a.step_dev, h->d_cur_step,
                     lflag);
     });
-    run(RBE_K_SCATTER, st, [&] {
-        launch_scatter(st, n, h->d_cid, h->d_rank, h->d_cell_start, h->d_perm_tmp, lflag);
+    run(RBE_K_SCATTER, sc, [&] {
+        launch_scatter(sc, n, h->d_cid, h->d_rank, h->d_cell_start, h->d_perm_tmp, lflag);
     });
-    run(RBE_K_CELL_ORDER, st, [&] {
-        launch_order(st, n, h->d_cid, h->d_cell_start, h->d_perm_tmp, mixed ? h->d_fx : nullptr,
+    run(RBE_K_CELL_ORDER, sc, [&] {
+        launch_order(sc, n, h->d_cid, h->d_cell_start, h->d_perm_tmp, mixed ? h->d_fx : nullptr,
                      h->d_spos, mixed ? nullptr : h->d_fx64, h->d_spos64, h->d_perm, lflag,
                      a.list ? h->d_iperm : nullptr);
     });
     if (a.list)
-        run(RBE_K_LIST_BUILD, st, [&] {
+        run(RBE_K_LIST_BUILD, sc, [&] {
             ListArgs la{};
             la.w = make_work(h, h->d_pblk, kBlockP, 0);
             la.nblk = h->npblk;
@@ -999,7 +1013,7 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
             la.sref = h->d_sref;
             la.stats = h->d_list_stats;
             la.err = h->d_err;
-            launch_list_build(st, one, la);
+            launch_list_build(sc, one, la);
         });
     if (fourier && !a.list) cudaStreamWaitEvent(st, h->ev_join, 0);
     RealArgs r = make_real_args(h, a.parts);
@@ -1023,11 +1037,20 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
         r.nbr_stride = std::max(h->ntot, 1);
         r.list_flag = h->d_list_flag;
         r.freal = h->d_freal;
-        // the real-space pass (concurrent with the structure factors), then
-        // the Fourier force, which adds it and applies the thermostat
+        // the real-space pass over a standing list right after the prep kernel
+        // (concurrent with the structure factors and the rebuild stream), or
+        // over the rebuilt list at the end of the rebuild stream; then the
+        // Fourier force, which adds it and applies the thermostat
+        r.list_when = 0;
         run(RBE_K_REAL, st, [&] { launch_real_list(st, one, r); });
         cudaEventRecord(h->ev_real, st);
+        RealArgs rb = r;
+        rb.list_when = 1;
+        launch_real_list(sc, one, rb);
+        ++count;
+        cudaEventRecord(h->ev_chain, sc);
         cudaStreamWaitEvent(st2, h->ev_real, 0);
+        cudaStreamWaitEvent(st2, h->ev_chain, 0);
         MdOut md;
         md.freal = h->d_freal;
         md.F_out = a.F;
@@ -1035,6 +1058,7 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
         md.md_vel = a.md_vel;
         md.nh = pa.nh;
         md.cur_step = h->d_cur_step;
+        md.list_flag = h->d_list_flag;
         run(RBE_K_FOURIER_FORCE, st2, [&] { launch_force(h, st2, true, md); });
         cudaEventRecord(h->ev_join, st2);
         cudaStreamWaitEvent(st, h->ev_join, 0);
@@ -1594,6 +1618,7 @@ rbe_status rbe_autotune(rbe_handle h, int32_t n, const float* pos_q, rbe_tuning*
             r.ncnt = h->d_ncnt;
             r.nbr_stride = std::max(h->ntot, 1);
             r.list_flag = h->d_list_flag;
+            r.list_when = 0;
             r.freal = h->d_freal;
             const float t = time_kernel(h, e0, e1, [&] { launch_real_list(h->stream, !h->batch, r); });
             if (t < best) { best = t; best_lsplit = ls; }

@@ -215,6 +215,7 @@ k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
     }
     // neighbour-list MD step: the total force and the thermostat, one thread
     // per particle (thread t: particle t of the tile)
+    if (md.list_flag && blockIdx.x == 0 && threadIdx.x == 0) *md.list_flag = 0;   // consumed
     __shared__ float4 s_t[kBlockP / SPLIT];
     if (active && sub == 0) {
         const float q = __uint_as_float(p.w);

@@ -396,6 +396,7 @@ struct MdOut {
     float4* md_vel;
     NhState* nh;
     const uint64_t* cur_step;
+    int* list_flag;          // nullable: cleared (the step's rebuild flag is consumed)
 };
 void launch_fourier_force_mixed(cudaStream_t st, bool one, const Work& w, int nblk, int split,
                                 const uint4* fx, const int4* ksamp, const float2* kab,
@@ -451,7 +452,8 @@ struct RealArgs {
     const int* nbr;
     const int* ncnt;
     int nbr_stride;
-    int* list_flag;          // cleared by the list kernel (consumed by this step)
+    const int* list_flag;    // rebuild flag of this step
+    int list_when;           // the list kernel works only when (*list_flag != 0) == list_when
     float4* freal;           // list kernel output: real-space force, caller's order
     double2* blk_e;          // per block (E_coul, E_lj), nullable
     double2* blk_w;          // per block (W_coul, W_lj): pair virials r.F, nullable

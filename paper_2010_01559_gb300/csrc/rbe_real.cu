@@ -542,14 +542,17 @@ __global__ void __launch_bounds__(kBlockP) k_list_build(const __grid_constant__ 
 // lanes) take every R-th entry of the particle's list and the pair terms of
 // those within the cutoffs (four gathers in flight per lane); the lanes' sums
 // are added and stored per particle.  It needs nothing from the Fourier part,
-// so it runs concurrently with the structure factors; the Fourier-force
-// kernel then completes the step.
+// so it runs concurrently with the structure factors (and, when the list
+// stands, with the no-op rebuild kernels); the Fourier-force kernel then
+// completes the step.
 template <int R, bool ONE>
 __global__ void __launch_bounds__(kBlockP) k_real_list(const __grid_constant__ RealArgs a) {
     constexpr int T = kBlockP / R;               // particles per block
     const Tile tl = tile_of<ONE>(a.lw);
+    // launched twice per step: right after the prep kernel (works when the list
+    // stands) and after the rebuild (works when the list was rebuilt)
+    if ((*a.list_flag != 0) != (a.list_when != 0)) return;
     const SysDev& S = sys_of<ONE>(a.lw, tl.sys);
-    if (blockIdx.x == 0 && threadIdx.x == 0) *a.list_flag = 0;   // consumed by this step
     const int p = threadIdx.x / R, l = threadIdx.x - p * R;
     const bool do_real = (a.parts & kPartReal) != 0;
     const bool do_lj = (a.parts & kPartLJ) != 0 && S.lj_eps != 0.0;
