@@ -646,8 +646,10 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_CUDA(h, cudaMemset(h->d_cell_cnt, 0, sizeof(int) * (h->ncell + 1)));
     RBE_CUDA(h, cudaMemset(h->d_err, 0, sizeof(int)));
     if (h->list) {
-        // sorted slots 0 until the first build (which the set flag forces)
+        // sorted slots 0 until the first build (which the set flag forces); list
+        // slots always hold valid indices (the list pass loads ahead of counts)
         RBE_CUDA(h, cudaMemset(h->d_iperm, 0, sizeof(int) * N));
+        RBE_CUDA(h, cudaMemset(h->d_nbr, 0, sizeof(int) * (size_t)h->list_cap * N));
         RBE_CUDA(h, cudaMemset(h->d_ncnt, 0, sizeof(int) * N));
         RBE_CUDA(h, cudaMemset(h->d_sref, 0, sizeof(uint4) * N));
         RBE_CUDA(h, cudaMemset(h->d_list_stats, 0, sizeof(unsigned long long) * 2));
@@ -1035,6 +1037,7 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
         r.nbr = h->d_nbr;
         r.ncnt = h->d_ncnt;
         r.nbr_stride = std::max(h->ntot, 1);
+        r.nbr_cap = h->list_cap;
         r.list_flag = h->d_list_flag;
         r.freal = h->d_freal;
         // the real-space pass over a standing list right after the prep kernel
@@ -1617,6 +1620,7 @@ rbe_status rbe_autotune(rbe_handle h, int32_t n, const float* pos_q, rbe_tuning*
             r.nbr = h->d_nbr;
             r.ncnt = h->d_ncnt;
             r.nbr_stride = std::max(h->ntot, 1);
+            r.nbr_cap = h->list_cap;
             r.list_flag = h->d_list_flag;
             r.list_when = 0;
             r.freal = h->d_freal;

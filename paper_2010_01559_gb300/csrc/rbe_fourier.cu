@@ -54,16 +54,22 @@ __device__ __forceinline__ double2 kcoef(const SysDev& S, int4 m,
 }
 
 // ----------------------------------------------------------------- rho (mixed)
+// Two threads per wave vector (threads l and l + kLTile), each over every
+// other particle of the chunk; their sums are added before the atomics.
+constexpr int kRhoHalves = 2;
+
 template <bool ONE>
-__global__ void __launch_bounds__(kLTile)
+__global__ void __launch_bounds__(kLTile * kRhoHalves)
 k_rho_mixed(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
             const double* __restrict__ kcoef, const uint4* __restrict__ fx,
             unsigned long long* __restrict__ rho_fx, int* __restrict__ kcnt,
             float2* __restrict__ kab) {
     __shared__ uint4 sp[kStage];
+    __shared__ float2 s_half[kLTile];
     const Tile ch = tile_of<ONE>(w);
     const SysDev& S = sys_of<ONE>(w, ch.sys);
-    const int l = blockIdx.y * kLTile + threadIdx.x;
+    const int half = threadIdx.x / kLTile;
+    const int l = blockIdx.y * kLTile + (threadIdx.x - half * kLTile);
     if (blockIdx.y * kLTile >= S.P) return;          // whole block beyond this system's P
     const bool active = l < S.P;
     int4 m = make_int4(0, 0, 0, 0);
@@ -77,7 +83,7 @@ k_rho_mixed(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
         __syncthreads();
         if (active) {
 #pragma unroll 4
-            for (int j = 0; j < cnt; ++j) {
+            for (int j = half; j < cnt; j += kRhoHalves) {
                 const uint4 p = sp[j];
                 const uint32_t ph = mx * p.x + my * p.y + mz * p.z;
                 const float th = (float)(int32_t)ph * kTwoPiOver2p32;
@@ -89,7 +95,13 @@ k_rho_mixed(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
             }
         }
     }
-    if (active) rho_accumulate(rho_fx + 2 * (S.off_k + l), (double)re, (double)im, S.rho_scale);
+    if (half == 1) s_half[threadIdx.x - kLTile] = make_float2(re, im);
+    __syncthreads();
+    if (half == 0 && active) {
+        const float2 o = s_half[threadIdx.x];
+        rho_accumulate(rho_fx + 2 * (S.off_k + l), (double)(re + o.x), (double)(im + o.y),
+                       S.rho_scale);
+    }
     // The last of the system's chunks to add its partials for this tile of
     // wave vectors finds rho(k) complete and turns it into the FP32 force
     // coefficients (A, B) of Eq. rbmapprox, once per k instead of once per
@@ -103,7 +115,7 @@ k_rho_mixed(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
     __syncthreads();
     if (s_last) {
         __threadfence();
-        if (active) {
+        if (active && half == 0) {
             const double2 r = rho_read(rho_fx + 2 * (S.off_k + l), S.rho_inv_scale);
             const double c = kcoef[S.off_k + l];
             kab[S.off_k + l] = make_float2((float)(c * r.y), (float)(c * r.x));
@@ -153,7 +165,8 @@ k_rho_f64(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
 struct KPhase { uint32_t mx, my, mz, pad; };
 struct KForce { float mx, my, mz, A; };
 
-template <int SPLIT, bool ONE>
+// PHI: also dE/dq (the forces path); MD steps need only the force.
+template <int SPLIT, bool PHI, bool ONE>
 __global__ void __launch_bounds__(kBlockP)
 k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
               const int4* __restrict__ ksamp, const float2* __restrict__ kab,
@@ -195,7 +208,7 @@ k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
             fx = fmaf(g, f.mx, fx);
             fy = fmaf(g, f.my, fy);
             fz = fmaf(g, f.mz, fz);
-            ph = fmaf(cs, B, fmaf(sn, f.A, ph));        // Re(e^{-i th} rho) * coef
+            if constexpr (PHI) ph = fmaf(cs, B, fmaf(sn, f.A, ph));   // Re(e^{-i th} rho) coef
         }
     }
 #pragma unroll
@@ -300,9 +313,11 @@ void launch_rho_mixed(cudaStream_t st, bool one, const Work& w, int nchunks, int
     if (nchunks <= 0 || ltiles <= 0) return;
     dim3 grid(nchunks, ltiles);
     if (one)
-        k_rho_mixed<true><<<grid, kLTile, 0, st>>>(w, ksamp, kcoef, fx, rho_fx, kcnt, kab);
+        k_rho_mixed<true><<<grid, kLTile * kRhoHalves, 0, st>>>(w, ksamp, kcoef, fx, rho_fx,
+                                                                kcnt, kab);
     else
-        k_rho_mixed<false><<<grid, kLTile, 0, st>>>(w, ksamp, kcoef, fx, rho_fx, kcnt, kab);
+        k_rho_mixed<false><<<grid, kLTile * kRhoHalves, 0, st>>>(w, ksamp, kcoef, fx, rho_fx,
+                                                                 kcnt, kab);
 }
 
 void launch_rho_f64(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
@@ -319,10 +334,13 @@ template <int SPLIT>
 static void force_mixed_split(cudaStream_t st, bool one, const Work& w, int nblk, const uint4* fx,
                               const int4* ksamp, const float2* kab, float4* fs,
                               const MdOut& md) {
-    if (one)
-        k_force_mixed<SPLIT, true><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, kab, fs, md);
-    else
-        k_force_mixed<SPLIT, false><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, kab, fs, md);
+    if (md.freal) {
+        if (one) k_force_mixed<SPLIT, false, true><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, kab, fs, md);
+        else k_force_mixed<SPLIT, false, false><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, kab, fs, md);
+    } else {
+        if (one) k_force_mixed<SPLIT, true, true><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, kab, fs, md);
+        else k_force_mixed<SPLIT, true, false><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, kab, fs, md);
+    }
 }
 
 void launch_fourier_force_mixed(cudaStream_t st, bool one, const Work& w, int nblk, int split,

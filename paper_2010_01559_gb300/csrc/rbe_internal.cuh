@@ -451,7 +451,7 @@ struct RealArgs {
     int nlblk, lsplit;
     const int* nbr;
     const int* ncnt;
-    int nbr_stride;
+    int nbr_stride, nbr_cap;
     const int* list_flag;    // rebuild flag of this step
     int list_when;           // the list kernel works only when (*list_flag != 0) == list_when
     float4* freal;           // list kernel output: real-space force, caller's order

@@ -538,9 +538,11 @@ __global__ void __launch_bounds__(kBlockP) k_list_build(const __grid_constant__ 
     if (blockIdx.x == 0 && t == 0) atomicAdd(la.stats, 1ull);
 }
 
+constexpr int kListU = 8;           // list entries per lane and batch of the list pass
+
 // The MD step's real-space pass over the list: R lanes per particle (adjacent
 // lanes) take every R-th entry of the particle's list and the pair terms of
-// those within the cutoffs (four gathers in flight per lane); the lanes' sums
+// those within the cutoffs (eight gathers in flight per lane); the lanes' sums
 // are added and stored per particle.  It needs nothing from the Fourier part,
 // so it runs concurrently with the structure factors (and, when the list
 // stands, with the no-op rebuild kernels); the Fourier-force kernel then
@@ -573,24 +575,33 @@ __global__ void __launch_bounds__(kBlockP) k_real_list(const __grid_constant__ R
         const uint4 si = a.spos[i];
         const float lbqi = kc.lB * __uint_as_float(si.w);
         const float Lu = S.L_over_2_32;
-        const int cnt = __ldg(a.ncnt + i);
         const int* nb = a.nbr + i;
         const size_t st = (size_t)a.nbr_stride;
-        int k = l;
-        for (; k + 3 * R < cnt; k += 4 * R) {
-            const int j0 = __ldg(nb + (size_t)k * st);
-            const int j1 = __ldg(nb + (size_t)(k + R) * st);
-            const int j2 = __ldg(nb + (size_t)(k + 2 * R) * st);
-            const int j3 = __ldg(nb + (size_t)(k + 3 * R) * st);
-            const uint4 s0 = __ldg(a.spos + j0), s1 = __ldg(a.spos + j1);
-            const uint4 s2 = __ldg(a.spos + j2), s3 = __ldg(a.spos + j3);
-            pair_fixed(si, s0, Lu, lbqi, kc, acc);
-            pair_fixed(si, s1, Lu, lbqi, kc, acc);
-            pair_fixed(si, s2, Lu, lbqi, kc, acc);
-            pair_fixed(si, s3, Lu, lbqi, kc, acc);
+        // batches of kListU entries per lane, all gathers of a batch in flight
+        // at once; the first batch is loaded alongside the count (slots within
+        // the capacity always hold valid indices: the list starts zeroed)
+        const int cnt = __ldg(a.ncnt + i);
+        int j[kListU];
+#pragma unroll
+        for (int q = 0; q < kListU; ++q) {
+            const int kk = l + q * R;
+            j[q] = kk < a.nbr_cap ? __ldg(nb + (size_t)kk * st) : 0;
         }
-        for (; k < cnt; k += R) pair_fixed(si, __ldg(a.spos + __ldg(nb + (size_t)k * st)), Lu,
-                                           lbqi, kc, acc);
+        for (int k0 = l;;) {
+            uint4 sj[kListU];
+#pragma unroll
+            for (int q = 0; q < kListU; ++q) sj[q] = __ldg(a.spos + j[q]);
+#pragma unroll
+            for (int q = 0; q < kListU; ++q)
+                if (k0 + q * R < cnt) pair_fixed(si, sj[q], Lu, lbqi, kc, acc);
+            k0 += kListU * R;
+            if (k0 >= cnt) break;
+#pragma unroll
+            for (int q = 0; q < kListU; ++q) {
+                const int kk = k0 + q * R;
+                j[q] = kk < cnt ? __ldg(nb + (size_t)kk * st) : 0;
+            }
+        }
     }
     float fx = acc.fx, fy = acc.fy, fz = acc.fz;
     if constexpr (R > 1) {
