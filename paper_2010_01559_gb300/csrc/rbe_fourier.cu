@@ -65,7 +65,7 @@ k_rho_mixed(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
             unsigned long long* __restrict__ rho_fx, int* __restrict__ kcnt,
             float2* __restrict__ kab) {
     __shared__ uint4 sp[kStage];
-    __shared__ float2 s_half[kLTile];
+    __shared__ double2 s_half[kLTile];
     const Tile ch = tile_of<ONE>(w);
     const SysDev& S = sys_of<ONE>(w, ch.sys);
     const int half = threadIdx.x / kLTile;
@@ -75,12 +75,15 @@ k_rho_mixed(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
     int4 m = make_int4(0, 0, 0, 0);
     if (active) m = ksamp[S.off_k + l];              // drawn by the prep kernel
     const uint32_t mx = (uint32_t)m.x, my = (uint32_t)m.y, mz = (uint32_t)m.z;
-    float re = 0.f, im = 0.f;
+    // FP32 sums over one staged pass (at most kStage / 2 terms), FP64 across
+    // passes and halves, so the rounding does not grow with the chunk size
+    double red = 0.0, imd = 0.0;
     for (int base = 0; base < ch.count; base += kStage) {
         const int cnt = min(kStage, ch.count - base);
         __syncthreads();
         for (int t = threadIdx.x; t < cnt; t += blockDim.x) sp[t] = fx[ch.first + base + t];
         __syncthreads();
+        float re = 0.f, im = 0.f;
         if (active) {
 #pragma unroll 4
             for (int j = half; j < cnt; j += kRhoHalves) {
@@ -94,13 +97,14 @@ k_rho_mixed(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
                 im = fmaf(q, sn, im);
             }
         }
+        red += (double)re;
+        imd += (double)im;
     }
-    if (half == 1) s_half[threadIdx.x - kLTile] = make_float2(re, im);
+    if (half == 1) s_half[threadIdx.x - kLTile] = make_double2(red, imd);
     __syncthreads();
     if (half == 0 && active) {
-        const float2 o = s_half[threadIdx.x];
-        rho_accumulate(rho_fx + 2 * (S.off_k + l), (double)(re + o.x), (double)(im + o.y),
-                       S.rho_scale);
+        const double2 o = s_half[threadIdx.x];
+        rho_accumulate(rho_fx + 2 * (S.off_k + l), red + o.x, imd + o.y, S.rho_scale);
     }
     // The last of the system's chunks to add its partials for this tile of
     // wave vectors finds rho(k) complete and turns it into the FP32 force
