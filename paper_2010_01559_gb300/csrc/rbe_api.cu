@@ -219,7 +219,6 @@ struct rbe_ctx {
     float4* d_freal = nullptr;                // real-space force of a list step
     cudaEvent_t ev_real = nullptr;            // list step: real-space pass done
     cudaStream_t stream3 = nullptr;           // list step: the rebuild branch
-    cudaEvent_t ev_prep = nullptr;            // list step: prep kernel done
     cudaEvent_t ev_chain = nullptr;           // list step: rebuild branch done
     unsigned long long* d_qsum_fx = nullptr;  // sum q per system (fixed point)
     double2* d_blk_e = nullptr;
@@ -699,7 +698,6 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_real, cudaEventDisableTiming));
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_chain, cudaEventDisableTiming));
-    RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_prep, cudaEventDisableTiming));
     RBE_CUDA(h, cudaStreamCreateWithFlags(&h->stream3, cudaStreamNonBlocking));
     return RBE_OK;
 }
@@ -728,7 +726,6 @@ void release(rbe_ctx* h) {
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->ev_real) cudaEventDestroy(h->ev_real);
     if (h->ev_chain) cudaEventDestroy(h->ev_chain);
-    if (h->ev_prep) cudaEventDestroy(h->ev_prep);
     if (h->stream3) cudaStreamDestroy(h->stream3);
     for (int k = 0; k < RBE_K_COUNT; ++k) {
         if (h->ev_beg[k]) cudaEventDestroy(h->ev_beg[k]);
@@ -880,13 +877,13 @@ RealArgs make_real_args(const rbe_ctx* h, int parts) {
 }
 
 // Structure factors: per-chunk partials added to the fixed-point rho(k).
-void launch_rho(const rbe_ctx* h, cudaStream_t st, bool mixed, const RhoOwn& own = RhoOwn{}) {
+void launch_rho(const rbe_ctx* h, cudaStream_t st, bool mixed) {
     const bool one = !h->batch;
     const int ltiles = (h->pmax + kLTile - 1) / kLTile;
     const Work w = make_work(h, h->d_chunks, h->cur_chunk, 1);
     if (mixed)
         launch_rho_mixed(st, one, w, h->nchunks, ltiles, h->d_ksamp, h->d_kcoef, h->d_fx,
-                         h->d_rho_fx, h->d_kcnt, h->d_kab, own);
+                         h->d_rho_fx, h->d_kcnt, h->d_kab);
     else
         launch_rho_f64(st, one, w, h->nchunks, ltiles, h->d_ksamp, h->d_fx64, h->d_rho_fx);
 }
@@ -940,10 +937,7 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     pa.step_arg = a.step;
     pa.cur_step = h->d_cur_step;
     pa.npblk = h->npblk;
-    // a list step with the exact sampler: the structure-factor kernel draws
-    // the k-batch and reads the positions itself, from the start of the step
-    const bool own = a.list && mixed && fourier && !h->mh;
-    pa.ktot = (fourier && !own) ? h->ktot : 0;
+    pa.ktot = fourier ? h->ktot : 0;
     pa.nsys = h->nsys;
     pa.kstart = h->d_kstart;
     pa.table = h->d_table;
@@ -967,19 +961,6 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
         h->list_valid = false;              // the sorted arrays are about to change
     }
     const int* lflag = a.list ? h->d_list_flag : nullptr;
-    if (own) {
-        pa.nrho = 0;                          // the accumulators were left zeroed
-        cudaEventRecord(h->ev_fork, st);
-        cudaStreamWaitEvent(st2, h->ev_fork, 0);
-        RhoOwn ro;
-        ro.pos = a.pos;
-        ro.table = h->d_table;
-        ro.tab_words = h->ttot <= 8192 ? h->ttot : 0;
-        ro.step_dev = a.step_dev;
-        ro.step_arg = a.step;
-        ro.err = h->d_err;
-        run(RBE_K_RHO, st2, [&] { launch_rho(h, st2, true, ro); });
-    }
     if (want_q)
         cudaMemsetAsync(h->d_qsum_fx, 0, sizeof(unsigned long long) * h->nsys, st);
     run(RBE_K_PREP, st, [&] {
@@ -990,7 +971,7 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
             launch_prep_f64(st, one, wp, h->npblk, a.pos64, h->d_fx64, h->d_cid, h->d_rank,
                             h->d_cell_cnt, pa);
     });
-    if (fourier && !own) {
+    if (fourier) {
         cudaEventRecord(h->ev_fork, st);
         cudaStreamWaitEvent(st2, h->ev_fork, 0);
         run(RBE_K_RHO, st2, [&] { launch_rho(h, st2, mixed); });
@@ -1004,14 +985,12 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     cudaStream_t sc = st;
     if (a.list) {
         sc = h->stream3;
-        cudaEventRecord(h->ev_prep, st);
-        cudaStreamWaitEvent(sc, h->ev_prep, 0);
+        if (!fourier) cudaEventRecord(h->ev_fork, st);
+        cudaStreamWaitEvent(sc, h->ev_fork, 0);
     }
-    // on a list step the Fourier-force kernel (the last) advances the step
-    // counter: the structure factors may still be reading it meanwhile
     run(RBE_K_SCAN, sc, [&] {
-        launch_scan(sc, h->d_cell_cnt, h->d_cell_start, h->ncell,
-                    a.list ? nullptr : a.step_dev, h->d_cur_step, lflag);
+        launch_scan(sc, h->d_cell_cnt, h->d_cell_start, h->ncell, a.step_dev, h->d_cur_step,
+                    lflag);
     });
     run(RBE_K_SCATTER, sc, [&] {
         launch_scatter(sc, n, h->d_cid, h->d_rank, h->d_cell_start, h->d_perm_tmp, lflag);
@@ -1082,7 +1061,6 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
         md.md_vel = a.md_vel;
         md.nh = pa.nh;
         md.cur_step = h->d_cur_step;
-        md.step_dev = a.step_dev;
         md.list_flag = h->d_list_flag;
         run(RBE_K_FOURIER_FORCE, st2, [&] { launch_force(h, st2, true, md); });
         cudaEventRecord(h->ev_join, st2);
@@ -1253,13 +1231,8 @@ rbe_status step_impl(rbe_ctx* h, int n, int prec, void* pos, void* vel, int nste
     }
     if (a.list) {
         // the first step after anything else touched the sorted arrays builds a list
-        // (and the structure-factor accumulators, which list steps leave zeroed,
-        // start from zero)
-        if (!h->list_valid && nsteps > 0) {
+        if (!h->list_valid && nsteps > 0)
             RBE_CUDA(h, cudaMemsetAsync(h->d_list_flag, 0xFF, sizeof(int), h->stream));
-            RBE_CUDA(h, cudaMemsetAsync(h->d_rho_fx, 0, sizeof(unsigned long long) * 2 * h->ktot,
-                                        h->stream));
-        }
         if (nsteps > 0) h->list_valid = true;
     } else if (nsteps > 0) {
         h->list_valid = false;
@@ -1638,8 +1611,6 @@ rbe_status rbe_autotune(rbe_handle h, int32_t n, const float* pos_q, rbe_tuning*
             EvalArgs b = a;
             b.list = true;
             RBE_CUDA(h, cudaMemsetAsync(h->d_list_flag, 0xFF, sizeof(int), h->stream));
-            RBE_CUDA(h, cudaMemsetAsync(h->d_rho_fx, 0, sizeof(unsigned long long) * 2 * h->ktot,
-                                        h->stream));
             enqueue_eval(h, h->stream, b);
             RealArgs r = make_real_args(h, RBE_PART_ALL);
             r.F_out = h->d_stage_F;

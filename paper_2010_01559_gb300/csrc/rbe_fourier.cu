@@ -58,21 +58,12 @@ __device__ __forceinline__ double2 kcoef(const SysDev& S, int4 m,
 // other particle of the chunk; their sums are added before the atomics.
 constexpr int kRhoHalves = 2;
 
-// OWN (neighbour-list MD steps with the exact sampler): the kernel depends on
-// nothing but the caller's positions and the sampling table, so it runs from
-// the start of the step, concurrently with the prep kernel.  Each block draws
-// its tile of the k-batch itself (Eq. probexpression, the same counters as
-// the prep kernel's sampler) and converts its chunk of positions to fixed
-// point; the last block of a tile stores the samples, the force coefficients
-// and then zeroes the tile's accumulators for the next step (no energy reads
-// them on this path).
-template <bool ONE, bool OWN>
+template <bool ONE>
 __global__ void __launch_bounds__(kLTile * kRhoHalves)
-k_rho_mixed(const __grid_constant__ Work w, int4* __restrict__ ksamp,
+k_rho_mixed(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
             const double* __restrict__ kcoef, const uint4* __restrict__ fx,
             unsigned long long* __restrict__ rho_fx, int* __restrict__ kcnt,
-            float2* __restrict__ kab, const __grid_constant__ RhoOwn own) {
-    extern __shared__ uint32_t s_tab[];               // OWN: the sampling tables
+            float2* __restrict__ kab) {
     __shared__ uint4 sp[kStage];
     __shared__ double2 s_half[kLTile];
     const Tile ch = tile_of<ONE>(w);
@@ -82,19 +73,7 @@ k_rho_mixed(const __grid_constant__ Work w, int4* __restrict__ ksamp,
     if (blockIdx.y * kLTile >= S.P) return;          // whole block beyond this system's P
     const bool active = l < S.P;
     int4 m = make_int4(0, 0, 0, 0);
-    if constexpr (OWN) {
-        if (own.tab_words > 0) {
-            for (int j = threadIdx.x; j < own.tab_words; j += blockDim.x)
-                s_tab[j] = (uint32_t)__ldg(own.table + j);
-            __syncthreads();
-        }
-        const uint64_t step = own.step_dev ? *own.step_dev : own.step_arg;
-        if (active)
-            m = own.tab_words > 0 ? sample_one_smem(S, s_tab + S.off_t, l, step, own.err)
-                                  : sample_one(S, own.table + S.off_t, l, step, own.err);
-    } else {
-        if (active) m = ksamp[S.off_k + l];          // drawn by the prep kernel
-    }
+    if (active) m = ksamp[S.off_k + l];              // drawn by the prep kernel
     const uint32_t mx = (uint32_t)m.x, my = (uint32_t)m.y, mz = (uint32_t)m.z;
     // FP32 sums over one staged pass (at most kStage / 2 terms), FP64 across
     // passes and halves, so the rounding does not grow with the chunk size
@@ -102,15 +81,7 @@ k_rho_mixed(const __grid_constant__ Work w, int4* __restrict__ ksamp,
     for (int base = 0; base < ch.count; base += kStage) {
         const int cnt = min(kStage, ch.count - base);
         __syncthreads();
-        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-            if constexpr (OWN) {
-                const float4 p = own.pos[ch.first + base + t];
-                sp[t] = make_uint4(to_fixed(p.x, S.fx_hi, S.fx_lo), to_fixed(p.y, S.fx_hi, S.fx_lo),
-                                   to_fixed(p.z, S.fx_hi, S.fx_lo), __float_as_uint(p.w));
-            } else {
-                sp[t] = fx[ch.first + base + t];
-            }
-        }
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) sp[t] = fx[ch.first + base + t];
         __syncthreads();
         float re = 0.f, im = 0.f;
         if (active) {
@@ -149,20 +120,8 @@ k_rho_mixed(const __grid_constant__ Work w, int4* __restrict__ ksamp,
     if (s_last) {
         __threadfence();
         if (active && half == 0) {
-            unsigned long long* acc = rho_fx + 2 * (S.off_k + l);
-            const double2 r = rho_read(acc, S.rho_inv_scale);
-            double c;
-            if constexpr (OWN) {
-                ksamp[S.off_k + l] = m;
-                const double tp = 2.0 * M_PI * S.invL;
-                const double k2 = tp * tp * ((double)m.x * m.x + (double)m.y * m.y +
-                                             (double)m.z * m.z);
-                c = S.coef_scale / k2;
-                acc[0] = 0ull;                        // ready for the next step
-                acc[1] = 0ull;
-            } else {
-                c = kcoef[S.off_k + l];
-            }
+            const double2 r = rho_read(rho_fx + 2 * (S.off_k + l), S.rho_inv_scale);
+            const double c = kcoef[S.off_k + l];
             kab[S.off_k + l] = make_float2((float)(c * r.y), (float)(c * r.x));
         }
         if (threadIdx.x == 0) kcnt[slot] = 0;        // ready for the next evaluation
@@ -273,10 +232,7 @@ k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
     }
     // neighbour-list MD step: the total force and the thermostat, one thread
     // per particle (thread t: particle t of the tile)
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (md.list_flag) *md.list_flag = 0;          // the rebuild flag is consumed
-        if (md.step_dev) *md.step_dev = *md.cur_step + 1;   // the step's last kernel
-    }
+    if (md.list_flag && blockIdx.x == 0 && threadIdx.x == 0) *md.list_flag = 0;   // consumed
     __shared__ float4 s_t[kBlockP / SPLIT];
     if (active && sub == 0) {
         const float q = __uint_as_float(p.w);
@@ -356,23 +312,16 @@ void launch_sample(cudaStream_t st, const SysDev* sys, int nsys, int ktot, const
 
 // The k-batch (ksamp) and coef_scale / k^2 (kcoef) come from the prep kernel.
 void launch_rho_mixed(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
-                      int4* ksamp, const double* kcoef, const uint4* fx,
-                      unsigned long long* rho_fx, int* kcnt, float2* kab, const RhoOwn& own) {
+                      const int4* ksamp, const double* kcoef, const uint4* fx,
+                      unsigned long long* rho_fx, int* kcnt, float2* kab) {
     if (nchunks <= 0 || ltiles <= 0) return;
     dim3 grid(nchunks, ltiles);
-    const int nt = kLTile * kRhoHalves;
-    if (own.pos) {
-        const size_t smem = sizeof(uint32_t) * (size_t)own.tab_words;
-        if (one)
-            k_rho_mixed<true, true><<<grid, nt, smem, st>>>(w, ksamp, kcoef, fx, rho_fx, kcnt, kab, own);
-        else
-            k_rho_mixed<false, true><<<grid, nt, smem, st>>>(w, ksamp, kcoef, fx, rho_fx, kcnt, kab, own);
-    } else {
-        if (one)
-            k_rho_mixed<true, false><<<grid, nt, 0, st>>>(w, ksamp, kcoef, fx, rho_fx, kcnt, kab, own);
-        else
-            k_rho_mixed<false, false><<<grid, nt, 0, st>>>(w, ksamp, kcoef, fx, rho_fx, kcnt, kab, own);
-    }
+    if (one)
+        k_rho_mixed<true><<<grid, kLTile * kRhoHalves, 0, st>>>(w, ksamp, kcoef, fx, rho_fx,
+                                                                kcnt, kab);
+    else
+        k_rho_mixed<false><<<grid, kLTile * kRhoHalves, 0, st>>>(w, ksamp, kcoef, fx, rho_fx,
+                                                                 kcnt, kab);
 }
 
 void launch_rho_f64(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,

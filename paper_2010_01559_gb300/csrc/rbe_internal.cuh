@@ -98,20 +98,6 @@ struct Tile {
     int sys, first, count, aux;
 };
 
-// Fixed-point fraction of the box, round(x 2^32 / L) mod 2^32, from a float
-// coordinate and 2^32 / L as the unevaluated pair hi + lo (error below one
-// unit of 2^-32 L).
-__device__ __forceinline__ uint32_t to_fixed(float x, float hi, float lo) {
-    const float p = x * hi;
-    const float e = fmaf(x, hi, -p);       // exact: x * hi = p + e
-    float corr = fmaf(x, lo, e);
-    const float pr = rintf(p);
-    corr += (p - pr);                      // exact (p and pr differ by < 1 ulp-scale)
-    const long long ip = (long long)pr;
-    const long long ic = __float2ll_rn(corr);
-    return (uint32_t)(unsigned long long)(ip + ic);
-}
-
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
 // multiplies, the key bumped by the Weyl constants between rounds.
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
@@ -396,20 +382,9 @@ __device__ __forceinline__ double2 rho_read(const unsigned long long* src, doubl
                         (double)(long long)__ldcg(src + 1) * inv_scale);
 }
 
-// Structure factors that draw their own k-batch from the caller's positions
-// (pos non-null): see k_rho_mixed.
-struct RhoOwn {
-    const float4* pos;       // null: read the prep kernel's samples and records
-    const uint64_t* table;
-    int tab_words;           // > 0: tables staged in shared memory
-    const uint64_t* step_dev;
-    uint64_t step_arg;
-    int* err;
-};
 void launch_rho_mixed(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
-                      int4* ksamp, const double* kcoef, const uint4* fx,
-                      unsigned long long* rho_fx, int* kcnt, float2* kab,
-                      const RhoOwn& own = RhoOwn{});
+                      const int4* ksamp, const double* kcoef, const uint4* fx,
+                      unsigned long long* rho_fx, int* kcnt, float2* kab);
 void launch_rho_f64(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
                     const int4* ksamp, const double4* fx64, unsigned long long* rho_fx);
 // The last stage of a neighbour-list MD step, run by the Fourier-force
@@ -421,7 +396,6 @@ struct MdOut {
     float4* md_vel;
     NhState* nh;
     const uint64_t* cur_step;
-    uint64_t* step_dev;      // nullable: advanced to cur_step + 1 (the step's last kernel)
     int* list_flag;          // nullable: cleared (the step's rebuild flag is consumed)
 };
 void launch_fourier_force_mixed(cudaStream_t st, bool one, const Work& w, int nblk, int split,
