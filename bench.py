@@ -234,7 +234,7 @@ def traffic_for(kernel, workload_name):
 
 FP32_LANES_PER_SM = 128
 # FP32-pipe operations the real-space pass needs: the distance test of a
-# candidate (3 subtractions, 1 multiply, 2 fused multiply-adds) and the terms
+# list entry (3 subtractions, 1 multiply, 2 fused multiply-adds) and the terms
 # of a pair inside the cutoff (erfc by the 5-term rational form, Gaussian,
 # G(r)/r, force, potential and energy accumulation: 25 operations, plus three
 # special-function operations counted separately).
@@ -242,23 +242,26 @@ REAL_OPS_PER_CANDIDATE = 6
 REAL_OPS_PER_PAIR = 25
 
 
+def list_skin(p):
+    """The neighbour-list skin the library uses for these parameters (0.1 r_c,
+    capped so that the cells of side r_c + skin stay at least 3 per edge, or
+    r_c + skin <= L/2 in the one-cell mode)."""
+    cap = p.box / 3 - p.r_c if p.box >= 3 * p.r_c else p.box / 2 - p.r_c
+    s = getattr(p, "skin", 0.0)
+    return max(0.0, min(s if s > 0 else 0.1 * p.r_c, cap))
+
+
 def pair_counts(wl):
-    """(candidates, pairs within r_c) of the real-space pass, counted on the host
-    from the cell occupancy and a k-d tree (ordered pairs, as the kernel visits them)."""
+    """(candidates, pairs within r_c) of the MD step's real-space pass, counted
+    on the host with a k-d tree: the list entries it visits (ordered pairs
+    within r_c + skin, self excluded) and the ordered pairs within r_c."""
     import numpy as np
     from scipy.spatial import cKDTree
     p = wl.params
-    L = p.box
-    ncd = min(256, int(L // p.r_c))
     pos = wl.pos.astype(np.float64)
-    cell = np.minimum((pos / L * ncd).astype(int), ncd - 1)
-    cid = (cell[:, 2] * ncd + cell[:, 1]) * ncd + cell[:, 0]
-    occ = np.bincount(cid, minlength=ncd ** 3).reshape(ncd, ncd, ncd)
-    nb = sum(np.roll(occ, (dz, dy, dx), axis=(0, 1, 2))
-             for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1))
-    candidates = int((occ * nb).sum() - wl.n)
-    tree = cKDTree(pos, boxsize=L)
-    pairs = int(tree.count_neighbors(tree, p.r_c)) - wl.n        # ordered pairs, self excluded
+    tree = cKDTree(pos, boxsize=p.box)
+    candidates = int(tree.count_neighbors(tree, p.r_c + list_skin(p))) - wl.n
+    pairs = int(tree.count_neighbors(tree, p.r_c)) - wl.n
     return candidates, pairs
 
 
@@ -322,8 +325,9 @@ def roofline(prof, wl, peaks, units, counts=None):
         achieved = work / avg_s / 1e12
         out = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
                "unit": "Tops/s", "frac": achieved / peak, "peak_basis": units["alu_basis"],
-               "algorithmic": f"{REAL_OPS_PER_CANDIDATE} ops x {cand} candidates + "
-                              f"{REAL_OPS_PER_PAIR} ops x {pairs} pairs within r_c"}
+               "algorithmic": f"{REAL_OPS_PER_CANDIDATE} ops x {cand} list entries (pairs "
+                              f"within r_c + skin) + {REAL_OPS_PER_PAIR} ops x {pairs} pairs "
+                              f"within r_c"}
     else:
         # bytes the kernel must move: records read/written per particle
         per_particle = {"prep": 16 + 16 + 4 + 4, "scatter": 4 + 4 + 4 + 4,

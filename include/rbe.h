@@ -309,9 +309,11 @@ enum {
 };
 
 /* Enable (1) or disable (0) per-kernel timing.  While enabled, rbe_forces*,
- * rbe_step* record CUDA events around every kernel on the handle's stream,
- * wait for them at the end of each evaluation and accumulate the device time
- * per kernel; graph replay is bypassed. */
+ * rbe_step* run every kernel of an evaluation on the handle's stream, one
+ * after another (the concurrent branches are serialised, so each time is the
+ * kernel's alone), record CUDA events around each, wait for them at the end of
+ * each evaluation and accumulate the device time per kernel; graph replay is
+ * bypassed. */
 rbe_status rbe_profile(rbe_handle h, int32_t enable);
 
 /* Read and reset the accumulated profile: ms[RBE_K_COUNT] device milliseconds

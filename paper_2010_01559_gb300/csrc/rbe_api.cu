@@ -914,7 +914,9 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     const int want_q = (fourier && (a.E || a.phi || a.phi64)) ? 1 : 0;
     const int n = h->batch ? h->ntot : h->cur_n;
     const bool prof = h->prof_on && st == h->stream;
-    cudaStream_t st2 = h->stream2;
+    // profiling runs the branches one after another on st, so that each
+    // kernel's event pair brackets that kernel alone
+    cudaStream_t st2 = prof ? st : h->stream2;
     bool used[RBE_K_COUNT] = {};
     int count = 0;
     auto run = [&](int kid, cudaStream_t s, auto&& launch) {
@@ -984,7 +986,7 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     // third stream, so that the list pass need not wait for it
     cudaStream_t sc = st;
     if (a.list) {
-        sc = h->stream3;
+        sc = prof ? st : h->stream3;
         if (!fourier) cudaEventRecord(h->ev_fork, st);
         cudaStreamWaitEvent(sc, h->ev_fork, 0);
     }
