@@ -187,6 +187,22 @@ k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
     const bool active = t < tl.count;
     uint4 p = make_uint4(0, 0, 0, 0);
     if (tl.count > 0) p = rec[i];
+    // neighbour-list MD step: the inputs of the closing update (thread t:
+    // particle t of the tile) and the thermostat's noise, fetched before the
+    // wave-vector loop -- nothing writes them during this kernel
+    const bool epi = md.freal && (int)threadIdx.x < tl.count;
+    const bool nhm = md.md_pos && md.nh && S.thermostat == RBE_THERMO_NOSE_HOOVER;
+    float4 e_fr = make_float4(0.f, 0.f, 0.f, 0.f), e_v = e_fr, e_r = e_fr;
+    MdNoise e_z{0.f, 0.f, 0.f, false};
+    if (epi) {
+        const int o = tl.first + threadIdx.x;
+        e_fr = md.freal[o];
+        if (md.md_pos) {
+            e_v = md.md_vel[o];
+            e_r = md.md_pos[o];
+            if (!nhm) e_z = md_noise(S, *md.cur_step, o);
+        }
+    }
     float fx = 0.f, fy = 0.f, fz = 0.f, ph = 0.f;
     for (int base = 0; base < S.P; base += kKT) {
         const int cnt = min(kKT, S.P - base);
@@ -240,19 +256,21 @@ k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
         s_t[t] = make_float4(sc * fx, sc * fy, sc * fz, 0.f);
     }
     __syncthreads();
-    const bool nhm = md.md_pos && md.nh && S.thermostat == RBE_THERMO_NOSE_HOOVER;
     unsigned long long k2 = 0ull;
-    if ((int)threadIdx.x < tl.count) {
+    if (epi) {
         const int o = tl.first + threadIdx.x;
-        const float4 fr = md.freal[o];
         const float4 ff = s_t[threadIdx.x];
-        const float Fx = fr.x + ff.x, Fy = fr.y + ff.y, Fz = fr.z + ff.z;
+        const float Fx = e_fr.x + ff.x, Fy = e_fr.y + ff.y, Fz = e_fr.z + ff.z;
         if (md.F_out) md.F_out[o] = make_float4(Fx, Fy, Fz, 0.f);
-        if (nhm)
-            k2 = nose_hoover_update(md.md_pos, md.md_vel, S, md.nh[tl.sys].f_va,
-                                    md.nh[tl.sys].f_vf, o, Fx, Fy, Fz);
-        else if (md.md_pos)
-            langevin_update(md.md_pos, md.md_vel, md.cur_step, S, o, Fx, Fy, Fz);
+        if (md.md_pos) {
+            if (nhm)
+                k2 = nose_hoover_apply(S, md.nh[tl.sys].f_va, md.nh[tl.sys].f_vf, Fx, Fy, Fz,
+                                       e_v, e_r);
+            else
+                md_apply(S, e_z, Fx, Fy, Fz, e_v, e_r);
+            md.md_vel[o] = e_v;
+            md.md_pos[o] = e_r;
+        }
     }
     if (nhm) warp_add_u64(k2, &md.nh[tl.sys].k2);
 }

@@ -131,23 +131,31 @@ __device__ __forceinline__ void drift_wrap(const SysDev& S, const float4& v, flo
     if (rp.z >= L) rp.z = 0.f;
 }
 
-// Nose-Hoover leapfrog step for particle o: v <- va v + vf F (the friction
-// taken half before and half after the kick), drift, wrap.  Returns m|v|^2/kT
-// in 64-bit fixed point (2^-32) for the kinetic sum of the step.
+// Nose-Hoover leapfrog step on v and rp in registers: v <- va v + vf F (the
+// friction taken half before and half after the kick), drift, wrap.  Returns
+// m|v|^2/kT in 64-bit fixed point (2^-32) for the kinetic sum of the step.
+__device__ __forceinline__ unsigned long long nose_hoover_apply(const SysDev& S, float va,
+                                                                float vf, float fx, float fy,
+                                                                float fz, float4& v, float4& rp) {
+    v.x = fmaf(va, v.x, vf * fx);
+    v.y = fmaf(va, v.y, vf * fy);
+    v.z = fmaf(va, v.z, vf * fz);
+    drift_wrap(S, v, rp);
+    const float v2 = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z));
+    return __double2ull_rn((double)v2 * S.nh_k2scale);
+}
+
+// The same for particle o, from and to memory.
 __device__ __forceinline__ unsigned long long nose_hoover_update(float4* md_pos, float4* md_vel,
                                                                  const SysDev& S, float va,
                                                                  float vf, int o, float fx,
                                                                  float fy, float fz) {
     float4 v = md_vel[o];
     float4 rp = md_pos[o];
-    v.x = fmaf(va, v.x, vf * fx);
-    v.y = fmaf(va, v.y, vf * fy);
-    v.z = fmaf(va, v.z, vf * fz);
-    drift_wrap(S, v, rp);
+    const unsigned long long k2 = nose_hoover_apply(S, va, vf, fx, fy, fz, v, rp);
     md_vel[o] = v;
     md_pos[o] = rp;
-    const float v2 = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z));
-    return __double2ull_rn((double)v2 * S.nh_k2scale);
+    return k2;
 }
 
 // Sum of a 64-bit value over the warp, added by lane 0 to *dst.
@@ -156,27 +164,24 @@ __device__ __forceinline__ void warp_add_u64(unsigned long long v, unsigned long
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
 }
 
-// Langevin step of Sec. 3.3 for particle o (caller index) with total force F:
-// kick, exact Ornstein-Uhlenbeck with Philox/Box-Muller normals, drift, wrap.
-__device__ __forceinline__ void langevin_update(float4* md_pos, float4* md_vel,
-                                                const uint64_t* cur_step, const SysDev& S, int o,
-                                                float fx, float fy, float fz) {
-    const uint64_t step = *cur_step;
+// The thermostat's random numbers for particle o at a step (they do not
+// depend on the force, so a kernel may draw them early): Langevin, the normals
+// of the Ornstein-Uhlenbeck step; Andersen, the collision test and the new
+// velocity's normals.
+struct MdNoise {
+    float xi0, xi1, xi2;
+    bool hit;                                // Andersen collision
+};
+
+__device__ __forceinline__ MdNoise md_noise(const SysDev& S, uint64_t step, int o) {
     const uint2 key = make_uint2((uint32_t)S.seed, (uint32_t)(S.seed >> 32));
     const uint32_t pid = (uint32_t)(o - S.off_p);
     const bool andersen = S.thermostat == RBE_THERMO_ANDERSEN;
     // Langevin: normals of the OU step; Andersen: collision word, then normals
     const uint4 c = philox4x32_10(make_uint4(pid, 0u, (uint32_t)step,
                                              (S.stream << 8) | (andersen ? 0x07u : 0x02u)), key);
-    const bool hit = andersen && (uint64_t)c.x < S.andersen_thr;
-    float4 v = md_vel[o];
-    float4 rp = md_pos[o];
-    const float dtm = S.f_dt_over_m;
-    v.x = fmaf(dtm, fx, v.x);
-    v.y = fmaf(dtm, fy, v.y);
-    v.z = fmaf(dtm, fz, v.z);
-    float xi0 = 0.f, xi1 = 0.f, xi2 = 0.f;
-    if (!andersen || hit) {
+    MdNoise z{0.f, 0.f, 0.f, andersen && (uint64_t)c.x < S.andersen_thr};
+    if (!andersen || z.hit) {
         const uint4 w = andersen ? philox4x32_10(make_uint4(pid, 1u, (uint32_t)step,
                                                             (S.stream << 8) | 0x07u), key)
                                  : c;
@@ -188,19 +193,42 @@ __device__ __forceinline__ void langevin_update(float4* md_pos, float4* md_vel,
         float s2, c2v, s4, c4;
         sincospif(2.f * u2, &s2, &c2v);
         sincospif(2.f * u4, &s4, &c4);
-        xi0 = r1 * c2v; xi1 = r1 * s2; xi2 = r3 * c4;
+        z.xi0 = r1 * c2v; z.xi1 = r1 * s2; z.xi2 = r3 * c4;
     }
-    if (!andersen) {                                   // exact Ornstein-Uhlenbeck step
+    return z;
+}
+
+// Langevin step of Sec. 3.3 (kick, exact Ornstein-Uhlenbeck, drift, wrap) or
+// the Andersen loop step (kick, drift, then the collision) on v and rp in
+// registers, with total force F and the step's noise z.
+__device__ __forceinline__ void md_apply(const SysDev& S, const MdNoise& z, float fx, float fy,
+                                         float fz, float4& v, float4& rp) {
+    const float dtm = S.f_dt_over_m;
+    v.x = fmaf(dtm, fx, v.x);
+    v.y = fmaf(dtm, fy, v.y);
+    v.z = fmaf(dtm, fz, v.z);
+    if (S.thermostat != RBE_THERMO_ANDERSEN) {         // exact Ornstein-Uhlenbeck step
         const float c1 = S.f_c1, c2 = S.f_c2;
-        v.x = fmaf(c1, v.x, c2 * xi0);
-        v.y = fmaf(c1, v.y, c2 * xi1);
-        v.z = fmaf(c1, v.z, c2 * xi2);
+        v.x = fmaf(c1, v.x, c2 * z.xi0);
+        v.y = fmaf(c1, v.y, c2 * z.xi1);
+        v.z = fmaf(c1, v.z, c2 * z.xi2);
     }
     drift_wrap(S, v, rp);
-    if (hit) {                                         // Andersen collision after the drift
+    if (z.hit) {                                        // Andersen collision after the drift
         const float sd = S.f_vsd;
-        v.x = sd * xi0; v.y = sd * xi1; v.z = sd * xi2;
+        v.x = sd * z.xi0; v.y = sd * z.xi1; v.z = sd * z.xi2;
     }
+}
+
+// Langevin or Andersen step for particle o (caller index) with total force F,
+// from and to memory.
+__device__ __forceinline__ void langevin_update(float4* md_pos, float4* md_vel,
+                                                const uint64_t* cur_step, const SysDev& S, int o,
+                                                float fx, float fy, float fz) {
+    const MdNoise z = md_noise(S, *cur_step, o);
+    float4 v = md_vel[o];
+    float4 rp = md_pos[o];
+    md_apply(S, z, fx, fy, fz, v, rp);
     md_vel[o] = v;
     md_pos[o] = rp;
 }
