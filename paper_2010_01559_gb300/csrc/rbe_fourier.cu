@@ -169,12 +169,20 @@ k_rho_f64(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
 struct KPhase { uint32_t mx, my, mz, pad; };
 struct KForce { float mx, my, mz, A; };
 
-// PHI: also dE/dq (the forces path); MD steps need only the force.
-template <int SPLIT, bool PHI, bool ONE>
-__global__ void __launch_bounds__(kBlockP)
+// SPLIT threads per particle (each a 1/SPLIT share of the wave vectors), or
+// with SPLIT = 1 PT = 2 particles per thread, which share each wave vector's
+// shared-memory loads and the loop overhead (the pass is issue-bound at large
+// N).  A block holds a tile of kBlockP / SPLIT particles and kBlockP / PT
+// threads.  PHI: also dE/dq (the forces path); MD steps need only the force.
+template <int SPLIT, int PT, bool PHI, bool ONE>
+__global__ void __launch_bounds__(kBlockP / PT)
 k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
               const int4* __restrict__ ksamp, const float2* __restrict__ kab,
               float4* __restrict__ fs, const __grid_constant__ MdOut md) {
+    static_assert(PT == 1 || SPLIT == 1, "two particles per thread only with one thread each");
+    constexpr int NT = kBlockP / PT;                // threads per block
+    constexpr int TILE = kBlockP / SPLIT;           // particles per block
+    constexpr int EP = (TILE + NT - 1) / NT;        // closing updates per thread
     constexpr int kKT = 256;                        // wave vectors staged per pass
     __shared__ KPhase kp[kKT];
     __shared__ KForce kf[kKT];
@@ -182,28 +190,40 @@ k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
     const Tile tl = tile_of<ONE>(w);
     const SysDev& S = sys_of<ONE>(w, tl.sys);
     const int sub = threadIdx.x % SPLIT;            // lane within the particle's group
-    const int t = threadIdx.x / SPLIT;
-    const int i = tl.first + min(t, max(tl.count - 1, 0));
-    const bool active = t < tl.count;
-    uint4 p = make_uint4(0, 0, 0, 0);
-    if (tl.count > 0) p = rec[i];
+    int tq[PT];
+    uint4 p[PT];
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+        tq[q] = threadIdx.x / SPLIT + q * (NT / SPLIT);
+        p[q] = make_uint4(0, 0, 0, 0);
+        if (tl.count > 0) p[q] = rec[tl.first + min(tq[q], tl.count - 1)];
+    }
     // neighbour-list MD step: the inputs of the closing update (thread t:
-    // particle t of the tile) and the thermostat's noise, fetched before the
-    // wave-vector loop -- nothing writes them during this kernel
-    const bool epi = md.freal && (int)threadIdx.x < tl.count;
+    // particles t, t + NT, .. of the tile) and the thermostat's noise, fetched
+    // before the wave-vector loop -- nothing writes them during this kernel
     const bool nhm = md.md_pos && md.nh && S.thermostat == RBE_THERMO_NOSE_HOOVER;
-    float4 e_fr = make_float4(0.f, 0.f, 0.f, 0.f), e_v = e_fr, e_r = e_fr;
-    MdNoise e_z{0.f, 0.f, 0.f, false};
-    if (epi) {
-        const int o = tl.first + threadIdx.x;
-        e_fr = md.freal[o];
-        if (md.md_pos) {
-            e_v = md.md_vel[o];
-            e_r = md.md_pos[o];
-            if (!nhm) e_z = md_noise(S, *md.cur_step, o);
+    float4 e_fr[EP], e_v[EP], e_r[EP];
+    MdNoise e_z[EP];
+#pragma unroll
+    for (int e = 0; e < EP; ++e) {
+        e_fr[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        e_v[e] = e_fr[e];
+        e_r[e] = e_fr[e];
+        e_z[e] = MdNoise{0.f, 0.f, 0.f, false};
+        const int te = threadIdx.x + e * NT;
+        if (md.freal && te < tl.count) {
+            const int o = tl.first + te;
+            e_fr[e] = md.freal[o];
+            if (md.md_pos) {
+                e_v[e] = md.md_vel[o];
+                e_r[e] = md.md_pos[o];
+                if (!nhm) e_z[e] = md_noise(S, *md.cur_step, o);
+            }
         }
     }
-    float fx = 0.f, fy = 0.f, fz = 0.f, ph = 0.f;
+    float fx[PT], fy[PT], fz[PT], ph[PT];
+#pragma unroll
+    for (int q = 0; q < PT; ++q) fx[q] = fy[q] = fz[q] = ph[q] = 0.f;
     for (int base = 0; base < S.P; base += kKT) {
         const int cnt = min(kKT, S.P - base);
         __syncthreads();
@@ -218,58 +238,68 @@ k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
 #pragma unroll 4
         for (int k = sub; k < cnt; k += SPLIT) {
             const KPhase a = kp[k];
-            const uint32_t phs = a.mx * p.x + a.my * p.y + a.mz * p.z;
-            const float th = (float)(int32_t)phs * kTwoPiOver2p32;
-            float sn, cs;
-            __sincosf(th, &sn, &cs);
             const KForce f = kf[k];
             const float B = kb[k];
-            const float g = fmaf(cs, f.A, -sn * B);     // Im(e^{-i th} rho) * coef
-            fx = fmaf(g, f.mx, fx);
-            fy = fmaf(g, f.my, fy);
-            fz = fmaf(g, f.mz, fz);
-            if constexpr (PHI) ph = fmaf(cs, B, fmaf(sn, f.A, ph));   // Re(e^{-i th} rho) coef
+#pragma unroll
+            for (int q = 0; q < PT; ++q) {
+                const uint32_t phs = a.mx * p[q].x + a.my * p[q].y + a.mz * p[q].z;
+                const float th = (float)(int32_t)phs * kTwoPiOver2p32;
+                float sn, cs;
+                __sincosf(th, &sn, &cs);
+                const float g = fmaf(cs, f.A, -sn * B);     // Im(e^{-i th} rho) * coef
+                fx[q] = fmaf(g, f.mx, fx[q]);
+                fy[q] = fmaf(g, f.my, fy[q]);
+                fz[q] = fmaf(g, f.mz, fz[q]);
+                if constexpr (PHI) ph[q] = fmaf(cs, B, fmaf(sn, f.A, ph[q]));   // Re(..) coef
+            }
         }
     }
 #pragma unroll
     for (int o = SPLIT / 2; o > 0; o >>= 1) {
-        fx += __shfl_down_sync(0xffffffffu, fx, o, SPLIT);
-        fy += __shfl_down_sync(0xffffffffu, fy, o, SPLIT);
-        fz += __shfl_down_sync(0xffffffffu, fz, o, SPLIT);
-        ph += __shfl_down_sync(0xffffffffu, ph, o, SPLIT);
+        fx[0] += __shfl_down_sync(0xffffffffu, fx[0], o, SPLIT);
+        fy[0] += __shfl_down_sync(0xffffffffu, fy[0], o, SPLIT);
+        fz[0] += __shfl_down_sync(0xffffffffu, fz[0], o, SPLIT);
+        ph[0] += __shfl_down_sync(0xffffffffu, ph[0], o, SPLIT);
     }
     if (!md.freal) {
-        if (active && sub == 0) {
-            const float q = __uint_as_float(p.w);
-            const float sc = -q * (float)(2.0 * M_PI) * S.f_invL;
-            fs[i] = make_float4(sc * fx, sc * fy, sc * fz, ph);
-        }
+#pragma unroll
+        for (int q = 0; q < PT; ++q)
+            if (tq[q] < tl.count && sub == 0) {
+                const float qc = __uint_as_float(p[q].w);
+                const float sc = -qc * (float)(2.0 * M_PI) * S.f_invL;
+                fs[tl.first + tq[q]] = make_float4(sc * fx[q], sc * fy[q], sc * fz[q], ph[q]);
+            }
         return;
     }
-    // neighbour-list MD step: the total force and the thermostat, one thread
-    // per particle (thread t: particle t of the tile)
+    // neighbour-list MD step: the total force and the thermostat
     if (md.list_flag && blockIdx.x == 0 && threadIdx.x == 0) *md.list_flag = 0;   // consumed
-    __shared__ float4 s_t[kBlockP / SPLIT];
-    if (active && sub == 0) {
-        const float q = __uint_as_float(p.w);
-        const float sc = -q * (float)(2.0 * M_PI) * S.f_invL;
-        s_t[t] = make_float4(sc * fx, sc * fy, sc * fz, 0.f);
-    }
+    __shared__ float4 s_t[TILE];
+#pragma unroll
+    for (int q = 0; q < PT; ++q)
+        if (tq[q] < tl.count && sub == 0) {
+            const float qc = __uint_as_float(p[q].w);
+            const float sc = -qc * (float)(2.0 * M_PI) * S.f_invL;
+            s_t[tq[q]] = make_float4(sc * fx[q], sc * fy[q], sc * fz[q], 0.f);
+        }
     __syncthreads();
     unsigned long long k2 = 0ull;
-    if (epi) {
-        const int o = tl.first + threadIdx.x;
-        const float4 ff = s_t[threadIdx.x];
-        const float Fx = e_fr.x + ff.x, Fy = e_fr.y + ff.y, Fz = e_fr.z + ff.z;
-        if (md.F_out) md.F_out[o] = make_float4(Fx, Fy, Fz, 0.f);
-        if (md.md_pos) {
-            if (nhm)
-                k2 = nose_hoover_apply(S, md.nh[tl.sys].f_va, md.nh[tl.sys].f_vf, Fx, Fy, Fz,
-                                       e_v, e_r);
-            else
-                md_apply(S, e_z, Fx, Fy, Fz, e_v, e_r);
-            md.md_vel[o] = e_v;
-            md.md_pos[o] = e_r;
+#pragma unroll
+    for (int e = 0; e < EP; ++e) {
+        const int te = threadIdx.x + e * NT;
+        if (te < tl.count) {
+            const int o = tl.first + te;
+            const float4 ff = s_t[te];
+            const float Fx = e_fr[e].x + ff.x, Fy = e_fr[e].y + ff.y, Fz = e_fr[e].z + ff.z;
+            if (md.F_out) md.F_out[o] = make_float4(Fx, Fy, Fz, 0.f);
+            if (md.md_pos) {
+                if (nhm)
+                    k2 += nose_hoover_apply(S, md.nh[tl.sys].f_va, md.nh[tl.sys].f_vf, Fx, Fy,
+                                            Fz, e_v[e], e_r[e]);
+                else
+                    md_apply(S, e_z[e], Fx, Fy, Fz, e_v[e], e_r[e]);
+                md.md_vel[o] = e_v[e];
+                md.md_pos[o] = e_r[e];
+            }
         }
     }
     if (nhm) warp_add_u64(k2, &md.nh[tl.sys].k2);
@@ -352,16 +382,17 @@ void launch_rho_f64(cudaStream_t st, bool one, const Work& w, int nchunks, int l
         k_rho_f64<false><<<grid, kLTile, 0, st>>>(w, ksamp, fx64, rho_fx);
 }
 
-template <int SPLIT>
+template <int SPLIT, int PT>
 static void force_mixed_split(cudaStream_t st, bool one, const Work& w, int nblk, const uint4* fx,
                               const int4* ksamp, const float2* kab, float4* fs,
                               const MdOut& md) {
+    constexpr int NT = kBlockP / PT;
     if (md.freal) {
-        if (one) k_force_mixed<SPLIT, false, true><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, kab, fs, md);
-        else k_force_mixed<SPLIT, false, false><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, kab, fs, md);
+        if (one) k_force_mixed<SPLIT, PT, false, true><<<nblk, NT, 0, st>>>(w, fx, ksamp, kab, fs, md);
+        else k_force_mixed<SPLIT, PT, false, false><<<nblk, NT, 0, st>>>(w, fx, ksamp, kab, fs, md);
     } else {
-        if (one) k_force_mixed<SPLIT, true, true><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, kab, fs, md);
-        else k_force_mixed<SPLIT, true, false><<<nblk, kBlockP, 0, st>>>(w, fx, ksamp, kab, fs, md);
+        if (one) k_force_mixed<SPLIT, PT, true, true><<<nblk, NT, 0, st>>>(w, fx, ksamp, kab, fs, md);
+        else k_force_mixed<SPLIT, PT, true, false><<<nblk, NT, 0, st>>>(w, fx, ksamp, kab, fs, md);
     }
 }
 
@@ -370,10 +401,10 @@ void launch_fourier_force_mixed(cudaStream_t st, bool one, const Work& w, int nb
                                 float4* fs, const MdOut& md) {
     if (nblk <= 0) return;
     switch (split) {
-        case 2: force_mixed_split<2>(st, one, w, nblk, fx, ksamp, kab, fs, md); break;
-        case 4: force_mixed_split<4>(st, one, w, nblk, fx, ksamp, kab, fs, md); break;
-        case 8: force_mixed_split<8>(st, one, w, nblk, fx, ksamp, kab, fs, md); break;
-        default: force_mixed_split<1>(st, one, w, nblk, fx, ksamp, kab, fs, md); break;
+        case 2: force_mixed_split<2, 1>(st, one, w, nblk, fx, ksamp, kab, fs, md); break;
+        case 4: force_mixed_split<4, 1>(st, one, w, nblk, fx, ksamp, kab, fs, md); break;
+        case 8: force_mixed_split<8, 1>(st, one, w, nblk, fx, ksamp, kab, fs, md); break;
+        default: force_mixed_split<1, 2>(st, one, w, nblk, fx, ksamp, kab, fs, md); break;
     }
 }
 

@@ -579,13 +579,15 @@ __global__ void __launch_bounds__(kBlockP) k_real_list(const __grid_constant__ R
         const size_t st = (size_t)a.nbr_stride;
         // batches of kListU entries per lane, all gathers of a batch in flight
         // at once; the first batch is loaded alongside the count (slots within
-        // the capacity always hold valid indices: the list starts zeroed)
-        const int cnt = __ldg(a.ncnt + i);
+        // the capacity always hold valid indices: the list starts zeroed).  The
+        // list is read once per step: streaming loads, so that it does not
+        // evict the records the gathers hit in L2.
+        const int cnt = __ldcs(a.ncnt + i);
         int j[kListU];
 #pragma unroll
         for (int q = 0; q < kListU; ++q) {
             const int kk = l + q * R;
-            j[q] = kk < a.nbr_cap ? __ldg(nb + (size_t)kk * st) : 0;
+            j[q] = kk < a.nbr_cap ? __ldcs(nb + (size_t)kk * st) : 0;
         }
         for (int k0 = l;;) {
             uint4 sj[kListU];
@@ -599,7 +601,7 @@ __global__ void __launch_bounds__(kBlockP) k_real_list(const __grid_constant__ R
 #pragma unroll
             for (int q = 0; q < kListU; ++q) {
                 const int kk = k0 + q * R;
-                j[q] = kk < cnt ? __ldg(nb + (size_t)kk * st) : 0;
+                j[q] = kk < cnt ? __ldcs(nb + (size_t)kk * st) : 0;
             }
         }
     }
