@@ -1015,6 +1015,7 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
             la.stride = std::max(h->ntot, 1);
             la.cap = h->list_cap;
             la.sref = h->d_sref;
+            la.perm = h->d_perm;
             la.stats = h->d_list_stats;
             la.err = h->d_err;
             launch_list_build(sc, one, la);

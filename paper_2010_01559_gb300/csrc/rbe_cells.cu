@@ -245,8 +245,10 @@ k_prep_mixed(const __grid_constant__ Work w, const float4* __restrict__ pos_q,
     int moved = 0;
     if (t < tl.count) {
         const int i = tl.first + t;
-        // list step: the sorted slot of the last build, loaded with the position
+        // list step: the sorted slot and the record of the last build, loaded
+        // with the position
         const int si = pa.list_flag ? __ldg(pa.iperm + i) : 0;
+        const uint4 r0 = pa.list_flag ? __ldg(pa.sref + i) : make_uint4(0, 0, 0, 0);
         const float4 p = pos_q[i];
         const uint32_t sx = to_fixed(p.x, S.fx_hi, S.fx_lo);
         const uint32_t sy = to_fixed(p.y, S.fx_hi, S.fx_lo);
@@ -264,7 +266,6 @@ k_prep_mixed(const __grid_constant__ Work w, const float4* __restrict__ pos_q,
             // neighbour-list step: the record goes to its sorted slot of the
             // last build, and a displacement beyond skin/2 since that build
             // (minimum image, from the fixed-point difference) asks for a new list
-            const uint4 r0 = pa.sref[si];
             const float Lu = S.L_over_2_32;
             const float dx = (float)(int32_t)(sx - r0.x) * Lu;
             const float dy = (float)(int32_t)(sy - r0.y) * Lu;

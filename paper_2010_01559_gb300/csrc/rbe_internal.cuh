@@ -357,7 +357,7 @@ struct PrepArgs {
     NhState* nh;             // MD steps: Nose-Hoover state per system (null otherwise)
     // neighbour-list MD steps: displacement test against the last build and
     // the sorted records for the list kernel (null otherwise)
-    const uint4* sref;       // [sorted] records at the last build
+    const uint4* sref;       // [caller index] records at the last build
     const int* iperm;        // caller index -> sorted index of the last build
     uint4* spos;             // [sorted] current records
     int* list_flag;          // set: rebuild the list in this step
@@ -388,7 +388,8 @@ struct ListArgs {
     int* nbr;                // [slot * stride + i]
     int* ncnt;               // [i]
     int stride, cap;
-    uint4* sref;             // copy of spos at the build
+    uint4* sref;             // the build's records, by caller index (perm)
+    const int* perm;         // sorted -> caller index
     unsigned long long* stats;   // [0] builds, [1] largest count
     int* err;
 };

@@ -489,7 +489,8 @@ k_real_seg(const __grid_constant__ RealArgs a) {
 // One thread per sorted particle: the 27 neighbour cells as 9 rows of three
 // x-adjacent cells (one row, once, with one cell per edge), every j != i whose
 // fixed-point minimum-image distance is within r_c + skin, in scan order.  The
-// record of the build is kept as the reference of the displacement test.
+// record of the build is kept, by caller index, as the reference of the
+// displacement test.
 template <bool ONE>
 __global__ void __launch_bounds__(kBlockP) k_list_build(const __grid_constant__ ListArgs la) {
     if (!*la.list_flag) return;
@@ -508,29 +509,37 @@ __global__ void __launch_bounds__(kBlockP) k_list_build(const __grid_constant__ 
         const int dlo = ncd < 3 ? 0 : -1, dhi = ncd < 3 ? 0 : 1;
         int* out = la.nbr + i;
         const size_t stride = (size_t)la.stride;
-        for (int dz = dlo; dz <= dhi; ++dz) {
-            for (int dy = dlo; dy <= dhi; ++dy) {
-                const int zz = wrapc(cz + dz, ncd), yy = wrapc(cy + dy, ncd);
-                int r0, e0, r1, e1;
-                row_ranges(la.cell_start, S.off_c + (zz * ncd + yy) * ncd, cx, ncd, r0, e0, r1, e1);
-                for (int part = 0; part < 2; ++part) {
-                    const int b = part ? r1 : r0, e = part ? e1 : e0;
-                    for (int j = b; j < e; ++j) {
-                        const uint4 sj = __ldg(la.spos + j);
-                        const float dx = (float)(int32_t)(sj.x - si.x) * Lu;
-                        const float dyy = (float)(int32_t)(sj.y - si.y) * Lu;
-                        const float dzz = (float)(int32_t)(sj.z - si.z) * Lu;
-                        const float r2 = fmaf(dx, dx, fmaf(dyy, dyy, dzz * dzz));
-                        if (r2 < cut2 && j != i) {
-                            if (cnt < la.cap) out[(size_t)cnt * stride] = j;
-                            ++cnt;
+        // two sweeps: the pairs within r_c first, then those in the skin, so
+        // that the lanes of a warp in the list pass mostly agree on the cutoff
+        // branch at the same position in their lists
+        const float rc2 = S.f_rc2;
+        for (int sweep = 0; sweep < 2; ++sweep) {
+            const float lo2 = sweep ? rc2 : -1.f, hi2 = sweep ? cut2 : rc2;
+            for (int dz = dlo; dz <= dhi; ++dz) {
+                for (int dy = dlo; dy <= dhi; ++dy) {
+                    const int zz = wrapc(cz + dz, ncd), yy = wrapc(cy + dy, ncd);
+                    int r0, e0, r1, e1;
+                    row_ranges(la.cell_start, S.off_c + (zz * ncd + yy) * ncd, cx, ncd, r0, e0,
+                               r1, e1);
+                    for (int part = 0; part < 2; ++part) {
+                        const int b = part ? r1 : r0, e = part ? e1 : e0;
+                        for (int j = b; j < e; ++j) {
+                            const uint4 sj = __ldg(la.spos + j);
+                            const float dx = (float)(int32_t)(sj.x - si.x) * Lu;
+                            const float dyy = (float)(int32_t)(sj.y - si.y) * Lu;
+                            const float dzz = (float)(int32_t)(sj.z - si.z) * Lu;
+                            const float r2 = fmaf(dx, dx, fmaf(dyy, dyy, dzz * dzz));
+                            if (r2 >= lo2 && r2 < hi2 && j != i) {
+                                if (cnt < la.cap) out[(size_t)cnt * stride] = j;
+                                ++cnt;
+                            }
                         }
                     }
                 }
             }
         }
         la.ncnt[i] = min(cnt, la.cap);
-        la.sref[i] = si;
+        la.sref[la.perm[i]] = si;           // by caller index: the prep kernel reads it in order
         if (cnt > la.cap) atomicOr(la.err, kErrList);
     }
     const unsigned wmax = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
