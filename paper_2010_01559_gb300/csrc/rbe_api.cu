@@ -220,6 +220,7 @@ struct rbe_ctx {
     cudaEvent_t ev_real = nullptr;            // list step: real-space pass done
     cudaStream_t stream3 = nullptr;           // list step: the rebuild branch
     cudaEvent_t ev_chain = nullptr;           // list step: rebuild branch done
+    cudaEvent_t ev_prep = nullptr;            // list step: prep kernel done
     unsigned long long* d_qsum_fx = nullptr;  // sum q per system (fixed point)
     double2* d_blk_e = nullptr;
     double2* d_blk_w = nullptr;               // per real-space block (W_coul, W_lj)
@@ -698,6 +699,7 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_real, cudaEventDisableTiming));
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_chain, cudaEventDisableTiming));
+    RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_prep, cudaEventDisableTiming));
     RBE_CUDA(h, cudaStreamCreateWithFlags(&h->stream3, cudaStreamNonBlocking));
     return RBE_OK;
 }
@@ -726,6 +728,7 @@ void release(rbe_ctx* h) {
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->ev_real) cudaEventDestroy(h->ev_real);
     if (h->ev_chain) cudaEventDestroy(h->ev_chain);
+    if (h->ev_prep) cudaEventDestroy(h->ev_prep);
     if (h->stream3) cudaStreamDestroy(h->stream3);
     for (int k = 0; k < RBE_K_COUNT; ++k) {
         if (h->ev_beg[k]) cudaEventDestroy(h->ev_beg[k]);
@@ -877,23 +880,24 @@ RealArgs make_real_args(const rbe_ctx* h, int parts) {
 }
 
 // Structure factors: per-chunk partials added to the fixed-point rho(k).
-void launch_rho(const rbe_ctx* h, cudaStream_t st, bool mixed) {
+void launch_rho(const rbe_ctx* h, cudaStream_t st, bool mixed, bool pdl = false) {
     const bool one = !h->batch;
     const int ltiles = (h->pmax + kLTile - 1) / kLTile;
     const Work w = make_work(h, h->d_chunks, h->cur_chunk, 1);
     if (mixed)
         launch_rho_mixed(st, one, w, h->nchunks, ltiles, h->d_ksamp, h->d_kcoef, h->d_fx,
-                         h->d_rho_fx, h->d_kcnt, h->d_kab);
+                         h->d_rho_fx, h->d_kcnt, h->d_kab, pdl);
     else
         launch_rho_f64(st, one, w, h->nchunks, ltiles, h->d_ksamp, h->d_fx64, h->d_rho_fx);
 }
 
-void launch_force(const rbe_ctx* h, cudaStream_t st, bool mixed, const MdOut& md = MdOut{}) {
+void launch_force(const rbe_ctx* h, cudaStream_t st, bool mixed, const MdOut& md = MdOut{},
+                  bool pdl = false) {
     const bool one = !h->batch;
     if (mixed) {
         const Work w = make_work(h, h->split == 1 ? h->d_pblk : h->d_fblk, kBlockP / h->split, 0);
         launch_fourier_force_mixed(st, one, w, h->split == 1 ? h->npblk : h->nfblk, h->split,
-                                   h->d_fx, h->d_ksamp, h->d_kab, h->d_fs, md);
+                                   h->d_fx, h->d_ksamp, h->d_kab, h->d_fs, md, pdl);
     } else {
         const Work w = make_work(h, h->d_pblk, kBlockP, 0);
         launch_fourier_force_f64(st, one, w, h->npblk, h->d_fx64, h->d_ksamp, h->d_rho_fx,
@@ -973,22 +977,26 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
             launch_prep_f64(st, one, wp, h->npblk, a.pos64, h->d_fx64, h->d_cid, h->d_rank,
                             h->d_cell_cnt, pa);
     });
-    if (fourier) {
+    if (a.list) {
+        // list step: prep -> structure factors -> Fourier force on st with
+        // programmatic dependent launches (each kernel's blocks are scheduled
+        // while the previous one drains); the list pass and the rebuild fork
+        // off after prep
+        cudaEventRecord(h->ev_prep, st);
+        if (fourier) run(RBE_K_RHO, st, [&] { launch_rho(h, st, mixed, !prof); });
+    } else if (fourier) {
         cudaEventRecord(h->ev_fork, st);
         cudaStreamWaitEvent(st2, h->ev_fork, 0);
         run(RBE_K_RHO, st2, [&] { launch_rho(h, st2, mixed); });
-        if (!a.list) {
-            run(RBE_K_FOURIER_FORCE, st2, [&] { launch_force(h, st2, mixed); });
-            cudaEventRecord(h->ev_join, st2);
-        }
+        run(RBE_K_FOURIER_FORCE, st2, [&] { launch_force(h, st2, mixed); });
+        cudaEventRecord(h->ev_join, st2);
     }
     // the cell list; on a list step the (usually no-op) rebuild runs on a
     // third stream, so that the list pass need not wait for it
     cudaStream_t sc = st;
     if (a.list) {
         sc = prof ? st : h->stream3;
-        if (!fourier) cudaEventRecord(h->ev_fork, st);
-        cudaStreamWaitEvent(sc, h->ev_fork, 0);
+        cudaStreamWaitEvent(sc, h->ev_prep, 0);
     }
     run(RBE_K_SCAN, sc, [&] {
         launch_scan(sc, h->d_cell_cnt, h->d_cell_start, h->ncell, a.step_dev, h->d_cur_step,
@@ -1048,15 +1056,16 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
         // over the rebuilt list at the end of the rebuild stream; then the
         // Fourier force, which adds it and applies the thermostat
         r.list_when = 0;
-        run(RBE_K_REAL, st, [&] { launch_real_list(st, one, r); });
-        cudaEventRecord(h->ev_real, st);
+        cudaStreamWaitEvent(st2, h->ev_prep, 0);
+        run(RBE_K_REAL, st2, [&] { launch_real_list(st2, one, r); });
+        cudaEventRecord(h->ev_real, st2);
         RealArgs rb = r;
         rb.list_when = 1;
         launch_real_list(sc, one, rb);
         ++count;
         cudaEventRecord(h->ev_chain, sc);
-        cudaStreamWaitEvent(st2, h->ev_real, 0);
-        cudaStreamWaitEvent(st2, h->ev_chain, 0);
+        cudaStreamWaitEvent(st, h->ev_real, 0);
+        cudaStreamWaitEvent(st, h->ev_chain, 0);
         MdOut md;
         md.freal = h->d_freal;
         md.F_out = a.F;
@@ -1065,9 +1074,7 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
         md.nh = pa.nh;
         md.cur_step = h->d_cur_step;
         md.list_flag = h->d_list_flag;
-        run(RBE_K_FOURIER_FORCE, st2, [&] { launch_force(h, st2, true, md); });
-        cudaEventRecord(h->ev_join, st2);
-        cudaStreamWaitEvent(st, h->ev_join, 0);
+        run(RBE_K_FOURIER_FORCE, st, [&] { launch_force(h, st, true, md, !prof); });
     } else {
         run(RBE_K_REAL, st, [&] {
             if (mixed) launch_real_mixed(st, one, r); else launch_real_f64(st, one, r);

@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(kBlockP)
 k_prep_mixed(const __grid_constant__ Work w, const float4* __restrict__ pos_q,
              uint4* __restrict__ fx, int* __restrict__ cid, int* __restrict__ rank,
              int* __restrict__ cell_cnt, const __grid_constant__ PrepArgs pa) {
+    pdl_trigger();                     // a dependent kernel may be scheduled meanwhile
     if ((int)blockIdx.x >= pa.npblk) {             // a k-sampling block
         if (pa.mh) draw_samples_mh<ONE>(w, pa);
         else draw_samples<ONE>(w, pa);

@@ -70,6 +70,8 @@ k_rho_mixed(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
     const SysDev& S = sys_of<ONE>(w, ch.sys);
     const int half = threadIdx.x / kLTile;
     const int l = blockIdx.y * kLTile + (threadIdx.x - half * kLTile);
+    pdl_trigger();                                    // the force kernel may be scheduled
+    pdl_wait();                                       // the prep kernel's samples and records
     if (blockIdx.y * kLTile >= S.P) return;          // whole block beyond this system's P
     const bool active = l < S.P;
     int4 m = make_int4(0, 0, 0, 0);
@@ -190,6 +192,7 @@ k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
     const Tile tl = tile_of<ONE>(w);
     const SysDev& S = sys_of<ONE>(w, tl.sys);
     const int sub = threadIdx.x % SPLIT;            // lane within the particle's group
+    pdl_wait();                                     // rho(k), kab and the real-space forces
     int tq[PT];
     uint4 p[PT];
 #pragma unroll
@@ -359,17 +362,31 @@ void launch_sample(cudaStream_t st, const SysDev* sys, int nsys, int ktot, const
 }
 
 // The k-batch (ksamp) and coef_scale / k^2 (kcoef) come from the prep kernel.
+// A launch configuration, with programmatic stream serialisation if pdl.
+struct PdlConfig {
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1]{};
+    PdlConfig(dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl) {
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = pdl ? 1 : 0;
+    }
+};
+
 void launch_rho_mixed(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
                       const int4* ksamp, const double* kcoef, const uint4* fx,
-                      unsigned long long* rho_fx, int* kcnt, float2* kab) {
+                      unsigned long long* rho_fx, int* kcnt, float2* kab, bool pdl) {
     if (nchunks <= 0 || ltiles <= 0) return;
-    dim3 grid(nchunks, ltiles);
+    PdlConfig c(dim3(nchunks, ltiles), dim3(kLTile * kRhoHalves), 0, st, pdl);
     if (one)
-        k_rho_mixed<true><<<grid, kLTile * kRhoHalves, 0, st>>>(w, ksamp, kcoef, fx, rho_fx,
-                                                                kcnt, kab);
+        cudaLaunchKernelEx(&c.cfg, k_rho_mixed<true>, w, ksamp, kcoef, fx, rho_fx, kcnt, kab);
     else
-        k_rho_mixed<false><<<grid, kLTile * kRhoHalves, 0, st>>>(w, ksamp, kcoef, fx, rho_fx,
-                                                                 kcnt, kab);
+        cudaLaunchKernelEx(&c.cfg, k_rho_mixed<false>, w, ksamp, kcoef, fx, rho_fx, kcnt, kab);
 }
 
 void launch_rho_f64(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
@@ -385,26 +402,26 @@ void launch_rho_f64(cudaStream_t st, bool one, const Work& w, int nchunks, int l
 template <int SPLIT, int PT>
 static void force_mixed_split(cudaStream_t st, bool one, const Work& w, int nblk, const uint4* fx,
                               const int4* ksamp, const float2* kab, float4* fs,
-                              const MdOut& md) {
-    constexpr int NT = kBlockP / PT;
+                              const MdOut& md, bool pdl) {
+    PdlConfig c(dim3(nblk), dim3(kBlockP / PT), 0, st, pdl);
     if (md.freal) {
-        if (one) k_force_mixed<SPLIT, PT, false, true><<<nblk, NT, 0, st>>>(w, fx, ksamp, kab, fs, md);
-        else k_force_mixed<SPLIT, PT, false, false><<<nblk, NT, 0, st>>>(w, fx, ksamp, kab, fs, md);
+        if (one) cudaLaunchKernelEx(&c.cfg, k_force_mixed<SPLIT, PT, false, true>, w, fx, ksamp, kab, fs, md);
+        else cudaLaunchKernelEx(&c.cfg, k_force_mixed<SPLIT, PT, false, false>, w, fx, ksamp, kab, fs, md);
     } else {
-        if (one) k_force_mixed<SPLIT, PT, true, true><<<nblk, NT, 0, st>>>(w, fx, ksamp, kab, fs, md);
-        else k_force_mixed<SPLIT, PT, true, false><<<nblk, NT, 0, st>>>(w, fx, ksamp, kab, fs, md);
+        if (one) cudaLaunchKernelEx(&c.cfg, k_force_mixed<SPLIT, PT, true, true>, w, fx, ksamp, kab, fs, md);
+        else cudaLaunchKernelEx(&c.cfg, k_force_mixed<SPLIT, PT, true, false>, w, fx, ksamp, kab, fs, md);
     }
 }
 
 void launch_fourier_force_mixed(cudaStream_t st, bool one, const Work& w, int nblk, int split,
                                 const uint4* fx, const int4* ksamp, const float2* kab,
-                                float4* fs, const MdOut& md) {
+                                float4* fs, const MdOut& md, bool pdl) {
     if (nblk <= 0) return;
     switch (split) {
-        case 2: force_mixed_split<2, 1>(st, one, w, nblk, fx, ksamp, kab, fs, md); break;
-        case 4: force_mixed_split<4, 1>(st, one, w, nblk, fx, ksamp, kab, fs, md); break;
-        case 8: force_mixed_split<8, 1>(st, one, w, nblk, fx, ksamp, kab, fs, md); break;
-        default: force_mixed_split<1, 2>(st, one, w, nblk, fx, ksamp, kab, fs, md); break;
+        case 2: force_mixed_split<2, 1>(st, one, w, nblk, fx, ksamp, kab, fs, md, pdl); break;
+        case 4: force_mixed_split<4, 1>(st, one, w, nblk, fx, ksamp, kab, fs, md, pdl); break;
+        case 8: force_mixed_split<8, 1>(st, one, w, nblk, fx, ksamp, kab, fs, md, pdl); break;
+        default: force_mixed_split<1, 2>(st, one, w, nblk, fx, ksamp, kab, fs, md, pdl); break;
     }
 }
 

@@ -233,6 +233,16 @@ __device__ __forceinline__ void langevin_update(float4* md_pos, float4* md_vel,
     md_pos[o] = rp;
 }
 
+// Programmatic dependent launch (a kernel launched with programmatic stream
+// serialisation may start while its predecessor in the stream finishes):
+// pdl_wait blocks until every prerequisite grid has completed and its writes
+// are visible (it returns at once without one); pdl_trigger lets this grid's
+// dependents be scheduled early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Where a kernel finds its tile of work and its system.  Batch handles pass
 // tables (tiles[blockIdx.x], then sysv[tile.sys]); single-system handles pass
 // the system's constants by value and the tile size, so a block finds both
@@ -411,9 +421,11 @@ __device__ __forceinline__ double2 rho_read(const unsigned long long* src, doubl
                         (double)(long long)__ldcg(src + 1) * inv_scale);
 }
 
+// pdl: launched with programmatic stream serialisation (the kernels wait for
+// their predecessor's results before reading them).
 void launch_rho_mixed(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
                       const int4* ksamp, const double* kcoef, const uint4* fx,
-                      unsigned long long* rho_fx, int* kcnt, float2* kab);
+                      unsigned long long* rho_fx, int* kcnt, float2* kab, bool pdl = false);
 void launch_rho_f64(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
                     const int4* ksamp, const double4* fx64, unsigned long long* rho_fx);
 // The last stage of a neighbour-list MD step, run by the Fourier-force
@@ -429,7 +441,7 @@ struct MdOut {
 };
 void launch_fourier_force_mixed(cudaStream_t st, bool one, const Work& w, int nblk, int split,
                                 const uint4* fx, const int4* ksamp, const float2* kab,
-                                float4* fs, const MdOut& md = MdOut{});
+                                float4* fs, const MdOut& md = MdOut{}, bool pdl = false);
 void launch_fourier_force_f64(cudaStream_t st, bool one, const Work& w, int nblk,
                               const double4* fx64, const int4* ksamp,
                               const unsigned long long* rho_fx, double4* fs64);
