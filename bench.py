@@ -209,7 +209,13 @@ def reduce_sum(x, world, device):
 
 # --------------------------------------------------------------------- roofline
 def source_hash(kernel_file):
-    return hashlib.sha256(open(kernel_file, "rb").read()).hexdigest()[:16]
+    """Hash of a kernel's source file together with the shared device header
+    it includes (a change to either makes committed counters stale)."""
+    h = hashlib.sha256(open(kernel_file, "rb").read())
+    hdr = os.path.join(os.path.dirname(kernel_file), "rbe_internal.cuh")
+    if os.path.exists(hdr):
+        h.update(open(hdr, "rb").read())
+    return h.hexdigest()[:16]
 
 
 def traffic_for(kernel, workload_name):
