@@ -509,34 +509,42 @@ __global__ void __launch_bounds__(kBlockP) k_list_build(const __grid_constant__ 
         const int dlo = ncd < 3 ? 0 : -1, dhi = ncd < 3 ? 0 : 1;
         int* out = la.nbr + i;
         const size_t stride = (size_t)la.stride;
-        // two sweeps: the pairs within r_c first, then those in the skin, so
-        // that the lanes of a warp in the list pass mostly agree on the cutoff
-        // branch at the same position in their lists
+        // one sweep: the pairs within r_c go to the front of the particle's
+        // slots, those in the skin to the back; the skin block then moves up
+        // behind the first, so that the lanes of a warp in the list pass mostly
+        // agree on the cutoff branch at the same position in their lists
         const float rc2 = S.f_rc2;
-        for (int sweep = 0; sweep < 2; ++sweep) {
-            const float lo2 = sweep ? rc2 : -1.f, hi2 = sweep ? cut2 : rc2;
-            for (int dz = dlo; dz <= dhi; ++dz) {
-                for (int dy = dlo; dy <= dhi; ++dy) {
-                    const int zz = wrapc(cz + dz, ncd), yy = wrapc(cy + dy, ncd);
-                    int r0, e0, r1, e1;
-                    row_ranges(la.cell_start, S.off_c + (zz * ncd + yy) * ncd, cx, ncd, r0, e0,
-                               r1, e1);
-                    for (int part = 0; part < 2; ++part) {
-                        const int b = part ? r1 : r0, e = part ? e1 : e0;
-                        for (int j = b; j < e; ++j) {
-                            const uint4 sj = __ldg(la.spos + j);
-                            const float dx = (float)(int32_t)(sj.x - si.x) * Lu;
-                            const float dyy = (float)(int32_t)(sj.y - si.y) * Lu;
-                            const float dzz = (float)(int32_t)(sj.z - si.z) * Lu;
-                            const float r2 = fmaf(dx, dx, fmaf(dyy, dyy, dzz * dzz));
-                            if (r2 >= lo2 && r2 < hi2 && j != i) {
-                                if (cnt < la.cap) out[(size_t)cnt * stride] = j;
-                                ++cnt;
+        int n_in = 0, n_sk = 0;
+        for (int dz = dlo; dz <= dhi; ++dz) {
+            for (int dy = dlo; dy <= dhi; ++dy) {
+                const int zz = wrapc(cz + dz, ncd), yy = wrapc(cy + dy, ncd);
+                int r0, e0, r1, e1;
+                row_ranges(la.cell_start, S.off_c + (zz * ncd + yy) * ncd, cx, ncd, r0, e0, r1, e1);
+                for (int part = 0; part < 2; ++part) {
+                    const int b = part ? r1 : r0, e = part ? e1 : e0;
+                    for (int j = b; j < e; ++j) {
+                        const uint4 sj = __ldg(la.spos + j);
+                        const float dx = (float)(int32_t)(sj.x - si.x) * Lu;
+                        const float dyy = (float)(int32_t)(sj.y - si.y) * Lu;
+                        const float dzz = (float)(int32_t)(sj.z - si.z) * Lu;
+                        const float r2 = fmaf(dx, dx, fmaf(dyy, dyy, dzz * dzz));
+                        if (r2 < cut2 && j != i) {
+                            if (n_in + n_sk < la.cap) {
+                                const int slot = r2 < rc2 ? n_in : la.cap - 1 - n_sk;
+                                out[(size_t)slot * stride] = j;
                             }
+                            if (r2 < rc2) ++n_in; else ++n_sk;
                         }
                     }
                 }
             }
+        }
+        cnt = n_in + n_sk;
+        if (cnt <= la.cap) {
+            // move the skin block [cap - n_sk, cap) to [n_in, n_in + n_sk);
+            // the destination never lies above the source: ascending is safe
+            for (int k = 0; k < n_sk; ++k)
+                out[(size_t)(n_in + k) * stride] = out[(size_t)(la.cap - n_sk + k) * stride];
         }
         la.ncnt[i] = min(cnt, la.cap);
         la.sref[la.perm[i]] = si;           // by caller index: the prep kernel reads it in order
