@@ -217,6 +217,9 @@ struct rbe_ctx {
     int* d_list_flag = nullptr;
     unsigned long long* d_list_stats = nullptr;   // builds, largest count
     float4* d_freal = nullptr;                // real-space force of a list step
+    // pinned host words: [0] the step index of a host-buffer call, [1] the
+    // device error word read back asynchronously behind the outputs
+    uint64_t* h_pin = nullptr;
     cudaEvent_t ev_real = nullptr;            // list step: real-space pass done
     cudaStream_t stream3 = nullptr;           // list step: the rebuild branch
     cudaEvent_t ev_chain = nullptr;           // list step: rebuild branch done
@@ -701,6 +704,8 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_chain, cudaEventDisableTiming));
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_prep, cudaEventDisableTiming));
     RBE_CUDA(h, cudaStreamCreateWithFlags(&h->stream3, cudaStreamNonBlocking));
+    RBE_CUDA(h, cudaHostAlloc((void**)&h->h_pin, 2 * sizeof(uint64_t), cudaHostAllocDefault));
+    h->h_pin[0] = h->h_pin[1] = 0;
     return RBE_OK;
 }
 
@@ -730,6 +735,7 @@ void release(rbe_ctx* h) {
     if (h->ev_chain) cudaEventDestroy(h->ev_chain);
     if (h->ev_prep) cudaEventDestroy(h->ev_prep);
     if (h->stream3) cudaStreamDestroy(h->stream3);
+    if (h->h_pin) cudaFreeHost(h->h_pin);
     for (int k = 0; k < RBE_K_COUNT; ++k) {
         if (h->ev_beg[k]) cudaEventDestroy(h->ev_beg[k]);
         if (h->ev_end[k]) cudaEventDestroy(h->ev_end[k]);
@@ -1480,8 +1486,9 @@ rbe_status rbe_step_host(rbe_handle h, int32_t n, float* pos_q, float* vel, int3
         RBE_CUDA(h, cudaMemcpyAsync(h->d_stage_pos, pos_q, bytes, cudaMemcpyHostToDevice, h->stream));
         RBE_CUDA(h, cudaMemcpyAsync(h->d_stage_vel, vel, bytes, cudaMemcpyHostToDevice, h->stream));
     }
-    RBE_CUDA(h, cudaMemcpyAsync(h->d_stage_step, &step0, sizeof(uint64_t), cudaMemcpyHostToDevice,
-                                h->stream));
+    h->h_pin[0] = step0;                     // pinned: the copy is asynchronous
+    RBE_CUDA(h, cudaMemcpyAsync(h->d_stage_step, h->h_pin, sizeof(uint64_t),
+                                cudaMemcpyHostToDevice, h->stream));
     s = step_impl(h, n, RBE_MIXED, h->d_stage_pos, h->d_stage_vel, nsteps, h->d_stage_step);
     if (s != RBE_OK) return s;
     if (n > 0) {
@@ -1493,9 +1500,12 @@ rbe_status rbe_step_host(rbe_handle h, int32_t n, float* pos_q, float* vel, int3
 
 rbe_status rbe_sync(rbe_handle h) {
     if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
+    // the error word follows the queued work in the stream: one synchronisation
+    RBE_CUDA(h, cudaMemcpyAsync(h->h_pin + 1, h->d_err, sizeof(int), cudaMemcpyDeviceToHost,
+                                h->stream));
     RBE_CUDA(h, cudaStreamSynchronize(h->stream));
     int err = 0;
-    RBE_CUDA(h, cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    std::memcpy(&err, h->h_pin + 1, sizeof(int));
     if (err) {
         RBE_CUDA(h, cudaMemset(h->d_err, 0, sizeof(int)));
         if (err & kErrSampler)
