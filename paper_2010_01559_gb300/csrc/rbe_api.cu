@@ -50,6 +50,9 @@ struct GraphEntry {
     const void* step;
     const void* F;
     int prec;
+    const void* host_pos;  // host-buffer graphs: the caller's pinned arrays (else null)
+    const void* host_vel;
+    int host_steps;        // host-buffer graphs: steps per replay
     cudaGraphExec_t exec;
     int kernels;           // kernels in one replay
 };
@@ -1221,8 +1224,16 @@ rbe_status observables_impl(rbe_ctx* h, int n, const float* pos_q, const float* 
     return finish(h, "rbe_observables");
 }
 
+// A host-buffer step (rbe_step_host): the caller's arrays copied into the
+// staging buffers before the steps and back after them, the step index from
+// the pinned word, the device error word back into the pinned word.
+struct HostIO {
+    float* pos;
+    float* vel;
+};
+
 rbe_status step_impl(rbe_ctx* h, int n, int prec, void* pos, void* vel, int nsteps,
-                     uint64_t* step_dev, float* F_out = nullptr) {
+                     uint64_t* step_dev, float* F_out = nullptr, const HostIO* io = nullptr) {
     if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
     rbe_status s = check_n(h, n);
     if (s != RBE_OK) return s;
@@ -1253,15 +1264,37 @@ rbe_status step_impl(rbe_ctx* h, int n, int prec, void* pos, void* vel, int nste
     } else if (nsteps > 0) {
         h->list_valid = false;
     }
+    const size_t bytes = sizeof(float4) * (size_t)n;
+    // the copies of a host-buffer call, on stream sq
+    auto copy_in = [&](cudaStream_t sq) {
+        if (n > 0) {
+            cudaMemcpyAsync(pos, io->pos, bytes, cudaMemcpyHostToDevice, sq);
+            cudaMemcpyAsync(vel, io->vel, bytes, cudaMemcpyHostToDevice, sq);
+        }
+        cudaMemcpyAsync(step_dev, h->h_pin, sizeof(uint64_t), cudaMemcpyHostToDevice, sq);
+    };
+    auto copy_out = [&](cudaStream_t sq) {
+        if (n > 0) {
+            cudaMemcpyAsync(io->pos, pos, bytes, cudaMemcpyDeviceToHost, sq);
+            cudaMemcpyAsync(io->vel, vel, bytes, cudaMemcpyDeviceToHost, sq);
+        }
+        cudaMemcpyAsync(h->h_pin + 1, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, sq);
+    };
+    // a host-buffer call replays one graph holding copies and steps (up to 4)
+    const bool host_graph = io && nsteps <= 4;
     if (!h->use_graph || h->prof_on) {
+        if (io) copy_in(h->stream);
         for (int k = 0; k < nsteps; ++k) enqueue_eval(h, h->stream, a);
+        if (io) copy_out(h->stream);
         return finish(h, "rbe_step");
     }
     cudaGraphExec_t exec = nullptr;
     int kernels = 0;
     for (auto& g : h->graphs)
         if (g.n == n && g.pos == pos && g.vel == vel && g.step == step_dev && g.prec == prec &&
-            g.F == (const void*)F_out) {
+            g.F == (const void*)F_out && g.host_pos == (host_graph ? io->pos : nullptr) &&
+            g.host_vel == (host_graph ? io->vel : nullptr) &&
+            g.host_steps == (host_graph ? nsteps : 0)) {
             exec = g.exec;
             kernels = g.kernels;
         }
@@ -1269,17 +1302,34 @@ rbe_status step_impl(rbe_ctx* h, int n, int prec, void* pos, void* vel, int nste
         // Capture on the handle's private stream, then replay on the caller's.
         RBE_CUDA(h, cudaStreamSynchronize(h->stream));
         RBE_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-        kernels = enqueue_eval(h, h->cap_stream, a);
+        if (host_graph) {
+            copy_in(h->cap_stream);
+            kernels = 0;
+            for (int k = 0; k < nsteps; ++k) kernels += enqueue_eval(h, h->cap_stream, a);
+            copy_out(h->cap_stream);
+        } else {
+            kernels = enqueue_eval(h, h->cap_stream, a);
+        }
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
-        h->graphs.push_back(GraphEntry{n, pos, vel, step_dev, F_out, prec, exec, kernels});
+        h->graphs.push_back(GraphEntry{n, pos, vel, step_dev, F_out, prec,
+                                       host_graph ? io->pos : nullptr,
+                                       host_graph ? io->vel : nullptr,
+                                       host_graph ? nsteps : 0, exec, kernels});
     }
-    for (int k = 0; k < nsteps; ++k) RBE_CUDA(h, cudaGraphLaunch(exec, h->stream));
-    h->kernel_count += (int64_t)kernels * nsteps;
+    if (host_graph) {
+        RBE_CUDA(h, cudaGraphLaunch(exec, h->stream));
+        h->kernel_count += kernels;
+    } else {
+        if (io) copy_in(h->stream);
+        for (int k = 0; k < nsteps; ++k) RBE_CUDA(h, cudaGraphLaunch(exec, h->stream));
+        if (io) copy_out(h->stream);
+        h->kernel_count += (int64_t)kernels * nsteps;
+    }
     return finish(h, "rbe_step");
 }
 
@@ -1301,6 +1351,25 @@ float time_kernel(rbe_ctx* h, cudaEvent_t e0, cudaEvent_t e1, F&& launch) {
     }
     return tot;
 }
+}  // namespace
+
+namespace {
+// The device error word as read back into the pinned word (after a
+// synchronisation): latched conditions become a status, and the word is cleared.
+rbe_status report_err(rbe_ctx* h) {
+    int err = 0;
+    std::memcpy(&err, h->h_pin + 1, sizeof(int));
+    if (err) {
+        RBE_CUDA(h, cudaMemset(h->d_err, 0, sizeof(int)));
+        if (err & kErrSampler)
+            return fail(h, RBE_ERR_SAMPLER, "a k-sample drew (0,0,0) on 32 attempts in a row");
+        if (err & kErrList)
+            return fail(h, RBE_ERR_LIST, "a particle had more neighbours within r_c + skin than "
+                                         "the list holds (" + std::to_string(h->list_cap) + ")");
+    }
+    return finish(h, "rbe_sync");
+}
+
 }  // namespace
 
 // ===================================================================== C ABI
@@ -1481,21 +1550,14 @@ rbe_status rbe_step_host(rbe_handle h, int32_t n, float* pos_q, float* vel, int3
     rbe_status s = check_n(h, n);
     if (s != RBE_OK) return s;
     if (n > 0 && (!pos_q || !vel)) return fail(h, RBE_ERR_ARG, "null host buffer");
-    const size_t bytes = sizeof(float4) * (size_t)n;
-    if (n > 0) {
-        RBE_CUDA(h, cudaMemcpyAsync(h->d_stage_pos, pos_q, bytes, cudaMemcpyHostToDevice, h->stream));
-        RBE_CUDA(h, cudaMemcpyAsync(h->d_stage_vel, vel, bytes, cudaMemcpyHostToDevice, h->stream));
-    }
     h->h_pin[0] = step0;                     // pinned: the copy is asynchronous
-    RBE_CUDA(h, cudaMemcpyAsync(h->d_stage_step, h->h_pin, sizeof(uint64_t),
-                                cudaMemcpyHostToDevice, h->stream));
-    s = step_impl(h, n, RBE_MIXED, h->d_stage_pos, h->d_stage_vel, nsteps, h->d_stage_step);
+    const HostIO io{pos_q, vel};
+    s = step_impl(h, n, RBE_MIXED, h->d_stage_pos, h->d_stage_vel, nsteps, h->d_stage_step,
+                  nullptr, &io);
     if (s != RBE_OK) return s;
-    if (n > 0) {
-        RBE_CUDA(h, cudaMemcpyAsync(pos_q, h->d_stage_pos, bytes, cudaMemcpyDeviceToHost, h->stream));
-        RBE_CUDA(h, cudaMemcpyAsync(vel, h->d_stage_vel, bytes, cudaMemcpyDeviceToHost, h->stream));
-    }
-    return rbe_sync(h);
+    // the outputs and the error word are queued: one synchronisation
+    RBE_CUDA(h, cudaStreamSynchronize(h->stream));
+    return report_err(h);
 }
 
 rbe_status rbe_sync(rbe_handle h) {
@@ -1504,17 +1566,7 @@ rbe_status rbe_sync(rbe_handle h) {
     RBE_CUDA(h, cudaMemcpyAsync(h->h_pin + 1, h->d_err, sizeof(int), cudaMemcpyDeviceToHost,
                                 h->stream));
     RBE_CUDA(h, cudaStreamSynchronize(h->stream));
-    int err = 0;
-    std::memcpy(&err, h->h_pin + 1, sizeof(int));
-    if (err) {
-        RBE_CUDA(h, cudaMemset(h->d_err, 0, sizeof(int)));
-        if (err & kErrSampler)
-            return fail(h, RBE_ERR_SAMPLER, "a k-sample drew (0,0,0) on 32 attempts in a row");
-        if (err & kErrList)
-            return fail(h, RBE_ERR_LIST, "a particle had more neighbours within r_c + skin than "
-                                         "the list holds (" + std::to_string(h->list_cap) + ")");
-    }
-    return finish(h, "rbe_sync");
+    return report_err(h);
 }
 
 rbe_status rbe_set_tuning(rbe_handle h, const rbe_tuning* t) {

@@ -117,6 +117,17 @@ def test_graph_replay_resume_and_host_calls_are_bitwise(rbe, c1):
         h.step_host(tp, tv, 1, s)
     assert np.array_equal(tp.numpy(), pa.cpu().numpy())
     assert np.array_equal(tv.numpy(), va.cpu().numpy())
+    # host buffers through one replayed graph per call (copies in, steps, copies
+    # out), one and two steps per call
+    h.set_graph(True)
+    for per in (1, 2):
+        tp = torch.from_numpy(c1.pos_q().copy()).pin_memory()
+        tv = torch.from_numpy(hv.copy()).pin_memory()
+        for s in range(0, 20, per):
+            h.step_host(tp, tv, per, s)
+        assert np.array_equal(tp.numpy(), pa.cpu().numpy()), per
+        assert np.array_equal(tv.numpy(), va.cpu().numpy()), per
+    h.set_graph(False)
     # forces through host buffers equal the device call
     F = torch.zeros((c1.n, 4), dtype=torch.float32)
     E = torch.zeros(4, dtype=torch.float64)
