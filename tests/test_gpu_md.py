@@ -121,8 +121,10 @@ def test_graph_replay_resume_and_host_calls_are_bitwise(rbe, c1):
     # out), one and two steps per call
     h.set_graph(True)
     for per in (1, 2):
+        v0 = np.zeros((c1.n, 4), np.float32)          # hv was updated in place above
+        v0[:, :3] = c1.vel
         tp = torch.from_numpy(c1.pos_q().copy()).pin_memory()
-        tv = torch.from_numpy(hv.copy()).pin_memory()
+        tv = torch.from_numpy(v0).pin_memory()
         for s in range(0, 20, per):
             h.step_host(tp, tv, per, s)
         assert np.array_equal(tp.numpy(), pa.cpu().numpy()), per
