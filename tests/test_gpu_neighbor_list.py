@@ -190,3 +190,35 @@ def test_list_overflow_is_reported_not_silent(rbe):
     assert ei.value.status == capi.RBE_ERR_LIST
     h.sync()                                             # the latch was cleared
     h.close()
+
+
+def test_list_step_with_mh_sampler_matches_oracle_chain(rbe):
+    """The paper's MH sampler on list steps: after 30 steps, the step force at
+    the positions it started from equals the oracle's estimator on the batch
+    its chain yields for that (31st) evaluation."""
+    import torch
+    import oracle
+    wl = workloads.config_small_fp64()
+    sp = copy.copy(wl.params)
+    sp.sampler = 1
+    h = rbe.RBE(rbe.params_from(sp, n_max=wl.n))
+    h.set_graph(True)
+    pos, vel = _state(wl, torch)
+    step = torch.zeros(1, dtype=torch.int64, device="cuda")
+    h.step(pos, vel, 30, step)
+    before = pos.clone()
+    F = torch.zeros((wl.n, 4), dtype=torch.float32, device="cuda")
+    h.step(pos, vel, 1, step, F_out=F)
+    h.sync()
+    chain = oracle.MHChain(sp.alpha, sp.box, sp.seed, sp.stream)
+    for _ in range(30):
+        chain.draw(sp.P)
+    m = chain.draw(sp.P)
+    ref = oracle.rbe_forces(before[:, :3].cpu().numpy().astype(np.float64),
+                            wl.q.astype(np.float64), sp.box, sp.alpha, sp.r_c, sp.P, sp.seed,
+                            sp.stream, 30, lB=sp.coulomb_prefactor, lj_eps=sp.lj_eps,
+                            lj_sigma=sp.lj_sigma, lj_rcut=sp.lj_rcut, m=m)
+    err = rel_rms(F[:, :3].cpu().numpy(), ref["F"])
+    print("MH list step force vs oracle rel-RMS", err)
+    assert err <= TOL_MIXED
+    h.close()
