@@ -316,17 +316,7 @@ def roofline(prof, wl, peaks, units, counts=None):
     name, (ms, cnt) = max(prof.items(), key=lambda kv: kv[1][0])
     avg_s = ms / max(cnt, 1) / 1e3
     N, P = wl.n, wl.params.P
-    if name == "fused_step":
-        # the whole step in one launch: the sines and cosines of the structure
-        # factors and of the Fourier force, two per (particle, wave vector) each
-        work = 4.0 * N * P
-        peak = units["sfu"]
-        achieved = work / avg_s / 1e12
-        out = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
-               "unit": "Tsfu/s", "frac": achieved / peak, "peak_basis": units["sfu_basis"],
-               "algorithmic": f"4 SFU ops per (particle, k) pair x {N} x {P} (structure "
-                              f"factors and Fourier force; the fused step's largest work unit)"}
-    elif name in ("rho", "fourier_force"):
+    if name in ("rho", "fourier_force"):
         # each (particle, wave vector) pair takes one sine and one cosine
         work = 2.0 * N * P
         peak = units["sfu"]

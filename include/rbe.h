@@ -275,9 +275,6 @@ typedef struct {
     int32_t real_seg;      /* cells along x per real-space block: 1 .. cells per edge           */
     int32_t list_split;    /* threads per particle in the neighbour-list pass of rbe_step:
                               1, 2, 4 or 8                                                   */
-    int32_t fused_step;    /* list steps of a single system with the exact sampler and
-                              P <= 1024 in one cooperative launch (phases separated by
-                              grid barriers): 0 = for n <= 65536, 1 = at any n, -1 = never */
 } rbe_tuning;
 
 /* Set the launch shapes (results change only by floating-point summation
@@ -308,8 +305,7 @@ enum {
     RBE_K_ENERGY = 8,        /* FP64 energy reduction                               */
     RBE_K_LIST_BUILD = 9,    /* neighbour-list build (list MD steps; returns at once
                                 when no particle moved beyond skin/2)             */
-    RBE_K_FUSED_STEP = 10,   /* the whole list step of a small system in one launch  */
-    RBE_K_COUNT = 11
+    RBE_K_COUNT = 10
 };
 
 /* Enable (1) or disable (0) per-kernel timing.  While enabled, rbe_forces*,

@@ -41,7 +41,7 @@ class rbe_params(ctypes.Structure):
 class rbe_tuning(ctypes.Structure):
     _fields_ = [("rho_chunk", ctypes.c_int32), ("force_split", ctypes.c_int32),
                 ("real_split", ctypes.c_int32), ("real_seg", ctypes.c_int32),
-                ("list_split", ctypes.c_int32), ("fused_step", ctypes.c_int32)]
+                ("list_split", ctypes.c_int32)]
 
 
 class rbe_peaks(ctypes.Structure):
@@ -98,7 +98,7 @@ _SIGS = {
 
 #: kernel names in RBE_K_* order
 KERNELS = ("prep", "scan", "scatter", "cell_order", "rho", "finalize", "fourier_force",
-           "real", "energy", "list_build", "fused_step")
+           "real", "energy", "list_build")
 
 #: every symbol include/rbe.h declares
 EXPORTED = tuple(_SIGS)

@@ -220,11 +220,6 @@ struct rbe_ctx {
     int* d_list_flag = nullptr;
     unsigned long long* d_list_stats = nullptr;   // builds, largest count
     float4* d_freal = nullptr;                // real-space force of a list step
-    // the fused single-system step (rbe_fused.cu): grid barrier words, the
-    // preference (0 automatic, 1 on where possible, -1 off) and the grid
-    unsigned* d_bar = nullptr;
-    int fused_pref = 0;
-    int fused_grid_blocks = -1, fused_grid_shape = -1;
     // pinned host words: [0] the step index of a host-buffer call, [1] the
     // device error word read back asynchronously behind the outputs
     uint64_t* h_pin = nullptr;
@@ -641,7 +636,6 @@ rbe_status allocate(rbe_ctx* h) {
         RBE_ALLOC(h->d_list_flag, 1);
         RBE_ALLOC(h->d_list_stats, 2);
         RBE_ALLOC(h->d_freal, N);
-        RBE_ALLOC(h->d_bar, 2);
     }
     RBE_ALLOC(h->d_kab, h->ktot);
     RBE_ALLOC(h->d_qsum_fx, h->nsys);
@@ -666,7 +660,6 @@ rbe_status allocate(rbe_ctx* h) {
         RBE_CUDA(h, cudaMemset(h->d_ncnt, 0, sizeof(int) * N));
         RBE_CUDA(h, cudaMemset(h->d_sref, 0, sizeof(uint4) * N));
         RBE_CUDA(h, cudaMemset(h->d_list_stats, 0, sizeof(unsigned long long) * 2));
-        RBE_CUDA(h, cudaMemset(h->d_bar, 0, sizeof(unsigned) * 2));
         const int one = 1;
         RBE_CUDA(h, cudaMemcpy(h->d_list_flag, &one, sizeof(int), cudaMemcpyHostToDevice));
     }
@@ -731,7 +724,7 @@ void release(rbe_ctx* h) {
                     h->d_cell_start, h->d_ksamp, h->d_rho_fx, h->d_kcnt, h->d_kab,
                     h->d_kcoef, h->d_mh_tq, h->d_mh_rho, h->d_mh_state, h->d_mh_pos, h->d_nh,
                     h->d_lblk, h->d_nbr, h->d_ncnt, h->d_sref, h->d_iperm, h->d_list_flag,
-                    h->d_list_stats, h->d_freal, h->d_bar,
+                    h->d_list_stats, h->d_freal,
                     h->d_qsum_fx, h->d_blk_e, h->d_blk_w, h->d_obs_m, h->d_obs_rho, h->d_obs_w,
                     h->d_obs_out, h->d_obs_part, h->d_blk_q, h->d_cur_step, h->d_stage_step,
                     h->d_err, h->d_stage_pos, h->d_stage_vel, h->d_stage_F, h->d_stage_E};
@@ -1231,58 +1224,6 @@ rbe_status observables_impl(rbe_ctx* h, int n, const float* pos_q, const float* 
     return finish(h, "rbe_observables");
 }
 
-// The fused single-system step (rbe_fused.cu) takes a list step of a single
-// system with the exact sampler and P <= kFusedMaxP, for n up to kFusedMaxN
-// unless the tuning says otherwise.
-bool use_fused(const rbe_ctx* h, int n) {
-    if (!h->list || h->batch || h->mh || n <= 0 || h->fused_pref < 0) return false;
-    if (h->sys[0].p.P > kFusedMaxP) return false;
-    return h->fused_pref > 0 || n <= kFusedMaxN;
-}
-
-FusedArgs make_fused_args(rbe_ctx* h, int n, void* pos, void* vel, uint64_t* step_dev,
-                          float* F_out) {
-    FusedArgs f{};
-    f.S = h->sysdev[0];
-    f.n = n;
-    f.pos = (const float4*)pos;
-    f.md_pos = (float4*)pos;
-    f.md_vel = (float4*)vel;
-    f.F_out = (float4*)F_out;
-    f.step_dev = step_dev;
-    f.step_arg = 0;
-    f.cur_step = h->d_cur_step;
-    f.fx = h->d_fx;
-    f.spos = h->d_spos;
-    f.perm = h->d_perm;
-    f.perm_tmp = h->d_perm_tmp;
-    f.iperm = h->d_iperm;
-    f.cid = h->d_cid;
-    f.rank = h->d_rank;
-    f.cell_cnt = h->d_cell_cnt;
-    f.cell_start = h->d_cell_start;
-    f.ncell = h->ncell;
-    f.nbr = h->d_nbr;
-    f.ncnt = h->d_ncnt;
-    f.nbr_stride = std::max(h->ntot, 1);
-    f.nbr_cap = h->list_cap;
-    f.sref = h->d_sref;
-    f.list_stats = h->d_list_stats;
-    f.list_flag = h->d_list_flag;
-    f.ksamp = h->d_ksamp;
-    f.table = h->d_table;
-    f.tab_words = h->ttot <= 8192 ? h->ttot : 0;
-    f.rho_fx = h->d_rho_fx;
-    f.freal = h->d_freal;
-    f.nh = h->d_nh;
-    f.err = h->d_err;
-    f.bar = h->d_bar;
-    f.rchunk = 128;
-    f.rsplit = n <= 16384 ? 8 : (n <= 32768 ? 4 : 2);
-    f.fsplit = n <= 16384 ? 8 : 4;
-    return f;
-}
-
 // A host-buffer step (rbe_step_host): the caller's arrays copied into the
 // staging buffers before the steps and back after them, the step index from
 // the pinned word, the device error word back into the pinned word.
@@ -1339,36 +1280,6 @@ rbe_status step_impl(rbe_ctx* h, int n, int prec, void* pos, void* vel, int nste
         }
         cudaMemcpyAsync(h->h_pin + 1, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, sq);
     };
-    if (prec == RBE_MIXED && use_fused(h, n)) {
-        const FusedArgs fa = make_fused_args(h, n, pos, vel, step_dev, F_out);
-        const int shape = fa.rsplit * 16 + fa.fsplit;
-        if (h->fused_grid_shape != shape) {
-            h->fused_grid_blocks = fused_grid(fa);
-            h->fused_grid_shape = shape;
-        }
-        if (h->fused_grid_blocks > 0) {
-            const bool prof = h->prof_on;
-            if (io) copy_in(h->stream);
-            for (int k = 0; k < nsteps; ++k) {
-                if (prof) cudaEventRecord(h->ev_beg[RBE_K_FUSED_STEP], h->stream);
-                cudaError_t e = launch_fused_step(h->stream, fa, h->fused_grid_blocks);
-                if (e != cudaSuccess) return cuda_fail(h, e, "fused step launch");
-                if (prof) {
-                    cudaEventRecord(h->ev_end[RBE_K_FUSED_STEP], h->stream);
-                    cudaEventSynchronize(h->ev_end[RBE_K_FUSED_STEP]);
-                    float ms = 0.f;
-                    if (cudaEventElapsedTime(&ms, h->ev_beg[RBE_K_FUSED_STEP],
-                                             h->ev_end[RBE_K_FUSED_STEP]) == cudaSuccess) {
-                        h->prof_ms[RBE_K_FUSED_STEP] += ms;
-                        h->prof_cnt[RBE_K_FUSED_STEP] += 1;
-                    }
-                }
-            }
-            if (io) copy_out(h->stream);
-            h->kernel_count += nsteps;
-            return finish(h, "rbe_step");
-        }
-    }
     // a host-buffer call replays one graph holding copies and steps (up to 4)
     const bool host_graph = io && nsteps <= 4;
     if (!h->use_graph || h->prof_on) {
@@ -1455,10 +1366,6 @@ rbe_status report_err(rbe_ctx* h) {
         if (err & kErrList)
             return fail(h, RBE_ERR_LIST, "a particle had more neighbours within r_c + skin than "
                                          "the list holds (" + std::to_string(h->list_cap) + ")");
-        if (err & kErrTimeout) {
-            if (h->d_bar) RBE_CUDA(h, cudaMemset(h->d_bar, 0, sizeof(unsigned) * 2));
-            return fail(h, RBE_ERR_TIMEOUT, "a grid barrier of the fused step gave up waiting");
-        }
     }
     return finish(h, "rbe_sync");
 }
@@ -1675,10 +1582,7 @@ rbe_status rbe_set_tuning(rbe_handle h, const rbe_tuning* t) {
     const int ls = t->list_split;
     if (ls != 0 && ls != 1 && ls != 2 && ls != 4 && ls != 8)
         return fail(h, RBE_ERR_ARG, "list_split must be 0, 1, 2, 4 or 8");
-    if (t->fused_step < -1 || t->fused_step > 1)
-        return fail(h, RBE_ERR_ARG, "fused_step must be -1, 0 or 1");
     h->list_split = ls;
-    h->fused_pref = t->fused_step;
     h->rho_chunk = c;
     h->force_split = f;
     h->real_split = r;
@@ -1705,7 +1609,6 @@ rbe_status rbe_get_tuning(rbe_handle h, rbe_tuning* t) {
                                                     : auto_real_seg(ntot, h->ncell, ncd_max));
     t->list_split = h->cur_lsplit > 0 ? h->cur_lsplit
                                       : (h->list_split > 0 ? h->list_split : auto_list_split(ntot));
-    t->fused_step = h->fused_pref;
     return RBE_OK;
 }
 

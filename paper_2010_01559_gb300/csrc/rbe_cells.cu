@@ -19,6 +19,21 @@
 
 namespace rbe {
 
+__device__ __forceinline__ uint32_t to_fixed(float x, float hi, float lo) {
+    const float p = x * hi;
+    const float e = fmaf(x, hi, -p);       // exact: x * hi = p + e
+    float corr = fmaf(x, lo, e);
+    const float pr = rintf(p);
+    corr += (p - pr);                      // exact (p and pr differ by < 1 ulp-scale)
+    const long long ip = (long long)pr;
+    const long long ic = __float2ll_rn(corr);
+    return (uint32_t)(unsigned long long)(ip + ic);
+}
+
+__device__ __forceinline__ int cell_of_fixed(uint32_t s, int ncd) {
+    return (int)(((unsigned long long)s * (unsigned long long)ncd) >> 32);
+}
+
 // Deterministic block sum of two doubles (fixed shuffle tree, then warps in order).
 __device__ __forceinline__ double2 block_sum2(double a, double b) {
     __shared__ double sa[32], sb[32];

@@ -28,6 +28,7 @@
 
 namespace rbe {
 
+constexpr float kTwoPiOver2p32 = 1.4629180792671596e-09f;   // 2 pi / 2^32
 constexpr int kStage = 512;                                 // particles staged per pass
 
 __global__ void k_sample(const SysDev* __restrict__ sysv, int nsys, int ktot,
@@ -165,6 +166,10 @@ k_rho_f64(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
 }
 
 // ----------------------------------------------------------------- force (mixed)
+// Shared-memory record per wave vector: the integer m (phase) and, as floats,
+// m (direction) with the two coefficients A = coef Im rho, B = coef Re rho.
+struct KPhase { uint32_t mx, my, mz, pad; };
+struct KForce { float mx, my, mz, A; };
 
 // SPLIT threads per particle (each a 1/SPLIT share of the wave vectors), or
 // with SPLIT = 1 PT = 2 particles per thread, which share each wave vector's

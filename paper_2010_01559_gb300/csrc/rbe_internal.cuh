@@ -36,7 +36,6 @@ constexpr int kLTile = 128;       // wave vectors per block of the structure-fac
 constexpr int kMaxAttempts = 32;  // bound on the (0,0,0) rejection loop
 constexpr int kErrSampler = 1;    // bits in the device error word
 constexpr int kErrList = 2;       // a neighbour list overflowed
-constexpr int kErrTimeout = 4;    // a bounded device wait gave up
 constexpr double kQScale = 4294967296.0;           // 2^32: fixed point of sum q
 
 // Per-system constants (device copy).  All derived in FP64 on the host.
@@ -98,119 +97,6 @@ struct NhState {
 struct Tile {
     int sys, first, count, aux;
 };
-
-// ------------------------------------------------ shared device helpers
-// Fixed-point fraction of the box, round(x 2^32 / L) mod 2^32, from a float
-// coordinate and 2^32 / L as the unevaluated pair hi + lo (within one unit of
-// 2^-32 L), and the cell of a fraction.
-__device__ __forceinline__ uint32_t to_fixed(float x, float hi, float lo) {
-    const float p = x * hi;
-    const float e = fmaf(x, hi, -p);       // exact: x * hi = p + e
-    float corr = fmaf(x, lo, e);
-    const float pr = rintf(p);
-    corr += (p - pr);                      // exact (p and pr differ by < 1 ulp-scale)
-    const long long ip = (long long)pr;
-    const long long ic = __float2ll_rn(corr);
-    return (uint32_t)(unsigned long long)(ip + ic);
-}
-
-__device__ __forceinline__ int cell_of_fixed(uint32_t s, int ncd) {
-    return (int)(((unsigned long long)s * (unsigned long long)ncd) >> 32);
-}
-
-constexpr float kTwoPiOver2p32 = 1.4629180792671596e-09f;   // 2 pi / 2^32
-
-// Shared-memory record per wave vector: the integer m (phase) and, as floats,
-// m (direction) with the two coefficients A = coef Im rho, B = coef Re rho.
-struct KPhase { uint32_t mx, my, mz, pad; };
-struct KForce { float mx, my, mz, A; };
-
-__device__ __forceinline__ int wrapc(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
-
-// The 27 neighbour cells as 9 rows (dz, dy) of three x-adjacent cells.  Cells
-// are numbered x fastest, so a row is one contiguous range of the sorted
-// particles unless it wraps around the box edge; then it is two ranges.
-__device__ __forceinline__ void row_ranges(const int* __restrict__ cs, int base, int cx, int ncd,
-                                           int& s0, int& e0, int& s1, int& e1) {
-    if (ncd < 3) {                                  // one cell per edge: the whole row once
-        s0 = __ldg(cs + base); e0 = __ldg(cs + base + ncd); s1 = 0; e1 = 0;
-    } else if (cx > 0 && cx < ncd - 1) {
-        s0 = __ldg(cs + base + cx - 1); e0 = __ldg(cs + base + cx + 2); s1 = 0; e1 = 0;
-    } else if (cx == 0) {
-        s0 = __ldg(cs + base); e0 = __ldg(cs + base + 2);
-        s1 = __ldg(cs + base + ncd - 1); e1 = __ldg(cs + base + ncd);
-    } else {
-        s0 = __ldg(cs + base + ncd - 2); e0 = __ldg(cs + base + ncd);
-        s1 = __ldg(cs + base); e1 = __ldg(cs + base + 1);
-    }
-}
-
-struct PairAcc {
-    float fx, fy, fz, phr, ec, elj, wc, wlj;     // wc, wlj: half the pair virials r.F
-};
-
-// erfc(x) for x >= 0 given e = exp(-x^2): the rational approximation of
-// Abramowitz & Stegun, Handbook of Mathematical Functions, formula 7.1.26
-// (after Hastings), |error| <= 1.5e-7.  It reuses the Gaussian the force needs
-// anyway, so erfc costs one reciprocal and five FMAs.
-__device__ __forceinline__ float erfc_as(float e, float x) {
-    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
-    float p = 1.061405429f;
-    p = fmaf(p, t, -1.453152027f);
-    p = fmaf(p, t, 1.421413741f);
-    p = fmaf(p, t, -0.284496736f);
-    p = fmaf(p, t, 0.254829592f);
-    return p * t * e;
-}
-
-// Per-system constants of the pair terms, in registers.
-struct PairConst {
-    float rc2, lj_rc2, alpha, sa, two_sa_spi, lB, lj_s2, lj_eps, lj_shift;
-    bool vir;                                   // accumulate the virials
-};
-
-// Pair terms for displacement r_ij = (dx, dy, dz), |r_ij|^2 = r2 > 0.
-__device__ __forceinline__ void pair_terms(float dx, float dy, float dz, float r2, float qj,
-                                           float lbqi, const PairConst& k, PairAcc& acc) {
-    const float inv_r = rsqrtf(r2);
-    if (r2 < k.rc2) {
-        const float x = k.sa * (r2 * inv_r);
-        const float ex = __expf(-k.alpha * r2);                  // exp(-x^2)
-        const float pot = erfc_as(ex, x) * inv_r;                 // erfc(sqrt(a) r) / r
-        const float g_over_r = fmaf(k.two_sa_spi, ex, pot) * inv_r * inv_r;   // G(r) / r
-        const float s_ = -lbqi * qj * g_over_r;
-        acc.fx = fmaf(s_, dx, acc.fx);
-        acc.fy = fmaf(s_, dy, acc.fy);
-        acc.fz = fmaf(s_, dz, acc.fz);
-        acc.phr = fmaf(k.lB * qj, pot, acc.phr);
-        acc.ec = fmaf(0.5f * lbqi * qj, pot, acc.ec);
-        // r.F of the pair: lB q_i q_j (erfc(sqrt(a) r)/r + 2 sqrt(a/pi) e^{-a r^2})
-        if (k.vir) acc.wc = fmaf(0.5f * lbqi * qj, fmaf(k.two_sa_spi, ex, pot), acc.wc);
-    }
-    if (r2 < k.lj_rc2) {
-        const float inv_r2 = inv_r * inv_r;
-        const float sr2 = k.lj_s2 * inv_r2;
-        const float sr6 = sr2 * sr2 * sr2;
-        const float mag = 24.f * k.lj_eps * (2.f * sr6 * sr6 - sr6) * inv_r2;
-        acc.fx = fmaf(-mag, dx, acc.fx);
-        acc.fy = fmaf(-mag, dy, acc.fy);
-        acc.fz = fmaf(-mag, dz, acc.fz);
-        acc.elj += 0.5f * (4.f * k.lj_eps * (sr6 * sr6 - sr6) + k.lj_shift);
-        if (k.vir) acc.wlj = fmaf(0.5f * mag, r2, acc.wlj);   // r.F = 24 eps (2 (s/r)^12 - (s/r)^6)
-    }
-}
-
-// Pair terms from two fixed-point records: the displacement is the 32-bit
-// difference of the coordinates, which is the minimum image (|r_ij| < L / 2),
-// rounded once to FP32 and scaled to length units.
-__device__ __forceinline__ void pair_fixed(const uint4& si, const uint4& sj, float Lu,
-                                           float lbqi, const PairConst& kc, PairAcc& acc) {
-    const float dx = (float)(int32_t)(sj.x - si.x) * Lu;
-    const float dy = (float)(int32_t)(sj.y - si.y) * Lu;
-    const float dz = (float)(int32_t)(sj.z - si.z) * Lu;
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    if (r2 > 0.f) pair_terms(dx, dy, dz, r2, __uint_as_float(sj.w), lbqi, kc, acc);
-}
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
 // multiplies, the key bumped by the Weyl constants between rounds.
@@ -624,53 +510,5 @@ void launch_energy(cudaStream_t st, bool one, const Work& w, int nsys, const int
                    const unsigned long long* rho_fx, const double2* blk_e,
                    const double2* blk_q, const double2* blk_w, int parts, int per_cell,
                    double* E_out, double* W_out);
-
-// One neighbour-list MD step of a single system in one cooperative launch
-// (rbe_fused.cu): every buffer the step's phases use.
-struct FusedArgs {
-    SysDev S;
-    int n;
-    const float4* pos;        // caller's positions (read in phase A)
-    float4* md_pos;           // updated in place (phase E)
-    float4* md_vel;
-    float4* F_out;            // nullable
-    uint64_t* step_dev;       // nullable: the step index (advanced at the end)
-    uint64_t step_arg;
-    uint64_t* cur_step;
-    uint4* fx;
-    uint4* spos;
-    int* perm;
-    int* perm_tmp;
-    int* iperm;
-    int* cid;
-    int* rank;
-    int* cell_cnt;
-    int* cell_start;
-    int ncell;
-    int* nbr;
-    int* ncnt;
-    int nbr_stride, nbr_cap;
-    uint4* sref;
-    unsigned long long* list_stats;
-    int* list_flag;
-    int4* ksamp;
-    const uint64_t* table;
-    int tab_words;
-    unsigned long long* rho_fx;
-    float4* freal;
-    NhState* nh;
-    int* err;
-    unsigned* bar;
-    int rchunk;               // particles per structure-factor item
-    int rsplit;               // lanes per particle of the list pass (1, 2, 4, 8)
-    int fsplit;               // lanes per particle of the Fourier force (1, 2, 4, 8)
-};
-
-// Blocks of the cooperative grid for this launch shape (0: not available),
-// and the launch.
-int fused_grid(const FusedArgs& a);
-cudaError_t launch_fused_step(cudaStream_t st, const FusedArgs& a, int grid);
-constexpr int kFusedMaxP = 1024;       // wave vectors the fused step holds on chip
-constexpr int kFusedMaxN = 65536;      // particles up to which it is chosen automatically
 
 }  // namespace rbe

@@ -52,6 +52,26 @@ __device__ __forceinline__ double2 block_sum2_real(double a, double b) {
     return r;
 }
 
+__device__ __forceinline__ int wrapc(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
+
+// The 27 neighbour cells as 9 rows (dz, dy) of three x-adjacent cells.  Cells
+// are numbered x fastest, so a row is one contiguous range of the sorted
+// particles unless it wraps around the box edge; then it is two ranges.
+__device__ __forceinline__ void row_ranges(const int* __restrict__ cs, int base, int cx, int ncd,
+                                           int& s0, int& e0, int& s1, int& e1) {
+    if (ncd < 3) {                                  // one cell per edge: the whole row once
+        s0 = __ldg(cs + base); e0 = __ldg(cs + base + ncd); s1 = 0; e1 = 0;
+    } else if (cx > 0 && cx < ncd - 1) {
+        s0 = __ldg(cs + base + cx - 1); e0 = __ldg(cs + base + cx + 2); s1 = 0; e1 = 0;
+    } else if (cx == 0) {
+        s0 = __ldg(cs + base); e0 = __ldg(cs + base + 2);
+        s1 = __ldg(cs + base + ncd - 1); e1 = __ldg(cs + base + ncd);
+    } else {
+        s0 = __ldg(cs + base + ncd - 2); e0 = __ldg(cs + base + ncd);
+        s1 = __ldg(cs + base); e1 = __ldg(cs + base + 1);
+    }
+}
+
 // ----------------------------------------------------------------- mixed
 // One block per cell.  The block stages the records of the 27 neighbouring
 // cells (9 rows, each one or two contiguous ranges of the cell-sorted records)
@@ -65,6 +85,61 @@ __device__ __forceinline__ double2 block_sum2_real(double a, double b) {
 // records from global memory instead.
 constexpr int kNbCap = 24;          // entries of each lane's neighbour list
 constexpr int kBatch = 2;           // candidates a thread tests per step of its scan
+
+struct PairAcc {
+    float fx, fy, fz, phr, ec, elj, wc, wlj;     // wc, wlj: half the pair virials r.F
+};
+
+// erfc(x) for x >= 0 given e = exp(-x^2): the rational approximation of
+// Abramowitz & Stegun, Handbook of Mathematical Functions, formula 7.1.26
+// (after Hastings), |error| <= 1.5e-7.  It reuses the Gaussian the force needs
+// anyway, so erfc costs one reciprocal and five FMAs.
+__device__ __forceinline__ float erfc_as(float e, float x) {
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+    float p = 1.061405429f;
+    p = fmaf(p, t, -1.453152027f);
+    p = fmaf(p, t, 1.421413741f);
+    p = fmaf(p, t, -0.284496736f);
+    p = fmaf(p, t, 0.254829592f);
+    return p * t * e;
+}
+
+// Per-system constants of the pair terms, in registers.
+struct PairConst {
+    float rc2, lj_rc2, alpha, sa, two_sa_spi, lB, lj_s2, lj_eps, lj_shift;
+    bool vir;                                   // accumulate the virials
+};
+
+// Pair terms for displacement r_ij = (dx, dy, dz), |r_ij|^2 = r2 > 0.
+__device__ __forceinline__ void pair_terms(float dx, float dy, float dz, float r2, float qj,
+                                           float lbqi, const PairConst& k, PairAcc& acc) {
+    const float inv_r = rsqrtf(r2);
+    if (r2 < k.rc2) {
+        const float x = k.sa * (r2 * inv_r);
+        const float ex = __expf(-k.alpha * r2);                  // exp(-x^2)
+        const float pot = erfc_as(ex, x) * inv_r;                 // erfc(sqrt(a) r) / r
+        const float g_over_r = fmaf(k.two_sa_spi, ex, pot) * inv_r * inv_r;   // G(r) / r
+        const float s_ = -lbqi * qj * g_over_r;
+        acc.fx = fmaf(s_, dx, acc.fx);
+        acc.fy = fmaf(s_, dy, acc.fy);
+        acc.fz = fmaf(s_, dz, acc.fz);
+        acc.phr = fmaf(k.lB * qj, pot, acc.phr);
+        acc.ec = fmaf(0.5f * lbqi * qj, pot, acc.ec);
+        // r.F of the pair: lB q_i q_j (erfc(sqrt(a) r)/r + 2 sqrt(a/pi) e^{-a r^2})
+        if (k.vir) acc.wc = fmaf(0.5f * lbqi * qj, fmaf(k.two_sa_spi, ex, pot), acc.wc);
+    }
+    if (r2 < k.lj_rc2) {
+        const float inv_r2 = inv_r * inv_r;
+        const float sr2 = k.lj_s2 * inv_r2;
+        const float sr6 = sr2 * sr2 * sr2;
+        const float mag = 24.f * k.lj_eps * (2.f * sr6 * sr6 - sr6) * inv_r2;
+        acc.fx = fmaf(-mag, dx, acc.fx);
+        acc.fy = fmaf(-mag, dy, acc.fy);
+        acc.fz = fmaf(-mag, dz, acc.fz);
+        acc.elj += 0.5f * (4.f * k.lj_eps * (sr6 * sr6 - sr6) + k.lj_shift);
+        if (k.vir) acc.wlj = fmaf(0.5f * mag, r2, acc.wlj);   // r.F = 24 eps (2 (s/r)^12 - (s/r)^6)
+    }
+}
 
 // Sum of a particle's R lanes (lanes l = 0 .. R-1 of its group), in lane
 // order; the result is valid in lane 0 of the group.
@@ -102,6 +177,18 @@ __device__ __forceinline__ int row_of(int l, int j) {
 // from below, exactly.
 __device__ __forceinline__ uint32_t corner_of(int c, const SysDev& S) {
     return (uint32_t)c * S.corner_q + ((uint32_t)c * S.corner_r) / (uint32_t)S.ncd;
+}
+
+// Pair terms from two fixed-point records: the displacement is the 32-bit
+// difference of the coordinates, which is the minimum image (|r_ij| < L / 2),
+// rounded once to FP32 and scaled to length units.
+__device__ __forceinline__ void pair_fixed(const uint4& si, const uint4& sj, float Lu,
+                                           float lbqi, const PairConst& kc, PairAcc& acc) {
+    const float dx = (float)(int32_t)(sj.x - si.x) * Lu;
+    const float dy = (float)(int32_t)(sj.y - si.y) * Lu;
+    const float dz = (float)(int32_t)(sj.z - si.z) * Lu;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (r2 > 0.f) pair_terms(dx, dy, dz, r2, __uint_as_float(sj.w), lbqi, kc, acc);
 }
 
 // One block per segment: nsc x-adjacent cells of one (y, z) row.  The block

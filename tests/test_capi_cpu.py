@@ -42,7 +42,7 @@ def test_params_layout_matches_header():
     assert capi.rbe_params.thermostat.offset == 124
     assert capi.rbe_params.nh_tau.offset == 128
     assert capi.rbe_params.skin.offset == 136
-    assert ctypes.sizeof(capi.rbe_tuning) == 24
+    assert ctypes.sizeof(capi.rbe_tuning) == 20
 
 
 def _create(lib, **kw):
