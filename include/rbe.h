@@ -255,7 +255,9 @@ rbe_status rbe_set_graph(rbe_handle h, int32_t use_graph);
  * memory, run, copy the outputs back and synchronise.  Staging buffers are
  * the handle's own.  rbe_forces_host: pos_q float4[n] in, F_out float4[n]
  * out, E_out (nullable) double[4 n_systems] out.  rbe_step_host: pos_q and
- * vel float4[n] in/out, steps step0 .. step0 + nsteps - 1. */
+ * vel float4[n] in/out, steps step0 .. step0 + nsteps - 1; when both arrays
+ * are page-locked (cudaHostAlloc, cudaHostRegister) the step's kernels read
+ * and write them in place over the host link instead of staging copies. */
 rbe_status rbe_forces_host(rbe_handle h, int32_t n, const float *pos_q, uint64_t step,
                            float *F_out, double *E_out);
 rbe_status rbe_step_host(rbe_handle h, int32_t n, float *pos_q, float *vel, int32_t nsteps,

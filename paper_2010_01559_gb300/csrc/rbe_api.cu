@@ -707,7 +707,7 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_chain, cudaEventDisableTiming));
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_prep, cudaEventDisableTiming));
     RBE_CUDA(h, cudaStreamCreateWithFlags(&h->stream3, cudaStreamNonBlocking));
-    RBE_CUDA(h, cudaHostAlloc((void**)&h->h_pin, 2 * sizeof(uint64_t), cudaHostAllocDefault));
+    RBE_CUDA(h, cudaHostAlloc((void**)&h->h_pin, 2 * sizeof(uint64_t), cudaHostAllocMapped));
     h->h_pin[0] = h->h_pin[1] = 0;
     return RBE_OK;
 }
@@ -1224,6 +1224,18 @@ rbe_status observables_impl(rbe_ctx* h, int n, const float* pos_q, const float* 
     return finish(h, "rbe_observables");
 }
 
+// The device address of page-locked host memory (its own address under
+// unified addressing), or null for pageable memory.
+void* mapped_host(void* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();                       // pageable memory on some drivers
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 // A host-buffer step (rbe_step_host): the caller's arrays copied into the
 // staging buffers before the steps and back after them, the step index from
 // the pinned word, the device error word back into the pinned word.
@@ -1550,11 +1562,24 @@ rbe_status rbe_step_host(rbe_handle h, int32_t n, float* pos_q, float* vel, int3
     rbe_status s = check_n(h, n);
     if (s != RBE_OK) return s;
     if (n > 0 && (!pos_q || !vel)) return fail(h, RBE_ERR_ARG, "null host buffer");
-    h->h_pin[0] = step0;                     // pinned: the copy is asynchronous
-    const HostIO io{pos_q, vel};
-    s = step_impl(h, n, RBE_MIXED, h->d_stage_pos, h->d_stage_vel, nsteps, h->d_stage_step,
-                  nullptr, &io);
-    if (s != RBE_OK) return s;
+    h->h_pin[0] = step0;
+    void* dpos = mapped_host(pos_q);
+    void* dvel = mapped_host(vel);
+    uint64_t* dstep = (uint64_t*)mapped_host(h->h_pin);
+    if (n > 0 && dpos && dvel && dstep) {
+        // page-locked arrays: the step's kernels read and write them in place
+        // over the host link (no staging copies); the step index advances in
+        // the pinned word
+        s = step_impl(h, n, RBE_MIXED, dpos, dvel, nsteps, dstep);
+        if (s != RBE_OK) return s;
+        RBE_CUDA(h, cudaMemcpyAsync(h->h_pin + 1, h->d_err, sizeof(int), cudaMemcpyDeviceToHost,
+                                    h->stream));
+    } else {
+        const HostIO io{pos_q, vel};          // pageable: staged through device buffers
+        s = step_impl(h, n, RBE_MIXED, h->d_stage_pos, h->d_stage_vel, nsteps, h->d_stage_step,
+                      nullptr, &io);
+        if (s != RBE_OK) return s;
+    }
     // the outputs and the error word are queued: one synchronisation
     RBE_CUDA(h, cudaStreamSynchronize(h->stream));
     return report_err(h);
