@@ -21,7 +21,9 @@
  *     neutralising background -pi (sum q)^2 / (2 V alpha), truncated U_2, LJ;
  *   - optionally dE/dq_i (the electrostatic potential at particle i).
  * One MD step (rbe_step) adds the Langevin thermostat of Sec. 3.3 as a kick /
- * exact Ornstein-Uhlenbeck / drift update, closing the loop of Algorithm 1.
+ * exact Ornstein-Uhlenbeck / drift update, closing the loop of Algorithm 1
+ * (or the Andersen / Nose-Hoover variants); its real-space pairs come from a
+ * Verlet neighbour list kept on the device (rbe_step_ex).
  *
  * Conventions for every entry point:
  *   - Array pointers are caller-owned DEVICE memory (except the *_host entry
@@ -102,7 +104,8 @@ typedef struct {
     double box;               /* L > 0: edge of the cubic periodic box (Sec. 2)          */
     double alpha;             /* Ewald splitting parameter, erfc(sqrt(alpha) r) (Sec. 2) */
     double r_c;               /* real-space cutoff, 0 < r_c <= L/2 (minimum image); cells of
-                                 side >= r_c, or one cell (all pairs) when r_c > L/3     */
+                                 side >= r_c + skin, or one cell (all pairs) when
+                                 r_c + skin > L/3                                         */
     double coulomb_prefactor; /* multiplies all Coulomb terms (Sec. 4.1: 1)              */
     double lj_eps;            /* shifted-LJ epsilon; 0 disables LJ (Eq. Ljpotential)     */
     double lj_sigma;          /* LJ sigma (r_off = 0)                                    */

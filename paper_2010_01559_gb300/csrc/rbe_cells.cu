@@ -2,8 +2,10 @@
 // cell assignment and a counting sort of the particles by cell.
 //
 // The real-space sum of Eq. force (second term) needs every pair closer than
-// r_c.  Cells of side >= r_c (n_cells_dim = floor(L / r_c) >= 3 per edge) make
-// that a walk over the 27 neighbouring cells.  The sort is a counting sort
+// r_c.  Cells of side >= r_c + skin (n_cells_dim = floor(L / (r_c + skin)) >= 3
+// per edge, skin 0 without a neighbour list) make that a walk over the 27
+// neighbouring cells, and the neighbour list of the MD step a walk over the
+// same cells with the cutoff r_c + skin.  The sort is a counting sort
 // (histogram with atomics, one exclusive scan, scatter), followed by a per-cell
 // re-ordering by original index so that the order inside a cell -- and with it
 // every floating-point sum over neighbours -- is the same on every run.

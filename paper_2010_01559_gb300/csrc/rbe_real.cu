@@ -3,14 +3,16 @@
 // total force / dE/dq, the Langevin update of Sec. 3.3, and the FP64 energy
 // reduction.
 //
-// Cells have side >= r_c and there are at least 3 per edge, so every pair
-// within r_c is met exactly once, as the minimum image, among the 27 cells
-// around a particle's own.  With r_c > L/3 (up to L/2) the box is one cell and
-// every particle meets every other once, again as the minimum image.  Mixed path: one block per segment of x-adjacent
-// cells with the neighbourhood staged in shared memory and R = 1, 3 or 9
-// threads per particle, each scanning 9/R neighbour rows (tuning choices).
-// FP64 path: G threads per particle reading the
-// neighbours from global memory.
+// Cells have side >= r_c (+ skin with a neighbour list) and there are at least
+// 3 per edge, so every pair within r_c is met exactly once, as the minimum
+// image, among the 27 cells around a particle's own.  With r_c > L/3 (up to
+// L/2) the box is one cell and every particle meets every other once, again as
+// the minimum image.  MD steps on the mixed path walk a Verlet list of the
+// pairs within r_c + skin (k_list_build, k_real_list); forces calls scan the
+// cells: one block per segment of x-adjacent cells with the neighbourhood
+// staged in shared memory and R = 1, 3 or 9 threads per particle, each scanning
+// 9/R neighbour rows (k_real_seg).  FP64 path: G threads per particle reading
+// the neighbours from global memory.
 //
 // Real-space pair terms for r < r_c (r_ij = r_j - r_i):
 //   F_i   += -lB q_i q_j G(r) r_ij / r,  G = erfc(sqrt(a) r)/r^2 + 2 sqrt(a) e^{-a r^2}/(sqrt(pi) r)
