@@ -473,6 +473,7 @@ def run_ours(args):
                                units)
         large["scaling"] = scaling_sweep(rbe, torch, wls, dev, stream, flush) + [
             {"N": large["N"], "ms_per_step": large["ms_per_step"], "value": large["value"]}]
+        large["batched_replicas"] = measure_replicas(rbe, torch, wls, dev, stream, flush)
 
     result = None
     if rank == 0:
@@ -487,7 +488,8 @@ def run_ours(args):
                        "FP64 rho(k) and energy sums)", "graph": True,
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
                        "tuning": {"rho_chunk": tuning[0], "force_split": tuning[1],
-                                  "real_split": tuning[2], "real_seg": tuning[3]},
+                                  "real_split": tuning[2], "real_seg": tuning[3],
+                                  "list_split": tuning[4]},
                        "parallelism": f"replicas x{world}"},
             "force_evals_per_s": value / wl.n,
             "clocks": clk,
@@ -622,6 +624,43 @@ def scaling_sweep(rbe, torch, wls, dev, stream, flush, sizes=(1 << 14, 1 << 16, 
     return out
 
 
+def measure_replicas(rbe, torch, wls, dev, stream, flush, K=20, W=3):
+    """The batched configuration: 64 independent 1:1 electrolytes (N log-uniform
+    in [1000, 65536], density 0.064, P = 100, one Philox stream each) stepped
+    together by one batch handle, graph replay, L2 flushed between steps."""
+    import numpy as np
+    reps = wls.config_replicas()
+    h = rbe.RBEBatch([rbe.params_from(w.params) for w in reps], [w.n for w in reps])
+    pos = torch.from_numpy(np.concatenate([w.pos_q() for w in reps])).to(dev)
+    vel = torch.zeros_like(pos)
+    vel[:, :3] = torch.from_numpy(np.concatenate([w.vel for w in reps])).to(dev)
+    n_all = int(pos.shape[0])
+    with torch.cuda.stream(stream):
+        tuning = h.autotune(pos)
+        step_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+        h.set_graph(True)
+        h.step(pos, vel, W, step_dev)
+    stream.synchronize()
+    evs = []
+    with torch.cuda.stream(stream):
+        for k in range(K):
+            flush.fill_(k & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.step(pos, vel, 1, step_dev)
+            e1.record(stream)
+            evs.append((e0, e1))
+    stream.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    stats = h.list_stats()
+    h.close()
+    return {"workload": f"{len(reps)} replicas, 1:1 electrolyte, N log-uniform in [1000, 65536], "
+                        f"density 0.064, P = 100", "systems": len(reps), "N_total": n_all,
+            "value": n_all * K / (ms / 1e3), "unit": UNIT, "steps": K, "ms_per_step": ms / K,
+            "tuning": list(tuning), "list_builds": stats["builds"]}
+
+
 def measure_system(rbe, torch, wl, dev, stream, K, W, flush, peaks, units):
     """Timed MD steps (mixed, graph replay, L2 flushed between steps), a
     profiled pass, the FP64 path and the mixed-vs-FP64 force agreement."""
@@ -677,7 +716,7 @@ def measure_system(rbe, torch, wl, dev, stream, K, W, flush, peaks, units):
            "r_c": wl.params.r_c, "value": value, "unit": UNIT, "steps": K,
            "ms_per_step": ms / K, "force_evals_per_s": K / (ms / 1e3),
            "tuning": {"rho_chunk": tuning[0], "force_split": tuning[1], "real_split": tuning[2],
-                      "real_seg": tuning[3]},
+                      "real_seg": tuning[3], "list_split": tuning[4]},
            "kernels_avg_us": {k: (t / c * 1e3 if c else 0.0) for k, (t, c) in prof.items()},
            "roofline": roofline(prof, wl, peaks, units, counts=pair_counts(wl)),
            "fourier_rooflines": fourier_rooflines(prof, wl, units),
