@@ -112,6 +112,8 @@ __device__ void draw_samples_mh(const Work& w, const PrepArgs& pa) {
     __shared__ unsigned char s_dec[3][kMhWin];   // decision if the state is the previous proposal
     __shared__ int s_st[3][kMhWin];
     __shared__ int s_state[3], s_emitted, s_used, s_bad;
+    __shared__ int s_wsum[kBlockP / 32];
+    static_assert(kMhWin == 2 * kBlockP, "emission takes two window iterations per thread");
     const int sys = (int)blockIdx.x - pa.npblk;
     if (sys >= pa.nsys) return;
     const SysDev& S = sys_of<ONE>(w, sys);
@@ -152,33 +154,74 @@ __device__ void draw_samples_mh(const Work& w, const PrepArgs& pa) {
         }
         __syncthreads();
         if (threadIdx.x < 3) {
+            // the walk: the state enters only through a compare and a select, so
+            // the proposals and decisions of eight iterations are loaded at once
             const int c = threadIdx.x;
             int st = s_state[c];
-            for (int it = 0; it < kMhWin; ++it) {
-                const int ms = s_prop[c][it];
-                const bool acc = (it > 0 && st == s_prop[c][it - 1])
-                                     ? s_dec[c][it] != 0
-                                     : __dmul_rn(s_u[c][it], s_rho[st + S.M]) < s_rho[ms + S.M];
-                if (acc) st = ms;
-                s_st[c][it] = st;
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int e = s_emitted, used = kMhWin;
-            for (int it = 0; it < kMhWin; ++it) {
-                const int mx = s_st[0][it], my = s_st[1][it], mz = s_st[2][it];
-                if (mx != 0 || my != 0 || mz != 0) {
-                    pa.ksamp[S.off_k + e] = make_int4(mx, my, mz, 1);
-                    if (++e == S.P) { used = it + 1; break; }
+            for (int it0 = 0; it0 < kMhWin; it0 += 8) {
+                int pr[9];
+                unsigned char dc[8];
+                pr[0] = it0 > 0 ? s_prop[c][it0 - 1] : 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    pr[q + 1] = s_prop[c][it0 + q];
+                    dc[q] = s_dec[c][it0 + q];
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int it = it0 + q, ms = pr[q + 1];
+                    const bool acc = (it > 0 && st == pr[q])
+                                         ? dc[q] != 0
+                                         : __dmul_rn(s_u[c][it], s_rho[st + S.M]) < s_rho[ms + S.M];
+                    if (acc) st = ms;
+                    s_st[c][it] = st;
                 }
             }
-            for (int c = 0; c < 3; ++c) s_state[c] = s_st[c][used - 1];
-            s_emitted = e;
-            s_used = used;
-            if (t0 + (uint64_t)used >= tmax && e < S.P) s_bad = 1;
         }
         __syncthreads();
+        // emission: the nonzero triples of the window in order, until P are out;
+        // each finds its slot from a block-wide prefix count of the nonzero ones
+        {
+            const int e0 = s_emitted, need = S.P - e0;
+            const int a0 = 2 * threadIdx.x, a1 = a0 + 1;          // kMhWin == 2 * kBlockP
+            const bool f0 = (s_st[0][a0] | s_st[1][a0] | s_st[2][a0]) != 0;
+            const bool f1 = (s_st[0][a1] | s_st[1][a1] | s_st[2][a1]) != 0;
+            const int mine = (int)f0 + (int)f1;
+            int incl = mine;
+            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) s_wsum[wid] = incl;
+            if (threadIdx.x == 0) s_used = kMhWin;
+            __syncthreads();
+            int before = 0, total = 0;
+            for (int k = 0; k < kBlockP / 32; ++k) {
+                if (k < wid) before += s_wsum[k];
+                total += s_wsum[k];
+            }
+            const int p0 = before + incl - mine;               // nonzero triples before a0
+            if (f0 && p0 < need) {
+                pa.ksamp[S.off_k + e0 + p0] = make_int4(s_st[0][a0], s_st[1][a0], s_st[2][a0], 1);
+                if (p0 == need - 1) s_used = a0 + 1;
+            }
+            const int p1 = p0 + (int)f0;
+            if (f1 && p1 < need) {
+                pa.ksamp[S.off_k + e0 + p1] = make_int4(s_st[0][a1], s_st[1][a1], s_st[2][a1], 1);
+                if (p1 == need - 1) s_used = a1 + 1;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const int used = s_used;
+                const int e = min(e0 + total, S.P);
+                for (int c = 0; c < 3; ++c) s_state[c] = s_st[c][used - 1];
+                s_emitted = e;
+                if (t0 + (uint64_t)used >= tmax && e < S.P) s_bad = 1;
+            }
+            __syncthreads();
+        }
         t0 += (uint64_t)s_used;
     }
     if (threadIdx.x == 0) {
