@@ -249,3 +249,41 @@ def test_list_step_on_water_like_system_matches_oracle(rbe):
     assert st["max_count"] > 400 and st["max_count"] <= st["capacity"]
     assert err <= TOL_MIXED
     h.close()
+
+
+def test_list_survives_particle_count_change_and_fp64_steps(rbe):
+    """One single-system handle: list steps with all 1000 particles, then with
+    the first 800 (a smaller n re-prepares the work tables; the list is built
+    afresh), then an FP64 step in between mixed ones (it reorders the shared
+    sorted arrays): each mixed step force against the cell scan at the same
+    positions."""
+    import torch
+    wl = workloads.config_small_fp64()
+    h = rbe.RBE(rbe.params_from(wl.params, n_max=wl.n))
+    hc = rbe.RBE(rbe.params_from(_no_list(wl.params), n_max=wl.n))
+    step = torch.zeros(1, dtype=torch.int64, device="cuda")
+    pos, vel = _state(wl, torch)
+    h.step(pos, vel, 5, step)
+    F = torch.zeros((wl.n, 4), dtype=torch.float32, device="cuda")
+    before = pos.clone()
+    h.step(pos, vel, 1, step, F_out=F)
+    _check_same(F, hc.forces(before, 5, energy=False)[0], "n = 1000")
+    m = 800                                              # the first 800 particles
+    p2, v2 = pos[:m].clone(), vel[:m].clone()
+    b0 = h.list_stats()["builds"]
+    before = p2.clone()
+    F2 = torch.zeros((m, 4), dtype=torch.float32, device="cuda")
+    h.step(p2, v2, 1, step, F_out=F2)
+    assert h.list_stats()["builds"] == b0 + 1
+    _check_same(F2, hc.forces(before, 6, energy=False)[0], "n = 800")
+    p64, v64 = p2.double().contiguous(), v2.double().contiguous()
+    h.step(p64, v64, 1, step)                            # FP64 step, index 7
+    p2, v2 = p64.float().contiguous(), v64.float().contiguous()
+    b1 = h.list_stats()["builds"]
+    before = p2.clone()
+    h.step(p2, v2, 1, step, F_out=F2)
+    assert h.list_stats()["builds"] == b1 + 1            # rebuilt after the FP64 step
+    _check_same(F2, hc.forces(before, 8, energy=False)[0], "after an FP64 step")
+    h.sync()
+    h.close()
+    hc.close()
