@@ -360,6 +360,8 @@ void fill_sysdev(const SysHost& s, SysDev& d) {
     d.nrb = 0;
     d.off_sg = 0;
     d.nsg = 0;
+    d.off_lb = 0;
+    d.nlb = 0;
     // rho(k) accumulators: |rho| <= sum |q| <= 4 n is assumed; the largest
     // power of two (at most 2^52) that keeps 4 n * scale below 2^62.
     int e = 52;
@@ -490,11 +492,13 @@ rbe_status prepare(rbe_ctx* h, int n) {
             if (sh.n == 0) break;
         }
         d.nrb = nrb;
+        d.off_lb = (int)lblk.size();
         if (h->list)
             for (int f = 0; f < sh.n || f == 0; f += ltile) {
                 lblk.push_back(Tile{s, sh.off_p + f, std::max(0, std::min(ltile, sh.n - f)), 0});
                 if (sh.n == 0) break;
             }
+        d.nlb = (int)lblk.size() - d.off_lb;
         d.off_sg = (int)segs.size();
         {
             const int ncd = sh.ncd, seg = std::min(rseg, ncd);
@@ -639,8 +643,11 @@ rbe_status allocate(rbe_ctx* h) {
     }
     RBE_ALLOC(h->d_kab, h->ktot);
     RBE_ALLOC(h->d_qsum_fx, h->nsys);
-    RBE_ALLOC(h->d_blk_e, std::max<long long>(rb, (long long)kSegChunks * (h->ncell + 1)));
-    RBE_ALLOC(h->d_blk_w, std::max<long long>(rb, (long long)kSegChunks * (h->ncell + 1)));
+    // per-block energy / virial partials: FP64 blocks, segment blocks or list blocks
+    const long long nblk_e = std::max<long long>(std::max<long long>(rb, (long long)kSegChunks *
+                                                 (h->ncell + 1)), (long long)h->max_lblk);
+    RBE_ALLOC(h->d_blk_e, nblk_e);
+    RBE_ALLOC(h->d_blk_w, nblk_e);
     RBE_ALLOC(h->d_blk_q, pb);
     RBE_ALLOC(h->d_cur_step, 1);
     RBE_ALLOC(h->d_stage_step, 1);
@@ -845,6 +852,7 @@ struct EvalArgs {
     double4* md_pos64;
     double4* md_vel64;
     bool list;                // mixed MD step over the neighbour list
+    bool list_forces;         // mixed forces call over the neighbour list
 };
 
 // Kernel work descriptor: tables for a batch, by-value constants and a tile
@@ -967,7 +975,8 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     pa.kcoef = h->d_kcoef;
     pa.err = h->d_err;
     pa.nh = (a.md_pos || a.md_pos64) ? h->d_nh : nullptr;
-    if (a.list) {
+    const bool lst = a.list || a.list_forces;     // the evaluation keeps the list
+    if (lst) {
         pa.sref = h->d_sref;
         pa.iperm = h->d_iperm;
         pa.spos = h->d_spos;
@@ -975,7 +984,7 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     } else {
         h->list_valid = false;              // the sorted arrays are about to change
     }
-    const int* lflag = a.list ? h->d_list_flag : nullptr;
+    const int* lflag = lst ? h->d_list_flag : nullptr;
     if (want_q)
         cudaMemsetAsync(h->d_qsum_fx, 0, sizeof(unsigned long long) * h->nsys, st);
     run(RBE_K_PREP, st, [&] {
@@ -1017,9 +1026,9 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     run(RBE_K_CELL_ORDER, sc, [&] {
         launch_order(sc, n, h->d_cid, h->d_cell_start, h->d_perm_tmp, mixed ? h->d_fx : nullptr,
                      h->d_spos, mixed ? nullptr : h->d_fx64, h->d_spos64, h->d_perm, lflag,
-                     a.list ? h->d_iperm : nullptr);
+                     lst ? h->d_iperm : nullptr);
     });
-    if (a.list)
+    if (lst)
         run(RBE_K_LIST_BUILD, sc, [&] {
             ListArgs la{};
             la.w = make_work(h, h->d_pblk, kBlockP, 0);
@@ -1084,15 +1093,32 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
         md.cur_step = h->d_cur_step;
         md.list_flag = h->d_list_flag;
         run(RBE_K_FOURIER_FORCE, st, [&] { launch_force(h, st, true, md, !prof); });
-    } else {
+    } else if (!a.list_forces) {
         run(RBE_K_REAL, st, [&] {
             if (mixed) launch_real_mixed(st, one, r); else launch_real_f64(st, one, r);
         });
     }
+    if (a.list_forces) {
+        // forces call: one pass over the (possibly rebuilt) list after the
+        // Fourier force, assembling F, dE/dq and the energy / virial partials
+        r.lw = make_work(h, h->d_lblk, kBlockP / h->lsplit, 0);
+        r.nlblk = h->nlblk;
+        r.lsplit = h->lsplit;
+        r.nbr = h->d_nbr;
+        r.ncnt = h->d_ncnt;
+        r.nbr_stride = std::max(h->ntot, 1);
+        r.nbr_cap = h->list_cap;
+        r.list_flag = h->d_list_flag;
+        r.list_when = 2;
+        r.fmode = 1;
+        r.flag_clear = h->d_list_flag;
+        run(RBE_K_REAL, st, [&] { launch_real_list(st, one, r); });
+    }
     if (a.E)
         run(RBE_K_ENERGY, st, [&] {
             launch_energy(st, one, make_work(h, nullptr, 0, 0), h->nsys, h->d_ksamp, h->d_rho_fx,
-                          h->d_blk_e, h->d_blk_q, r.blk_w, a.parts, mixed ? 1 : 0, a.E,
+                          h->d_blk_e, h->d_blk_q, r.blk_w, a.parts,
+                          a.list_forces ? 2 : (mixed ? 1 : 0), a.E,
                           r.blk_w ? a.W : nullptr);
         });
     if (prof) {
@@ -1126,6 +1152,18 @@ rbe_status finish(rbe_ctx* h, const char* where) {
     return RBE_OK;
 }
 
+// A mixed forces call on a handle that keeps a neighbour list goes over the
+// list too (rebuilt when a particle moved more than skin/2); the first such
+// call after anything else touched the sorted arrays builds it.
+rbe_status use_list_forces(rbe_ctx* h, int n, EvalArgs& a) {
+    if (!h->list || a.prec != RBE_MIXED || n <= 0) return RBE_OK;
+    a.list_forces = true;
+    if (!h->list_valid)
+        RBE_CUDA(h, cudaMemsetAsync(h->d_list_flag, 0xFF, sizeof(int), h->stream));
+    h->list_valid = true;
+    return RBE_OK;
+}
+
 rbe_status forces_impl(rbe_ctx* h, int n, int prec, const void* pos, uint64_t step, int parts,
                        void* F, double* E, void* phi) {
     if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
@@ -1148,6 +1186,7 @@ rbe_status forces_impl(rbe_ctx* h, int n, int prec, const void* pos, uint64_t st
         a.F64 = (double4*)F;
         a.phi64 = (double*)phi;
     }
+    if ((s = use_list_forces(h, n, a)) != RBE_OK) return s;
     enqueue_eval(h, h->stream, a);
     return finish(h, "rbe_forces");
 }
@@ -1208,6 +1247,7 @@ rbe_status observables_impl(rbe_ctx* h, int n, const float* pos_q, const float* 
     a.pos = (const float4*)pos_q;
     a.E = h->d_stage_E;
     a.W = h->d_obs_w;
+    if ((s = use_list_forces(h, n, a)) != RBE_OK) return s;
     enqueue_eval(h, h->stream, a);
     for (int sy = 0; sy < h->nsys; ++sy) {
         const SysHost& sh = h->sys[sy];

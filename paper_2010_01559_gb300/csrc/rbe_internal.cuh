@@ -62,6 +62,7 @@ struct SysDev {
     int off_b, nb;          // first per-particle block and block count (prep)
     int off_rb, nrb;        // first real-space block and block count (FP64 path)
     int off_sg, nsg;        // first real-space segment and segment count (mixed path)
+    int off_lb, nlb;        // first neighbour-list block and block count
     // FP32 copies of the pair and Langevin constants, rounded once on the host
     // (kernels then hold no double-to-float conversions)
     float f_rc2, f_lj_rc2, f_alpha, f_sqrt_alpha, f_two_sa_spi, f_lB;
@@ -495,6 +496,9 @@ struct RealArgs {
     int nbr_stride, nbr_cap;
     const int* list_flag;    // rebuild flag of this step
     int list_when;           // the list kernel works only when (*list_flag != 0) == list_when
+                             // (2: always)
+    int fmode;               // forces call: assemble F, phi, energy and virial partials
+    int* flag_clear;         // forces call: the rebuild flag to clear
     float4* freal;           // list kernel output: real-space force, caller's order
     double2* blk_e;          // per block (E_coul, E_lj), nullable
     double2* blk_w;          // per block (W_coul, W_lj): pair virials r.F, nullable

@@ -566,14 +566,24 @@ constexpr int kListU = 8;           // list entries per lane and batch of the li
 // so it runs concurrently with the structure factors (and, when the list
 // stands, with the no-op rebuild kernels); the Fourier-force kernel then
 // completes the step.
-template <int R, bool ONE>
+//
+// FM (forces calls): the pass runs once, after the rebuild and the Fourier
+// force, and assembles per particle the total force (+ F^F), dE/dq (+ the
+// Fourier part, self and background terms) and per-block FP64 partials of the
+// real-space and LJ energies and virials, as the cell-scan pass does.
+template <int R, bool ONE, bool FM>
 __global__ void __launch_bounds__(kBlockP) k_real_list(const __grid_constant__ RealArgs a) {
     constexpr int T = kBlockP / R;               // particles per block
     const Tile tl = tile_of<ONE>(a.lw);
-    // launched twice per step: right after the prep kernel (works when the list
-    // stands) and after the rebuild (works when the list was rebuilt)
-    if ((*a.list_flag != 0) != (a.list_when != 0)) return;
-    const SysDev& S = sys_of<ONE>(a.lw, tl.sys);
+    if constexpr (!FM) {
+        // launched twice per step: right after the prep kernel (works when the
+        // list stands) and after the rebuild (works when the list was rebuilt)
+        if ((*a.list_flag != 0) != (a.list_when != 0)) return;
+    } else {
+        if (a.flag_clear && blockIdx.x == 0 && threadIdx.x == 0) *a.flag_clear = 0;
+    }
+    const int sys = tl.sys;
+    const SysDev& S = sys_of<ONE>(a.lw, sys);
     const int p = threadIdx.x / R, l = threadIdx.x - p * R;
     const bool do_real = (a.parts & kPartReal) != 0;
     const bool do_lj = (a.parts & kPartLJ) != 0 && S.lj_eps != 0.0;
@@ -587,7 +597,7 @@ __global__ void __launch_bounds__(kBlockP) k_real_list(const __grid_constant__ R
     kc.lj_s2 = S.f_lj_sigma2;
     kc.lj_eps = S.f_lj_eps;
     kc.lj_shift = S.f_lj_shift;
-    kc.vir = false;
+    kc.vir = FM && a.blk_w != nullptr;
     PairAcc acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (p < tl.count && (do_real || do_lj)) {
         const int i = tl.first + p;
@@ -624,26 +634,75 @@ __global__ void __launch_bounds__(kBlockP) k_real_list(const __grid_constant__ R
             }
         }
     }
-    float fx = acc.fx, fy = acc.fy, fz = acc.fz;
+    float fx = acc.fx, fy = acc.fy, fz = acc.fz, ph = acc.phr;
+    float ec = acc.ec, el = acc.elj, wc = acc.wc, wl = acc.wlj;
     if constexpr (R > 1) {
 #pragma unroll
         for (int o = R / 2; o > 0; o >>= 1) {
             fx += __shfl_down_sync(0xffffffffu, fx, o, R);
             fy += __shfl_down_sync(0xffffffffu, fy, o, R);
             fz += __shfl_down_sync(0xffffffffu, fz, o, R);
+            if constexpr (FM) {
+                ph += __shfl_down_sync(0xffffffffu, ph, o, R);
+                ec += __shfl_down_sync(0xffffffffu, ec, o, R);
+                el += __shfl_down_sync(0xffffffffu, el, o, R);
+                wc += __shfl_down_sync(0xffffffffu, wc, o, R);
+                wl += __shfl_down_sync(0xffffffffu, wl, o, R);
+            }
         }
         __shared__ float4 s_f[T];
-        if (p < tl.count && l == 0) s_f[p] = make_float4(fx, fy, fz, 0.f);
+        __shared__ float4 s_e[FM ? T : 1];
+        if (p < tl.count && l == 0) {
+            s_f[p] = make_float4(fx, fy, fz, ph);
+            if constexpr (FM) s_e[p] = make_float4(ec, el, wc, wl);
+        }
         __syncthreads();
         if ((int)threadIdx.x < tl.count) {
             const float4 f = s_f[threadIdx.x];
-            fx = f.x; fy = f.y; fz = f.z;
+            fx = f.x; fy = f.y; fz = f.z; ph = f.w;
+            if constexpr (FM) {
+                const float4 e = s_e[threadIdx.x];
+                ec = e.x; el = e.y; wc = e.z; wl = e.w;
+            }
         }
     }
-    // the real-space force in the caller's order, for the Fourier-force
-    // kernel that adds its part and applies the thermostat
-    if ((int)threadIdx.x < tl.count)
-        a.freal[a.perm[tl.first + threadIdx.x]] = make_float4(fx, fy, fz, 0.f);
+    if constexpr (!FM) {
+        // the real-space force in the caller's order, for the Fourier-force
+        // kernel that adds its part and applies the thermostat
+        if ((int)threadIdx.x < tl.count)
+            a.freal[a.perm[tl.first + threadIdx.x]] = make_float4(fx, fy, fz, 0.f);
+    } else {
+        double e_c = 0.0, e_l = 0.0, w_c = 0.0, w_l = 0.0;
+        if ((int)threadIdx.x < tl.count) {
+            const int i = tl.first + threadIdx.x;
+            const int o = a.perm[i];
+            float phi = ph;
+            if (a.parts & kPartFourier) {
+                const float4 f = a.fs[o];
+                fx += f.x; fy += f.y; fz += f.z;
+                if (a.phi_out) {
+                    const double qi = (double)__uint_as_float(a.spos[i].w);
+                    const double qs = (double)(long long)__ldcg(a.qsum_fx + sys) / kQScale;
+                    phi += f.w - (float)(2.0 * S.self_coef * qi + S.bg_coef * qs);
+                }
+            }
+            if (a.F_out) a.F_out[o] = make_float4(fx, fy, fz, 0.f);
+            if (a.phi_out) a.phi_out[o] = phi;
+            e_c = (double)ec;
+            e_l = (double)el;
+            w_c = (double)wc;
+            w_l = (double)wl;
+        }
+        if (a.blk_e) {
+            const double2 r = block_sum2_real(e_c, e_l);
+            if (threadIdx.x == 0) a.blk_e[blockIdx.x] = r;
+        }
+        if (a.blk_w) {
+            __syncthreads();                            // the partial buffers are reused
+            const double2 r = block_sum2_real(w_c, w_l);
+            if (threadIdx.x == 0) a.blk_w[blockIdx.x] = r;
+        }
+    }
 }
 
 // ----------------------------------------------------------------- FP64
@@ -840,8 +899,9 @@ __global__ void k_energy(const __grid_constant__ Work w, const int4* __restrict_
             q2 += v.y;
         }
     }
-    const int off = per_cell ? S.off_sg * kSegChunks : S.off_rb;
-    const int nb = per_cell ? S.nsg * kSegChunks : S.nrb;
+    // partials per FP64 block (0), per segment block (1) or per list block (2)
+    const int off = per_cell == 2 ? S.off_lb : (per_cell ? S.off_sg * kSegChunks : S.off_rb);
+    const int nb = per_cell == 2 ? S.nlb : (per_cell ? S.nsg * kSegChunks : S.nrb);
     double wc = 0.0, wlj = 0.0;
     if (blk_e)
         for (int b = threadIdx.x; b < nb; b += blockDim.x) {
@@ -935,8 +995,13 @@ void launch_real_mixed(cudaStream_t st, bool one, const RealArgs& a) {
 
 template <int R>
 static void real_list_r(cudaStream_t st, bool one, const RealArgs& a) {
-    if (one) k_real_list<R, true><<<a.nlblk, kBlockP, 0, st>>>(a);
-    else k_real_list<R, false><<<a.nlblk, kBlockP, 0, st>>>(a);
+    if (a.fmode) {
+        if (one) k_real_list<R, true, true><<<a.nlblk, kBlockP, 0, st>>>(a);
+        else k_real_list<R, false, true><<<a.nlblk, kBlockP, 0, st>>>(a);
+    } else {
+        if (one) k_real_list<R, true, false><<<a.nlblk, kBlockP, 0, st>>>(a);
+        else k_real_list<R, false, false><<<a.nlblk, kBlockP, 0, st>>>(a);
+    }
 }
 
 void launch_real_list(cudaStream_t st, bool one, const RealArgs& a) {

@@ -107,7 +107,7 @@ def test_list_step_force_matches_oracle_after_60_steps(rbe):
     h.close()
 
 
-def test_list_rebuilt_after_forces_call_and_after_caller_moves_particles(rbe):
+def test_list_across_forces_calls_and_after_caller_moves_particles(rbe):
     import torch
     wl = workloads.config_small_fp64()
     h = rbe.RBE(rbe.params_from(wl.params, n_max=wl.n))
@@ -117,11 +117,16 @@ def test_list_rebuilt_after_forces_call_and_after_caller_moves_particles(rbe):
     F = torch.zeros((wl.n, 4), dtype=torch.float32, device="cuda")
     h.step(pos, vel, 5, step)
     b0 = h.list_stats()["builds"]
-    h.forces(pos, 5)                                   # reorders the shared sorted arrays
+    # a mixed forces call at these positions goes over the same list: no rebuild
+    Ff, _, _ = h.forces(pos, 5, energy=False)
+    assert h.list_stats()["builds"] == b0
+    _check_same(Ff, hc.forces(pos, 5, energy=False)[0], "forces call over the list")
+    # an FP64 forces call reorders the shared sorted arrays: the next step rebuilds
+    h.forces_f64(pos.double().contiguous(), 5, energy=False)
     before = pos.clone()
     h.step(pos, vel, 1, step, F_out=F)
     assert h.list_stats()["builds"] == b0 + 1
-    _check_same(F, hc.forces(before, 5, energy=False)[0], "after forces call")
+    _check_same(F, hc.forces(before, 5, energy=False)[0], "after an FP64 forces call")
     # the caller moves one particle by half a box edge: the next step sees it
     b1 = h.list_stats()["builds"]
     pos[17, 0] = (pos[17, 0] + 0.5 * wl.params.box) % wl.params.box

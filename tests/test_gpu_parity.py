@@ -7,6 +7,8 @@ Tolerances:
   * mixed path: relative RMS <= 1e-5 per part (Fourier, real-space Coulomb,
     LJ) and for the total force, dE/dq <= 1e-5, energies <= 1e-6.
 """
+import copy
+
 import numpy as np
 import pytest
 
@@ -30,8 +32,14 @@ def rbe():
     return rbe
 
 
-def _handle(rbe, wl, n_max=None):
-    return rbe.RBE(rbe.params_from(wl.params, n_max=wl.n if n_max is None else n_max))
+def _handle(rbe, wl, n_max=None, path="list"):
+    """path "list": mixed forces over the neighbour list (the default);
+    "cells": the per-call cell scan (skin < 0 turns the list off)."""
+    p = wl.params
+    if path == "cells":
+        p = copy.copy(p)
+        p.skin = -1.0
+    return rbe.RBE(rbe.params_from(p, n_max=wl.n if n_max is None else n_max))
 
 
 def _dev(wl, dtype="float32"):
@@ -125,19 +133,25 @@ def test_one_cell_box_all_pairs_match_oracle(rbe):
     assert rel_rms(F64[:, :3].cpu().numpy(), ref["F"]) <= TOL_F64
     assert energy_rel(E64.cpu().numpy()[0], ref["E"]) <= TOL_F64
     assert rel_rms(phi64.cpu().numpy(), ref["phi"]) <= TOL_F64
-    for R in (1, 3, 9):
-        h.set_tuning(0, 0, R, 0)
-        F, E, phi = h.forces(_dev(wl), step, phi=True)
+    F, E, phi = h.forces(_dev(wl), step, phi=True)          # over the neighbour list
+    assert rel_rms(F[:, :3].cpu().numpy(), ref["F"]) <= TOL_MIXED
+    assert energy_rel(E.cpu().numpy()[0], ref["E"]) <= TOL_E_MIXED
+    assert rel_rms(phi.cpu().numpy(), ref["phi"]) <= TOL_MIXED
+    hc = _handle(rbe, wl, path="cells")
+    for R in (1, 3, 9):                                      # the cell scan's lane splits
+        hc.set_tuning(0, 0, R, 0)
+        F, E, phi = hc.forces(_dev(wl), step, phi=True)
         assert rel_rms(F[:, :3].cpu().numpy(), ref["F"]) <= TOL_MIXED, R
         assert energy_rel(E.cpu().numpy()[0], ref["E"]) <= TOL_E_MIXED, R
         assert rel_rms(phi.cpu().numpy(), ref["phi"]) <= TOL_MIXED, R
 
 
 # ------------------------------------------------------------------ mixed path
+@pytest.mark.parametrize("path", ["list", "cells"])
 @pytest.mark.parametrize("cfg", ["c1", "c2"])
-def test_mixed_path_matches_oracle_per_part(rbe, cfg, request):
+def test_mixed_path_matches_oracle_per_part(rbe, cfg, path, request):
     wl = request.getfixturevalue(cfg)
-    h = _handle(rbe, wl)
+    h = _handle(rbe, wl, path=path)
     x = _dev(wl)
     step = 11
     ref = oracle_eval(wl, step, want_phi=True)
@@ -262,12 +276,20 @@ def test_tuning_does_not_change_results_beyond_rounding(rbe, c2):
         assert energy_rel(E.cpu().numpy()[0], ref["E"]) <= TOL_E_MIXED
         if chunk:
             assert h.get_tuning()[:3] == (chunk, split, rsplit)
-    for seg in (1, 2, 8):                  # 8 cells per edge: side >= r_c + skin
-        h.set_tuning(128, 2, 3, seg)
+    for ls in (1, 2, 4, 8):                # lanes per particle of the list pass
+        h.set_tuning(128, 2, 3, 0, ls)
         F, E, _ = h.forces(x, 6)
+        assert rel_rms(F[:, :3].cpu().numpy(), ref["F"]) <= TOL_MIXED, ls
+        assert energy_rel(E.cpu().numpy()[0], ref["E"]) <= TOL_E_MIXED
+        assert h.get_tuning()[4] == ls
+    hc = _handle(rbe, c2, path="cells")
+    for seg in (1, 2, 8):                  # segment lengths of the cell scan
+        hc.set_tuning(128, 2, 3, seg)
+        F, E, _ = hc.forces(x, 6)
         assert rel_rms(F[:, :3].cpu().numpy(), ref["F"]) <= TOL_MIXED, seg
         assert energy_rel(E.cpu().numpy()[0], ref["E"]) <= TOL_E_MIXED
-        assert h.get_tuning()[3] == seg
+        assert hc.get_tuning()[3] == seg
+    hc.close()
     c, s, r, sg, ls = h.autotune(x)
     assert c >= 32 and s in (1, 2, 4, 8) and r in (1, 3, 9) and sg >= 1
     assert h.get_tuning() == (c, s, r, sg, ls)
