@@ -500,7 +500,7 @@ def run_ours(args):
             "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_io,
                     "d2h_bytes_per_step": bytes_io,
-                    "api": "rbe_step_host on pinned host pos/vel: every step reads them from and writes them to host memory (the step's kernels access the page-locked arrays in place over the host link)"},
+                    "api": "rbe_step_host on pinned host pos/vel: every step reads them from and writes them to host memory (the step's kernels access the page-locked arrays in place over the host link; the call returns when the closing kernel's completion word reaches mapped host memory)"},
             "fp64_path": {"value": value64, "unit": UNIT, "steps": K64,
                           "ms_per_step": ms64 / K64},
             "speedup_vs_fp64": value / value64,

@@ -260,7 +260,12 @@ rbe_status rbe_set_graph(rbe_handle h, int32_t use_graph);
  * out, E_out (nullable) double[4 n_systems] out.  rbe_step_host: pos_q and
  * vel float4[n] in/out, steps step0 .. step0 + nsteps - 1; when both arrays
  * are page-locked (cudaHostAlloc, cudaHostRegister) the step's kernels read
- * and write them in place over the host link instead of staging copies. */
+ * and write them in place over the host link instead of staging copies, and
+ * on a neighbour-list handle the call returns as soon as the step's closing
+ * kernel has written a completion word to the handle's mapped host memory
+ * (every output store is visible to the host by then; the kernel's last
+ * blocks may still be retiring, and later work on h's stream is ordered
+ * after them as usual).  Errors as rbe_step and rbe_sync. */
 rbe_status rbe_forces_host(rbe_handle h, int32_t n, const float *pos_q, uint64_t step,
                            float *F_out, double *E_out);
 rbe_status rbe_step_host(rbe_handle h, int32_t n, float *pos_q, float *vel, int32_t nsteps,

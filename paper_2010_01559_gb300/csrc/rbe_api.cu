@@ -15,6 +15,7 @@
 //   T_j = min(floor((c_j / Z) * 2^32), 2^32 - 1) for j < 2M;  T_2M = 2^32
 //   H   = Z,  S = H^3 - 1.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -53,6 +54,7 @@ struct GraphEntry {
     const void* host_pos;  // host-buffer graphs: the caller's pinned arrays (else null)
     const void* host_vel;
     int host_steps;        // host-buffer graphs: steps per replay
+    const void* done;      // completion word of a zero-copy host step (else null)
     cudaGraphExec_t exec;
     int kernels;           // kernels in one replay
 };
@@ -220,9 +222,12 @@ struct rbe_ctx {
     int* d_list_flag = nullptr;
     unsigned long long* d_list_stats = nullptr;   // builds, largest count
     float4* d_freal = nullptr;                // real-space force of a list step
-    // pinned host words: [0] the step index of a host-buffer call, [1] the
-    // device error word read back asynchronously behind the outputs
+    // mapped page-locked host words: [0] the step index of a host-buffer
+    // call, [1] the device error word read back behind the outputs, [2] the
+    // completion word of a zero-copy list step (the step index after it)
     uint64_t* h_pin = nullptr;
+    uint64_t* h_pin_dev = nullptr;            // h_pin as the device sees it
+    unsigned int* d_done_cnt = nullptr;       // blocks of the closing kernel finished
     cudaEvent_t ev_real = nullptr;            // list step: real-space pass done
     cudaStream_t stream3 = nullptr;           // list step: the rebuild branch
     cudaEvent_t ev_chain = nullptr;           // list step: rebuild branch done
@@ -714,8 +719,11 @@ rbe_status allocate(rbe_ctx* h) {
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_chain, cudaEventDisableTiming));
     RBE_CUDA(h, cudaEventCreateWithFlags(&h->ev_prep, cudaEventDisableTiming));
     RBE_CUDA(h, cudaStreamCreateWithFlags(&h->stream3, cudaStreamNonBlocking));
-    RBE_CUDA(h, cudaHostAlloc((void**)&h->h_pin, 2 * sizeof(uint64_t), cudaHostAllocMapped));
-    h->h_pin[0] = h->h_pin[1] = 0;
+    RBE_CUDA(h, cudaHostAlloc((void**)&h->h_pin, 4 * sizeof(uint64_t), cudaHostAllocMapped));
+    h->h_pin[0] = h->h_pin[1] = h->h_pin[2] = h->h_pin[3] = 0;
+    RBE_CUDA(h, cudaHostGetDevicePointer((void**)&h->h_pin_dev, h->h_pin, 0));
+    RBE_CUDA(h, cudaMalloc(&h->d_done_cnt, sizeof(unsigned int)));
+    RBE_CUDA(h, cudaMemset(h->d_done_cnt, 0, sizeof(unsigned int)));
     return RBE_OK;
 }
 
@@ -734,7 +742,8 @@ void release(rbe_ctx* h) {
                     h->d_list_stats, h->d_freal,
                     h->d_qsum_fx, h->d_blk_e, h->d_blk_w, h->d_obs_m, h->d_obs_rho, h->d_obs_w,
                     h->d_obs_out, h->d_obs_part, h->d_blk_q, h->d_cur_step, h->d_stage_step,
-                    h->d_err, h->d_stage_pos, h->d_stage_vel, h->d_stage_F, h->d_stage_E};
+                    h->d_err, h->d_stage_pos, h->d_stage_vel, h->d_stage_F, h->d_stage_E,
+                    h->d_done_cnt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -853,6 +862,7 @@ struct EvalArgs {
     double4* md_vel64;
     bool list;                // mixed MD step over the neighbour list
     bool list_forces;         // mixed forces call over the neighbour list
+    unsigned long long* done; // list step, nullable: completion word (mapped host memory)
 };
 
 // Kernel work descriptor: tables for a batch, by-value constants and a tile
@@ -1084,7 +1094,7 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
         cudaEventRecord(h->ev_chain, sc);
         cudaStreamWaitEvent(st, h->ev_real, 0);
         cudaStreamWaitEvent(st, h->ev_chain, 0);
-        MdOut md;
+        MdOut md{};
         md.freal = h->d_freal;
         md.F_out = a.F;
         md.md_pos = a.md_pos;
@@ -1092,6 +1102,12 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
         md.nh = pa.nh;
         md.cur_step = h->d_cur_step;
         md.list_flag = h->d_list_flag;
+        if (a.done) {
+            md.done_cnt = h->d_done_cnt;
+            md.done_host = a.done;
+            md.err_host = (int*)(a.done - 1);
+            md.err = h->d_err;
+        }
         run(RBE_K_FOURIER_FORCE, st, [&] { launch_force(h, st, true, md, !prof); });
     } else if (!a.list_forces) {
         run(RBE_K_REAL, st, [&] {
@@ -1285,7 +1301,8 @@ struct HostIO {
 };
 
 rbe_status step_impl(rbe_ctx* h, int n, int prec, void* pos, void* vel, int nsteps,
-                     uint64_t* step_dev, float* F_out = nullptr, const HostIO* io = nullptr) {
+                     uint64_t* step_dev, float* F_out = nullptr, const HostIO* io = nullptr,
+                     unsigned long long* done = nullptr) {
     if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
     rbe_status s = check_n(h, n);
     if (s != RBE_OK) return s;
@@ -1303,6 +1320,7 @@ rbe_status step_impl(rbe_ctx* h, int n, int prec, void* pos, void* vel, int nste
         a.md_vel = (float4*)vel;
         a.F = (float4*)F_out;
         a.list = h->list;
+        a.done = h->list ? done : nullptr;
     } else {
         a.pos64 = (const double4*)pos;
         a.md_pos64 = (double4*)pos;
@@ -1346,7 +1364,7 @@ rbe_status step_impl(rbe_ctx* h, int n, int prec, void* pos, void* vel, int nste
         if (g.n == n && g.pos == pos && g.vel == vel && g.step == step_dev && g.prec == prec &&
             g.F == (const void*)F_out && g.host_pos == (host_graph ? io->pos : nullptr) &&
             g.host_vel == (host_graph ? io->vel : nullptr) &&
-            g.host_steps == (host_graph ? nsteps : 0)) {
+            g.host_steps == (host_graph ? nsteps : 0) && g.done == (const void*)a.done) {
             exec = g.exec;
             kernels = g.kernels;
         }
@@ -1371,7 +1389,7 @@ rbe_status step_impl(rbe_ctx* h, int n, int prec, void* pos, void* vel, int nste
         h->graphs.push_back(GraphEntry{n, pos, vel, step_dev, F_out, prec,
                                        host_graph ? io->pos : nullptr,
                                        host_graph ? io->vel : nullptr,
-                                       host_graph ? nsteps : 0, exec, kernels});
+                                       host_graph ? nsteps : 0, a.done, exec, kernels});
     }
     if (host_graph) {
         RBE_CUDA(h, cudaGraphLaunch(exec, h->stream));
@@ -1603,15 +1621,28 @@ rbe_status rbe_step_host(rbe_handle h, int32_t n, float* pos_q, float* vel, int3
     if (s != RBE_OK) return s;
     if (n > 0 && (!pos_q || !vel)) return fail(h, RBE_ERR_ARG, "null host buffer");
     h->h_pin[0] = step0;
-    void* dpos = mapped_host(pos_q);
-    void* dvel = mapped_host(vel);
-    uint64_t* dstep = (uint64_t*)mapped_host(h->h_pin);
-    if (n > 0 && dpos && dvel && dstep) {
+    void* dpos = n > 0 ? mapped_host(pos_q) : nullptr;
+    void* dvel = n > 0 ? mapped_host(vel) : nullptr;
+    if (n > 0 && dpos && dvel) {
         // page-locked arrays: the step's kernels read and write them in place
         // over the host link (no staging copies); the step index advances in
-        // the pinned word
-        s = step_impl(h, n, RBE_MIXED, dpos, dvel, nsteps, dstep);
+        // the pinned word.  A list step's closing kernel also delivers the
+        // error word and then a completion word there, which this thread
+        // polls instead of waiting on the stream.
+        const bool signal = h->list && nsteps > 0;
+        const uint64_t want = step0 + (uint64_t)nsteps;
+        volatile uint64_t* done = h->h_pin + 2;
+        if (signal) *done = ~want;
+        s = step_impl(h, n, RBE_MIXED, dpos, dvel, nsteps, h->h_pin_dev, nullptr, nullptr,
+                      signal ? (unsigned long long*)(h->h_pin_dev + 2) : nullptr);
         if (s != RBE_OK) return s;
+        if (signal) {
+            for (unsigned it = 1; *done != want; ++it)
+                if ((it & 1023u) == 0 && cudaStreamQuery(h->stream) != cudaErrorNotReady) break;
+            std::atomic_thread_fence(std::memory_order_acquire);
+            if (*done == want) return report_err(h);
+            // the stream ended without the signal: its status decides
+        }
         RBE_CUDA(h, cudaMemcpyAsync(h->h_pin + 1, h->d_err, sizeof(int), cudaMemcpyDeviceToHost,
                                     h->stream));
     } else {

@@ -306,6 +306,17 @@ k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
         }
     }
     if (nhm) warp_add_u64(k2, &md.nh[tl.sys].k2);
+    if (md.done_host) {
+        __threadfence_system();                     // this thread's pos / vel stores
+        __syncthreads();
+        if (threadIdx.x == 0 && atomicAdd(md.done_cnt, 1u) == gridDim.x - 1) {
+            __threadfence_system();                 // every block's stores, then the words
+            *md.done_cnt = 0u;
+            *(volatile int*)md.err_host = *(const volatile int*)md.err;
+            __threadfence_system();
+            *(volatile unsigned long long*)md.done_host = *md.cur_step + 1ull;
+        }
+    }
 }
 
 // ----------------------------------------------------------------- force (FP64)

@@ -439,6 +439,14 @@ struct MdOut {
     NhState* nh;
     const uint64_t* cur_step;
     int* list_flag;          // nullable: cleared (the step's rebuild flag is consumed)
+    // nullable: completion signal of a host-buffer step.  The last block to
+    // finish copies the device error word to err_host and then writes the
+    // step index after this step (*cur_step + 1) to done_host, both in mapped
+    // page-locked memory, after every block's stores are visible system-wide.
+    unsigned int* done_cnt;  // blocks finished (device; back to 0 by the last)
+    unsigned long long* done_host;
+    int* err_host;
+    const int* err;
 };
 void launch_fourier_force_mixed(cudaStream_t st, bool one, const Work& w, int nblk, int split,
                                 const uint4* fx, const int4* ksamp, const float2* kab,

@@ -117,18 +117,31 @@ def test_graph_replay_resume_and_host_calls_are_bitwise(rbe, c1):
         h.step_host(tp, tv, 1, s)
     assert np.array_equal(tp.numpy(), pa.cpu().numpy())
     assert np.array_equal(tv.numpy(), va.cpu().numpy())
-    # host buffers through one replayed graph per call (copies in, steps, copies
-    # out), one and two steps per call
-    h.set_graph(True)
-    for per in (1, 2):
-        v0 = np.zeros((c1.n, 4), np.float32)          # hv was updated in place above
+    # page-locked host buffers, read and written in place by the step's
+    # kernels; the call returns on the completion word the closing kernel
+    # writes.  Direct launches and graph replay, one, two and three steps per
+    # call, repeated step indices (a stale completion word must not count).
+    for graph in (False, True):
+        h.set_graph(graph)
+        for per in (1, 2):
+            v0 = np.zeros((c1.n, 4), np.float32)      # hv was updated in place above
+            v0[:, :3] = c1.vel
+            tp = torch.from_numpy(c1.pos_q().copy()).pin_memory()
+            tv = torch.from_numpy(v0).pin_memory()
+            for s in range(0, 20, per):
+                h.step_host(tp, tv, per, s)
+            assert np.array_equal(tp.numpy(), pa.cpu().numpy()), (graph, per)
+            assert np.array_equal(tv.numpy(), va.cpu().numpy()), (graph, per)
+        # the same step index twice from the same state gives the same result
+        v0 = np.zeros((c1.n, 4), np.float32)
         v0[:, :3] = c1.vel
-        tp = torch.from_numpy(c1.pos_q().copy()).pin_memory()
-        tv = torch.from_numpy(v0).pin_memory()
-        for s in range(0, 20, per):
-            h.step_host(tp, tv, per, s)
-        assert np.array_equal(tp.numpy(), pa.cpu().numpy()), per
-        assert np.array_equal(tv.numpy(), va.cpu().numpy()), per
+        outs = []
+        for _ in range(2):
+            tp = torch.from_numpy(c1.pos_q().copy()).pin_memory()
+            tv = torch.from_numpy(v0.copy()).pin_memory()
+            h.step_host(tp, tv, 3, 7)
+            outs.append((tp.clone(), tv.clone()))
+        assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
     h.set_graph(False)
     # forces through host buffers equal the device call
     F = torch.zeros((c1.n, 4), dtype=torch.float32)

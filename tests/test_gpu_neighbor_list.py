@@ -194,6 +194,14 @@ def test_list_overflow_is_reported_not_silent(rbe):
         h.sync()
     assert ei.value.status == capi.RBE_ERR_LIST
     h.sync()                                             # the latch was cleared
+    # a host-buffer step on page-locked arrays returns the error itself (the
+    # closing kernel delivers the error word with its completion word)
+    hp, hv = pos.cpu().pin_memory(), vel.cpu().pin_memory()
+    hp[:, :3] += 0.5                                     # moved > skin/2: a rebuild
+    with pytest.raises(capi.RBEError) as ei:
+        h.step_host(hp, hv, 1, 1)
+    assert ei.value.status == capi.RBE_ERR_LIST
+    h.sync()
     h.close()
 
 
