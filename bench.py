@@ -295,8 +295,14 @@ def unit_peaks(rbe, clk_mhz):
             "sfu_basis": basis, "alu_basis": basis_alu, "probe": pk}
 
 
+# SFU operations per (particle, wave vector) pair: the structure factors take
+# a sine and a cosine; the MD step's Fourier force, with the coefficient in
+# polar form, one sine (R sin(phi - theta))
+SFU_OPS_PER_PAIR = {"rho": 2, "fourier_force": 1}
+
+
 def fourier_rooflines(prof, wl, units):
-    """SFU roofline of both Fourier kernels (one sine and one cosine per pair)."""
+    """SFU roofline of both Fourier kernels of an MD step."""
     out = {}
     peak = units["sfu"]
     for name in ("rho", "fourier_force"):
@@ -304,7 +310,7 @@ def fourier_rooflines(prof, wl, units):
         if not cnt:
             continue
         avg_s = ms / cnt / 1e3
-        achieved = 2.0 * wl.n * wl.params.P / avg_s / 1e12
+        achieved = SFU_OPS_PER_PAIR[name] * wl.n * wl.params.P / avg_s / 1e12
         out[name] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tsfu/s",
                      "frac": achieved / peak, "avg_launch_us": avg_s * 1e6,
                      "traffic": traffic_for(name, wl.name)}
@@ -317,13 +323,14 @@ def roofline(prof, wl, peaks, units, counts=None):
     avg_s = ms / max(cnt, 1) / 1e3
     N, P = wl.n, wl.params.P
     if name in ("rho", "fourier_force"):
-        # each (particle, wave vector) pair takes one sine and one cosine
-        work = 2.0 * N * P
+        ops = SFU_OPS_PER_PAIR[name]
+        work = float(ops) * N * P
         peak = units["sfu"]
         achieved = work / avg_s / 1e12
         out = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
                "unit": "Tsfu/s", "frac": achieved / peak, "peak_basis": units["sfu_basis"],
-               "algorithmic": f"2 SFU ops per (particle, k) pair x {N} x {P}"}
+               "algorithmic": f"{ops} SFU op{'s' if ops > 1 else ''} per (particle, k) pair x "
+                              f"{N} x {P}"}
     elif name == "real" and counts is not None:
         cand, pairs = counts
         work = REAL_OPS_PER_CANDIDATE * cand + REAL_OPS_PER_PAIR * pairs

@@ -13,8 +13,9 @@
 //               reduction pass;
 //  k_force      per particle: F*_i = -q_i sum_l coef_l k_l Im(e^{-i k_l.r_i} rho_l)
 //               (Eq. rbmapprox) and the Fourier part of dE/dq_i, with the k-batch
-//               and coef_l (Im rho, Re rho), coef_l = (S/P) 4 pi / (V k^2) formed
-//               in FP64, staged in shared memory.
+//               and coef_l rho_l, coef_l = (S/P) 4 pi / (V k^2) formed in FP64, staged
+//               in shared memory; the mixed path holds coef_l rho_l in polar form
+//               (R_l, phi_l), so that an MD step's force takes one sine per pair.
 //
 // Mixed path phases: theta = 2 pi (m . s mod 1) with s the 32-bit fixed-point
 // fraction of the position; the product is exact in 32-bit integer arithmetic,
@@ -109,10 +110,13 @@ k_rho_mixed(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
         rho_accumulate(rho_fx + 2 * (S.off_k + l), red + o.x, imd + o.y, S.rho_scale);
     }
     // The last of the system's chunks to add its partials for this tile of
-    // wave vectors finds rho(k) complete and turns it into the FP32 force
-    // coefficients (A, B) of Eq. rbmapprox, once per k instead of once per
-    // force block.  Fence, then count: every chunk's atomics are visible to
-    // the block that takes the last count (no waiting on other blocks).
+    // wave vectors finds rho(k) complete and turns it into the force
+    // coefficient of Eq. rbmapprox in polar form, once per k instead of once
+    // per force block: with A = coef Im rho and B = coef Re rho,
+    // A cos(theta) - B sin(theta) = R sin(phi - theta) for R = |(A, B)| and
+    // phi = atan2(A, B), stored as (R, phi in 2^-32 turns).  Fence, then
+    // count: every chunk's atomics are visible to the block that takes the
+    // last count (no waiting on other blocks).
     __shared__ int s_last;
     __threadfence();
     __syncthreads();
@@ -124,7 +128,10 @@ k_rho_mixed(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
         if (active && half == 0) {
             const double2 r = rho_read(rho_fx + 2 * (S.off_k + l), S.rho_inv_scale);
             const double c = kcoef[S.off_k + l];
-            kab[S.off_k + l] = make_float2((float)(c * r.y), (float)(c * r.x));
+            const float A = (float)(c * r.y), B = (float)(c * r.x);
+            const float turns = atan2f(A, B) * 0.15915494309189535f;      // (-1/2, 1/2]
+            const uint32_t phi = (uint32_t)(long long)llrintf(turns * 4294967296.0f);
+            kab[S.off_k + l] = make_float2(hypotf(A, B), __uint_as_float(phi));
         }
         if (threadIdx.x == 0) kcnt[slot] = 0;        // ready for the next evaluation
     }
@@ -166,10 +173,13 @@ k_rho_f64(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
 }
 
 // ----------------------------------------------------------------- force (mixed)
-// Shared-memory record per wave vector: the integer m (phase) and, as floats,
-// m (direction) with the two coefficients A = coef Im rho, B = coef Re rho.
-struct KPhase { uint32_t mx, my, mz, pad; };
-struct KForce { float mx, my, mz, A; };
+// Shared-memory record per wave vector: -m and phi (the phase of the
+// coefficient, 2^-32 turns) as integers, and m (direction) with the magnitude
+// R as floats.  phi - m.s is exact in 32-bit arithmetic, so one sine per
+// (particle, k) pair gives Im(e^{-i k.r} rho) coef = R sin(phi - theta) (and
+// the cosine, in the same SFU pair, the dE/dq term R cos(phi - theta)).
+struct KPhase { uint32_t nmx, nmy, nmz, phi; };
+struct KForce { float mx, my, mz, R; };
 
 // SPLIT threads per particle (each a 1/SPLIT share of the wave vectors), or
 // with SPLIT = 1 PT = 2 particles per thread, which share each wave vector's
@@ -188,7 +198,6 @@ k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
     constexpr int kKT = 256;                        // wave vectors staged per pass
     __shared__ KPhase kp[kKT];
     __shared__ KForce kf[kKT];
-    __shared__ float kb[kKT];
     const Tile tl = tile_of<ONE>(w);
     const SysDev& S = sys_of<ONE>(w, tl.sys);
     const int sub = threadIdx.x % SPLIT;            // lane within the particle's group
@@ -232,28 +241,32 @@ k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
         __syncthreads();
         for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
             const int4 m = ksamp[S.off_k + base + k];
-            const float2 ab = kab[S.off_k + base + k];
-            kp[k] = KPhase{(uint32_t)m.x, (uint32_t)m.y, (uint32_t)m.z, 0u};
-            kf[k] = KForce{(float)m.x, (float)m.y, (float)m.z, ab.x};
-            kb[k] = ab.y;
+            const float2 rp = kab[S.off_k + base + k];
+            kp[k] = KPhase{0u - (uint32_t)m.x, 0u - (uint32_t)m.y, 0u - (uint32_t)m.z,
+                           __float_as_uint(rp.y)};
+            kf[k] = KForce{(float)m.x, (float)m.y, (float)m.z, rp.x};
         }
         __syncthreads();
 #pragma unroll 4
         for (int k = sub; k < cnt; k += SPLIT) {
             const KPhase a = kp[k];
             const KForce f = kf[k];
-            const float B = kb[k];
 #pragma unroll
             for (int q = 0; q < PT; ++q) {
-                const uint32_t phs = a.mx * p[q].x + a.my * p[q].y + a.mz * p[q].z;
-                const float th = (float)(int32_t)phs * kTwoPiOver2p32;
-                float sn, cs;
-                __sincosf(th, &sn, &cs);
-                const float g = fmaf(cs, f.A, -sn * B);     // Im(e^{-i th} rho) * coef
+                const uint32_t d = a.phi + a.nmx * p[q].x + a.nmy * p[q].y + a.nmz * p[q].z;
+                const float t = (float)(int32_t)d * kTwoPiOver2p32;          // phi - theta
+                float g;                                    // Im(e^{-i theta} rho) * coef
+                if constexpr (PHI) {
+                    float sn, cs;
+                    __sincosf(t, &sn, &cs);
+                    g = f.R * sn;
+                    ph[q] = fmaf(f.R, cs, ph[q]);           // Re(e^{-i theta} rho) * coef
+                } else {
+                    g = f.R * __sinf(t);
+                }
                 fx[q] = fmaf(g, f.mx, fx[q]);
                 fy[q] = fmaf(g, f.my, fy[q]);
                 fz[q] = fmaf(g, f.mz, fz[q]);
-                if constexpr (PHI) ph[q] = fmaf(cs, B, fmaf(sn, f.A, ph[q]));   // Re(..) coef
             }
         }
     }
