@@ -15,7 +15,6 @@
 //   T_j = min(floor((c_j / Z) * 2^32), 2^32 - 1) for j < 2M;  T_2M = 2^32
 //   H   = Z,  S = H^3 - 1.
 #include <algorithm>
-#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1631,16 +1630,18 @@ rbe_status rbe_step_host(rbe_handle h, int32_t n, float* pos_q, float* vel, int3
         // polls instead of waiting on the stream.
         const bool signal = h->list && nsteps > 0;
         const uint64_t want = step0 + (uint64_t)nsteps;
-        volatile uint64_t* done = h->h_pin + 2;
-        if (signal) *done = ~want;
+        uint64_t* done = h->h_pin + 2;
+        if (signal) __atomic_store_n(done, ~want, __ATOMIC_RELAXED);
         s = step_impl(h, n, RBE_MIXED, dpos, dvel, nsteps, h->h_pin_dev, nullptr, nullptr,
                       signal ? (unsigned long long*)(h->h_pin_dev + 2) : nullptr);
         if (s != RBE_OK) return s;
         if (signal) {
-            for (unsigned it = 1; *done != want; ++it)
+            // acquire: the outputs and the error word, stored before the word
+            // on the device side, are read after it here
+            bool seen = false;
+            for (unsigned it = 1; !(seen = __atomic_load_n(done, __ATOMIC_ACQUIRE) == want); ++it)
                 if ((it & 1023u) == 0 && cudaStreamQuery(h->stream) != cudaErrorNotReady) break;
-            std::atomic_thread_fence(std::memory_order_acquire);
-            if (*done == want) return report_err(h);
+            if (seen || __atomic_load_n(done, __ATOMIC_ACQUIRE) == want) return report_err(h);
             // the stream ended without the signal: its status decides
         }
         RBE_CUDA(h, cudaMemcpyAsync(h->h_pin + 1, h->d_err, sizeof(int), cudaMemcpyDeviceToHost,
