@@ -377,15 +377,18 @@ rbe_status rbe_probe_peaks(rbe_peaks *out);
  * handle.
  *
  * p: system parameters (box, alpha, P, seed, stream, coulomb_prefactor are
- * used).  pos_q: device float4[n] (x, y, z, q), caller-owned.  F_out: device
- * float4[n] receives the RBE Fourier force (caller's order).  E_out (device,
- * nullable): one double, the Fourier energy including self and background
- * terms.  cuda_stream: a cudaStream_t or NULL.  The k-batch of `step` is the
- * same one rbe_forces draws for the same parameters.
+ * used; sampler must be RBE_SAMPLER_EXACT, the i.i.d. draws of Sec. 3.1, else
+ * RBE_ERR_ARG).  pos_q: device float4[n] (x, y, z, q), caller-owned.  F_out:
+ * device float4[n] receives the RBE Fourier force (caller's order).  E_out
+ * (device, nullable): one double, the Fourier energy including self and
+ * background terms.  n = 0 without E_out returns RBE_OK at once (nothing to
+ * compute).  cuda_stream: a cudaStream_t or NULL.  The k-batch of `step` is
+ * the same one rbe_forces draws for the same parameters.
  *
  * Scratch: a 4 MiB file-scope device array inside librbe, held by every GPU
  * that loads the library until the process exits.  Limits, checked on the host
- * (RBE_ERR_ARG with a message from rbe_last_error(NULL)): 1 <= P <= 1024, a
+ * (RBE_ERR_ARG with a message from rbe_last_error(NULL)): finite box, alpha
+ * and coulomb_prefactor, 1 <= P <= 1024, a
  * sampling table of at most 4096 entries, and n * P small enough that the
  * per-chunk partial sums fit (chunks of up to 65536 particles; e.g. n = 2^20
  * with P = 500 fits).  The first call on each device looks up the array's
@@ -393,7 +396,8 @@ rbe_status rbe_probe_peaks(rbe_peaks *out);
  * first call before any stream capture.  Every call shares the array and
  * overwrites what it reads, so no state carries over between calls, but calls
  * that overlap on the GPU (e.g. on two streams) race on it and must be
- * serialised.  The call synchronises cuda_stream before returning.  It calls
+ * serialised.  The call synchronises cuda_stream (not the device) before
+ * returning; the sampler's error word is read back on that stream.  It calls
  * no cudaMalloc, cudaFree or other allocating routine. */
 rbe_status rbe_fourier_forces_noalloc(const rbe_params *p, int32_t n, const float *pos_q,
                                       uint64_t step, float *F_out, double *E_out,

@@ -119,8 +119,20 @@ def _load():
                                              ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, _D]
         lib.orc_nose_hoover_step.restype = None
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_set_threads.restype = None
+        lib.orc_get_threads.argtypes = []
+        lib.orc_get_threads.restype = ctypes.c_int
         _lib = lib
         return lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's OpenMP loops (n <= 0: all processors); returns
+    the count in effect.  Results do not depend on it (rows are owned whole)."""
+    lib = _load()
+    lib.orc_set_threads(int(n))
+    return int(lib.orc_get_threads())
 
 
 def _dp(a):

@@ -737,3 +737,12 @@ void orc_nose_hoover_step(int N, double *pos, double *vel, const double *F, doub
     }
     state[1] = k2;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Thread count of the OpenMP loops (for timing the oracle on one core and on */
+/* all cores).  Each thread owns whole rows of every outer loop, so results   */
+/* do not depend on this setting.  n <= 0 restores all available processors. */
+/* ------------------------------------------------------------------------- */
+#include <omp.h>
+void orc_set_threads(int n) { omp_set_num_threads(n > 0 ? n : omp_get_num_procs()); }
+int orc_get_threads(void) { return omp_get_max_threads(); }

@@ -122,7 +122,9 @@ k_na_rho(Args a, const float4* __restrict__ pos_q, unsigned char* __restrict__ s
         }
         if (c == 0) ksamp[l] = m;
     }
-    float re = 0.f, im = 0.f;
+    // FP32 sums over one staged pass (at most kStageN terms), carried in FP64
+    // across passes, so that the rounding does not grow with the chunk size
+    double red = 0.0, imd = 0.0;
     double qs = 0.0, q2s = 0.0;
     for (int base = 0; base < count; base += kStageN) {
         const int cnt = min(kStageN, count - base);
@@ -138,6 +140,7 @@ k_na_rho(Args a, const float4* __restrict__ pos_q, unsigned char* __restrict__ s
         }
         __syncthreads();
         if (active) {
+            float re = 0.f, im = 0.f;
             for (int j = 0; j < cnt; ++j) {
                 const uint4 p = sp[j];
                 const uint32_t ph = (uint32_t)m.x * p.x + (uint32_t)m.y * p.y + (uint32_t)m.z * p.z;
@@ -147,9 +150,13 @@ k_na_rho(Args a, const float4* __restrict__ pos_q, unsigned char* __restrict__ s
                 re = fmaf(q, cs, re);
                 im = fmaf(q, sn, im);
             }
+            red += (double)re;
+            imd += (double)im;
         }
     }
-    if (active) part[(size_t)c * a.P + l] = make_float2(re, im);
+    // the chunk's partial, rounded once to FP32 (a relative 2^-24 of the
+    // chunk's sum; the chunks are then added in FP64)
+    if (active) part[(size_t)c * a.P + l] = make_float2((float)red, (float)imd);
     if (blockIdx.y == 0) {
         __shared__ double sq[kThreads], sq2[kThreads];
         sq[threadIdx.x] = qs;
@@ -310,7 +317,14 @@ extern "C" rbe_status rbe_fourier_forces_noalloc(const rbe_params* p, int32_t n,
     using namespace rbe::noalloc;
     if (!p) return na_fail(RBE_ERR_ARG, "params is NULL");
     if (n < 0 || (n > 0 && (!pos_q || !F_out))) return na_fail(RBE_ERR_ARG, "bad n or null buffer");
-    if (!(p->box > 0.0) || !(p->alpha > 0.0)) return na_fail(RBE_ERR_ARG, "box and alpha must be > 0");
+    if (!(p->box > 0.0) || !(p->alpha > 0.0) || !std::isfinite(p->box) ||
+        !std::isfinite(p->alpha))
+        return na_fail(RBE_ERR_ARG, "box and alpha must be finite and > 0");
+    if (!std::isfinite(p->coulomb_prefactor))
+        return na_fail(RBE_ERR_ARG, "coulomb_prefactor must be finite");
+    if (p->sampler != RBE_SAMPLER_EXACT)
+        return na_fail(RBE_ERR_ARG, "the no-allocation entry point draws the k-batch with the "
+                                    "exact sampler only (sampler must be RBE_SAMPLER_EXACT)");
     if (p->P < 1 || p->P > kMaxP) return na_fail(RBE_ERR_ARG, "P must be in [1, 1024] for the no-allocation entry point");
     const double L = p->box;
     const int M = (int)std::ceil(std::sqrt(p->alpha * L * L * (64.0 * std::log(2.0))) / M_PI);
@@ -328,6 +342,7 @@ extern "C" rbe_status rbe_fourier_forces_noalloc(const rbe_params* p, int32_t n,
         chunk <<= 1;
     }
     const Layout Lay = layout(p->P, nchunk);
+    if (n == 0 && !E_out) return RBE_OK;              // nothing to compute
     // sampling table: the same FP64 arithmetic as rbe_create, on the stack
     uint64_t table[kMaxTable];
     double Z = 0.0;
@@ -390,11 +405,13 @@ extern "C" rbe_status rbe_fourier_forces_noalloc(const rbe_params* p, int32_t n,
     if (E_out) k_na_energy<<<1, 256, 0, st>>>(a, scratch, E_out);
     e = cudaGetLastError();
     if (e != cudaSuccess) return na_fail(RBE_ERR_CUDA, cudaGetErrorString(e));
-    // The table copy reads host stack memory: make sure it has been consumed.
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return na_fail(RBE_ERR_CUDA, cudaGetErrorString(e));
+    // The sampler's error word comes back on the caller's stream, behind the
+    // kernels; one synchronisation of that stream (not of the device) then
+    // covers it and the table copy, which reads host stack memory.
     int h_err = 0;
-    e = cudaMemcpy(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost);
+    e = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return na_fail(RBE_ERR_CUDA, cudaGetErrorString(e));
+    e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return na_fail(RBE_ERR_CUDA, cudaGetErrorString(e));
     if (h_err & rbe::kErrSampler)
         return na_fail(RBE_ERR_SAMPLER, "a k-sample drew (0,0,0) on 32 attempts in a row");

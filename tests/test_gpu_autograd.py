@@ -12,7 +12,7 @@ charges, no LJ).
 import numpy as np
 import pytest
 
-from gpu_util import energy_rel, need_gpu, oracle_eval, rel_rms
+from gpu_util import assert_per_particle, energy_rel, need_gpu, oracle_eval, rel_rms
 from paper_2010_01559_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -47,6 +47,8 @@ def test_autograd_matches_oracle_gradients(rbe, n_mol, sub):
     print("water", n_mol, "dE/dr vs -F", e_f, "dE/dq vs phi", e_phi)
     assert e_f <= TOL_MIXED
     assert e_phi <= TOL_MIXED
+    assert_per_particle(-gpos, ref["F"], "dE/dr")
+    assert_per_particle(gq, ref["phi"], "dE/dq")
     if sub is None:
         assert energy_rel([E.item()] + list(ref["E"][1:]), ref["E"]) <= 1e-6
 

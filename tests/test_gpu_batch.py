@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import energy_rel, need_gpu, oracle_eval, rel_rms
+from gpu_util import assert_per_particle, energy_rel, need_gpu, oracle_eval, rel_rms
 from paper_2010_01559_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -72,6 +72,7 @@ def test_batch_matches_oracle_smallest_median_largest(rbe, replicas):
         err = rel_rms(Fr, ref["F"])
         print("replica", r, "N", w.n, "rel-RMS", err)
         assert err <= TOL_MIXED, (r, w.n, err)
+        assert_per_particle(Fr, ref["F"], ("replica", r))
         if sub is None:
             assert energy_rel(E[r], ref["E"]) <= 1e-6
 

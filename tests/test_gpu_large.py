@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import need_gpu, oracle_eval, rel_rms
+from gpu_util import assert_per_particle, need_gpu, oracle_eval, rel_rms
 from paper_2010_01559_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -49,11 +49,14 @@ def test_large_system_sampled_parity(rbe, large):
         print("N=2^20 sampled rel-RMS", name, err)
         assert err <= TOL_MIXED
     assert rel_rms(phi.cpu().numpy()[sub], ref["phi"]) <= TOL_MIXED
+    assert_per_particle(Fs, ref["F"], "F sampled")
+    assert_per_particle(phi.cpu().numpy()[sub], ref["phi"], "phi sampled")
     F64, E64, _ = h.forces_f64(x.double().contiguous(), step)
     err_all = rel_rms(Fs, F64[:, :3].cpu().numpy()[sub])
     err_full = (F[:, :3].double() - F64[:, :3]).norm().item() / F64[:, :3].norm().item()
     print("mixed vs FP64 GPU over all 2^20 particles", err_full)
     assert err_full <= TOL_MIXED and err_all <= TOL_MIXED
+    assert_per_particle(F[:, :3].cpu().numpy(), F64[:, :3].cpu().numpy(), "mixed vs FP64, all")
     assert abs(E[0, 0].item() - E64[0, 0].item()) <= 1e-6 * E64[0, 1:].abs().sum().item()
 
 

@@ -1,0 +1,152 @@
+"""The kernels an MD step launches, in every launch shape, against the oracle.
+
+An MD step on the mixed path runs the Fourier force in its step mode (one sine
+per particle-wave-vector pair, no dE/dq, closing thermostat update) and the
+real-space pass over the neighbour list in its step mode (real-space force
+only, handed to the closing update).  Forces calls run other instantiations
+of both kernels, so these tests take each step's total force out through
+rbe_step_ex and compare it with
+
+* the oracle's estimator (Eq. rbmapprox plus the real-space and LJ terms of
+  Eq. force and Eq. Ljpotential) at the positions the step started from and
+  the step's own k-batch: rel-RMS <= 1e-5 and a per-particle bound;
+* a forces call of a handle without a neighbour list (the cell scan) at the
+  same positions and step: the Fourier part is computed from the same
+  fixed-point structure factors, so the two differ by FP32 summation order
+  only (per particle <= 1e-5 + 1e-6 |F|, while one pair within r_c missing
+  from the list moves a force by ~1e-4).
+
+At N = 8001 every lane split of both kernels runs (1, 2, 4, 8 threads per
+particle; 1 means two particles per thread in the Fourier force); at N = 2^20
+the launch shapes the autotuner picks for the benchmark, and the two list
+splits it chooses between.
+"""
+import copy
+
+import numpy as np
+import pytest
+
+from gpu_util import assert_per_particle, need_gpu, oracle_eval, rel_rms
+from paper_2010_01559_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+TOL_MIXED = 1e-5
+
+
+@pytest.fixture(scope="module")
+def rbe():
+    need_gpu()
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2010_01559_gb300 as rbe
+    return rbe
+
+
+def _state(wl, torch):
+    pos = torch.from_numpy(wl.pos_q()).cuda().contiguous()
+    vel = torch.zeros((wl.n, 4), dtype=torch.float32, device="cuda")
+    vel[:, :3] = torch.from_numpy(wl.vel).cuda()
+    return pos, vel
+
+
+def _no_list(sp):
+    sp = copy.copy(sp)
+    sp.skin = -1.0
+    return sp
+
+
+def _check_same(F_step, F_cell, what):
+    a = F_step[:, :3].cpu().numpy().astype(np.float64)
+    b = F_cell[:, :3].cpu().numpy().astype(np.float64)
+    dev = np.linalg.norm(a - b, axis=1)
+    bound = 1e-5 + 1e-6 * np.linalg.norm(b, axis=1)
+    worst = int(np.argmax(dev / bound))
+    assert np.all(dev <= bound), (what, worst, dev[worst], bound[worst])
+    return float(dev.max())
+
+
+def _step_force(h, pos, vel, step, torch):
+    """One MD step; returns (positions it started from, its total force, step index)."""
+    before = pos.clone()
+    k = int(step.item())
+    F = torch.zeros_like(pos)
+    h.step(pos, vel, 1, step, F_out=F)
+    h.sync()
+    return before, F, k
+
+
+@pytest.mark.parametrize("force_split", [1, 2, 4, 8])
+@pytest.mark.parametrize("list_split", [1, 2, 4, 8])
+def test_md_step_kernels_every_split_n8001(rbe, force_split, list_split):
+    import torch
+    wl = workloads.config_2to1_mixed()
+    h = rbe.RBE(rbe.params_from(wl.params, n_max=wl.n))
+    h.set_tuning(128, force_split, 3, 0, list_split)
+    h.set_graph(True)
+    hc = rbe.RBE(rbe.params_from(_no_list(wl.params), n_max=wl.n))
+    pos, vel = _state(wl, torch)
+    step = torch.zeros(1, dtype=torch.int64, device="cuda")
+    # step 0 builds the list (the pass after the rebuild), step 3 walks the
+    # standing list (the pass launched right after prep)
+    checked = []
+    for s in range(4):
+        before, F, k = _step_force(h, pos, vel, step, torch)
+        if s not in (0, 3):
+            continue
+        w2 = copy.copy(wl)
+        w2.pos = before[:, :3].cpu().numpy()
+        ref = oracle_eval(w2, k)
+        err = rel_rms(F[:, :3].cpu().numpy(), ref["F"])
+        assert err <= TOL_MIXED, (force_split, list_split, k, err)
+        assert_per_particle(F[:, :3].cpu().numpy(), ref["F"], (force_split, list_split, k))
+        Fc, _, _ = hc.forces(before, k, energy=False)
+        torch.cuda.synchronize()
+        _check_same(F, Fc, (force_split, list_split, k))
+        checked.append((k, err))
+    assert h.get_tuning()[1] == force_split and h.get_tuning()[4] == list_split
+    print("force_split", force_split, "list_split", list_split, checked, h.list_stats())
+    h.close()
+    hc.close()
+
+
+@pytest.fixture(scope="module")
+def large():
+    return workloads.config_large()
+
+
+def test_md_step_kernels_at_2p20_in_the_benchmark_launch_shapes(rbe, large):
+    """N = 2^20, P = 500: the autotuned shapes (as the benchmark picks them),
+    then list splits 1 and 2 with one Fourier-force thread per two particles;
+    each step's force against the oracle on 1024 evenly spaced particles and
+    against the cell scan over all 2^20."""
+    import torch
+    wl = large
+    h = rbe.RBE(rbe.params_from(wl.params, n_max=wl.n))
+    hc = rbe.RBE(rbe.params_from(_no_list(wl.params), n_max=wl.n))
+    pos, vel = _state(wl, torch)
+    tuned = h.autotune(pos)
+    h.set_graph(True)
+    step = torch.zeros(1, dtype=torch.int64, device="cuda")
+    h.step(pos, vel, 2, step)
+    sub = np.linspace(0, wl.n - 1, 1024).astype(int)
+    shapes = [tuple(tuned), (tuned[0], 1, tuned[2], tuned[3], 2),
+              (tuned[0], 1, tuned[2], tuned[3], 1)]
+    for shape in shapes:
+        h.set_tuning(*shape)
+        h.step(pos, vel, 1, step)             # the list is rebuilt after a tuning change
+        before, F, k = _step_force(h, pos, vel, step, torch)
+        assert h.get_tuning() == shape
+        w2 = copy.copy(wl)
+        w2.pos = before[:, :3].cpu().numpy()
+        ref = oracle_eval(w2, k, sub=sub)
+        Fs = F[:, :3].cpu().numpy()[sub]
+        err = rel_rms(Fs, ref["F"])
+        print("2^20 step", k, "shape", shape, "rel-RMS vs oracle (1024 sampled)", err)
+        assert err <= TOL_MIXED, (shape, err)
+        assert_per_particle(Fs, ref["F"], shape)
+        Fc, _, _ = hc.forces(before, k, energy=False)
+        torch.cuda.synchronize()
+        worst = _check_same(F, Fc, shape)
+        print("  largest |dF| against the cell scan over all 2^20:", worst)
+    h.close()
+    hc.close()

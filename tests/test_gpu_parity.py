@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import energy_rel, need_gpu, oracle_eval, rel_rms
+from gpu_util import assert_per_particle, energy_rel, need_gpu, oracle_eval, rel_rms
 from paper_2010_01559_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -135,6 +135,7 @@ def test_one_cell_box_all_pairs_match_oracle(rbe):
     assert rel_rms(phi64.cpu().numpy(), ref["phi"]) <= TOL_F64
     F, E, phi = h.forces(_dev(wl), step, phi=True)          # over the neighbour list
     assert rel_rms(F[:, :3].cpu().numpy(), ref["F"]) <= TOL_MIXED
+    assert_per_particle(F[:, :3].cpu().numpy(), ref["F"], "one cell, list")
     assert energy_rel(E.cpu().numpy()[0], ref["E"]) <= TOL_E_MIXED
     assert rel_rms(phi.cpu().numpy(), ref["phi"]) <= TOL_MIXED
     hc = _handle(rbe, wl, path="cells")
@@ -144,6 +145,8 @@ def test_one_cell_box_all_pairs_match_oracle(rbe):
         assert rel_rms(F[:, :3].cpu().numpy(), ref["F"]) <= TOL_MIXED, R
         assert energy_rel(E.cpu().numpy()[0], ref["E"]) <= TOL_E_MIXED, R
         assert rel_rms(phi.cpu().numpy(), ref["phi"]) <= TOL_MIXED, R
+        assert_per_particle(F[:, :3].cpu().numpy(), ref["F"], ("F", R))
+        assert_per_particle(phi.cpu().numpy(), ref["phi"], ("phi", R))
 
 
 # ------------------------------------------------------------------ mixed path
@@ -159,12 +162,14 @@ def test_mixed_path_matches_oracle_per_part(rbe, cfg, path, request):
     for mask, name in ((1, "F_fourier"), (2, "F_real"), (4, "F_lj"), (7, "F")):
         F, E, phi = h.forces(x, step, parts=mask, phi=True)
         errs[name] = rel_rms(F[:, :3].cpu().numpy(), ref[name])
+        assert_per_particle(F[:, :3].cpu().numpy(), ref[name], (cfg, path, name))
     print(cfg, errs)
     for name, e in errs.items():
         assert e <= TOL_MIXED, (name, e)
     E = E.cpu().numpy()[0]
     assert energy_rel(E, ref["E"]) <= TOL_E_MIXED
     assert rel_rms(phi.cpu().numpy(), ref["phi"]) <= TOL_MIXED
+    assert_per_particle(phi.cpu().numpy(), ref["phi"], (cfg, path, "phi"))
 
 
 def test_mixed_vs_fp64_gpu(rbe, c2):
@@ -172,6 +177,7 @@ def test_mixed_vs_fp64_gpu(rbe, c2):
     F, E, _ = h.forces(_dev(c2), 3)
     F64, E64, _ = h.forces_f64(_dev(c2, "float64"), 3)
     assert rel_rms(F[:, :3].cpu().numpy(), F64[:, :3].cpu().numpy()) <= TOL_MIXED
+    assert_per_particle(F[:, :3].cpu().numpy(), F64[:, :3].cpu().numpy(), "mixed vs FP64")
     assert abs(E[0, 0].item() - E64[0, 0].item()) <= TOL_E_MIXED * E64[0, 1:].abs().sum().item()
 
 
@@ -182,6 +188,8 @@ def test_water_like_no_lj_fp32_charges(rbe):
     F, E, phi = h.forces(_dev(wl), 2, phi=True)
     assert rel_rms(F[:, :3].cpu().numpy(), ref["F"]) <= TOL_MIXED
     assert rel_rms(phi.cpu().numpy(), ref["phi"]) <= TOL_MIXED
+    assert_per_particle(F[:, :3].cpu().numpy(), ref["F"], "water F")
+    assert_per_particle(phi.cpu().numpy(), ref["phi"], "water phi")
     F64, E64, phi64 = h.forces_f64(_dev(wl, "float64"), 2, phi=True)
     assert rel_rms(F64[:, :3].cpu().numpy(), ref["F"]) <= TOL_F64
     assert energy_rel(E64.cpu().numpy()[0], ref["E"]) <= TOL_F64
@@ -197,6 +205,7 @@ def test_ragged_sizes(rbe, n, P):
     F, E, _ = h.forces(_dev(wl), 1)
     F64, E64, _ = h.forces_f64(_dev(wl, "float64"), 1)
     assert rel_rms(F[:, :3].cpu().numpy(), ref["F"]) <= TOL_MIXED
+    assert_per_particle(F[:, :3].cpu().numpy(), ref["F"], (n, P))
     assert rel_rms(F64[:, :3].cpu().numpy(), ref["F"]) <= TOL_F64
     assert energy_rel(E64.cpu().numpy()[0], ref["E"]) <= TOL_F64
 
@@ -224,6 +233,7 @@ def test_positions_outside_box_are_wrapped(rbe, c1):
     wrapped = np.mod(y[:, :3].cpu().numpy().astype(np.float64), 25.0)
     ref = oracle_eval(c1, 5, pos=wrapped)
     assert rel_rms(F1[:, :3].cpu().numpy(), ref["F"]) <= TOL_MIXED
+    assert_per_particle(F1[:, :3].cpu().numpy(), ref["F"], "wrapped")
     x64 = _dev(c1, "float64")
     y64 = x64.clone()
     y64[:, :3] += shift.double()
@@ -273,6 +283,7 @@ def test_tuning_does_not_change_results_beyond_rounding(rbe, c2):
         h.set_tuning(chunk, split, rsplit)
         F, E, phi = h.forces(x, 6, phi=True)
         assert rel_rms(F[:, :3].cpu().numpy(), ref["F"]) <= TOL_MIXED, (chunk, split, rsplit)
+        assert_per_particle(F[:, :3].cpu().numpy(), ref["F"], (chunk, split, rsplit))
         assert energy_rel(E.cpu().numpy()[0], ref["E"]) <= TOL_E_MIXED
         if chunk:
             assert h.get_tuning()[:3] == (chunk, split, rsplit)
@@ -280,6 +291,7 @@ def test_tuning_does_not_change_results_beyond_rounding(rbe, c2):
         h.set_tuning(128, 2, 3, 0, ls)
         F, E, _ = h.forces(x, 6)
         assert rel_rms(F[:, :3].cpu().numpy(), ref["F"]) <= TOL_MIXED, ls
+        assert_per_particle(F[:, :3].cpu().numpy(), ref["F"], ("list_split", ls))
         assert energy_rel(E.cpu().numpy()[0], ref["E"]) <= TOL_E_MIXED
         assert h.get_tuning()[4] == ls
     hc = _handle(rbe, c2, path="cells")
@@ -287,6 +299,7 @@ def test_tuning_does_not_change_results_beyond_rounding(rbe, c2):
         hc.set_tuning(128, 2, 3, seg)
         F, E, _ = hc.forces(x, 6)
         assert rel_rms(F[:, :3].cpu().numpy(), ref["F"]) <= TOL_MIXED, seg
+        assert_per_particle(F[:, :3].cpu().numpy(), ref["F"], ("seg", seg))
         assert energy_rel(E.cpu().numpy()[0], ref["E"]) <= TOL_E_MIXED
         assert hc.get_tuning()[3] == seg
     hc.close()
