@@ -89,18 +89,36 @@ def _close_pairs(pos: np.ndarray, L: float, dmin: float) -> np.ndarray:
     return tree.query_pairs(dmin, output_type="ndarray")
 
 
+def _close_pairs_with(pos: np.ndarray, L: float, dmin: float, idx: np.ndarray) -> np.ndarray:
+    """The pairs (i < j) closer than dmin that involve a particle of idx."""
+    from scipy.spatial import cKDTree
+    tree = cKDTree(pos.astype(np.float64), boxsize=L)
+    nb = tree.query_ball_point(pos[idx].astype(np.float64), dmin, return_sorted=False)
+    out = set()
+    for a, lst in zip(idx.tolist(), nb):
+        for b in lst:
+            if b != a:
+                out.add((min(a, b), max(a, b)))
+    return np.array(sorted(out), dtype=np.int64).reshape(-1, 2)
+
+
 def place_uniform(n: int, L: float, min_sep: float, rng: np.random.Generator,
                   max_rounds: int = 1000) -> np.ndarray:
-    """n points in [0,L)^3 with all minimum-image separations >= min_sep."""
+    """n points in [0,L)^3 with all minimum-image separations >= min_sep.
+
+    Each round re-draws the higher-indexed particle of every close pair.  Only
+    pairs that involve a particle re-drawn in the previous round can be close
+    after the first round, so later rounds look only at those."""
     pos = _to_box32(rng.uniform(0.0, L, size=(n, 3)), L)
     if n < 2 or min_sep <= 0:
         return pos
+    pairs = _close_pairs(pos, L, min_sep)
     for _ in range(max_rounds):
-        pairs = _close_pairs(pos, L, min_sep)
         if len(pairs) == 0:
             return pos
         redo = np.unique(pairs[:, 1])
         pos[redo] = _to_box32(rng.uniform(0.0, L, size=(len(redo), 3)), L)
+        pairs = _close_pairs_with(pos, L, min_sep, redo)
     raise RuntimeError("placement did not converge; density too high for min_sep")
 
 
