@@ -1736,14 +1736,22 @@ rbe_status rbe_autotune(rbe_handle h, int32_t n, const float* pos_q, rbe_tuning*
         if (t < best) { best = t; best_chunk = c; }
     }
     h->rho_chunk = best_chunk;
-    // Fourier-force split
+    // Fourier-force split, timed in the form the handle's MD steps run it
+    // (with a neighbour list: the step variant, which adds the real-space
+    // force and takes one sine per pair; without: the forces variant)
     best = 1e30f;
     int best_split = 1;
     for (int sp = 1; sp <= 8 && s == RBE_OK; sp <<= 1) {
         h->force_split = sp;
         if ((s = prepare(h, n)) != RBE_OK) break;
         enqueue_eval(h, h->stream, a);
-        const float t = time_kernel(h, e0, e1, [&] { launch_force(h, h->stream, true); });
+        MdOut md{};
+        if (h->list) {
+            md.freal = h->d_freal;            // contents irrelevant: only timed
+            md.F_out = h->d_stage_F;
+            md.cur_step = h->d_cur_step;
+        }
+        const float t = time_kernel(h, e0, e1, [&] { launch_force(h, h->stream, true, md); });
         if (t < best) { best = t; best_split = sp; }
     }
     h->force_split = best_split;

@@ -174,12 +174,13 @@ k_rho_f64(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
 
 // ----------------------------------------------------------------- force (mixed)
 // Shared-memory record per wave vector: -m and phi (the phase of the
-// coefficient, 2^-32 turns) as integers, and m (direction) with the magnitude
-// R as floats.  phi - m.s is exact in 32-bit arithmetic, so one sine per
-// (particle, k) pair gives Im(e^{-i k.r} rho) coef = R sin(phi - theta) (and
-// the cosine, in the same SFU pair, the dE/dq term R cos(phi - theta)).
+// coefficient, 2^-32 turns) as integers, and R m (the direction scaled by the
+// coefficient's magnitude) with R as floats.  phi - m.s is exact in 32-bit
+// arithmetic, so one sine per (particle, k) pair gives the force term
+// R m sin(phi - theta) = m coef Im(e^{-i k.r} rho) (and the cosine, in the
+// same SFU pair, the dE/dq term R cos(phi - theta)).
 struct KPhase { uint32_t nmx, nmy, nmz, phi; };
-struct KForce { float mx, my, mz, R; };
+struct KForce { float rmx, rmy, rmz, R; };
 
 // SPLIT threads per particle (each a 1/SPLIT share of the wave vectors), or
 // with SPLIT = 1 PT = 2 particles per thread, which share each wave vector's
@@ -244,7 +245,7 @@ k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
             const float2 rp = kab[S.off_k + base + k];
             kp[k] = KPhase{0u - (uint32_t)m.x, 0u - (uint32_t)m.y, 0u - (uint32_t)m.z,
                            __float_as_uint(rp.y)};
-            kf[k] = KForce{(float)m.x, (float)m.y, (float)m.z, rp.x};
+            kf[k] = KForce{rp.x * (float)m.x, rp.x * (float)m.y, rp.x * (float)m.z, rp.x};
         }
         __syncthreads();
 #pragma unroll 4
@@ -255,18 +256,17 @@ k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
             for (int q = 0; q < PT; ++q) {
                 const uint32_t d = a.phi + a.nmx * p[q].x + a.nmy * p[q].y + a.nmz * p[q].z;
                 const float t = (float)(int32_t)d * kTwoPiOver2p32;          // phi - theta
-                float g;                                    // Im(e^{-i theta} rho) * coef
+                float sn;                                   // Im(e^{-i theta} rho) coef / R
                 if constexpr (PHI) {
-                    float sn, cs;
+                    float cs;
                     __sincosf(t, &sn, &cs);
-                    g = f.R * sn;
                     ph[q] = fmaf(f.R, cs, ph[q]);           // Re(e^{-i theta} rho) * coef
                 } else {
-                    g = f.R * __sinf(t);
+                    sn = __sinf(t);
                 }
-                fx[q] = fmaf(g, f.mx, fx[q]);
-                fy[q] = fmaf(g, f.my, fy[q]);
-                fz[q] = fmaf(g, f.mz, fz[q]);
+                fx[q] = fmaf(sn, f.rmx, fx[q]);
+                fy[q] = fmaf(sn, f.rmy, fy[q]);
+                fz[q] = fmaf(sn, f.rmz, fz[q]);
             }
         }
     }
