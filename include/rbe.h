@@ -39,8 +39,9 @@
  *   - No exception crosses the ABI; every call returns an rbe_status.  Argument
  *     errors are detected on the host before anything is enqueued.  CUDA errors
  *     are reported as RBE_ERR_CUDA.  Device-side conditions (a k-sample that
- *     exhausted its 32 attempts) are latched in a device word and reported by
- *     the next rbe_sync (or *_host call).  rbe_last_error(h) gives a message.
+ *     exhausted its 32 attempts, an overflowing neighbour list, a NaN or
+ *     infinite input) are latched in a device word and reported by the next
+ *     rbe_sync (or *_host call).  rbe_last_error(h) gives a message.
  *   - Units are the caller's; coulomb_prefactor multiplies every Coulomb term
  *     (1 in the reduced units of Sec. 4.1, the Bjerrum length in Sec. 4.2).
  */
@@ -61,13 +62,18 @@ typedef enum {
     RBE_ERR_CUDA = 2,       /* a CUDA runtime call failed                              */
     RBE_ERR_OOM = 3,        /* device allocation failed                                */
     RBE_ERR_SAMPLER = 4,    /* a k-sample hit (0,0,0) on 32 attempts in a row           */
-    RBE_ERR_TIMEOUT = 5,    /* reserved: a bounded device wait gave up                  */
-    RBE_ERR_NONFINITE = 6,  /* reserved: non-finite input detected                      */
+    RBE_ERR_TIMEOUT = 5,    /* a host wait ran past the handle's wait limit
+                               (rbe_set_wait_limit); the work is still queued          */
+    RBE_ERR_NONFINITE = 6,  /* a position or charge of an input was NaN or infinite
+                               (latched on the device, reported at the next sync)     */
     RBE_ERR_STATE = 7,      /* call not valid for this handle (e.g. wrong n for a batch) */
-    RBE_ERR_LIST = 8        /* a particle had more neighbours within r_c + skin than the
+    RBE_ERR_LIST = 8,       /* a particle had more neighbours within r_c + skin than the
                                list holds (a much denser region than the mean density):
                                the steps since the last rbe_sync missed pairs; run with
                                skin < 0 (no list) or a smaller skin */
+    RBE_ERR_BOUNDS = 9      /* only in the bounds-checked build (RBE_CHECK_BOUNDS): an
+                               index computed on the device fell outside its array; the
+                               access was skipped and the results are not meaningful */
 } rbe_status;
 
 enum { RBE_FP64 = 0, RBE_MIXED = 1 };
@@ -272,8 +278,19 @@ rbe_status rbe_step_host(rbe_handle h, int32_t n, float *pos_q, float *vel, int3
                          uint64_t step0);
 
 /* Synchronise h's stream and report latched device conditions
- * (RBE_ERR_SAMPLER) and asynchronous CUDA errors.  Clears the latch. */
+ * (RBE_ERR_SAMPLER, RBE_ERR_LIST, RBE_ERR_NONFINITE, RBE_ERR_BOUNDS) and
+ * asynchronous CUDA errors.  Clears the latch. */
 rbe_status rbe_sync(rbe_handle h);
+
+/* Failure detection on the host side: the longest time, in seconds, that a
+ * call of h waiting for the GPU (rbe_sync, rbe_forces_host, rbe_step_host)
+ * may wait (0, the default: no limit).  When it passes, the call returns
+ * RBE_ERR_TIMEOUT at once; the work stays queued on h's stream and the
+ * caller must call rbe_sync (which waits again, under the same limit) before
+ * reading or freeing the buffers of the call.  Not an RBE operation: it lets
+ * an MD driver notice a GPU that stopped answering without blocking forever.
+ * Errors: RBE_ERR_ARG for a null handle or a negative or non-finite limit. */
+rbe_status rbe_set_wait_limit(rbe_handle h, double seconds);
 
 /* Launch shapes of the per-particle kernels (0 = automatic for every field). */
 typedef struct {
@@ -397,7 +414,8 @@ rbe_status rbe_probe_peaks(rbe_peaks *out);
  * overwrites what it reads, so no state carries over between calls, but calls
  * that overlap on the GPU (e.g. on two streams) race on it and must be
  * serialised.  The call synchronises cuda_stream (not the device) before
- * returning; the sampler's error word is read back on that stream.  It calls
+ * returning; the error word (RBE_ERR_SAMPLER, RBE_ERR_NONFINITE for a NaN or
+ * infinite input) is read back on that stream.  It calls
  * no cudaMalloc, cudaFree or other allocating routine. */
 rbe_status rbe_fourier_forces_noalloc(const rbe_params *p, int32_t n, const float *pos_q,
                                       uint64_t step, float *F_out, double *E_out,

@@ -108,6 +108,12 @@ class _HandleBase:
     def sync(self):
         capi.check(self.lib.rbe_sync(self._h), self._h)
 
+    def set_wait_limit(self, seconds):
+        """Longest host wait for the GPU in seconds (0: none); past it a call
+        raises RBEError(RBE_ERR_TIMEOUT) with the work still queued
+        (``rbe_set_wait_limit``)."""
+        capi.check(self.lib.rbe_set_wait_limit(self._h, float(seconds)), self._h)
+
     def set_tuning(self, rho_chunk=0, force_split=0, real_split=0, real_seg=0, list_split=0):
         t = capi.rbe_tuning(rho_chunk, force_split, real_split, real_seg, list_split)
         capi.check(self.lib.rbe_set_tuning(self._h, ctypes.byref(t)), self._h)

@@ -4,6 +4,13 @@ Each .cu file under csrc/ is compiled in parallel with nvcc into an object, and
 the objects are linked into ``_build/librbe.so`` next to this file.  Host code
 is compiled without floating-point contraction so that the FP64 sampling
 table is reproducible bit for bit.
+
+``build(check_bounds=True)`` makes the bounds-checked variant
+``_build/checked/librbe.so`` (compiled with -DRBE_CHECK_BOUNDS): every index the
+kernels compute from data (cell ids, sorted slots, neighbour-list entries,
+caller indices) is tested against its array before the access; a failed test
+skips the access and latches RBE_ERR_BOUNDS, reported by the next rbe_sync.
+It is a debugging aid for the tests, not the product's library.
 """
 from __future__ import annotations
 
@@ -42,22 +49,30 @@ def _deps():
                                                                   os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+CHECKED_LIB = os.path.join(BUILD, "checked", "librbe.so")
+
+
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          check_bounds: bool = False) -> str:
+    lib = CHECKED_LIB if check_bounds else LIB
+    if not force and up_to_date(lib):
+        return lib
+    out_dir = os.path.dirname(lib)
+    os.makedirs(out_dir, exist_ok=True)
     exe = nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    if check_bounds:
+        extra += ["-DRBE_CHECK_BOUNDS"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [exe] + ARCH + NVCC_FLAGS + extra + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -70,13 +85,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         for _, log in results:
             if log:
                 print(log)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [exe] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

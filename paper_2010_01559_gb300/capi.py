@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "librbe.so")
 
 RBE_OK, RBE_ERR_ARG, RBE_ERR_CUDA, RBE_ERR_OOM = 0, 1, 2, 3
 RBE_ERR_SAMPLER, RBE_ERR_TIMEOUT, RBE_ERR_NONFINITE, RBE_ERR_STATE, RBE_ERR_LIST = 4, 5, 6, 7, 8
+RBE_ERR_BOUNDS = 9
 RBE_FP64, RBE_MIXED = 0, 1
 RBE_PART_FOURIER, RBE_PART_REAL, RBE_PART_LJ, RBE_PART_ALL = 1, 2, 4, 7
 RBE_SAMPLER_EXACT, RBE_SAMPLER_MH = 0, 1
@@ -23,7 +24,7 @@ RBE_THERMO_LANGEVIN, RBE_THERMO_ANDERSEN, RBE_THERMO_NOSE_HOOVER = 0, 1, 2
 
 STATUS_NAMES = {0: "RBE_OK", 1: "RBE_ERR_ARG", 2: "RBE_ERR_CUDA", 3: "RBE_ERR_OOM",
                 4: "RBE_ERR_SAMPLER", 5: "RBE_ERR_TIMEOUT", 6: "RBE_ERR_NONFINITE",
-                7: "RBE_ERR_STATE", 8: "RBE_ERR_LIST"}
+                7: "RBE_ERR_STATE", 8: "RBE_ERR_LIST", 9: "RBE_ERR_BOUNDS"}
 
 
 class rbe_params(ctypes.Structure):
@@ -81,6 +82,7 @@ _SIGS = {
     "rbe_forces_host": ([_H, ctypes.c_int32, _P, ctypes.c_uint64, _P, _P], ctypes.c_int),
     "rbe_step_host": ([_H, ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_uint64], ctypes.c_int),
     "rbe_sync": ([_H], ctypes.c_int),
+    "rbe_set_wait_limit": ([_H, ctypes.c_double], ctypes.c_int),
     "rbe_set_tuning": ([_H, ctypes.POINTER(rbe_tuning)], ctypes.c_int),
     "rbe_get_tuning": ([_H, ctypes.POINTER(rbe_tuning)], ctypes.c_int),
     "rbe_autotune": ([_H, ctypes.c_int32, _P, ctypes.POINTER(rbe_tuning)], ctypes.c_int),

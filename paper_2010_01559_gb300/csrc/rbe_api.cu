@@ -15,10 +15,12 @@
 //   T_j = min(floor((c_j / Z) * 2^32), 2^32 - 1) for j < 2M;  T_2M = 2^32
 //   H   = Z,  S = H^3 - 1.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "rbe.h"
@@ -164,6 +166,7 @@ struct rbe_ctx {
     int max_pblk = 0, max_fblk = 0, max_rblk = 0, max_chunks = 0, max_seg = 0;
     size_t max_part = 0;
     bool use_graph = false;
+    double wait_limit = 0.0;                  // seconds a host wait may take (0: no limit)
     std::vector<GraphEntry> graphs;
     std::string err;
     // per-kernel profile
@@ -264,6 +267,13 @@ rbe_status fail(rbe_ctx* h, rbe_status s, const std::string& msg) {
 rbe_status cuda_fail(rbe_ctx* h, cudaError_t e, const char* where) {
     std::string m = std::string(where) + ": " + cudaGetErrorString(e);
     return fail(h, RBE_ERR_CUDA, m);
+}
+
+// A host wait ran out (rbe_set_wait_limit): the work stays queued on the stream.
+rbe_status timeout_fail(rbe_ctx* h) {
+    return fail(h, RBE_ERR_TIMEOUT, "the wait limit passed before the GPU work finished; it is "
+                                    "still queued: call rbe_sync before reading or freeing the "
+                                    "call's buffers");
 }
 
 #define RBE_CUDA(h, call)                                   \
@@ -902,6 +912,7 @@ RealArgs make_real_args(const rbe_ctx* h, int parts) {
     r.fs = h->d_fs;
     r.spos64 = h->d_spos64;
     r.fs64 = h->d_fs64;
+    r.err = h->d_err;
     return r;
 }
 
@@ -983,6 +994,8 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     pa.ksamp = h->d_ksamp;
     pa.kcoef = h->d_kcoef;
     pa.err = h->d_err;
+    pa.ncell = h->ncell;
+    pa.ntot = n;
     pa.nh = (a.md_pos || a.md_pos64) ? h->d_nh : nullptr;
     const bool lst = a.list || a.list_forces;     // the evaluation keeps the list
     if (lst) {
@@ -1030,12 +1043,13 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
                     lflag);
     });
     run(RBE_K_SCATTER, sc, [&] {
-        launch_scatter(sc, n, h->d_cid, h->d_rank, h->d_cell_start, h->d_perm_tmp, lflag);
+        launch_scatter(sc, n, h->d_cid, h->d_rank, h->d_cell_start, h->d_perm_tmp, lflag,
+                       h->d_err);
     });
     run(RBE_K_CELL_ORDER, sc, [&] {
         launch_order(sc, n, h->d_cid, h->d_cell_start, h->d_perm_tmp, mixed ? h->d_fx : nullptr,
                      h->d_spos, mixed ? nullptr : h->d_fx64, h->d_spos64, h->d_perm, lflag,
-                     lst ? h->d_iperm : nullptr);
+                     lst ? h->d_iperm : nullptr, h->d_err);
     });
     if (lst)
         run(RBE_K_LIST_BUILD, sc, [&] {
@@ -1423,6 +1437,27 @@ float time_kernel(rbe_ctx* h, cudaEvent_t e0, cudaEvent_t e1, F&& launch) {
 }  // namespace
 
 namespace {
+// Wait until h's stream has finished its queued work.  Without a wait limit
+// this is cudaStreamSynchronize; with one (rbe_set_wait_limit) the stream is
+// polled until it is idle or the limit has passed, and then the call returns
+// RBE_ERR_TIMEOUT with the work still queued.
+rbe_status wait_stream(rbe_ctx* h, const char* where) {
+    if (!(h->wait_limit > 0.0)) {
+        RBE_CUDA(h, cudaStreamSynchronize(h->stream));
+        return RBE_OK;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = cudaStreamQuery(h->stream);
+        if (e == cudaSuccess) return RBE_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(h, e, where);
+        const double dt =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (dt > h->wait_limit) return timeout_fail(h);
+        std::this_thread::yield();
+    }
+}
+
 // The device error word as read back into the pinned word (after a
 // synchronisation): latched conditions become a status, and the word is cleared.
 rbe_status report_err(rbe_ctx* h) {
@@ -1435,6 +1470,13 @@ rbe_status report_err(rbe_ctx* h) {
         if (err & kErrList)
             return fail(h, RBE_ERR_LIST, "a particle had more neighbours within r_c + skin than "
                                          "the list holds (" + std::to_string(h->list_cap) + ")");
+        if (err & kErrNonfinite)
+            return fail(h, RBE_ERR_NONFINITE, "a position or charge of the input was NaN or "
+                                              "infinite (the results of those calls are not "
+                                              "meaningful)");
+        if (err & kErrBounds)
+            return fail(h, RBE_ERR_BOUNDS, "the bounds-checked build found an index outside its "
+                                           "array (the access was skipped)");
     }
     return finish(h, "rbe_sync");
 }
@@ -1639,8 +1681,15 @@ rbe_status rbe_step_host(rbe_handle h, int32_t n, float* pos_q, float* vel, int3
             // acquire: the outputs and the error word, stored before the word
             // on the device side, are read after it here
             bool seen = false;
-            for (unsigned it = 1; !(seen = __atomic_load_n(done, __ATOMIC_ACQUIRE) == want); ++it)
+            const bool limited = h->wait_limit > 0.0;
+            const auto t0 = std::chrono::steady_clock::now();
+            for (unsigned it = 1; !(seen = __atomic_load_n(done, __ATOMIC_ACQUIRE) == want); ++it) {
                 if ((it & 1023u) == 0 && cudaStreamQuery(h->stream) != cudaErrorNotReady) break;
+                if (limited && (it & 63u) == 0 &&
+                    std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() >
+                        h->wait_limit)
+                    return timeout_fail(h);
+            }
             if (seen || __atomic_load_n(done, __ATOMIC_ACQUIRE) == want) return report_err(h);
             // the stream ended without the signal: its status decides
         }
@@ -1653,7 +1702,7 @@ rbe_status rbe_step_host(rbe_handle h, int32_t n, float* pos_q, float* vel, int3
         if (s != RBE_OK) return s;
     }
     // the outputs and the error word are queued: one synchronisation
-    RBE_CUDA(h, cudaStreamSynchronize(h->stream));
+    if ((s = wait_stream(h, "rbe_step_host")) != RBE_OK) return s;
     return report_err(h);
 }
 
@@ -1662,8 +1711,17 @@ rbe_status rbe_sync(rbe_handle h) {
     // the error word follows the queued work in the stream: one synchronisation
     RBE_CUDA(h, cudaMemcpyAsync(h->h_pin + 1, h->d_err, sizeof(int), cudaMemcpyDeviceToHost,
                                 h->stream));
-    RBE_CUDA(h, cudaStreamSynchronize(h->stream));
+    const rbe_status s = wait_stream(h, "rbe_sync");
+    if (s != RBE_OK) return s;
     return report_err(h);
+}
+
+rbe_status rbe_set_wait_limit(rbe_handle h, double seconds) {
+    if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
+    if (!(seconds >= 0.0) || !std::isfinite(seconds))
+        return fail(h, RBE_ERR_ARG, "the wait limit must be a finite number of seconds >= 0");
+    h->wait_limit = seconds;
+    return RBE_OK;
 }
 
 rbe_status rbe_set_tuning(rbe_handle h, const rbe_tuning* t) {

@@ -296,6 +296,11 @@ k_prep_mixed(const __grid_constant__ Work w, const float4* __restrict__ pos_q,
         const int si = pa.list_flag ? __ldg(pa.iperm + i) : 0;
         const uint4 r0 = pa.list_flag ? __ldg(pa.sref + i) : make_uint4(0, 0, 0, 0);
         const float4 p = pos_q[i];
+        // a NaN or infinite input is latched (RBE_ERR_NONFINITE at the next
+        // synchronisation); its fixed-point record is some 32-bit pattern, so
+        // every index derived from it stays in range
+        latch_any(!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(p.w)), pa.err,
+                  kErrNonfinite);
         const uint32_t sx = to_fixed(p.x, S.fx_hi, S.fx_lo);
         const uint32_t sy = to_fixed(p.y, S.fx_hi, S.fx_lo);
         const uint32_t sz = to_fixed(p.z, S.fx_hi, S.fx_lo);
@@ -303,7 +308,7 @@ k_prep_mixed(const __grid_constant__ Work w, const float4* __restrict__ pos_q,
         const int c = S.off_c + (cell_of_fixed(sz, ncd) * ncd + cell_of_fixed(sy, ncd)) * ncd +
                       cell_of_fixed(sx, ncd);
         cid[i] = c;
-        rank[i] = atomicAdd(cell_cnt + c, 1);
+        rank[i] = RBE_IN_BOUNDS(c, pa.ncell, pa.err) ? atomicAdd(cell_cnt + c, 1) : 0;
         const uint4 rec = make_uint4(sx, sy, sz, __float_as_uint(p.w));
         fx[i] = rec;
         qs = (double)p.w;
@@ -317,7 +322,7 @@ k_prep_mixed(const __grid_constant__ Work w, const float4* __restrict__ pos_q,
             const float dy = (float)(int32_t)(sy - r0.y) * Lu;
             const float dz = (float)(int32_t)(sz - r0.z) * Lu;
             moved = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > S.f_half_skin2;
-            pa.spos[si] = rec;
+            if (RBE_IN_BOUNDS(si, pa.ntot, pa.err)) pa.spos[si] = rec;
         }
     }
     if (pa.list_flag) {
@@ -365,6 +370,8 @@ k_prep_f64(const __grid_constant__ Work w, const double4* __restrict__ pos_q,
     if (t < tl.count) {
         const int i = tl.first + t;
         const double4 p = pos_q[i];
+        latch_any(!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(p.w)), pa.err,
+                  kErrNonfinite);
         const double x = wrap_f64(p.x, S.L, S.invL);
         const double y = wrap_f64(p.y, S.L, S.invL);
         const double z = wrap_f64(p.z, S.L, S.invL);
@@ -373,7 +380,7 @@ k_prep_f64(const __grid_constant__ Work w, const double4* __restrict__ pos_q,
                       (cell_of_f64(z, S.invL, ncd) * ncd + cell_of_f64(y, S.invL, ncd)) * ncd +
                       cell_of_f64(x, S.invL, ncd);
         cid[i] = c;
-        rank[i] = atomicAdd(cell_cnt + c, 1);
+        rank[i] = RBE_IN_BOUNDS(c, pa.ncell, pa.err) ? atomicAdd(cell_cnt + c, 1) : 0;
         fx64[i] = make_double4(x, y, z, p.w);
         qs = p.w;
         q2s = p.w * p.w;
@@ -457,10 +464,11 @@ k_scan(int* __restrict__ cell_cnt, int* __restrict__ cell_start, int ncell,
 // inside each cell).
 __global__ void k_scatter(int n, const int* __restrict__ cid, const int* __restrict__ rank,
                           const int* __restrict__ cell_start, int* __restrict__ perm_tmp,
-                          const int* __restrict__ list_flag) {
+                          const int* __restrict__ list_flag, int* __restrict__ err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || (list_flag && !*list_flag)) return;
-    perm_tmp[cell_start[cid[i]] + rank[i]] = i;
+    const int slot = cell_start[cid[i]] + rank[i];
+    if (RBE_IN_BOUNDS(slot, n, err)) perm_tmp[slot] = i;
 }
 
 // Canonical order inside each cell: the particle at atomic slot s goes to
@@ -472,10 +480,12 @@ __global__ void k_order(int n, const int* __restrict__ cid, const int* __restric
                         const int* __restrict__ perm_tmp, const uint4* __restrict__ fx,
                         uint4* __restrict__ spos, const double4* __restrict__ fx64,
                         double4* __restrict__ spos64, int* __restrict__ perm,
-                        const int* __restrict__ list_flag, int* __restrict__ iperm) {
+                        const int* __restrict__ list_flag, int* __restrict__ iperm,
+                        int* __restrict__ err) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n || (list_flag && !*list_flag)) return;
     const int i = perm_tmp[s];
+    if (!RBE_IN_BOUNDS(i, n, err)) return;
     const int c = cid[i];
     const int b = cell_start[c], e = cell_start[c + 1];
     int r = 0;
@@ -491,6 +501,7 @@ __global__ void k_order(int n, const int* __restrict__ cid, const int* __restric
         for (int k = b; k < e; ++k) r += (__ldg(perm_tmp + k) < i) ? 1 : 0;
     }
     const int dst = b + r;
+    if (!RBE_IN_BOUNDS(dst, n, err)) return;
     perm[dst] = i;
     if (iperm) iperm[i] = dst;
     if (fx) spos[dst] = fx[i];
@@ -531,17 +542,18 @@ void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell, uin
 }
 
 void launch_scatter(cudaStream_t st, int n, const int* cid, const int* rank,
-                    const int* cell_start, int* perm_tmp, const int* list_flag) {
+                    const int* cell_start, int* perm_tmp, const int* list_flag, int* err) {
     if (n <= 0) return;
-    k_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, cid, rank, cell_start, perm_tmp, list_flag);
+    k_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, cid, rank, cell_start, perm_tmp, list_flag,
+                                               err);
 }
 
 void launch_order(cudaStream_t st, int n, const int* cid, const int* cell_start,
                   const int* perm_tmp, const uint4* fx, uint4* spos, const double4* fx64,
-                  double4* spos64, int* perm, const int* list_flag, int* iperm) {
+                  double4* spos64, int* perm, const int* list_flag, int* iperm, int* err) {
     if (n <= 0) return;
     k_order<<<(n + 255) / 256, 256, 0, st>>>(n, cid, cell_start, perm_tmp, fx, spos, fx64, spos64,
-                                             perm, list_flag, iperm);
+                                             perm, list_flag, iperm, err);
 }
 
 }  // namespace rbe

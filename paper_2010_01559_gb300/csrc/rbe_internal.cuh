@@ -36,6 +36,8 @@ constexpr int kLTile = 128;       // wave vectors per block of the structure-fac
 constexpr int kMaxAttempts = 32;  // bound on the (0,0,0) rejection loop
 constexpr int kErrSampler = 1;    // bits in the device error word
 constexpr int kErrList = 2;       // a neighbour list overflowed
+constexpr int kErrNonfinite = 4;  // a position or charge of the input was NaN or infinite
+constexpr int kErrBounds = 8;     // (bounds-checked build) an index fell outside its array
 constexpr double kQScale = 4294967296.0;           // 2^32: fixed point of sum q
 
 // Per-system constants (device copy).  All derived in FP64 on the host.
@@ -98,6 +100,28 @@ struct NhState {
 struct Tile {
     int sys, first, count, aux;
 };
+
+// Index checks of the bounds-checked build (compiled with -DRBE_CHECK_BOUNDS):
+// RBE_IN_BOUNDS(i, n, err) is true when 0 <= i < n; otherwise it latches
+// kErrBounds in the device error word and is false, and the caller skips the
+// access.  In the normal build it is the constant true and costs nothing.
+#ifdef RBE_CHECK_BOUNDS
+__device__ __forceinline__ bool rbe_in_bounds(long long i, long long n, int* err) {
+    if (i >= 0 && i < n) return true;
+    if (err) atomicOr(err, kErrBounds);
+    return false;
+}
+#define RBE_IN_BOUNDS(i, n, err) ::rbe::rbe_in_bounds((long long)(i), (long long)(n), (err))
+#else
+#define RBE_IN_BOUNDS(i, n, err) true
+#endif
+
+// A warp-aggregated latch of a device condition: the lowest lane that saw it
+// sets the bit, one atomic per warp at most.
+__device__ __forceinline__ void latch_any(bool cond, int* err, int bit) {
+    const unsigned m = __ballot_sync(__activemask(), cond);
+    if (m && err && (int)(threadIdx.x & 31) == __ffs(m) - 1) atomicOr(err, bit);
+}
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
 // multiplies, the key bumped by the Weyl constants between rounds.
@@ -372,6 +396,7 @@ struct PrepArgs {
     const int* iperm;        // caller index -> sorted index of the last build
     uint4* spos;             // [sorted] current records
     int* list_flag;          // set: rebuild the list in this step
+    int ncell, ntot;         // cells and particles of all systems (index checks)
 };
 void launch_prep_mixed(cudaStream_t st, bool one, const Work& w, int nblk, const float4* pos_q,
                        uint4* fx, int* cid, int* rank, int* cell_cnt, const PrepArgs& pa);
@@ -381,12 +406,15 @@ void launch_prep_f64(cudaStream_t st, bool one, const Work& w, int nblk, const d
 // (the scan then only clears the counts the prep kernel left).
 void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell, uint64_t* step_dev,
                  const uint64_t* cur_step, const int* list_flag = nullptr);
+// err (nullable): the device error word, for the index checks of the
+// bounds-checked build.
 void launch_scatter(cudaStream_t st, int n, const int* cid, const int* rank,
-                    const int* cell_start, int* perm_tmp, const int* list_flag = nullptr);
+                    const int* cell_start, int* perm_tmp, const int* list_flag = nullptr,
+                    int* err = nullptr);
 void launch_order(cudaStream_t st, int n, const int* cid, const int* cell_start,
                   const int* perm_tmp, const uint4* fx, uint4* spos, const double4* fx64,
                   double4* spos64, int* perm, const int* list_flag = nullptr,
-                  int* iperm = nullptr);
+                  int* iperm = nullptr, int* err = nullptr);
 
 // Neighbour-list build (rbe_real.cu): for every sorted particle the sorted
 // indices of the particles within r_c + skin among its 27 neighbour cells.
@@ -510,6 +538,7 @@ struct RealArgs {
     float4* freal;           // list kernel output: real-space force, caller's order
     double2* blk_e;          // per block (E_coul, E_lj), nullable
     double2* blk_w;          // per block (W_coul, W_lj): pair virials r.F, nullable
+    int* err;                // device error word (index checks of the bounds-checked build)
 };
 void launch_real_mixed(cudaStream_t st, bool one, const RealArgs& a);
 void launch_real_f64(cudaStream_t st, bool one, const RealArgs& a);

@@ -131,6 +131,8 @@ k_na_rho(Args a, const float4* __restrict__ pos_q, unsigned char* __restrict__ s
         __syncthreads();
         for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
             const float4 p = pos_q[first + base + t];
+            latch_any(!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(p.w)), err,
+                      kErrNonfinite);
             sp[t] = make_uint4(na_fixed(p.x, a.fx_hi, a.fx_lo), na_fixed(p.y, a.fx_hi, a.fx_lo),
                                na_fixed(p.z, a.fx_hi, a.fx_lo), __float_as_uint(p.w));
             if (blockIdx.y == 0) {
@@ -415,5 +417,7 @@ extern "C" rbe_status rbe_fourier_forces_noalloc(const rbe_params* p, int32_t n,
     if (e != cudaSuccess) return na_fail(RBE_ERR_CUDA, cudaGetErrorString(e));
     if (h_err & rbe::kErrSampler)
         return na_fail(RBE_ERR_SAMPLER, "a k-sample drew (0,0,0) on 32 attempts in a row");
+    if (h_err & rbe::kErrNonfinite)
+        return na_fail(RBE_ERR_NONFINITE, "a position or charge was NaN or infinite");
     return RBE_OK;
 }

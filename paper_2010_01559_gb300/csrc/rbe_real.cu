@@ -525,6 +525,7 @@ __global__ void __launch_bounds__(kBlockP) k_list_build(const __grid_constant__ 
                 for (int part = 0; part < 2; ++part) {
                     const int b = part ? r1 : r0, e = part ? e1 : e0;
                     for (int j = b; j < e; ++j) {
+                        if (!RBE_IN_BOUNDS(j, la.stride, la.err)) break;
                         const uint4 sj = __ldg(la.spos + j);
                         const float dx = (float)(int32_t)(sj.x - si.x) * Lu;
                         const float dyy = (float)(int32_t)(sj.y - si.y) * Lu;
@@ -549,7 +550,9 @@ __global__ void __launch_bounds__(kBlockP) k_list_build(const __grid_constant__ 
                 out[(size_t)(n_in + k) * stride] = out[(size_t)(la.cap - n_sk + k) * stride];
         }
         la.ncnt[i] = min(cnt, la.cap);
-        la.sref[la.perm[i]] = si;           // by caller index: the prep kernel reads it in order
+        const int o = la.perm[i];
+        if (RBE_IN_BOUNDS(o, la.stride, la.err))
+            la.sref[o] = si;                // by caller index: the prep kernel reads it in order
         if (cnt > la.cap) atomicOr(la.err, kErrList);
     }
     const unsigned wmax = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
@@ -621,7 +624,10 @@ __global__ void __launch_bounds__(kBlockP) k_real_list(const __grid_constant__ R
         for (int k0 = l;;) {
             uint4 sj[kListU];
 #pragma unroll
-            for (int q = 0; q < kListU; ++q) sj[q] = __ldg(a.spos + j[q]);
+            for (int q = 0; q < kListU; ++q) {
+                if (!RBE_IN_BOUNDS(j[q], a.nbr_stride, a.err)) j[q] = i;
+                sj[q] = __ldg(a.spos + j[q]);
+            }
 #pragma unroll
             for (int q = 0; q < kListU; ++q)
                 if (k0 + q * R < cnt) pair_fixed(si, sj[q], Lu, lbqi, kc, acc);
@@ -669,8 +675,10 @@ __global__ void __launch_bounds__(kBlockP) k_real_list(const __grid_constant__ R
     if constexpr (!FM) {
         // the real-space force in the caller's order, for the Fourier-force
         // kernel that adds its part and applies the thermostat
-        if ((int)threadIdx.x < tl.count)
-            a.freal[a.perm[tl.first + threadIdx.x]] = make_float4(fx, fy, fz, 0.f);
+        if ((int)threadIdx.x < tl.count) {
+            const int o = a.perm[tl.first + threadIdx.x];
+            if (RBE_IN_BOUNDS(o, a.nbr_stride, a.err)) a.freal[o] = make_float4(fx, fy, fz, 0.f);
+        }
     } else {
         double e_c = 0.0, e_l = 0.0, w_c = 0.0, w_l = 0.0;
         if ((int)threadIdx.x < tl.count) {
