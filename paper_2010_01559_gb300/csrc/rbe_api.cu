@@ -1039,6 +1039,13 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
         cudaStreamWaitEvent(sc, h->ev_prep, 0);
     }
     run(RBE_K_SCAN, sc, [&] {
+        // on a list evaluation the cells are assigned here, only for a rebuild
+        // (the prep kernel skips them): counted with the scan in the profile
+        if (lst && mixed) {
+            launch_cell_assign(sc, one, wp, h->npblk, h->d_fx, h->d_cid, h->d_rank,
+                               h->d_cell_cnt, h->ncell, lflag, h->d_err);
+            ++count;
+        }
         launch_scan(sc, h->d_cell_cnt, h->d_cell_start, h->ncell, a.step_dev, h->d_cur_step,
                     lflag);
     });

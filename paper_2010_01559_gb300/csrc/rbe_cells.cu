@@ -304,11 +304,17 @@ k_prep_mixed(const __grid_constant__ Work w, const float4* __restrict__ pos_q,
         const uint32_t sx = to_fixed(p.x, S.fx_hi, S.fx_lo);
         const uint32_t sy = to_fixed(p.y, S.fx_hi, S.fx_lo);
         const uint32_t sz = to_fixed(p.z, S.fx_hi, S.fx_lo);
-        const int ncd = S.ncd;
-        const int c = S.off_c + (cell_of_fixed(sz, ncd) * ncd + cell_of_fixed(sy, ncd)) * ncd +
-                      cell_of_fixed(sx, ncd);
-        cid[i] = c;
-        rank[i] = RBE_IN_BOUNDS(c, pa.ncell, pa.err) ? atomicAdd(cell_cnt + c, 1) : 0;
+        if (!pa.list_flag) {
+            // the cell of the particle and its slot in the cell's count; a
+            // neighbour-list evaluation leaves this to k_cell_assign, which
+            // runs only when the list is rebuilt
+            const int ncd = S.ncd;
+            const int c = S.off_c +
+                          (cell_of_fixed(sz, ncd) * ncd + cell_of_fixed(sy, ncd)) * ncd +
+                          cell_of_fixed(sx, ncd);
+            cid[i] = c;
+            rank[i] = RBE_IN_BOUNDS(c, pa.ncell, pa.err) ? atomicAdd(cell_cnt + c, 1) : 0;
+        }
         const uint4 rec = make_uint4(sx, sy, sz, __float_as_uint(p.w));
         fx[i] = rec;
         qs = (double)p.w;
@@ -394,6 +400,28 @@ k_prep_f64(const __grid_constant__ Work w, const double4* __restrict__ pos_q,
     }
 }
 
+// Neighbour-list evaluations: the cells of the particles and their slots in
+// the cell counts, from the fixed-point records of the prep kernel, only when
+// this evaluation rebuilds the list (the prep kernel set the flag).
+template <bool ONE>
+__global__ void __launch_bounds__(kBlockP)
+k_cell_assign(const __grid_constant__ Work w, const uint4* __restrict__ fx, int* __restrict__ cid,
+              int* __restrict__ rank, int* __restrict__ cell_cnt, int ncell,
+              const int* __restrict__ list_flag, int* __restrict__ err) {
+    if (!*list_flag) return;
+    const Tile tl = tile_of<ONE>(w);
+    const SysDev& S = sys_of<ONE>(w, tl.sys);
+    const int t = threadIdx.x;
+    if (t >= tl.count) return;
+    const int i = tl.first + t;
+    const uint4 r = fx[i];
+    const int ncd = S.ncd;
+    const int c = S.off_c + (cell_of_fixed(r.z, ncd) * ncd + cell_of_fixed(r.y, ncd)) * ncd +
+                  cell_of_fixed(r.x, ncd);
+    cid[i] = c;
+    rank[i] = RBE_IN_BOUNDS(c, ncell, err) ? atomicAdd(cell_cnt + c, 1) : 0;
+}
+
 // Exclusive scan of the cell counts (one block), zeroing the counts for the
 // next call.
 constexpr int kScanThreads = 1024;
@@ -404,10 +432,9 @@ k_scan(int* __restrict__ cell_cnt, int* __restrict__ cell_start, int ncell,
        uint64_t* __restrict__ step_dev, const uint64_t* __restrict__ cur_step,
        const int* __restrict__ list_flag) {
     if (step_dev && threadIdx.x == 0) *step_dev = *cur_step + 1;   // one increment per step
-    if (list_flag && !*list_flag) {               // the list stands: only clear the counts
-        for (int i = threadIdx.x; i < ncell; i += blockDim.x) cell_cnt[i] = 0;
-        return;
-    }
+    // the list stands: no cell was counted (k_cell_assign counts only for a
+    // rebuild, and every scan leaves the counts at zero)
+    if (list_flag && !*list_flag) return;
     __shared__ int warp_tot[kScanThreads / 32];
     __shared__ int carry_s;
     if (threadIdx.x == 0) carry_s = 0;
@@ -533,6 +560,18 @@ void launch_prep_f64(cudaStream_t st, bool one, const Work& w, int nblk, const d
         k_prep_f64<true><<<nblk, kBlockP, smem, st>>>(w, pos_q, fx64, cid, rank, cell_cnt, pa);
     else
         k_prep_f64<false><<<nblk, kBlockP, smem, st>>>(w, pos_q, fx64, cid, rank, cell_cnt, pa);
+}
+
+void launch_cell_assign(cudaStream_t st, bool one, const Work& w, int nblk, const uint4* fx,
+                        int* cid, int* rank, int* cell_cnt, int ncell, const int* list_flag,
+                        int* err) {
+    if (nblk <= 0) return;
+    if (one)
+        k_cell_assign<true><<<nblk, kBlockP, 0, st>>>(w, fx, cid, rank, cell_cnt, ncell,
+                                                      list_flag, err);
+    else
+        k_cell_assign<false><<<nblk, kBlockP, 0, st>>>(w, fx, cid, rank, cell_cnt, ncell,
+                                                       list_flag, err);
 }
 
 void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell, uint64_t* step_dev,

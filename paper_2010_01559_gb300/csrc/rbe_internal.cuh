@@ -402,8 +402,13 @@ void launch_prep_mixed(cudaStream_t st, bool one, const Work& w, int nblk, const
                        uint4* fx, int* cid, int* rank, int* cell_cnt, const PrepArgs& pa);
 void launch_prep_f64(cudaStream_t st, bool one, const Work& w, int nblk, const double4* pos_q,
                      double4* fx64, int* cid, int* rank, int* cell_cnt, const PrepArgs& pa);
+// Neighbour-list evaluations: cell ids and slots (cid, rank, cell_cnt) of the
+// particles from their fixed-point records, only when *list_flag is set.
+void launch_cell_assign(cudaStream_t st, bool one, const Work& w, int nblk, const uint4* fx,
+                        int* cid, int* rank, int* cell_cnt, int ncell, const int* list_flag,
+                        int* err);
 // list_flag (nullable): the cell list is rebuilt only when *list_flag is set
-// (the scan then only clears the counts the prep kernel left).
+// (the scan returns at once otherwise: no cell was counted).
 void launch_scan(cudaStream_t st, int* cell_cnt, int* cell_start, int ncell, uint64_t* step_dev,
                  const uint64_t* cur_step, const int* list_flag = nullptr);
 // err (nullable): the device error word, for the index checks of the
