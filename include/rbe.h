@@ -312,6 +312,15 @@ rbe_status rbe_set_tuning(rbe_handle h, const rbe_tuning *t);
  * choices resolved). */
 rbe_status rbe_get_tuning(rbe_handle h, rbe_tuning *t);
 
+/* Fusion of a mixed-precision list MD step (rbe_step*, rbe_step_ex): with
+ * on = 1 (the default) the structure factors (Eq. rbmapprox's rho(k)) and the
+ * real-space pass over a standing neighbour list run as one launch whose
+ * blocks take either kind of work, so that every SM runs both; with on = 0 they
+ * are two launches on two streams.  The results are the same to the last bit
+ * either way.  Captured step graphs are dropped.  RBE_ERR_ARG unless on is 0
+ * or 1. */
+rbe_status rbe_set_fusion(rbe_handle h, int32_t on);
+
 /* Time the candidate launch shapes of each tunable kernel on the given input
  * (device pos_q, n particles) with CUDA events, keep the fastest and return
  * them in *out (nullable). */
@@ -332,7 +341,9 @@ enum {
     RBE_K_ENERGY = 8,        /* FP64 energy reduction                               */
     RBE_K_LIST_BUILD = 9,    /* neighbour-list build (list MD steps; returns at once
                                 when no particle moved beyond skin/2)             */
-    RBE_K_COUNT = 10
+    RBE_K_RHO_LIST = 10,     /* list MD steps with fusion on: RBE_K_RHO and the pass
+                                over a standing neighbour list in one launch       */
+    RBE_K_COUNT = 11
 };
 
 /* Enable (1) or disable (0) per-kernel timing.  While enabled, rbe_forces*,

@@ -114,6 +114,11 @@ class _HandleBase:
         (``rbe_set_wait_limit``)."""
         capi.check(self.lib.rbe_set_wait_limit(self._h, float(seconds)), self._h)
 
+    def set_fusion(self, on):
+        """Structure factors and the standing-list pass of a mixed list MD
+        step in one launch (True, the default) or two (``rbe_set_fusion``)."""
+        capi.check(self.lib.rbe_set_fusion(self._h, 1 if on else 0), self._h)
+
     def set_tuning(self, rho_chunk=0, force_split=0, real_split=0, real_seg=0, list_split=0):
         t = capi.rbe_tuning(rho_chunk, force_split, real_split, real_seg, list_split)
         capi.check(self.lib.rbe_set_tuning(self._h, ctypes.byref(t)), self._h)

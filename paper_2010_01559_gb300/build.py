@@ -28,7 +28,10 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librbe.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
+# -ftz=true: FP32 subnormals flush to zero, so the approximate reciprocal,
+# square root and exponential of the pair terms need no subnormal fix-ups (no
+# FP32 quantity of the method comes near 1e-38; FP64 work is unaffected).
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-ftz=true", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-ffp-contract=off", "-Xcompiler", "-Wno-deprecated-declarations",
               "-diag-suppress", "1444", "-I", INCLUDE, "-I", CSRC]
 

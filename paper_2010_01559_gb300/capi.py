@@ -83,6 +83,7 @@ _SIGS = {
     "rbe_step_host": ([_H, ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_uint64], ctypes.c_int),
     "rbe_sync": ([_H], ctypes.c_int),
     "rbe_set_wait_limit": ([_H, ctypes.c_double], ctypes.c_int),
+    "rbe_set_fusion": ([_H, ctypes.c_int32], ctypes.c_int),
     "rbe_set_tuning": ([_H, ctypes.POINTER(rbe_tuning)], ctypes.c_int),
     "rbe_get_tuning": ([_H, ctypes.POINTER(rbe_tuning)], ctypes.c_int),
     "rbe_autotune": ([_H, ctypes.c_int32, _P, ctypes.POINTER(rbe_tuning)], ctypes.c_int),
@@ -100,7 +101,7 @@ _SIGS = {
 
 #: kernel names in RBE_K_* order
 KERNELS = ("prep", "scan", "scatter", "cell_order", "rho", "finalize", "fourier_force",
-           "real", "energy", "list_build")
+           "real", "energy", "list_build", "rho_list")
 
 #: every symbol include/rbe.h declares
 EXPORTED = tuple(_SIGS)

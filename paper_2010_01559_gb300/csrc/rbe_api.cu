@@ -167,6 +167,7 @@ struct rbe_ctx {
     size_t max_part = 0;
     bool use_graph = false;
     double wait_limit = 0.0;                  // seconds a host wait may take (0: no limit)
+    bool fuse_list = true;                    // list steps: structure factors + list pass fused
     std::vector<GraphEntry> graphs;
     std::string err;
     // per-kernel profile
@@ -415,7 +416,7 @@ void fill_sysdev(const SysHost& s, SysDev& d) {
 }
 
 int auto_chunk(const rbe_ctx* h, long long ntot) {
-    const int ltiles = (h->pmax + kLTile - 1) / kLTile;
+    const int ltiles = (h->pmax + kRhoKT - 1) / kRhoKT;
     const long long target_blocks = 152LL * 12;
     long long chunks = std::max(1LL, target_blocks / std::max(1, ltiles));
     long long c = (ntot + chunks - 1) / chunks;
@@ -919,7 +920,8 @@ RealArgs make_real_args(const rbe_ctx* h, int parts) {
 // Structure factors: per-chunk partials added to the fixed-point rho(k).
 void launch_rho(const rbe_ctx* h, cudaStream_t st, bool mixed, bool pdl = false) {
     const bool one = !h->batch;
-    const int ltiles = (h->pmax + kLTile - 1) / kLTile;
+    const int kt = mixed ? kRhoKT : kLTile;           // wave vectors per tile
+    const int ltiles = (h->pmax + kt - 1) / kt;
     const Work w = make_work(h, h->d_chunks, h->cur_chunk, 1);
     if (mixed)
         launch_rho_mixed(st, one, w, h->nchunks, ltiles, h->d_ksamp, h->d_kcoef, h->d_fx,
@@ -958,6 +960,9 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     // profiling runs the branches one after another on st, so that each
     // kernel's event pair brackets that kernel alone
     cudaStream_t st2 = prof ? st : h->stream2;
+    // a list step's structure factors and standing-list pass share one launch
+    // (timed as RBE_K_RHO_LIST when profiling)
+    const bool fused = a.list && mixed && (a.parts & RBE_PART_FOURIER) && h->fuse_list;
     bool used[RBE_K_COUNT] = {};
     int count = 0;
     auto run = [&](int kid, cudaStream_t s, auto&& launch) {
@@ -1023,7 +1028,29 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
         // while the previous one drains); the list pass and the rebuild fork
         // off after prep
         cudaEventRecord(h->ev_prep, st);
-        if (fourier) run(RBE_K_RHO, st, [&] { launch_rho(h, st, mixed, !prof); });
+        if (fused) {
+            // the structure factors and the pass over a standing list in one
+            // launch whose blocks take either kind of work
+            RealArgs rl = make_real_args(h, a.parts);
+            rl.lw = make_work(h, h->d_lblk, kBlockP / h->lsplit, 0);
+            rl.nlblk = h->nlblk;
+            rl.lsplit = h->lsplit;
+            rl.nbr = h->d_nbr;
+            rl.ncnt = h->d_ncnt;
+            rl.nbr_stride = std::max(h->ntot, 1);
+            rl.nbr_cap = h->list_cap;
+            rl.list_flag = h->d_list_flag;
+            rl.freal = h->d_freal;
+            rl.list_when = 0;
+            const int ltiles = (h->pmax + kRhoKT - 1) / kRhoKT;
+            run(RBE_K_RHO_LIST, st, [&] {
+                launch_rho_list(st, one, make_work(h, h->d_chunks, h->cur_chunk, 1), h->nchunks,
+                                ltiles, h->d_ksamp, h->d_kcoef, h->d_fx, h->d_rho_fx, h->d_kcnt,
+                                h->d_kab, rl, !prof);
+            });
+        } else if (fourier) {
+            run(RBE_K_RHO, st, [&] { launch_rho(h, st, mixed, !prof); });
+        }
     } else if (fourier) {
         cudaEventRecord(h->ev_fork, st);
         cudaStreamWaitEvent(st2, h->ev_fork, 0);
@@ -1104,15 +1131,17 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
         // over the rebuilt list at the end of the rebuild stream; then the
         // Fourier force, which adds it and applies the thermostat
         r.list_when = 0;
-        cudaStreamWaitEvent(st2, h->ev_prep, 0);
-        run(RBE_K_REAL, st2, [&] { launch_real_list(st2, one, r); });
-        cudaEventRecord(h->ev_real, st2);
+        if (!fused) {
+            cudaStreamWaitEvent(st2, h->ev_prep, 0);
+            run(RBE_K_REAL, st2, [&] { launch_real_list(st2, one, r); });
+            cudaEventRecord(h->ev_real, st2);
+        }
         RealArgs rb = r;
         rb.list_when = 1;
         launch_real_list(sc, one, rb);
         ++count;
         cudaEventRecord(h->ev_chain, sc);
-        cudaStreamWaitEvent(st, h->ev_real, 0);
+        if (!fused) cudaStreamWaitEvent(st, h->ev_real, 0);
         cudaStreamWaitEvent(st, h->ev_chain, 0);
         MdOut md{};
         md.freal = h->d_freal;
@@ -1731,6 +1760,15 @@ rbe_status rbe_set_wait_limit(rbe_handle h, double seconds) {
     return RBE_OK;
 }
 
+rbe_status rbe_set_fusion(rbe_handle h, int32_t on) {
+    if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
+    if (on != 0 && on != 1) return fail(h, RBE_ERR_ARG, "fusion must be 0 or 1");
+    h->fuse_list = on != 0;
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    return RBE_OK;
+}
+
 rbe_status rbe_set_tuning(rbe_handle h, const rbe_tuning* t) {
     if (!h || !t) return fail(h, RBE_ERR_ARG, "null argument");
     const int c = t->rho_chunk, f = t->force_split, r = t->real_split, sg = t->real_seg;
@@ -1843,33 +1881,56 @@ rbe_status rbe_autotune(rbe_handle h, int32_t n, const float* pos_q, rbe_tuning*
     }
     h->real_split = best_rsplit;
     h->real_seg = best_seg;
-    // neighbour-list pass: lanes per particle, timed on a list built for this input
+    // neighbour-list pass: lanes per particle, timed on a list built for this
+    // input.  With fusion on it is timed inside the launch it shares with the
+    // structure factors, and the structure-factor chunk is re-chosen with it
+    // (the shapes fastest alone are not always the fastest together).
     int best_lsplit = 0;
     if (h->list) {
         best = 1e30f;
-        for (int ls = 1; ls <= 8 && s == RBE_OK; ls <<= 1) {
-            h->list_split = ls;
-            if ((s = prepare(h, n)) != RBE_OK) break;
-            EvalArgs b = a;
-            b.list = true;
-            RBE_CUDA(h, cudaMemsetAsync(h->d_list_flag, 0xFF, sizeof(int), h->stream));
-            enqueue_eval(h, h->stream, b);
-            RealArgs r = make_real_args(h, RBE_PART_ALL);
-            r.F_out = h->d_stage_F;
-            r.lw = make_work(h, h->d_lblk, kBlockP / h->lsplit, 0);
-            r.nlblk = h->nlblk;
-            r.lsplit = h->lsplit;
-            r.nbr = h->d_nbr;
-            r.ncnt = h->d_ncnt;
-            r.nbr_stride = std::max(h->ntot, 1);
-            r.nbr_cap = h->list_cap;
-            r.list_flag = h->d_list_flag;
-            r.list_when = 0;
-            r.freal = h->d_freal;
-            const float t = time_kernel(h, e0, e1, [&] { launch_real_list(h->stream, !h->batch, r); });
-            if (t < best) { best = t; best_lsplit = ls; }
+        std::vector<int> chunks{best_chunk};
+        if (h->fuse_list) {
+            if (best_chunk / 2 >= 32) chunks.insert(chunks.begin(), best_chunk / 2);
+            if (best_chunk * 2 <= 4096) chunks.push_back(best_chunk * 2);
+        }
+        int best_fchunk = best_chunk;
+        for (int c : chunks) {
+            h->rho_chunk = c;
+            for (int ls = 1; ls <= 8 && s == RBE_OK; ls <<= 1) {
+                h->list_split = ls;
+                if ((s = prepare(h, n)) != RBE_OK) break;
+                EvalArgs b = a;
+                b.list = true;
+                RBE_CUDA(h, cudaMemsetAsync(h->d_list_flag, 0xFF, sizeof(int), h->stream));
+                enqueue_eval(h, h->stream, b);
+                RealArgs r = make_real_args(h, RBE_PART_ALL);
+                r.F_out = h->d_stage_F;
+                r.lw = make_work(h, h->d_lblk, kBlockP / h->lsplit, 0);
+                r.nlblk = h->nlblk;
+                r.lsplit = h->lsplit;
+                r.nbr = h->d_nbr;
+                r.ncnt = h->d_ncnt;
+                r.nbr_stride = std::max(h->ntot, 1);
+                r.nbr_cap = h->list_cap;
+                r.list_flag = h->d_list_flag;
+                r.list_when = 0;
+                r.freal = h->d_freal;
+                const int ltiles = (h->pmax + kRhoKT - 1) / kRhoKT;
+                const float t = time_kernel(h, e0, e1, [&] {
+                    if (h->fuse_list)
+                        launch_rho_list(h->stream, !h->batch,
+                                        make_work(h, h->d_chunks, h->cur_chunk, 1), h->nchunks,
+                                        ltiles, h->d_ksamp, h->d_kcoef, h->d_fx, h->d_rho_fx,
+                                        h->d_kcnt, h->d_kab, r, false);
+                    else
+                        launch_real_list(h->stream, !h->batch, r);
+                });
+                if (t < best) { best = t; best_lsplit = ls; best_fchunk = c; }
+            }
         }
         h->list_split = best_lsplit;
+        best_chunk = best_fchunk;
+        h->rho_chunk = best_chunk;
         h->list_valid = false;
     }
     h->prof_on = prof;

@@ -26,6 +26,7 @@
 #include <cmath>
 
 #include "rbe_internal.cuh"
+#include "rbe_list_body.cuh"
 
 namespace rbe {
 
@@ -55,59 +56,113 @@ __device__ __forceinline__ double2 kcoef(const SysDev& S, int4 m,
 }
 
 // ----------------------------------------------------------------- rho (mixed)
-// Two threads per wave vector (threads l and l + kLTile), each over every
+// Two threads per wave vector (threads t and t + kLTile), each over every
 // other particle of the chunk; their sums are added before the atomics.
 constexpr int kRhoHalves = 2;
 
-template <bool ONE>
-__global__ void __launch_bounds__(kLTile * kRhoHalves)
-k_rho_mixed(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
-            const double* __restrict__ kcoef, const uint4* __restrict__ fx,
-            unsigned long long* __restrict__ rho_fx, int* __restrict__ kcnt,
-            float2* __restrict__ kab) {
+// rho_body: chunk ctile of the particles and tile ktile of kRhoKT wave
+// vectors (HALVES * kLTile threads; it synchronises the block), for the kernel
+// of its own and for the fused structure-factor + list launch of the MD step.
+// Each thread takes kRhoK wave vectors, t and t + kLTile of the tile, so that
+// one shared-memory load of a particle serves kRhoK (particle, k) pairs.
+// With one thread per wave vector (HALVES = 1) the even and odd particles go
+// to separate sums that are added as the two halves' are: rho(k) comes out the
+// same to the last bit either way.
+template <bool ONE, int HALVES>
+__device__ __forceinline__ void rho_body(const Work& w, const int4* __restrict__ ksamp,
+                                         const double* __restrict__ kcoef,
+                                         const uint4* __restrict__ fx,
+                                         unsigned long long* __restrict__ rho_fx,
+                                         int* __restrict__ kcnt, float2* __restrict__ kab,
+                                         int ctile, int ktile) {
+    constexpr int KR = kRhoK;
     __shared__ uint4 sp[kStage];
-    __shared__ double2 s_half[kLTile];
-    const Tile ch = tile_of<ONE>(w);
+    __shared__ double2 s_half[HALVES > 1 ? kLTile * KR : 1];
+    const Tile ch = tile_at<ONE>(w, ctile);
     const SysDev& S = sys_of<ONE>(w, ch.sys);
     const int half = threadIdx.x / kLTile;
-    const int l = blockIdx.y * kLTile + (threadIdx.x - half * kLTile);
-    pdl_trigger();                                    // the force kernel may be scheduled
-    pdl_wait();                                       // the prep kernel's samples and records
-    if (blockIdx.y * kLTile >= S.P) return;          // whole block beyond this system's P
-    const bool active = l < S.P;
-    int4 m = make_int4(0, 0, 0, 0);
-    if (active) m = ksamp[S.off_k + l];              // drawn by the prep kernel
-    const uint32_t mx = (uint32_t)m.x, my = (uint32_t)m.y, mz = (uint32_t)m.z;
+    const int t = threadIdx.x - half * kLTile;
+    if (ktile * kRhoKT >= S.P) return;               // whole block beyond this system's P
+    uint32_t mx[KR], my[KR], mz[KR];
+    bool active[KR];
+#pragma unroll
+    for (int r = 0; r < KR; ++r) {
+        const int l = ktile * kRhoKT + t + r * kLTile;
+        active[r] = l < S.P;
+        int4 m = make_int4(0, 0, 0, 0);
+        if (active[r]) m = ksamp[S.off_k + l];       // drawn by the prep kernel
+        mx[r] = (uint32_t)m.x;
+        my[r] = (uint32_t)m.y;
+        mz[r] = (uint32_t)m.z;
+    }
     // FP32 sums over one staged pass (at most kStage / 2 terms), FP64 across
     // passes and halves, so the rounding does not grow with the chunk size
-    double red = 0.0, imd = 0.0;
+    double red[KR], imd[KR], red_o[KR], imd_o[KR];
+#pragma unroll
+    for (int r = 0; r < KR; ++r) red[r] = imd[r] = red_o[r] = imd_o[r] = 0.0;
+    float re[KR], im[KR], re_o[KR], im_o[KR];
+    auto terms = [&](const uint4 p, float* re_, float* im_) {
+        const float q = __uint_as_float(p.w);
+#pragma unroll
+        for (int r = 0; r < KR; ++r) {
+            const uint32_t ph = mx[r] * p.x + my[r] * p.y + mz[r] * p.z;
+            const float th = (float)(int32_t)ph * kTwoPiOver2p32;
+            float sn, cs;
+            __sincosf(th, &sn, &cs);
+            re_[r] = fmaf(q, cs, re_[r]);
+            im_[r] = fmaf(q, sn, im_[r]);
+        }
+    };
+    const bool any = active[0];                      // t + kLTile < P only if t < P
     for (int base = 0; base < ch.count; base += kStage) {
         const int cnt = min(kStage, ch.count - base);
         __syncthreads();
-        for (int t = threadIdx.x; t < cnt; t += blockDim.x) sp[t] = fx[ch.first + base + t];
+        for (int u = threadIdx.x; u < cnt; u += blockDim.x) sp[u] = fx[ch.first + base + u];
         __syncthreads();
-        float re = 0.f, im = 0.f;
-        if (active) {
-#pragma unroll 4
-            for (int j = half; j < cnt; j += kRhoHalves) {
-                const uint4 p = sp[j];
-                const uint32_t ph = mx * p.x + my * p.y + mz * p.z;
-                const float th = (float)(int32_t)ph * kTwoPiOver2p32;
-                float sn, cs;
-                __sincosf(th, &sn, &cs);
-                const float q = __uint_as_float(p.w);
-                re = fmaf(q, cs, re);
-                im = fmaf(q, sn, im);
+#pragma unroll
+        for (int r = 0; r < KR; ++r) re[r] = im[r] = re_o[r] = im_o[r] = 0.f;
+        if (any) {
+            if constexpr (HALVES == 1) {
+                int j = 0;
+                for (; j + 1 < cnt; j += 2) {
+                    terms(sp[j], re, im);
+                    terms(sp[j + 1], re_o, im_o);
+                }
+                if (j < cnt) terms(sp[j], re, im);
+            } else {
+#pragma unroll 2
+                for (int j = half; j < cnt; j += HALVES) terms(sp[j], re, im);
             }
         }
-        red += (double)re;
-        imd += (double)im;
+#pragma unroll
+        for (int r = 0; r < KR; ++r) {
+            red[r] += (double)re[r];
+            imd[r] += (double)im[r];
+            red_o[r] += (double)re_o[r];
+            imd_o[r] += (double)im_o[r];
+        }
     }
-    if (half == 1) s_half[threadIdx.x - kLTile] = make_double2(red, imd);
-    __syncthreads();
-    if (half == 0 && active) {
-        const double2 o = s_half[threadIdx.x];
-        rho_accumulate(rho_fx + 2 * (S.off_k + l), red + o.x, imd + o.y, S.rho_scale);
+    if constexpr (HALVES > 1) {
+        if (half == 1) {
+#pragma unroll
+            for (int r = 0; r < KR; ++r) s_half[t + r * kLTile] = make_double2(red[r], imd[r]);
+        }
+        __syncthreads();
+        if (half == 0) {
+#pragma unroll
+            for (int r = 0; r < KR; ++r) {
+                const double2 o = s_half[t + r * kLTile];
+                if (active[r])
+                    rho_accumulate(rho_fx + 2 * (S.off_k + ktile * kRhoKT + t + r * kLTile),
+                                   red[r] + o.x, imd[r] + o.y, S.rho_scale);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < KR; ++r)
+            if (active[r])
+                rho_accumulate(rho_fx + 2 * (S.off_k + ktile * kRhoKT + t + r * kLTile),
+                               red[r] + red_o[r], imd[r] + imd_o[r], S.rho_scale);
     }
     // The last of the system's chunks to add its partials for this tile of
     // wave vectors finds rho(k) complete and turns it into the force
@@ -120,12 +175,14 @@ k_rho_mixed(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
     __shared__ int s_last;
     __threadfence();
     __syncthreads();
-    const int slot = S.off_k + blockIdx.y * kLTile;
+    const int slot = S.off_k + ktile * kRhoKT;
     if (threadIdx.x == 0) s_last = atomicAdd(kcnt + slot, 1) == S.nchunk - 1;
     __syncthreads();
     if (s_last) {
         __threadfence();
-        if (active && half == 0) {
+        for (int u = threadIdx.x; u < kRhoKT; u += blockDim.x) {
+            const int l = ktile * kRhoKT + u;
+            if (l >= S.P) break;
             const double2 r = rho_read(rho_fx + 2 * (S.off_k + l), S.rho_inv_scale);
             const double c = kcoef[S.off_k + l];
             const float A = (float)(c * r.y), B = (float)(c * r.x);
@@ -135,6 +192,46 @@ k_rho_mixed(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
         }
         if (threadIdx.x == 0) kcnt[slot] = 0;        // ready for the next evaluation
     }
+}
+
+template <bool ONE>
+__global__ void __launch_bounds__(kLTile * kRhoHalves)
+k_rho_mixed(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
+            const double* __restrict__ kcoef, const uint4* __restrict__ fx,
+            unsigned long long* __restrict__ rho_fx, int* __restrict__ kcnt,
+            float2* __restrict__ kab) {
+    pdl_trigger();                                    // the force kernel may be scheduled
+    pdl_wait();                                       // the prep kernel's samples and records
+    rho_body<ONE, kRhoHalves>(w, ksamp, kcoef, fx, rho_fx, kcnt, kab, blockIdx.x, blockIdx.y);
+}
+
+// ------------------------------------------- structure factors + list pass
+// The MD step's structure factors and its real-space pass over a standing
+// neighbour list in one launch of kLTile-thread blocks: block b takes
+// structure-factor work when floor((b + 1) nrho / total) > floor(b nrho /
+// total), else a tile of the list pass, so that the two kinds are spread evenly
+// over the grid and each SM holds both at once -- the structure factors keep
+// the special-function unit busy while the pair terms use the ALU and FMA
+// pipes and wait on their gathers.  The list tiles work only when the list
+// stands (the pass after a rebuild runs on the rebuild branch, as before).
+template <int R, bool ONE>
+__global__ void __launch_bounds__(kLTile)
+k_rho_list(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
+           const double* __restrict__ kcoef, const uint4* __restrict__ fx,
+           unsigned long long* __restrict__ rho_fx, int* __restrict__ kcnt,
+           float2* __restrict__ kab, const __grid_constant__ RealArgs a, int nchunks, int nrho,
+           int nlist) {
+    pdl_trigger();                                    // the force kernel may be scheduled
+    pdl_wait();                                       // the prep kernel's samples and records
+    const int b = blockIdx.x, total = nrho + nlist;
+    const int r0 = (int)((long long)b * nrho / total);
+    const int r1 = (int)((long long)(b + 1) * nrho / total);
+    if (r1 > r0) {
+        rho_body<ONE, 1>(w, ksamp, kcoef, fx, rho_fx, kcnt, kab, r0 % nchunks, r0 / nchunks);
+        return;
+    }
+    if ((*a.list_flag != 0) != (a.list_when != 0)) return;
+    list_body<R, ONE, false>(a, b - r1, threadIdx.x);
 }
 
 // ----------------------------------------------------------------- rho (FP64)
@@ -411,6 +508,34 @@ void launch_rho_mixed(cudaStream_t st, bool one, const Work& w, int nchunks, int
         cudaLaunchKernelEx(&c.cfg, k_rho_mixed<true>, w, ksamp, kcoef, fx, rho_fx, kcnt, kab);
     else
         cudaLaunchKernelEx(&c.cfg, k_rho_mixed<false>, w, ksamp, kcoef, fx, rho_fx, kcnt, kab);
+}
+
+template <int R>
+static void rho_list_r(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
+                       const int4* ksamp, const double* kcoef, const uint4* fx,
+                       unsigned long long* rho_fx, int* kcnt, float2* kab, const RealArgs& a,
+                       bool pdl) {
+    const int nrho = nchunks * ltiles;
+    PdlConfig c(dim3(nrho + a.nlblk), dim3(kLTile), 0, st, pdl);
+    if (one)
+        cudaLaunchKernelEx(&c.cfg, k_rho_list<R, true>, w, ksamp, kcoef, fx, rho_fx, kcnt, kab, a,
+                           nchunks, nrho, a.nlblk);
+    else
+        cudaLaunchKernelEx(&c.cfg, k_rho_list<R, false>, w, ksamp, kcoef, fx, rho_fx, kcnt, kab,
+                           a, nchunks, nrho, a.nlblk);
+}
+
+void launch_rho_list(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
+                     const int4* ksamp, const double* kcoef, const uint4* fx,
+                     unsigned long long* rho_fx, int* kcnt, float2* kab, const RealArgs& a,
+                     bool pdl) {
+    if (nchunks <= 0 || ltiles <= 0) return;
+    switch (a.lsplit) {
+        case 2: rho_list_r<2>(st, one, w, nchunks, ltiles, ksamp, kcoef, fx, rho_fx, kcnt, kab, a, pdl); break;
+        case 4: rho_list_r<4>(st, one, w, nchunks, ltiles, ksamp, kcoef, fx, rho_fx, kcnt, kab, a, pdl); break;
+        case 8: rho_list_r<8>(st, one, w, nchunks, ltiles, ksamp, kcoef, fx, rho_fx, kcnt, kab, a, pdl); break;
+        default: rho_list_r<1>(st, one, w, nchunks, ltiles, ksamp, kcoef, fx, rho_fx, kcnt, kab, a, pdl); break;
+    }
 }
 
 void launch_rho_f64(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,

@@ -32,7 +32,9 @@
 namespace rbe {
 
 constexpr int kBlockP = 128;      // particles per block of the per-particle kernels
-constexpr int kLTile = 128;       // wave vectors per block of the structure-factor kernel
+constexpr int kLTile = 128;       // threads per wave-vector row of the structure-factor kernels
+constexpr int kRhoK = 2;          // wave vectors per thread of the mixed structure factors
+constexpr int kRhoKT = kLTile * kRhoK;   // wave vectors per tile of the mixed structure factors
 constexpr int kMaxAttempts = 32;  // bound on the (0,0,0) rejection loop
 constexpr int kErrSampler = 1;    // bits in the device error word
 constexpr int kErrList = 2;       // a neighbour list overflowed
@@ -288,6 +290,17 @@ __device__ __forceinline__ Tile tile_of(const Work& w) {
                     (int)blockIdx.x * w.aux_stride};
     } else {
         return w.tiles[blockIdx.x];
+    }
+}
+
+// Tile idx of the work (as tile_of, for a block whose index is not the tile's).
+template <bool ONE>
+__device__ __forceinline__ Tile tile_at(const Work& w, int idx) {
+    if constexpr (ONE) {
+        const int first = idx * w.tile;
+        return Tile{0, first, max(0, min(w.tile, w.one.n - first)), idx * w.aux_stride};
+    } else {
+        return w.tiles[idx];
     }
 }
 
@@ -548,6 +561,12 @@ struct RealArgs {
 void launch_real_mixed(cudaStream_t st, bool one, const RealArgs& a);
 void launch_real_f64(cudaStream_t st, bool one, const RealArgs& a);
 void launch_real_list(cudaStream_t st, bool one, const RealArgs& a);
+// The MD step's structure factors and its pass over a standing list in one
+// launch (rbe_fourier.cu); `a` as for launch_real_list with list_when = 0.
+void launch_rho_list(cudaStream_t st, bool one, const Work& w, int nchunks, int ltiles,
+                     const int4* ksamp, const double* kcoef, const uint4* fx,
+                     unsigned long long* rho_fx, int* kcnt, float2* kab, const RealArgs& a,
+                     bool pdl);
 void launch_observables(cudaStream_t st, const SysDev& S, const uint4* fx, int first, int n,
                         const int4* mlist, int K, unsigned long long* rho_fx, double2* part,
                         const float4* pos_q, const float4* vel, const double* E_in,

@@ -31,28 +31,12 @@
 #include <cmath>
 
 #include "rbe_internal.cuh"
+#include "rbe_pair.cuh"
+#include "rbe_list_body.cuh"
 
 namespace rbe {
 
-constexpr int kPartFourier = 1, kPartReal = 2, kPartLJ = 4;
 
-__device__ __forceinline__ double2 block_sum2_real(double a, double b) {
-    __shared__ double sa[32], sb[32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
-    }
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { sa[w] = a; sb[w] = b; }
-    __syncthreads();
-    double2 r = make_double2(0.0, 0.0);
-    if (threadIdx.x == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-        for (int k = 0; k < nw; ++k) { r.x += sa[k]; r.y += sb[k]; }
-    }
-    return r;
-}
 
 __device__ __forceinline__ int wrapc(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
 
@@ -87,61 +71,6 @@ __device__ __forceinline__ void row_ranges(const int* __restrict__ cs, int base,
 // records from global memory instead.
 constexpr int kNbCap = 24;          // entries of each lane's neighbour list
 constexpr int kBatch = 2;           // candidates a thread tests per step of its scan
-
-struct PairAcc {
-    float fx, fy, fz, phr, ec, elj, wc, wlj;     // wc, wlj: half the pair virials r.F
-};
-
-// erfc(x) for x >= 0 given e = exp(-x^2): the rational approximation of
-// Abramowitz & Stegun, Handbook of Mathematical Functions, formula 7.1.26
-// (after Hastings), |error| <= 1.5e-7.  It reuses the Gaussian the force needs
-// anyway, so erfc costs one reciprocal and five FMAs.
-__device__ __forceinline__ float erfc_as(float e, float x) {
-    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
-    float p = 1.061405429f;
-    p = fmaf(p, t, -1.453152027f);
-    p = fmaf(p, t, 1.421413741f);
-    p = fmaf(p, t, -0.284496736f);
-    p = fmaf(p, t, 0.254829592f);
-    return p * t * e;
-}
-
-// Per-system constants of the pair terms, in registers.
-struct PairConst {
-    float rc2, lj_rc2, alpha, sa, two_sa_spi, lB, lj_s2, lj_eps, lj_shift;
-    bool vir;                                   // accumulate the virials
-};
-
-// Pair terms for displacement r_ij = (dx, dy, dz), |r_ij|^2 = r2 > 0.
-__device__ __forceinline__ void pair_terms(float dx, float dy, float dz, float r2, float qj,
-                                           float lbqi, const PairConst& k, PairAcc& acc) {
-    const float inv_r = rsqrtf(r2);
-    if (r2 < k.rc2) {
-        const float x = k.sa * (r2 * inv_r);
-        const float ex = __expf(-k.alpha * r2);                  // exp(-x^2)
-        const float pot = erfc_as(ex, x) * inv_r;                 // erfc(sqrt(a) r) / r
-        const float g_over_r = fmaf(k.two_sa_spi, ex, pot) * inv_r * inv_r;   // G(r) / r
-        const float s_ = -lbqi * qj * g_over_r;
-        acc.fx = fmaf(s_, dx, acc.fx);
-        acc.fy = fmaf(s_, dy, acc.fy);
-        acc.fz = fmaf(s_, dz, acc.fz);
-        acc.phr = fmaf(k.lB * qj, pot, acc.phr);
-        acc.ec = fmaf(0.5f * lbqi * qj, pot, acc.ec);
-        // r.F of the pair: lB q_i q_j (erfc(sqrt(a) r)/r + 2 sqrt(a/pi) e^{-a r^2})
-        if (k.vir) acc.wc = fmaf(0.5f * lbqi * qj, fmaf(k.two_sa_spi, ex, pot), acc.wc);
-    }
-    if (r2 < k.lj_rc2) {
-        const float inv_r2 = inv_r * inv_r;
-        const float sr2 = k.lj_s2 * inv_r2;
-        const float sr6 = sr2 * sr2 * sr2;
-        const float mag = 24.f * k.lj_eps * (2.f * sr6 * sr6 - sr6) * inv_r2;
-        acc.fx = fmaf(-mag, dx, acc.fx);
-        acc.fy = fmaf(-mag, dy, acc.fy);
-        acc.fz = fmaf(-mag, dz, acc.fz);
-        acc.elj += 0.5f * (4.f * k.lj_eps * (sr6 * sr6 - sr6) + k.lj_shift);
-        if (k.vir) acc.wlj = fmaf(0.5f * mag, r2, acc.wlj);   // r.F = 24 eps (2 (s/r)^12 - (s/r)^6)
-    }
-}
 
 // Sum of a particle's R lanes (lanes l = 0 .. R-1 of its group), in lane
 // order; the result is valid in lane 0 of the group.
@@ -181,17 +110,6 @@ __device__ __forceinline__ uint32_t corner_of(int c, const SysDev& S) {
     return (uint32_t)c * S.corner_q + ((uint32_t)c * S.corner_r) / (uint32_t)S.ncd;
 }
 
-// Pair terms from two fixed-point records: the displacement is the 32-bit
-// difference of the coordinates, which is the minimum image (|r_ij| < L / 2),
-// rounded once to FP32 and scaled to length units.
-__device__ __forceinline__ void pair_fixed(const uint4& si, const uint4& sj, float Lu,
-                                           float lbqi, const PairConst& kc, PairAcc& acc) {
-    const float dx = (float)(int32_t)(sj.x - si.x) * Lu;
-    const float dy = (float)(int32_t)(sj.y - si.y) * Lu;
-    const float dz = (float)(int32_t)(sj.z - si.z) * Lu;
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    if (r2 > 0.f) pair_terms(dx, dy, dz, r2, __uint_as_float(sj.w), lbqi, kc, acc);
-}
 
 // One block per segment: nsc x-adjacent cells of one (y, z) row.  The block
 // copies, for each of the 9 neighbour rows, the segment's cells plus one halo
@@ -558,159 +476,6 @@ __global__ void __launch_bounds__(kBlockP) k_list_build(const __grid_constant__ 
     const unsigned wmax = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
     if ((t & 31) == 0 && wmax) atomicMax(la.stats + 1, (unsigned long long)wmax);
     if (blockIdx.x == 0 && t == 0) atomicAdd(la.stats, 1ull);
-}
-
-constexpr int kListU = 8;           // list entries per lane and batch of the list pass
-
-// The MD step's real-space pass over the list: R lanes per particle (adjacent
-// lanes) take every R-th entry of the particle's list and the pair terms of
-// those within the cutoffs (eight gathers in flight per lane); the lanes' sums
-// are added and stored per particle.  It needs nothing from the Fourier part,
-// so it runs concurrently with the structure factors (and, when the list
-// stands, with the no-op rebuild kernels); the Fourier-force kernel then
-// completes the step.
-//
-// FM (forces calls): the pass runs once, after the rebuild and the Fourier
-// force, and assembles per particle the total force (+ F^F), dE/dq (+ the
-// Fourier part, self and background terms) and per-block FP64 partials of the
-// real-space and LJ energies and virials, as the cell-scan pass does.
-template <int R, bool ONE, bool FM>
-__global__ void __launch_bounds__(kBlockP) k_real_list(const __grid_constant__ RealArgs a) {
-    constexpr int T = kBlockP / R;               // particles per block
-    const Tile tl = tile_of<ONE>(a.lw);
-    if constexpr (!FM) {
-        // launched twice per step: right after the prep kernel (works when the
-        // list stands) and after the rebuild (works when the list was rebuilt)
-        if ((*a.list_flag != 0) != (a.list_when != 0)) return;
-    } else {
-        if (a.flag_clear && blockIdx.x == 0 && threadIdx.x == 0) *a.flag_clear = 0;
-    }
-    const int sys = tl.sys;
-    const SysDev& S = sys_of<ONE>(a.lw, sys);
-    const int p = threadIdx.x / R, l = threadIdx.x - p * R;
-    const bool do_real = (a.parts & kPartReal) != 0;
-    const bool do_lj = (a.parts & kPartLJ) != 0 && S.lj_eps != 0.0;
-    PairConst kc;
-    kc.rc2 = do_real ? S.f_rc2 : 0.f;
-    kc.lj_rc2 = do_lj ? S.f_lj_rc2 : 0.f;
-    kc.alpha = S.f_alpha;
-    kc.sa = S.f_sqrt_alpha;
-    kc.two_sa_spi = S.f_two_sa_spi;
-    kc.lB = S.f_lB;
-    kc.lj_s2 = S.f_lj_sigma2;
-    kc.lj_eps = S.f_lj_eps;
-    kc.lj_shift = S.f_lj_shift;
-    kc.vir = FM && a.blk_w != nullptr;
-    PairAcc acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (p < tl.count && (do_real || do_lj)) {
-        const int i = tl.first + p;
-        const uint4 si = a.spos[i];
-        const float lbqi = kc.lB * __uint_as_float(si.w);
-        const float Lu = S.L_over_2_32;
-        const int* nb = a.nbr + i;
-        const size_t st = (size_t)a.nbr_stride;
-        // batches of kListU entries per lane, all gathers of a batch in flight
-        // at once; the first batch is loaded alongside the count (slots within
-        // the capacity always hold valid indices: the list starts zeroed).  The
-        // list is read once per step: streaming loads, so that it does not
-        // evict the records the gathers hit in L2.
-        const int cnt = __ldcs(a.ncnt + i);
-        int j[kListU];
-#pragma unroll
-        for (int q = 0; q < kListU; ++q) {
-            const int kk = l + q * R;
-            j[q] = kk < a.nbr_cap ? __ldcs(nb + (size_t)kk * st) : 0;
-        }
-        for (int k0 = l;;) {
-            uint4 sj[kListU];
-#pragma unroll
-            for (int q = 0; q < kListU; ++q) {
-                if (!RBE_IN_BOUNDS(j[q], a.nbr_stride, a.err)) j[q] = i;
-                sj[q] = __ldg(a.spos + j[q]);
-            }
-#pragma unroll
-            for (int q = 0; q < kListU; ++q)
-                if (k0 + q * R < cnt) pair_fixed(si, sj[q], Lu, lbqi, kc, acc);
-            k0 += kListU * R;
-            if (k0 >= cnt) break;
-#pragma unroll
-            for (int q = 0; q < kListU; ++q) {
-                const int kk = k0 + q * R;
-                j[q] = kk < cnt ? __ldcs(nb + (size_t)kk * st) : 0;
-            }
-        }
-    }
-    float fx = acc.fx, fy = acc.fy, fz = acc.fz, ph = acc.phr;
-    float ec = acc.ec, el = acc.elj, wc = acc.wc, wl = acc.wlj;
-    if constexpr (R > 1) {
-#pragma unroll
-        for (int o = R / 2; o > 0; o >>= 1) {
-            fx += __shfl_down_sync(0xffffffffu, fx, o, R);
-            fy += __shfl_down_sync(0xffffffffu, fy, o, R);
-            fz += __shfl_down_sync(0xffffffffu, fz, o, R);
-            if constexpr (FM) {
-                ph += __shfl_down_sync(0xffffffffu, ph, o, R);
-                ec += __shfl_down_sync(0xffffffffu, ec, o, R);
-                el += __shfl_down_sync(0xffffffffu, el, o, R);
-                wc += __shfl_down_sync(0xffffffffu, wc, o, R);
-                wl += __shfl_down_sync(0xffffffffu, wl, o, R);
-            }
-        }
-        __shared__ float4 s_f[T];
-        __shared__ float4 s_e[FM ? T : 1];
-        if (p < tl.count && l == 0) {
-            s_f[p] = make_float4(fx, fy, fz, ph);
-            if constexpr (FM) s_e[p] = make_float4(ec, el, wc, wl);
-        }
-        __syncthreads();
-        if ((int)threadIdx.x < tl.count) {
-            const float4 f = s_f[threadIdx.x];
-            fx = f.x; fy = f.y; fz = f.z; ph = f.w;
-            if constexpr (FM) {
-                const float4 e = s_e[threadIdx.x];
-                ec = e.x; el = e.y; wc = e.z; wl = e.w;
-            }
-        }
-    }
-    if constexpr (!FM) {
-        // the real-space force in the caller's order, for the Fourier-force
-        // kernel that adds its part and applies the thermostat
-        if ((int)threadIdx.x < tl.count) {
-            const int o = a.perm[tl.first + threadIdx.x];
-            if (RBE_IN_BOUNDS(o, a.nbr_stride, a.err)) a.freal[o] = make_float4(fx, fy, fz, 0.f);
-        }
-    } else {
-        double e_c = 0.0, e_l = 0.0, w_c = 0.0, w_l = 0.0;
-        if ((int)threadIdx.x < tl.count) {
-            const int i = tl.first + threadIdx.x;
-            const int o = a.perm[i];
-            float phi = ph;
-            if (a.parts & kPartFourier) {
-                const float4 f = a.fs[o];
-                fx += f.x; fy += f.y; fz += f.z;
-                if (a.phi_out) {
-                    const double qi = (double)__uint_as_float(a.spos[i].w);
-                    const double qs = (double)(long long)__ldcg(a.qsum_fx + sys) / kQScale;
-                    phi += f.w - (float)(2.0 * S.self_coef * qi + S.bg_coef * qs);
-                }
-            }
-            if (a.F_out) a.F_out[o] = make_float4(fx, fy, fz, 0.f);
-            if (a.phi_out) a.phi_out[o] = phi;
-            e_c = (double)ec;
-            e_l = (double)el;
-            w_c = (double)wc;
-            w_l = (double)wl;
-        }
-        if (a.blk_e) {
-            const double2 r = block_sum2_real(e_c, e_l);
-            if (threadIdx.x == 0) a.blk_e[blockIdx.x] = r;
-        }
-        if (a.blk_w) {
-            __syncthreads();                            // the partial buffers are reused
-            const double2 r = block_sum2_real(w_c, w_l);
-            if (threadIdx.x == 0) a.blk_w[blockIdx.x] = r;
-        }
-    }
 }
 
 // ----------------------------------------------------------------- FP64

@@ -11,10 +11,12 @@ rbe_step_ex and compare it with
   Eq. force and Eq. Ljpotential) at the positions the step started from and
   the step's own k-batch: rel-RMS <= 1e-5 and a per-particle bound;
 * a forces call of a handle without a neighbour list (the cell scan) at the
-  same positions and step: the Fourier part is computed from the same
-  fixed-point structure factors, so the two differ by FP32 summation order
-  only (per particle <= 1e-5 + 1e-6 |F|, while one pair within r_c missing
-  from the list moves a force by ~1e-4).
+  same positions and step, with the same structure-factor chunk: the Fourier
+  part is computed from the same fixed-point structure factors (the FP32
+  partial sums of rho(k) run over the same particles in the same order), so
+  the two differ by FP32 summation order only (per particle <= 1e-5 +
+  1e-6 |F|, while one pair within r_c missing from the list moves a force by
+  ~1e-4).
 
 At N = 8001 every lane split of both kernels runs (1, 2, 4, 8 threads per
 particle; 1 means two particles per thread in the Fourier force); at N = 2^20
@@ -84,6 +86,7 @@ def test_md_step_kernels_every_split_n8001(rbe, force_split, list_split):
     h.set_tuning(128, force_split, 3, 0, list_split)
     h.set_graph(True)
     hc = rbe.RBE(rbe.params_from(_no_list(wl.params), n_max=wl.n))
+    hc.set_tuning(128, 0, 0, 0, 0)
     pos, vel = _state(wl, torch)
     step = torch.zeros(1, dtype=torch.int64, device="cuda")
     # step 0 builds the list (the pass after the rebuild), step 3 walks the
@@ -133,6 +136,7 @@ def test_md_step_kernels_at_2p20_in_the_benchmark_launch_shapes(rbe, large):
               (tuned[0], 1, tuned[2], tuned[3], 1)]
     for shape in shapes:
         h.set_tuning(*shape)
+        hc.set_tuning(shape[0], 0, 0, 0, 0)
         h.step(pos, vel, 1, step)             # the list is rebuilt after a tuning change
         before, F, k = _step_force(h, pos, vel, step, torch)
         assert h.get_tuning() == shape
@@ -150,3 +154,65 @@ def test_md_step_kernels_at_2p20_in_the_benchmark_launch_shapes(rbe, large):
         print("  largest |dF| against the cell scan over all 2^20:", worst)
     h.close()
     hc.close()
+
+
+def _fusion_pair(rbe, wl, tuning, torch):
+    hf = rbe.RBE(rbe.params_from(wl.params, n_max=wl.n))
+    hs = rbe.RBE(rbe.params_from(wl.params, n_max=wl.n))
+    hs.set_fusion(False)
+    for h in (hf, hs):
+        h.set_tuning(*tuning)
+        h.set_graph(True)
+    return hf, hs
+
+
+@pytest.mark.parametrize("list_split", [1, 2, 4, 8])
+def test_fused_and_separate_launches_agree_bitwise_n8001(rbe, list_split):
+    """The structure factors and the standing-list pass in one launch or in
+    two: the same trajectory to the last bit (rho(k) is summed in the same
+    order and added in fixed point; each particle's list terms are added by
+    the same lanes in the same order), over steps that build the list and
+    steps that walk it."""
+    import torch
+    wl = workloads.config_2to1_mixed()
+    hf, hs = _fusion_pair(rbe, wl, (128, 1, 3, 0, list_split), torch)
+    pf, vf = _state(wl, torch)
+    ps, vs = pf.clone(), vf.clone()
+    sf = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ss = sf.clone()
+    for s in range(6):
+        _, Ff, kf = _step_force(hf, pf, vf, sf, torch)
+        _, Fs, ks = _step_force(hs, ps, vs, ss, torch)
+        assert kf == ks == s
+        assert torch.equal(Ff, Fs), (list_split, s)
+        assert torch.equal(pf, ps) and torch.equal(vf, vs), (list_split, s)
+    # profiled, the fused launch has its own slot and the separate pass none
+    hf.profile(True)
+    _step_force(hf, pf, vf, sf, torch)
+    prof = hf.profile_read()
+    hf.profile(False)
+    assert prof["rho_list"][1] == 1 and prof["rho"][1] == 0, prof
+    hf.close()
+    hs.close()
+
+
+def test_fused_and_separate_launches_agree_bitwise_at_2p20(rbe, large):
+    """As above at N = 2^20 in the autotuned launch shapes."""
+    import torch
+    wl = large
+    h0 = rbe.RBE(rbe.params_from(wl.params, n_max=wl.n))
+    pf, vf = _state(wl, torch)
+    tuned = tuple(h0.autotune(pf))
+    h0.close()
+    hf, hs = _fusion_pair(rbe, wl, tuned, torch)
+    ps, vs = pf.clone(), vf.clone()
+    sf = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ss = sf.clone()
+    for s in range(4):
+        _, Ff, _ = _step_force(hf, pf, vf, sf, torch)
+        _, Fs, _ = _step_force(hs, ps, vs, ss, torch)
+        assert torch.equal(Ff, Fs), (tuned, s)
+        assert torch.equal(pf, ps) and torch.equal(vf, vs), (tuned, s)
+    print("2^20 fused vs separate: bitwise equal over 4 steps, shape", tuned)
+    hf.close()
+    hs.close()
