@@ -94,6 +94,8 @@ def parse(argv=None):
                     "real_split,real_seg,list_split (0 = the library's choice); empty: autotune")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
     ap.add_argument("--graph", action="store_true", help="profile case: graph replay")
+    ap.add_argument("--no-fusion", action="store_true", help="profile case: structure factors "
+                    "and the standing-list pass as two launches")
     return ap.parse_args(argv)
 
 
@@ -286,12 +288,15 @@ def reduce_sum(x, world, device):
 
 # --------------------------------------------------------------------- roofline
 def source_hash(kernel_file):
-    """Hash of a kernel's source file together with the shared device header
-    it includes (a change to either makes committed counters stale)."""
+    """Hash of a kernel's source file, the device headers next to it and the
+    compiler flags (a change to any of them makes committed counters stale)."""
+    import glob as _glob
+    from paper_2010_01559_gb300 import build as _build
     h = hashlib.sha256(open(kernel_file, "rb").read())
-    hdr = os.path.join(os.path.dirname(kernel_file), "rbe_internal.cuh")
-    if os.path.exists(hdr):
+    for hdr in sorted(_glob.glob(os.path.join(os.path.dirname(kernel_file), "*.cuh"))):
         h.update(open(hdr, "rb").read())
+    h.update(" ".join(_build.ARCH + [f for f in _build.NVCC_FLAGS
+                                     if not os.path.isabs(f)]).encode())
     return h.hexdigest()[:16]
 
 
@@ -1091,6 +1096,7 @@ def profile_case(args):
     elif args.precision == "mixed":
         h.autotune(pos)
     h.set_graph(args.graph)
+    h.set_fusion(not args.no_fusion)
     step = torch.zeros(1, dtype=torch.int64, device="cuda")
     h.step(pos, vel, args.warmup, step)
     torch.cuda.synchronize()
@@ -1103,6 +1109,7 @@ def profile_case(args):
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     print(json.dumps({"workload": wl.name, "N": wl.n, "tuning": list(h.get_tuning()),
+                      "fusion": not args.no_fusion,
                       "steps": args.steps, "ms_per_step": e0.elapsed_time(e1) / args.steps}))
     h.close()
 

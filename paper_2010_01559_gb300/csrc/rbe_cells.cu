@@ -21,15 +21,23 @@
 
 namespace rbe {
 
+// FP32 and 32-bit integer work only (64-bit conversions would go through the
+// FP64 pipe, which is narrow on this part): the integer pr is first reduced
+// modulo 2^32 in FP32, exactly, to r in [-2^31, 2^31] (for |pr| >= 2^31 the
+// result is a multiple of ulp(pr) >= 2^8 below 2^31 in magnitude, so it is a
+// float; below that pr is left as it is).  Same fraction as the 64-bit sum
+// ip + ic mod 2^32 for |x| < 2^31 L.
 __device__ __forceinline__ uint32_t to_fixed(float x, float hi, float lo) {
     const float p = x * hi;
     const float e = fmaf(x, hi, -p);       // exact: x * hi = p + e
     float corr = fmaf(x, lo, e);
     const float pr = rintf(p);
     corr += (p - pr);                      // exact (p and pr differ by < 1 ulp-scale)
-    const long long ip = (long long)pr;
-    const long long ic = __float2ll_rn(corr);
-    return (uint32_t)(unsigned long long)(ip + ic);
+    const float n = rintf(pr * 2.3283064365386963e-10f);        // pr / 2^32, nearest
+    const float r = fmaf(-4294967296.0f, n, pr);                 // exact, |r| <= 2^31
+    // 2^31 and -2^31 are the same fraction; the conversion saturates at 2^31 - 1
+    const uint32_t ur = r >= 2147483648.0f ? 0x80000000u : (uint32_t)__float2int_rz(r);
+    return ur + (uint32_t)__float2int_rn(corr);
 }
 
 __device__ __forceinline__ int cell_of_fixed(uint32_t s, int ncd) {
@@ -317,8 +325,10 @@ k_prep_mixed(const __grid_constant__ Work w, const float4* __restrict__ pos_q,
         }
         const uint4 rec = make_uint4(sx, sy, sz, __float_as_uint(p.w));
         fx[i] = rec;
-        qs = (double)p.w;
-        q2s = (double)p.w * (double)p.w;
+        if (pa.want_q) {
+            qs = (double)p.w;
+            q2s = (double)p.w * (double)p.w;
+        }
         if (pa.list_flag) {
             // neighbour-list step: the record goes to its sorted slot of the
             // last build, and a displacement beyond skin/2 since that build

@@ -242,6 +242,37 @@ def test_positions_outside_box_are_wrapped(rbe, c1):
     assert rel_rms(G1[:, :3].cpu().numpy(), G0[:, :3].cpu().numpy()) <= 1e-11
 
 
+def test_whole_box_shifts_give_the_same_fixed_point_records(rbe):
+    """L = 16 and positions on a 2^-12 grid, so that x + 16 m is exact in
+    float32 for |m| <= 128: the fixed-point fraction round(2^32 x / L) mod 2^32
+    is then the same for every shift, and so is every force to the last bit
+    (both real-space paths).  The shifts take 2^32 x / L through
+    [-2^39, 2^39]: the modulo-2^32 reduction, negative inputs, and x = L/2,
+    whose product 2^31 is the one value that converts through the tie."""
+    import torch
+    wl = workloads.electrolyte_1to1(256, 0.0625, 0.5, 5.0, 64, seed=11)
+    assert abs(wl.params.box - 16.0) < 1e-9
+    wl.params.box = 16.0
+    wl.pos = (np.floor(wl.pos.astype(np.float64) * 4096.0) / 4096.0).astype(np.float32)
+    wl.pos[0, 0] = np.float32(8.0)
+    for path in ("list", "cells"):
+        h = _handle(rbe, wl, path=path)
+        x = _dev(wl)
+        F0, E0, _ = h.forces(x, 3)
+        for m in [(1, 0, 0), (-1, 2, -3), (100, -127, 64), (-128, 127, 1), (0, 0, -1)]:
+            sh = torch.tensor(m, dtype=torch.float32, device="cuda") * 16.0
+            y = x.clone()
+            y[:, :3] += sh
+            back = y[:, :3].double() - sh.double()
+            assert torch.equal(back, x[:, :3].double()), m          # the shift is exact
+            F1, E1, _ = h.forces(y, 3)
+            assert torch.equal(F1, F0), (path, m)
+            assert torch.equal(E1, E0), (path, m)
+        ref = oracle_eval(wl, 3)
+        assert rel_rms(F0[:, :3].cpu().numpy(), ref["F"]) <= TOL_MIXED
+        h.close()
+
+
 def test_non_neutral_charges_background(rbe):
     wl = workloads.electrolyte_1to1(600, 0.064, 0.3, 5.0, 64, seed=3)
     wl.q[:7] = np.float32(0.5)            # sum q != 0
