@@ -696,7 +696,7 @@ def measure_water_autograd(rbe, torch, dev, stream, flush, units, K=20):
     return {"workload": wl.name, "N": wl.n, "P": wl.params.P, "ms_per_fwd_bwd": ms,
             "fwd_bwd_per_s": 1e3 / ms, "particle_steps_per_s": wl.n / (ms / 1e3),
             "iterations": K,
-            "kernels_avg_us": {k: (t / c * 1e3 if c else 0.0) for k, (t, c) in prof.items()},
+            "kernels_avg_us": {k: t / c * 1e3 for k, (t, c) in prof.items() if c},
             "sfu_roofline": {"bound": "alu", "achieved": sfu_ops / (ms / 1e3) / 1e12,
                              "peak": units["sfu"], "unit": "Tsfu/s",
                              "frac": sfu_ops / (ms / 1e3) / 1e12 / units["sfu"],
