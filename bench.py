@@ -94,8 +94,11 @@ def parse(argv=None):
                     "real_split,real_seg,list_split (0 = the library's choice); empty: autotune")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
     ap.add_argument("--graph", action="store_true", help="profile case: graph replay")
-    ap.add_argument("--no-fusion", action="store_true", help="profile case: structure factors "
-                    "and the standing-list pass as two launches")
+    ap.add_argument("--fusion", choices=["auto", "on", "off"], default="auto",
+                    help="profile case: structure factors and the standing-list pass in one "
+                    "launch (on), two (off), or as the library chooses (auto)")
+    ap.add_argument("--no-fusion", dest="fusion", action="store_const", const="off",
+                    help="profile case: same as --fusion off")
     return ap.parse_args(argv)
 
 
@@ -616,12 +619,13 @@ def measure_system(rbe, torch, wl, dev, stream, flush, peaks, units, K=200):
     per-kernel profile and rooflines, the FP64 path and an MD step's accuracy."""
     h, pos, vel, step, tuning = md_handle(rbe, torch, wl, dev, stream)
     ms = timed_steps(torch, h, pos, vel, step, K, stream, flush)
+    fused = h.get_fusion()
     timed_steps(torch, h, pos, vel, step, max(3, K // 4), stream, flush, profile=True)
     prof_step = h.profile_read()
     h.set_fusion(False)
     timed_steps(torch, h, pos, vel, step, max(3, K // 4), stream, flush, profile=True)
     prof = h.profile_read()
-    h.set_fusion(True)
+    h.set_fusion(None)
     acc = step_accuracy(torch, h, pos, vel, step, stream)
     h.close()
     h64 = rbe.RBE(rbe.params_from(wl.params, n_max=wl.n))
@@ -638,6 +642,7 @@ def measure_system(rbe, torch, wl, dev, stream, flush, peaks, units, K=200):
     return {"workload": wl.name, "N": wl.n, "P": wl.params.P, "alpha": wl.params.alpha,
             "r_c": wl.params.r_c, "value": value, "unit": UNIT, "steps": K,
             "ms_per_step": ms / K, "force_evals_per_s": K / (ms / 1e3), "tuning": list(tuning),
+            "fused_list_step": fused,
             "kernels_avg_us": {k: t / c * 1e3 for k, (t, c) in prof.items() if c},
             "step_kernels_avg_us": {k: t / c * 1e3 for k, (t, c) in prof_step.items() if c},
             "roofline": roofline(prof_step, wl, peaks, units, counts=counts),
@@ -820,13 +825,14 @@ def run_ours(args):
     # per-kernel profile of the same steps (events around each kernel): once as
     # the timed steps run them (structure factors and standing-list pass in one
     # launch), once with the two launched apart, each timed alone
+    fused = h.get_fusion()
     nprof = max(3, min(K, 50))
     timed_steps(torch, h, pos, vel, step_dev, nprof, stream, flush, profile=True)
     prof_step = h.profile_read()
     h.set_fusion(False)
     timed_steps(torch, h, pos, vel, step_dev, nprof, stream, flush, profile=True)
     prof = h.profile_read()
-    h.set_fusion(True)
+    h.set_fusion(None)
     kernels_us = {k: (ms / c * 1e3 if c else 0.0) for k, (ms, c) in prof.items() if c}
     step_kernels_us = {k: (ms / c * 1e3 if c else 0.0) for k, (ms, c) in prof_step.items()
                        if c}
@@ -861,6 +867,7 @@ def run_ours(args):
                        "tuning": {"rho_chunk": tuning[0], "force_split": tuning[1],
                                   "real_split": tuning[2], "real_seg": tuning[3],
                                   "list_split": tuning[4]},
+                       "fused_list_step": fused,
                        "parallelism": f"replicas x{world}"},
             "force_evals_per_s": value / wl.n,
             "clocks": hl["clocks"],
@@ -1096,7 +1103,7 @@ def profile_case(args):
     elif args.precision == "mixed":
         h.autotune(pos)
     h.set_graph(args.graph)
-    h.set_fusion(not args.no_fusion)
+    h.set_fusion({"auto": None, "on": True, "off": False}[args.fusion])
     step = torch.zeros(1, dtype=torch.int64, device="cuda")
     h.step(pos, vel, args.warmup, step)
     torch.cuda.synchronize()
@@ -1109,7 +1116,7 @@ def profile_case(args):
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     print(json.dumps({"workload": wl.name, "N": wl.n, "tuning": list(h.get_tuning()),
-                      "fusion": not args.no_fusion,
+                      "fused_list_step": h.get_fusion(),
                       "steps": args.steps, "ms_per_step": e0.elapsed_time(e1) / args.steps}))
     h.close()
 

@@ -313,17 +313,23 @@ rbe_status rbe_set_tuning(rbe_handle h, const rbe_tuning *t);
 rbe_status rbe_get_tuning(rbe_handle h, rbe_tuning *t);
 
 /* Fusion of a mixed-precision list MD step (rbe_step*, rbe_step_ex): with
- * on = 1 (the default) the structure factors (Eq. rbmapprox's rho(k)) and the
- * real-space pass over a standing neighbour list run as one launch whose
- * blocks take either kind of work, so that every SM runs both; with on = 0 they
- * are two launches on two streams.  The results are the same to the last bit
- * either way.  Captured step graphs are dropped.  RBE_ERR_ARG unless on is 0
- * or 1. */
+ * on = 1 the structure factors (Eq. rbmapprox's rho(k)) and the real-space
+ * pass over a standing neighbour list run as one launch whose blocks take
+ * either kind of work, so that every SM runs both; with on = 0 they are two
+ * launches on two streams; with on = -1 (the default) rbe_autotune times a
+ * list evaluation both ways and keeps the faster, and before any autotune
+ * systems of 2^19 particles and more (over all replicas) fuse.  The results
+ * are the same to the last bit either way.  Captured step graphs are
+ * dropped.  RBE_ERR_ARG unless on is -1, 0 or 1. */
 rbe_status rbe_set_fusion(rbe_handle h, int32_t on);
+
+/* *on = 1 if a list MD step at the current particle count runs fused, else 0. */
+rbe_status rbe_get_fusion(rbe_handle h, int32_t *on);
 
 /* Time the candidate launch shapes of each tunable kernel on the given input
  * (device pos_q, n particles) with CUDA events, keep the fastest and return
- * them in *out (nullable). */
+ * them in *out (nullable).  With a neighbour list and fusion automatic it also
+ * chooses between the fused and the separate list step (rbe_set_fusion). */
 rbe_status rbe_autotune(rbe_handle h, int32_t n, const float *pos_q, rbe_tuning *out);
 
 /* Kernels of one evaluation, in launch order (per-kernel profile indices). */

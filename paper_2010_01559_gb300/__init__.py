@@ -116,8 +116,16 @@ class _HandleBase:
 
     def set_fusion(self, on):
         """Structure factors and the standing-list pass of a mixed list MD
-        step in one launch (True, the default) or two (``rbe_set_fusion``)."""
-        capi.check(self.lib.rbe_set_fusion(self._h, 1 if on else 0), self._h)
+        step in one launch (True), two (False), or chosen by the autotuner
+        and the system size (None, the default) (``rbe_set_fusion``)."""
+        v = -1 if on is None else (1 if on else 0)
+        capi.check(self.lib.rbe_set_fusion(self._h, v), self._h)
+
+    def get_fusion(self):
+        """Whether a list MD step at the current particle count runs fused."""
+        v = ctypes.c_int32(0)
+        capi.check(self.lib.rbe_get_fusion(self._h, ctypes.byref(v)), self._h)
+        return bool(v.value)
 
     def set_tuning(self, rho_chunk=0, force_split=0, real_split=0, real_seg=0, list_split=0):
         t = capi.rbe_tuning(rho_chunk, force_split, real_split, real_seg, list_split)

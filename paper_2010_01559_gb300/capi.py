@@ -84,6 +84,7 @@ _SIGS = {
     "rbe_sync": ([_H], ctypes.c_int),
     "rbe_set_wait_limit": ([_H, ctypes.c_double], ctypes.c_int),
     "rbe_set_fusion": ([_H, ctypes.c_int32], ctypes.c_int),
+    "rbe_get_fusion": ([_H, _P], ctypes.c_int),
     "rbe_set_tuning": ([_H, ctypes.POINTER(rbe_tuning)], ctypes.c_int),
     "rbe_get_tuning": ([_H, ctypes.POINTER(rbe_tuning)], ctypes.c_int),
     "rbe_autotune": ([_H, ctypes.c_int32, _P, ctypes.POINTER(rbe_tuning)], ctypes.c_int),

@@ -167,7 +167,12 @@ struct rbe_ctx {
     size_t max_part = 0;
     bool use_graph = false;
     double wait_limit = 0.0;                  // seconds a host wait may take (0: no limit)
-    bool fuse_list = true;                    // list steps: structure factors + list pass fused
+    // list steps: structure factors + standing-list pass in one launch:
+    // fusion_mode -1 automatic, 0 off, 1 on; fuse_tuned the autotuner's choice
+    // (-1 before the first autotune: then systems of kFuseMinN particles and
+    // more fuse)
+    int fusion_mode = -1;
+    int fuse_tuned = -1;
     std::vector<GraphEntry> graphs;
     std::string err;
     // per-kernel profile
@@ -413,6 +418,19 @@ void fill_sysdev(const SysHost& s, SysDev& d) {
     d.f_half_skin2 = (float)(0.25 * s.skin * s.skin * (1.0 - 1e-5));
     d.corner_q = (uint32_t)(4294967296ull / (unsigned long long)std::max(1, s.ncd));
     d.corner_r = (uint32_t)(4294967296ull - (unsigned long long)d.corner_q * std::max(1, s.ncd));
+}
+
+// Smallest system (particles over all replicas) that fuses the structure
+// factors with the standing-list pass when no autotune has chosen: one launch
+// of both kinds of block gains once each kind alone fills the GPU (2^20: 0.58
+// against 0.62 ms per step; 2^18: 0.176 against 0.172 ms).
+constexpr long long kFuseMinN = 1LL << 19;
+
+bool fusion_on(const rbe_ctx* h) {
+    if (h->fusion_mode >= 0) return h->fusion_mode == 1;
+    if (h->fuse_tuned >= 0) return h->fuse_tuned == 1;
+    const long long ntot = h->batch ? h->ntot : std::max(h->cur_n, 0);
+    return ntot >= kFuseMinN;
 }
 
 int auto_chunk(const rbe_ctx* h, long long ntot) {
@@ -962,7 +980,7 @@ int enqueue_eval(rbe_ctx* h, cudaStream_t st, const EvalArgs& a) {
     cudaStream_t st2 = prof ? st : h->stream2;
     // a list step's structure factors and standing-list pass share one launch
     // (timed as RBE_K_RHO_LIST when profiling)
-    const bool fused = a.list && mixed && (a.parts & RBE_PART_FOURIER) && h->fuse_list;
+    const bool fused = a.list && mixed && (a.parts & RBE_PART_FOURIER) && fusion_on(h);
     bool used[RBE_K_COUNT] = {};
     int count = 0;
     auto run = [&](int kid, cudaStream_t s, auto&& launch) {
@@ -1762,10 +1780,17 @@ rbe_status rbe_set_wait_limit(rbe_handle h, double seconds) {
 
 rbe_status rbe_set_fusion(rbe_handle h, int32_t on) {
     if (!h) return fail(nullptr, RBE_ERR_ARG, "null handle");
-    if (on != 0 && on != 1) return fail(h, RBE_ERR_ARG, "fusion must be 0 or 1");
-    h->fuse_list = on != 0;
+    if (on != -1 && on != 0 && on != 1)
+        return fail(h, RBE_ERR_ARG, "fusion must be -1 (automatic), 0 or 1");
+    h->fusion_mode = on;
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
+    return RBE_OK;
+}
+
+rbe_status rbe_get_fusion(rbe_handle h, int32_t* on) {
+    if (!h || !on) return fail(h, RBE_ERR_ARG, "null argument");
+    *on = fusion_on(h) ? 1 : 0;
     return RBE_OK;
 }
 
@@ -1882,55 +1907,93 @@ rbe_status rbe_autotune(rbe_handle h, int32_t n, const float* pos_q, rbe_tuning*
     h->real_split = best_rsplit;
     h->real_seg = best_seg;
     // neighbour-list pass: lanes per particle, timed on a list built for this
-    // input.  With fusion on it is timed inside the launch it shares with the
+    // input.  Fused, it is timed inside the launch it shares with the
     // structure factors, and the structure-factor chunk is re-chosen with it
-    // (the shapes fastest alone are not always the fastest together).
+    // (the shapes fastest alone are not always the fastest together).  With
+    // fusion automatic both forms are tuned, a whole list evaluation is timed
+    // in each, and the faster is kept.
     int best_lsplit = 0;
     if (h->list) {
-        best = 1e30f;
-        std::vector<int> chunks{best_chunk};
-        if (h->fuse_list) {
-            if (best_chunk / 2 >= 32) chunks.insert(chunks.begin(), best_chunk / 2);
-            if (best_chunk * 2 <= 4096) chunks.push_back(best_chunk * 2);
-        }
-        int best_fchunk = best_chunk;
-        for (int c : chunks) {
-            h->rho_chunk = c;
-            for (int ls = 1; ls <= 8 && s == RBE_OK; ls <<= 1) {
-                h->list_split = ls;
-                if ((s = prepare(h, n)) != RBE_OK) break;
-                EvalArgs b = a;
-                b.list = true;
-                RBE_CUDA(h, cudaMemsetAsync(h->d_list_flag, 0xFF, sizeof(int), h->stream));
-                enqueue_eval(h, h->stream, b);
-                RealArgs r = make_real_args(h, RBE_PART_ALL);
-                r.F_out = h->d_stage_F;
-                r.lw = make_work(h, h->d_lblk, kBlockP / h->lsplit, 0);
-                r.nlblk = h->nlblk;
-                r.lsplit = h->lsplit;
-                r.nbr = h->d_nbr;
-                r.ncnt = h->d_ncnt;
-                r.nbr_stride = std::max(h->ntot, 1);
-                r.nbr_cap = h->list_cap;
-                r.list_flag = h->d_list_flag;
-                r.list_when = 0;
-                r.freal = h->d_freal;
-                const int ltiles = (h->pmax + kRhoKT - 1) / kRhoKT;
-                const float t = time_kernel(h, e0, e1, [&] {
-                    if (h->fuse_list)
-                        launch_rho_list(h->stream, !h->batch,
-                                        make_work(h, h->d_chunks, h->cur_chunk, 1), h->nchunks,
-                                        ltiles, h->d_ksamp, h->d_kcoef, h->d_fx, h->d_rho_fx,
-                                        h->d_kcnt, h->d_kab, r, false);
-                    else
-                        launch_real_list(h->stream, !h->batch, r);
-                });
-                if (t < best) { best = t; best_lsplit = ls; best_fchunk = c; }
+        const int mode = h->fusion_mode;
+        const int rho_best_chunk = best_chunk;
+        auto build_list = [&](EvalArgs& b) -> rbe_status {
+            rbe_status st = prepare(h, n);
+            if (st != RBE_OK) return st;
+            b = a;
+            b.list = true;
+            RBE_CUDA(h, cudaMemsetAsync(h->d_list_flag, 0xFF, sizeof(int), h->stream));
+            enqueue_eval(h, h->stream, b);
+            return RBE_OK;
+        };
+        // the list split (and, fused, the chunk) of one form: its best kernel time
+        auto tune_form = [&](bool fused, int& out_chunk, int& out_ls) {
+            h->fusion_mode = fused ? 1 : 0;
+            std::vector<int> chunks{rho_best_chunk};
+            if (fused) {
+                if (rho_best_chunk / 2 >= 32) chunks.insert(chunks.begin(), rho_best_chunk / 2);
+                if (rho_best_chunk * 2 <= 4096) chunks.push_back(rho_best_chunk * 2);
             }
+            float bt = 1e30f;
+            out_chunk = rho_best_chunk;
+            out_ls = 1;
+            for (int c : chunks) {
+                h->rho_chunk = c;
+                for (int ls = 1; ls <= 8 && s == RBE_OK; ls <<= 1) {
+                    h->list_split = ls;
+                    EvalArgs b{};
+                    if ((s = build_list(b)) != RBE_OK) break;
+                    RealArgs r = make_real_args(h, RBE_PART_ALL);
+                    r.F_out = h->d_stage_F;
+                    r.lw = make_work(h, h->d_lblk, kBlockP / h->lsplit, 0);
+                    r.nlblk = h->nlblk;
+                    r.lsplit = h->lsplit;
+                    r.nbr = h->d_nbr;
+                    r.ncnt = h->d_ncnt;
+                    r.nbr_stride = std::max(h->ntot, 1);
+                    r.nbr_cap = h->list_cap;
+                    r.list_flag = h->d_list_flag;
+                    r.list_when = 0;
+                    r.freal = h->d_freal;
+                    const int ltiles = (h->pmax + kRhoKT - 1) / kRhoKT;
+                    const float t = time_kernel(h, e0, e1, [&] {
+                        if (fused)
+                            launch_rho_list(h->stream, !h->batch,
+                                            make_work(h, h->d_chunks, h->cur_chunk, 1),
+                                            h->nchunks, ltiles, h->d_ksamp, h->d_kcoef, h->d_fx,
+                                            h->d_rho_fx, h->d_kcnt, h->d_kab, r, false);
+                        else
+                            launch_real_list(h->stream, !h->batch, r);
+                    });
+                    if (t < bt) { bt = t; out_chunk = c; out_ls = ls; }
+                }
+            }
+        };
+        // a whole evaluation over the standing list in one form and shape
+        auto time_form = [&](bool fused, int chunk, int ls) -> float {
+            h->fusion_mode = fused ? 1 : 0;
+            h->rho_chunk = chunk;
+            h->list_split = ls;
+            EvalArgs b{};
+            if ((s = build_list(b)) != RBE_OK) return 1e30f;
+            return time_kernel(h, e0, e1, [&] { enqueue_eval(h, h->stream, b); });
+        };
+        int fc = rho_best_chunk, fls = 1, sc = rho_best_chunk, sls = 1;
+        float tf = 1e30f, ts = 1e30f;
+        if (mode != 0 && s == RBE_OK) {
+            tune_form(true, fc, fls);
+            if (s == RBE_OK) tf = time_form(true, fc, fls);
         }
-        h->list_split = best_lsplit;
-        best_chunk = best_fchunk;
+        if (mode != 1 && s == RBE_OK) {
+            tune_form(false, sc, sls);
+            if (s == RBE_OK) ts = time_form(false, sc, sls);
+        }
+        const bool fuse = mode == 1 || (mode == -1 && tf < ts);
+        h->fusion_mode = mode;
+        if (mode == -1) h->fuse_tuned = fuse ? 1 : 0;
+        best_chunk = fuse ? fc : sc;
+        best_lsplit = fuse ? fls : sls;
         h->rho_chunk = best_chunk;
+        h->list_split = best_lsplit;
         h->list_valid = false;
     }
     h->prof_on = prof;

@@ -159,6 +159,7 @@ def test_md_step_kernels_at_2p20_in_the_benchmark_launch_shapes(rbe, large):
 def _fusion_pair(rbe, wl, tuning, torch):
     hf = rbe.RBE(rbe.params_from(wl.params, n_max=wl.n))
     hs = rbe.RBE(rbe.params_from(wl.params, n_max=wl.n))
+    hf.set_fusion(True)
     hs.set_fusion(False)
     for h in (hf, hs):
         h.set_tuning(*tuning)
@@ -216,3 +217,32 @@ def test_fused_and_separate_launches_agree_bitwise_at_2p20(rbe, large):
     print("2^20 fused vs separate: bitwise equal over 4 steps, shape", tuned)
     hf.close()
     hs.close()
+
+
+def test_fusion_choice(rbe):
+    """Automatic fusion: before an autotune a system of 2^19 particles or more
+    fuses and a smaller one does not; the autotuner's choice is reported; an
+    explicit setting holds through an autotune; -1, 0 and 1 are the only
+    settings."""
+    import torch
+    wl = workloads.config_2to1_mixed()
+    h = rbe.RBE(rbe.params_from(wl.params, n_max=wl.n))
+    pos, vel = _state(wl, torch)
+    step = torch.zeros(1, dtype=torch.int64, device="cuda")
+    h.step(pos, vel, 1, step)
+    assert h.get_fusion() is False
+    h.autotune(pos)
+    assert h.get_fusion() in (True, False)
+    h.set_fusion(True)
+    h.autotune(pos)
+    assert h.get_fusion() is True
+    h.step(pos, vel, 2, step)
+    with pytest.raises(rbe.RBEError):
+        rbe.capi.check(h.lib.rbe_set_fusion(h._h, 2), h._h)
+    h.close()
+    big = workloads.config_large(1 << 19)
+    hb = rbe.RBE(rbe.params_from(big.params, n_max=big.n))
+    pb, vb = _state(big, torch)
+    hb.step(pb, vb, 1, torch.zeros(1, dtype=torch.int64, device="cuda"))
+    assert hb.get_fusion() is True
+    hb.close()
