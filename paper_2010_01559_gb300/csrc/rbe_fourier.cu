@@ -124,6 +124,7 @@ __device__ __forceinline__ void rho_body(const Work& w, const int4* __restrict__
         if (any) {
             if constexpr (HALVES == 1) {
                 int j = 0;
+#pragma unroll 8
                 for (; j + 1 < cnt; j += 2) {
                     terms(sp[j], re, im);
                     terms(sp[j + 1], re_o, im_o);
@@ -345,7 +346,7 @@ k_force_mixed(const __grid_constant__ Work w, const uint4* __restrict__ rec,
             kf[k] = KForce{rp.x * (float)m.x, rp.x * (float)m.y, rp.x * (float)m.z, rp.x};
         }
         __syncthreads();
-#pragma unroll 4
+#pragma unroll 8
         for (int k = sub; k < cnt; k += SPLIT) {
             const KPhase a = kp[k];
             const KForce f = kf[k];
