@@ -246,3 +246,48 @@ def test_fusion_choice(rbe):
     hb.step(pb, vb, 1, torch.zeros(1, dtype=torch.int64, device="cuda"))
     assert hb.get_fusion() is True
     hb.close()
+
+
+def test_fused_and_separate_agree_bitwise_heterogeneous_batch(rbe):
+    """A batch of four systems of different size, P, cutoff and thermostat
+    (Langevin, Andersen, Nose-Hoover; one with r_c > L/3): the fused launch's
+    multi-system form against the separate launches, the same trajectory to
+    the last bit over steps that build the lists and steps that walk them, and
+    the fused step's force against the oracle per system."""
+    import torch
+    e = workloads.electrolyte_1to1
+    systems = [e(600, 0.05, 0.25, 5.5, 60, seed=31, stream=1),
+               e(900, 0.08, 0.35, 4.5, 150, seed=32, stream=2, thermostat=1, andersen_nu=20.0,
+                 dt=2e-3),
+               e(400, 0.064, 0.3, 5.0, 40, seed=33, stream=3, thermostat=2, nh_tau=0.05),
+               e(300, 0.064, 0.2, 6.0, 30, seed=34, stream=4)]
+    hs = []
+    for fuse in (True, False):
+        h = rbe.RBEBatch([rbe.params_from(w.params) for w in systems], [w.n for w in systems])
+        h.set_fusion(fuse)
+        h.set_graph(True)
+        hs.append(h)
+    states = []
+    for _ in hs:
+        pos = torch.from_numpy(np.concatenate([w.pos_q() for w in systems])).cuda()
+        vel = torch.zeros((pos.shape[0], 4), dtype=torch.float32, device="cuda")
+        vel[:, :3] = torch.from_numpy(np.concatenate([w.vel for w in systems])).cuda()
+        states.append((pos, vel, torch.zeros(1, dtype=torch.int64, device="cuda")))
+    for s in range(8):
+        outs = [_step_force(h, *st, torch) for h, st in zip(hs, states)]
+        (b0, F0, k0), (_, F1, k1) = outs
+        assert k0 == k1 == s
+        assert torch.equal(F0, F1), s
+        assert torch.equal(states[0][0], states[1][0]) and torch.equal(states[0][1], states[1][1])
+    off = 0
+    for w in systems:
+        w2 = copy.copy(w)
+        w2.pos = b0[off:off + w.n, :3].cpu().numpy()
+        ref = oracle_eval(w2, k0)
+        Fs = F0[off:off + w.n, :3].cpu().numpy()
+        assert rel_rms(Fs, ref["F"]) <= TOL_MIXED, w.name
+        assert_per_particle(Fs, ref["F"], w.name)
+        off += w.n
+    assert hs[0].get_fusion() is True and hs[1].get_fusion() is False
+    for h in hs:
+        h.close()
