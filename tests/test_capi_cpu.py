@@ -88,6 +88,8 @@ def test_null_arguments_are_rejected(lib):
     assert lib.rbe_nose_hoover_xi(None, None, 0) == capi.RBE_ERR_ARG
     assert lib.rbe_list_stats(None, None, None, None) == capi.RBE_ERR_ARG
     assert lib.rbe_step_ex(None, 0, None, None, 1, None, None) == capi.RBE_ERR_ARG
+    assert lib.rbe_set_fusion(None, 1) == capi.RBE_ERR_ARG
+    assert lib.rbe_get_fusion(None, None) == capi.RBE_ERR_ARG
     lib.rbe_destroy(None)
     n = ctypes.c_int32(0)
     assert lib.rbe_create_batch(None, ctypes.byref(n), 0, None) == capi.RBE_ERR_ARG
