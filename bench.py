@@ -290,14 +290,27 @@ def reduce_sum(x, world, device):
 
 
 # --------------------------------------------------------------------- roofline
+def _local_includes(path, seen):
+    """The file and the quoted #include files it reaches, in a fixed order."""
+    if path in seen or not os.path.exists(path):
+        return
+    seen.append(path)
+    for line in open(path, encoding="utf-8", errors="replace"):
+        s = line.strip()
+        if s.startswith("#include") and '"' in s:
+            _local_includes(os.path.join(os.path.dirname(path), s.split('"')[1]), seen)
+
+
 def source_hash(kernel_file):
-    """Hash of a kernel's source file, the device headers next to it and the
-    compiler flags (a change to any of them makes committed counters stale)."""
-    import glob as _glob
+    """Hash of a kernel's source file, the device headers it includes (directly
+    or through others) and the compiler flags: a change to any of them makes
+    committed counters stale."""
     from paper_2010_01559_gb300 import build as _build
-    h = hashlib.sha256(open(kernel_file, "rb").read())
-    for hdr in sorted(_glob.glob(os.path.join(os.path.dirname(kernel_file), "*.cuh"))):
-        h.update(open(hdr, "rb").read())
+    files = []
+    _local_includes(kernel_file, files)
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(f, "rb").read())
     h.update(" ".join(_build.ARCH + [f for f in _build.NVCC_FLAGS
                                      if not os.path.isabs(f)]).encode())
     return h.hexdigest()[:16]

@@ -87,7 +87,8 @@ __device__ __forceinline__ void pair_terms(float dx, float dy, float dz, float r
 
 // Pair terms from two fixed-point records: the displacement is the 32-bit
 // difference of the coordinates, which is the minimum image (|r_ij| < L / 2),
-// rounded once to FP32 and scaled to length units.
+// rounded once to FP32 and scaled to length units.  A zero displacement (the
+// particle itself) adds nothing.
 __device__ __forceinline__ void pair_fixed(const uint4& si, const uint4& sj, float Lu,
                                            float lbqi, const PairConst& kc, PairAcc& acc) {
     const float dx = (float)(int32_t)(sj.x - si.x) * Lu;
