@@ -68,8 +68,8 @@ __device__ __forceinline__ double2 block_sum2(double a, double b) {
 // cell-count scan, a later kernel, so every block of this one reads the same
 // value.
 __device__ __forceinline__ void latch_step(const uint64_t* step_dev, uint64_t step_arg,
-                                          uint64_t* cur_step) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *cur_step = step_dev ? *step_dev : step_arg;
+                                          uint64_t* cur_step, int pb) {
+    if (pb == 0 && threadIdx.x == 0) *cur_step = step_dev ? *step_dev : step_arg;
 }
 
 // Nose-Hoover (the equations of motion of Sec. 3.3): thread s of block 0
@@ -79,8 +79,8 @@ __device__ __forceinline__ void latch_step(const uint64_t* step_dev, uint64_t st
 // real-space kernel of this step, launched after this one, reads them and
 // accumulates the next sum.
 template <bool ONE>
-__device__ __forceinline__ void nh_advance(const Work& w, const PrepArgs& pa) {
-    if (!pa.nh || blockIdx.x != 0) return;
+__device__ __forceinline__ void nh_advance(const Work& w, const PrepArgs& pa, int pb) {
+    if (!pa.nh || pb != 0) return;
     for (int s = threadIdx.x; s < pa.nsys; s += blockDim.x) {
         const SysDev& S = sys_of<ONE>(w, s);
         if (S.thermostat != RBE_THERMO_NOSE_HOOVER) continue;
@@ -97,7 +97,7 @@ __device__ __forceinline__ void nh_advance(const Work& w, const PrepArgs& pa) {
     }
 }
 
-// The k-batch of this step (Eq. probexpression): the blocks after the particle
+// The k-batch of this step (Eq. probexpression): the blocks before the particle
 // blocks draw one sample per thread and its coefficient coef_scale / k^2 of
 // Eq. rbmapprox, for the structure-factor and force passes that follow.
 // The paper's Metropolis-Hastings sampler (Sec. 3.1), one block per system:
@@ -111,7 +111,7 @@ __device__ __forceinline__ void nh_advance(const Work& w, const PrepArgs& pa) {
 constexpr int kMhWin = 256;
 
 template <bool ONE>
-__device__ void draw_samples_mh(const Work& w, const PrepArgs& pa) {
+__device__ void draw_samples_mh(const Work& w, const PrepArgs& pa, int sb) {
     extern __shared__ __align__(16) unsigned char mh_smem[];
     double* s_rho = (double*)mh_smem;                          // [mh_words]
     uint32_t* s_tq = (uint32_t*)(s_rho + pa.mh_words);         // [mh_words]
@@ -122,7 +122,7 @@ __device__ void draw_samples_mh(const Work& w, const PrepArgs& pa) {
     __shared__ int s_state[3], s_emitted, s_used, s_bad;
     __shared__ int s_wsum[kBlockP / 32];
     static_assert(kMhWin == 2 * kBlockP, "emission takes two window iterations per thread");
-    const int sys = (int)blockIdx.x - pa.npblk;
+    const int sys = sb;
     if (sys >= pa.nsys) return;
     const SysDev& S = sys_of<ONE>(w, sys);
     const int n = 2 * S.M + 1;
@@ -250,14 +250,14 @@ __device__ void draw_samples_mh(const Work& w, const PrepArgs& pa) {
 }
 
 template <bool ONE>
-__device__ __forceinline__ void draw_samples(const Work& w, const PrepArgs& pa) {
+__device__ __forceinline__ void draw_samples(const Work& w, const PrepArgs& pa, int sb) {
     extern __shared__ uint32_t s_tab[];
     if (pa.tab_words > 0) {
         for (int j = threadIdx.x; j < pa.tab_words; j += blockDim.x)
             s_tab[j] = (uint32_t)__ldg(pa.table + j);
         __syncthreads();
     }
-    const int g = ((int)blockIdx.x - pa.npblk) * blockDim.x + threadIdx.x;
+    const int g = sb * blockDim.x + threadIdx.x;
     if (g >= pa.ktot) return;
     const int s = ONE ? 0 : find_sys(pa.kstart, pa.nsys, g);
     const SysDev& S = sys_of<ONE>(w, s);
@@ -272,9 +272,10 @@ __device__ __forceinline__ void draw_samples(const Work& w, const PrepArgs& pa) 
 }
 
 // Zero the rho(k) accumulators for this evaluation (stride over the nblk
-// particle blocks; the sampling blocks after them do not take part).
-__device__ __forceinline__ void clear_rho(unsigned long long* rho_fx, int nrho, int nblk) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 2 * nrho; k += nblk * blockDim.x)
+// particle blocks, pb the block's index among them; the sampling blocks do not
+// take part).
+__device__ __forceinline__ void clear_rho(unsigned long long* rho_fx, int nrho, int nblk, int pb) {
+    for (int k = pb * blockDim.x + threadIdx.x; k < 2 * nrho; k += nblk * blockDim.x)
         rho_fx[k] = 0ull;
 }
 
@@ -284,15 +285,19 @@ k_prep_mixed(const __grid_constant__ Work w, const float4* __restrict__ pos_q,
              uint4* __restrict__ fx, int* __restrict__ cid, int* __restrict__ rank,
              int* __restrict__ cell_cnt, const __grid_constant__ PrepArgs pa) {
     pdl_trigger();                     // a dependent kernel may be scheduled meanwhile
-    if ((int)blockIdx.x >= pa.npblk) {             // a k-sampling block
-        if (pa.mh) draw_samples_mh<ONE>(w, pa);
-        else draw_samples<ONE>(w, pa);
+    // the k-sampling blocks come first, so that their table staging and
+    // searches run alongside the particle blocks instead of after them
+    const int nsb = (int)gridDim.x - pa.npblk;
+    if ((int)blockIdx.x < nsb) {
+        if (pa.mh) draw_samples_mh<ONE>(w, pa, (int)blockIdx.x);
+        else draw_samples<ONE>(w, pa, (int)blockIdx.x);
         return;
     }
-    latch_step(pa.step_dev, pa.step_arg, pa.cur_step);
-    nh_advance<ONE>(w, pa);
-    clear_rho(pa.rho_fx, pa.nrho, pa.npblk);
-    const Tile tl = tile_of<ONE>(w);
+    const int pb = (int)blockIdx.x - nsb;          // this particle block
+    latch_step(pa.step_dev, pa.step_arg, pa.cur_step, pb);
+    nh_advance<ONE>(w, pa, pb);
+    clear_rho(pa.rho_fx, pa.nrho, pa.npblk, pb);
+    const Tile tl = tile_at<ONE>(w, pb);
     const SysDev& S = sys_of<ONE>(w, tl.sys);
     const int t = threadIdx.x;
     double qs = 0.0, q2s = 0.0;
@@ -347,7 +352,7 @@ k_prep_mixed(const __grid_constant__ Work w, const float4* __restrict__ pos_q,
     if (pa.want_q) {
         const double2 r = block_sum2(qs, q2s);
         if (t == 0) {
-            pa.blk_q[blockIdx.x] = r;
+            pa.blk_q[pb] = r;
             atomicAdd(pa.qsum_fx + tl.sys, (unsigned long long)__double2ll_rn(r.x * kQScale));
         }
     }
@@ -371,15 +376,19 @@ __global__ void __launch_bounds__(kBlockP)
 k_prep_f64(const __grid_constant__ Work w, const double4* __restrict__ pos_q,
            double4* __restrict__ fx64, int* __restrict__ cid, int* __restrict__ rank,
            int* __restrict__ cell_cnt, const __grid_constant__ PrepArgs pa) {
-    if ((int)blockIdx.x >= pa.npblk) {             // a k-sampling block
-        if (pa.mh) draw_samples_mh<ONE>(w, pa);
-        else draw_samples<ONE>(w, pa);
+    // the k-sampling blocks come first, so that their table staging and
+    // searches run alongside the particle blocks instead of after them
+    const int nsb = (int)gridDim.x - pa.npblk;
+    if ((int)blockIdx.x < nsb) {
+        if (pa.mh) draw_samples_mh<ONE>(w, pa, (int)blockIdx.x);
+        else draw_samples<ONE>(w, pa, (int)blockIdx.x);
         return;
     }
-    latch_step(pa.step_dev, pa.step_arg, pa.cur_step);
-    nh_advance<ONE>(w, pa);
-    clear_rho(pa.rho_fx, pa.nrho, pa.npblk);
-    const Tile tl = tile_of<ONE>(w);
+    const int pb = (int)blockIdx.x - nsb;          // this particle block
+    latch_step(pa.step_dev, pa.step_arg, pa.cur_step, pb);
+    nh_advance<ONE>(w, pa, pb);
+    clear_rho(pa.rho_fx, pa.nrho, pa.npblk, pb);
+    const Tile tl = tile_at<ONE>(w, pb);
     const SysDev& S = sys_of<ONE>(w, tl.sys);
     const int t = threadIdx.x;
     double qs = 0.0, q2s = 0.0;
@@ -404,7 +413,7 @@ k_prep_f64(const __grid_constant__ Work w, const double4* __restrict__ pos_q,
     if (pa.want_q) {
         const double2 r = block_sum2(qs, q2s);
         if (t == 0) {
-            pa.blk_q[blockIdx.x] = r;
+            pa.blk_q[pb] = r;
             atomicAdd(pa.qsum_fx + tl.sys, (unsigned long long)__double2ll_rn(r.x * kQScale));
         }
     }

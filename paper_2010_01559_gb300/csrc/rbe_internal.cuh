@@ -387,7 +387,7 @@ struct PrepArgs {
     uint64_t* step_dev;
     uint64_t step_arg;
     uint64_t* cur_step;
-    // k-batch drawn by the blocks after the particle blocks (one sample per thread)
+    // k-batch drawn by the blocks before the particle blocks (one sample per thread)
     int npblk;               // particle blocks; blocks npblk .. draw samples
     int ktot, nsys;
     const int* kstart;       // first sample of each system (nsys + 1)
