@@ -214,7 +214,9 @@ k_rho_mixed(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
 // over the grid and each SM holds both at once -- the structure factors keep
 // the special-function unit busy while the pair terms use the ALU and FMA
 // pipes and wait on their gathers.  The list tiles work only when the list
-// stands (the pass after a rebuild runs on the rebuild branch, as before).
+// stands (over a rebuilt list the pass runs on the rebuild stream, after the
+// build), and keep the per-slot count tests: padded batches cost this
+// issue-bound launch more than they save.
 template <int R, bool ONE>
 __global__ void __launch_bounds__(kLTile)
 k_rho_list(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
