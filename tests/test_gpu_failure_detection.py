@@ -10,9 +10,10 @@
   rbe_step_host return RBE_ERR_TIMEOUT with the step still queued; rbe_sync
   then completes it, and the trajectory equals the one run without a limit.
 * The bounds-checked build (-DRBE_CHECK_BOUNDS) runs MD steps with frequent
-  list rebuilds, forces calls, the FP64 path and a heterogeneous batch with
-  every data-derived index checked, reports no violation, and gives bitwise
-  the same forces as the normal build.
+  list rebuilds (with the structure factors and the list pass launched apart
+  and in one launch), forces calls, the FP64 path and a heterogeneous batch
+  with every data-derived index checked, reports no violation, and gives
+  bitwise the same forces as the normal build.
 """
 import copy
 import ctypes
@@ -149,6 +150,18 @@ out["builds"] = h.list_stats()["builds"]
 Ff, E, phi = h.forces(pos, 31, phi=True)
 F64, E64, _ = h.forces_f64(pos.double().contiguous(), 31)
 h.sync()
+# the same steps with the structure factors and the list pass in one launch
+h2 = rbe.RBE(rbe.params_from(sp, n_max=wl.n))
+h2.set_fusion(True)
+h2.set_graph(True)
+pos2 = torch.from_numpy(wl.pos_q()).cuda()
+vel2 = torch.zeros_like(pos2)
+vel2[:, :3] = torch.from_numpy(wl.vel * 3.0).cuda()
+step2 = torch.zeros(1, dtype=torch.int64, device="cuda")
+F2 = torch.zeros_like(pos2)
+h2.step(pos2, vel2, 30, step2, F_out=F2)
+h2.sync()
+out["builds_fused"] = h2.list_stats()["builds"]
 reps = workloads.config_replicas(n_rep=5, n_hi=4000)
 hb = rbe.RBEBatch([rbe.params_from(w.params) for w in reps], [w.n for w in reps])
 xb = torch.from_numpy(np.concatenate([w.pos_q() for w in reps])).cuda()
@@ -157,8 +170,13 @@ sb = torch.zeros(1, dtype=torch.int64, device="cuda")
 hb.step(xb, vb, 5, sb)
 Fb, _, _ = hb.forces(xb, 6)
 hb.sync()
+hb.set_fusion(True)
+Fbs = torch.zeros_like(xb)
+hb.step(xb, vb, 3, sb, F_out=Fbs)
+hb.sync()
 np.savez({path!r}, F=F.cpu().numpy(), Ff=Ff.cpu().numpy(), phi=phi.cpu().numpy(),
-         F64=F64.cpu().numpy(), Fb=Fb.cpu().numpy(), pos=pos.cpu().numpy())
+         F64=F64.cpu().numpy(), Fb=Fb.cpu().numpy(), pos=pos.cpu().numpy(),
+         F2=F2.cpu().numpy(), pos2=pos2.cpu().numpy(), Fbs=Fbs.cpu().numpy())
 print(json.dumps(out))
 """
 
@@ -174,6 +192,9 @@ def test_bounds_checked_build_finds_no_violation_and_matches(rbe, tmp_path):
     a = _run_scenario(True, str(tmp_path / "checked.npz"))
     b = _run_scenario(False, str(tmp_path / "normal.npz"))
     assert a["builds"] >= 3 and a["builds"] == b["builds"]
+    assert a["builds_fused"] == a["builds"] == b["builds_fused"]
     ca, cb = np.load(tmp_path / "checked.npz"), np.load(tmp_path / "normal.npz")
-    for k in ("F", "Ff", "phi", "F64", "Fb", "pos"):
+    for k in ("F", "Ff", "phi", "F64", "Fb", "pos", "F2", "pos2", "Fbs"):
         assert np.array_equal(ca[k], cb[k]), k
+    # the fused and the separate list step give the same trajectory
+    assert np.array_equal(ca["F2"], ca["F"]) and np.array_equal(ca["pos2"], ca["pos"])
