@@ -104,3 +104,36 @@ def test_traffic_lookup_needs_the_sources_it_was_taken_on(bench, tmp_path, monke
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.traffic_for("rho", "w") is None
     assert bench.traffic_for("rho", "other") is None
+
+
+def test_roofline_of_the_fused_launch_counts_the_structure_factors(bench):
+    """The fused structure-factor + list-pass launch as the dominant kernel: its
+    algorithmic work is the structure factors' two SFU operations per pair."""
+    wl = _wl(8192, 500)
+    units = {"sfu": 5.0, "alu": 38.0, "sfu_basis": "sfu", "alu_basis": "alu"}
+    r = bench.roofline({"rho_list": (3.2, 10), "fourier_force": (2.0, 10), "prep": (0.3, 10)},
+                       wl, {}, units)
+    assert r["kernel"] == "rho_list" and r["unit"] == "Tsfu/s"
+    assert r["achieved"] == pytest.approx(2 * 8192 * 500 / 3.2e-4 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / 5.0)
+    assert r["algorithmic"].startswith("2 SFU ops per") and "list" in r["algorithmic"]
+
+
+def test_source_hash_follows_the_include_chain(bench, tmp_path):
+    """A kernel file's counters go stale with a header it reaches through
+    #include (directly or through another header), not with one it does not
+    include; an include cycle is walked once."""
+    d = tmp_path / "csrc"
+    d.mkdir()
+    (d / "k.cu").write_text('#include "a.cuh"\n__global__ void k() {}\n')
+    (d / "a.cuh").write_text('#pragma once\n#include "b.cuh"\n')
+    (d / "b.cuh").write_text('#pragma once\n#include "a.cuh"\nconstexpr int kB = 1;\n')
+    (d / "other.cuh").write_text('constexpr int kO = 1;\n')
+    files = []
+    bench._local_includes(str(d / "k.cu"), files)
+    assert [os.path.basename(f) for f in files] == ["k.cu", "a.cuh", "b.cuh"]
+    h0 = bench.source_hash(str(d / "k.cu"))
+    (d / "other.cuh").write_text('constexpr int kO = 2;\n')
+    assert bench.source_hash(str(d / "k.cu")) == h0
+    (d / "b.cuh").write_text('#pragma once\n#include "a.cuh"\nconstexpr int kB = 2;\n')
+    assert bench.source_hash(str(d / "k.cu")) != h0
