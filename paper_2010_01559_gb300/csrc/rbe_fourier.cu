@@ -234,7 +234,7 @@ k_rho_list(const __grid_constant__ Work w, const int4* __restrict__ ksamp,
         return;
     }
     if ((*a.list_flag != 0) != (a.list_when != 0)) return;
-    list_body<R, ONE, false, false>(a, b - r1, threadIdx.x);
+    list_body<R, ONE, false, false, 8>(a, b - r1, threadIdx.x);
 }
 
 // ----------------------------------------------------------------- rho (FP64)

@@ -8,11 +8,9 @@
 
 namespace rbe {
 
-constexpr int kListU = 8;           // list entries per lane and batch of the list pass
-
 // The MD step's real-space pass over the list: R lanes per particle (adjacent
 // lanes) take every R-th entry of the particle's list and the pair terms of
-// those within the cutoffs (eight gathers in flight per lane); the lanes' sums
+// those within the cutoffs (U gathers in flight per lane); the lanes' sums
 // are added and stored per particle.  It needs nothing from the Fourier part,
 // so it runs concurrently with the structure factors (and, when the list
 // stands, with the no-op rebuild kernels); the Fourier-force kernel then
@@ -32,7 +30,12 @@ constexpr int kListU = 8;           // list entries per lane and batch of the li
 // tested one by one: the same sums, with lanes that stay converged.  Faster
 // for the pass on its own (2^20: 135 -> 122 us); inside the fused launch,
 // which is issue-bound, it gains nothing, and the fused launch keeps the tests.
-template <int R, bool ONE, bool FM, bool PAD = true>
+//
+// U: list entries per lane and batch, all gathers of a batch in flight at
+// once.  The pass on its own takes 4 (40 registers, more resident warps to
+// hide the gathers: 2^20 122 -> 111 us); the fused launch, whose registers
+// are set by its structure-factor blocks' company, takes 8.
+template <int R, bool ONE, bool FM, bool PAD = true, int U = 4>
 __device__ __forceinline__ void list_body(const RealArgs& a, int tile, int tid) {
     constexpr int T = kBlockP / R;               // particles per block
     const Tile tl = tile_at<ONE>(a.lw, tile);
@@ -60,37 +63,37 @@ __device__ __forceinline__ void list_body(const RealArgs& a, int tile, int tid) 
         const float Lu = S.L_over_2_32;
         const int* nb = a.nbr + i;
         const size_t st = (size_t)a.nbr_stride;
-        // batches of kListU entries per lane, all gathers of a batch in flight
+        // batches of U entries per lane, all gathers of a batch in flight
         // at once; the first batch is loaded alongside the count (slots within
         // the capacity always hold valid indices: the list starts zeroed).  The
         // list is read once per step: streaming loads, so that it does not
         // evict the records the gathers hit in L2.
         const int cnt = __ldcs(a.ncnt + i);
-        int j[kListU];
+        int j[U];
 #pragma unroll
-        for (int q = 0; q < kListU; ++q) {
+        for (int q = 0; q < U; ++q) {
             const int kk = l + q * R;
             j[q] = kk < a.nbr_cap ? __ldcs(nb + (size_t)kk * st) : (PAD ? i : 0);
         }
         if constexpr (PAD) {
 #pragma unroll
-            for (int q = 0; q < kListU; ++q)
+            for (int q = 0; q < U; ++q)
                 if (l + q * R >= cnt) j[q] = i;
         }
         for (int k0 = l;;) {
-            uint4 sj[kListU];
+            uint4 sj[U];
 #pragma unroll
-            for (int q = 0; q < kListU; ++q) {
+            for (int q = 0; q < U; ++q) {
                 if (!RBE_IN_BOUNDS(j[q], a.nbr_stride, a.err)) j[q] = i;
                 sj[q] = __ldg(a.spos + j[q]);
             }
 #pragma unroll
-            for (int q = 0; q < kListU; ++q)
+            for (int q = 0; q < U; ++q)
                 if (PAD || k0 + q * R < cnt) pair_fixed(si, sj[q], Lu, lbqi, kc, acc);
-            k0 += kListU * R;
+            k0 += U * R;
             if (k0 >= cnt) break;
 #pragma unroll
-            for (int q = 0; q < kListU; ++q) {
+            for (int q = 0; q < U; ++q) {
                 const int kk = k0 + q * R;
                 j[q] = kk < cnt ? __ldcs(nb + (size_t)kk * st) : (PAD ? i : 0);
             }
